@@ -1,0 +1,142 @@
+"""FP64 CPU oracle (test infrastructure only).
+
+Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline / reference leg may
+import this package.  It shares no code with the CUDA path.  The arithmetic lives in
+pc_oracle.c (plain double-precision loops following the paper's Algorithm 2 and the
+definitions of Sections 1-3); this file only compiles and calls it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pc_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_dp = ctypes.POINTER(ctypes.c_double)
+_u8p = ctypes.POINTER(ctypes.c_ubyte)
+
+
+def build(force: bool = False) -> str:
+    """Compile pc_oracle.c with gcc + OpenMP into oracle/_build/liboracle.so."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.run(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"],
+                       check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        I, D = ctypes.c_int, ctypes.c_int64
+        lib.or_daubechies.argtypes = [I, _dp]
+        lib.or_dwt.argtypes = [I, I, I, I, _dp, _dp]
+        lib.or_idwt.argtypes = [I, I, I, I, _dp, _dp]
+        lib.or_pc_apply.argtypes = [I, I, I, I, I, _dp, _dp, _dp, _dp]
+        lib.or_theta_columns.argtypes = [I, I, I, I, I, I, I, _dp, _dp, D, _i64p, _dp, I]
+        lib.or_in_pattern.argtypes = [I, I, I, I, I, I, D, D]
+        lib.or_pattern_mask.argtypes = [I, I, I, I, I, I, D, _u8p]
+        lib.or_theta_grad.argtypes = [I, I, I, I, I, I, I, _dp, _dp, D, _i64p, _dp, _dp, _dp, I]
+        lib.or_max_threads.argtypes = []
+        _lib = lib
+    return _lib
+
+
+def _d(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_dp)
+
+
+def _check(rc, what):
+    if rc < 0:
+        raise ValueError(f"oracle: {what} failed (rc={rc})")
+
+
+def max_threads() -> int:
+    return int(_load().or_max_threads())
+
+
+def daubechies(delta: int) -> np.ndarray:
+    """Low-pass taps h[0..2 delta - 1] (minimum phase, sum sqrt 2)."""
+    h = np.zeros(64)
+    rc = _load().or_daubechies(delta, h.ctypes.data_as(_dp))
+    _check(rc, "daubechies")
+    return h[:rc].copy()
+
+
+def dwt(d, n, L, delta, f):
+    """Forward periodic transform Psi^* of pixels f (n^d, row-major) -> canonical coefficients."""
+    f, fp = _d(np.asarray(f).reshape(-1))
+    c = np.zeros(f.size)
+    _check(_load().or_dwt(d, n, L, delta, fp, c.ctypes.data_as(_dp)), "dwt")
+    return c
+
+
+def idwt(d, n, L, delta, c):
+    """Inverse periodic transform Psi: canonical coefficients -> pixels."""
+    c, cp = _d(np.asarray(c).reshape(-1))
+    f = np.zeros(c.size)
+    _check(_load().or_idwt(d, n, L, delta, cp, f.ctypes.data_as(_dp)), "idwt")
+    return f
+
+
+def pc_apply(op, f, u=None, v=None):
+    """H f for the operator (direct periodic convolution)."""
+    u, up = _d(op.u if u is None else u)
+    v, vp = _d(op.v if v is None else v)
+    f, fp = _d(np.asarray(f).reshape(-1))
+    w = np.zeros(op.N)
+    _check(_load().or_pc_apply(op.d, op.n, u.shape[0], op.r, op.order, up, vp, fp,
+                               w.ctypes.data_as(_dp)), "pc_apply")
+    return w
+
+
+def theta_columns(op, cols, u=None, v=None, nthreads: int = 0):
+    """Columns Theta[:, cols] of Psi^* H Psi by Algorithm 2.  Returns (len(cols), N)."""
+    u, up = _d(op.u if u is None else u)
+    v, vp = _d(op.v if v is None else v)
+    cols = np.ascontiguousarray(cols, dtype=np.int64)
+    out = np.zeros((cols.size, op.N))
+    rc = _load().or_theta_columns(op.d, op.n, op.levels, op.delta, u.shape[0], op.r, op.order,
+                                  up, vp, cols.size, cols.ctypes.data_as(_i64p),
+                                  out.ctypes.data_as(_dp), nthreads)
+    _check(rc, "theta_columns")
+    return out
+
+
+def in_pattern(op, mu: int, lam: int) -> bool:
+    return bool(_load().or_in_pattern(op.d, op.n, op.levels, op.delta, op.r, op.gap, int(mu), int(lam)))
+
+
+def pattern_column(op, lam: int) -> np.ndarray:
+    """Boolean mask over mu of the pattern entries (mu, lam)."""
+    mask = np.zeros(op.N, dtype=np.uint8)
+    _load().or_pattern_mask(op.d, op.n, op.levels, op.delta, op.r, op.gap, int(lam),
+                            mask.ctypes.data_as(_u8p))
+    return mask.astype(bool)
+
+
+def theta_grad(op, cols, G, u=None, v=None, nthreads: int = 0):
+    """(dL/du, dL/dv) for a loss whose gradient w.r.t. Theta[:, cols] is G (len(cols), N);
+    G must already be zero outside the pattern."""
+    u, up = _d(op.u if u is None else u)
+    v, vp = _d(op.v if v is None else v)
+    cols = np.ascontiguousarray(cols, dtype=np.int64)
+    G, Gp = _d(G)
+    du = np.zeros(u.shape)
+    dv = np.zeros(v.shape)
+    rc = _load().or_theta_grad(op.d, op.n, op.levels, op.delta, u.shape[0], op.r, op.order,
+                               up, vp, cols.size, cols.ctypes.data_as(_i64p), Gp,
+                               du.ctypes.data_as(_dp), dv.ctypes.data_as(_dp), nthreads)
+    _check(rc, "theta_grad")
+    return du, dv

@@ -1,0 +1,475 @@
+/*
+ * FP64 CPU oracle for the wavelet matrix of a product-convolution operator.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference leg of bench.py may load this library.  It shares no code
+ * with the CUDA path (paper_2005_09870_gb300/) and neither side includes the other.
+ *
+ * What it computes (Escande & Weiss, "Fast wavelet decomposition of linear operators
+ * through product-convolution expansions"):
+ *   H f = sum_k u_k * (v_k . f)                         Eq. (2), Section 1  (order 0)
+ *   H f = sum_k v_k . (u_k * f)                         convolution first     (order 1)
+ *   Theta = Psi^* H Psi,  Theta[mu, lambda] = <psi_mu, H psi_lambda>        Section 3.2
+ * column by column, exactly as the paper's naive Algorithm 2 (Section 4.2): get
+ * psi_lambda, apply H, take the forward wavelet transform.  Everything is plain
+ * double-precision loops over the full periodic grid; no localisation, no blocking.
+ *
+ * Conventions (the paper leaves them open; see the readings in the design notes):
+ *   - levels j = 1 (finest) .. L (coarsest); level j has n_j = n / 2^j translates per axis;
+ *   - Daubechies low-pass h with Lf = 2*delta taps on [0, Lf-1], minimum phase, sum sqrt(2);
+ *     high-pass g[i] = (-1)^(1-i) h[1-i] on [2-Lf, 1]                    (Section 2.1);
+ *   - analysis a_j[l] = sum_n h[n-2l] a_{j-1}[n],  d_j[l] = sum_n g[n-2l] a_{j-1}[n],
+ *     indices mod n_{j-1} (the recursion of Section 2.1 on the torus);
+ *   - 2-D separable bands e = (e0, e1), e0 on axis 0 (rows, slow index);
+ *   - canonical coefficient order: approximation band (level L) first, then levels
+ *     L..1, bands (0,1), (1,0), (1,1) within a level, translates row-major;
+ *   - convolution (u * f)(y) = sum_t u(t) f(y - t), t in [-r, r]^d, stencil row-major.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_MAXTAPS 40
+
+/* ------------------------------------------------------------------------------------
+ * Daubechies filter by spectral factorisation (Daubechies 1988; Section 2.1 cites
+ * Mallat Thm 7.5 / 7.9 for supp h = [0, 2 delta - 1] and delta vanishing moments).
+ * |m0|^2 = cos^(2 delta)(w/2) P(sin^2(w/2)),  P(y) = sum_{k<delta} C(delta-1+k, k) y^k.
+ * Each root y_i of P gives z + 1/z = 2 - 4 y_i; keep the root with |z| > 1 for the
+ * polynomial sum_n h[n] z^n (minimum phase), multiply by (1+z)^delta, normalise sum h = sqrt 2.
+ * ---------------------------------------------------------------------------------- */
+static double binom(int a, int b)
+{
+    double r = 1.0;
+    for (int i = 1; i <= b; ++i) r = r * (double)(a - b + i) / (double)i;
+    return r;
+}
+
+/* roots of the real polynomial sum_k c[k] y^k (degree deg) by Durand-Kerner */
+static void poly_roots(const double *c, int deg, double complex *roots)
+{
+    double complex a[OR_MAXTAPS];
+    for (int k = 0; k <= deg; ++k) a[k] = c[k] / c[deg];        /* monic */
+    for (int i = 0; i < deg; ++i) roots[i] = cpow(0.4 + 0.9 * I, i);
+    for (int it = 0; it < 2000; ++it) {
+        double moved = 0.0;
+        for (int i = 0; i < deg; ++i) {
+            double complex p = 1.0, den = 1.0;
+            for (int k = deg - 1; k >= 0; --k) p = p * roots[i] + a[k];
+            /* p above evaluated a monic poly via Horner: start value 1 = leading coeff */
+            for (int q = 0; q < deg; ++q)
+                if (q != i) den *= roots[i] - roots[q];
+            double complex step = p / den;
+            roots[i] -= step;
+            moved = fmax(moved, cabs(step));
+        }
+        if (moved < 1e-17) break;
+    }
+}
+
+int or_daubechies(int delta, double *h)
+{
+    if (delta < 1 || 2 * delta > OR_MAXTAPS) return -1;
+    double complex poly[OR_MAXTAPS + 1];
+    for (int i = 0; i <= OR_MAXTAPS; ++i) poly[i] = 0.0;
+    poly[0] = 1.0;
+    int deg = 0;
+    /* (1 + z)^delta */
+    for (int k = 0; k < delta; ++k) {
+        for (int i = deg + 1; i >= 1; --i) poly[i] += poly[i - 1];
+        ++deg;
+    }
+    if (delta > 1) {
+        double c[OR_MAXTAPS];
+        for (int k = 0; k < delta; ++k) c[k] = binom(delta - 1 + k, k);
+        double complex y[OR_MAXTAPS];
+        poly_roots(c, delta - 1, y);
+        for (int i = 0; i < delta - 1; ++i) {
+            double complex b = 2.0 - 4.0 * y[i];                 /* z^2 - b z + 1 = 0 */
+            double complex s = csqrt(b * b - 4.0);
+            double complex z = (b + s) / 2.0;
+            if (cabs(z) < 1.0) z = (b - s) / 2.0;
+            /* multiply by (z_var - z) */
+            for (int q = deg + 1; q >= 0; --q) {
+                double complex lower = (q >= 1) ? poly[q - 1] : 0.0;
+                poly[q] = lower - z * poly[q];
+            }
+            ++deg;
+        }
+    }
+    double sum = 0.0;
+    for (int i = 0; i <= deg; ++i) sum += creal(poly[i]);
+    for (int i = 0; i <= deg; ++i) h[i] = creal(poly[i]) * sqrt(2.0) / sum;
+    return 2 * delta;
+}
+
+/* g[i] = (-1)^(1-i) h[1-i] for i in [2-Lf, 1], stored at g_arr[i - (2 - Lf)] */
+static void highpass(const double *h, int Lf, double *g_arr)
+{
+    for (int i = 2 - Lf; i <= 1; ++i) {
+        int s = ((1 - i) % 2 == 0) ? 1 : -1;
+        g_arr[i - (2 - Lf)] = s * h[1 - i];
+    }
+}
+
+static inline int64_t pmod(int64_t a, int64_t m) { int64_t r = a % m; return r < 0 ? r + m : r; }
+
+/* ------------------------------------------------------------------------------------
+ * One analysis / synthesis step on a strided periodic line of length M (M even).
+ * ---------------------------------------------------------------------------------- */
+static void analysis_line(const double *h, const double *g, int Lf, int64_t M,
+                          const double *x, int64_t sx, double *a, double *d, int64_t so)
+{
+    for (int64_t l = 0; l < M / 2; ++l) {
+        double sa = 0.0, sd = 0.0;
+        for (int i = 0; i < Lf; ++i) sa += h[i] * x[pmod(2 * l + i, M) * sx];
+        for (int i = 2 - Lf; i <= 1; ++i) sd += g[i - (2 - Lf)] * x[pmod(2 * l + i, M) * sx];
+        a[l * so] = sa;
+        d[l * so] = sd;
+    }
+}
+
+/* transpose of analysis_line: x[(2l+i) mod M] += h[i] a[l] + g[i] d[l] (x zeroed first) */
+static void synthesis_line(const double *h, const double *g, int Lf, int64_t M,
+                           const double *a, const double *d, int64_t si, double *x, int64_t sx)
+{
+    for (int64_t q = 0; q < M; ++q) x[q * sx] = 0.0;
+    for (int64_t l = 0; l < M / 2; ++l) {
+        for (int i = 0; i < Lf; ++i) x[pmod(2 * l + i, M) * sx] += h[i] * a[l * si];
+        for (int i = 2 - Lf; i <= 1; ++i) x[pmod(2 * l + i, M) * sx] += g[i - (2 - Lf)] * d[l * si];
+    }
+}
+
+/* forward transform Psi^*: f (n^d pixels, row-major) -> c (canonical order) */
+int or_dwt(int d, int n, int L, int delta, const double *f, double *c)
+{
+    double h[OR_MAXTAPS], g[OR_MAXTAPS];
+    int Lf = or_daubechies(delta, h);
+    if (Lf < 0 || (n >> L) < 1 || (d != 1 && d != 2)) return -1;
+    highpass(h, Lf, g);
+    int64_t N = (d == 1) ? n : (int64_t)n * n;
+    double *cur = malloc(sizeof(double) * N), *tmp = malloc(sizeof(double) * N);
+    memcpy(cur, f, sizeof(double) * N);
+    for (int j = 1; j <= L; ++j) {
+        int64_t M = n >> (j - 1), Mh = M / 2;           /* current LL is M^d */
+        if (d == 1) {
+            /* a -> tmp[0..Mh), detail -> c[Mh .. 2Mh) = level j detail slot */
+            analysis_line(h, g, Lf, M, cur, 1, tmp, c + Mh, 1);
+            memcpy(cur, tmp, sizeof(double) * Mh);
+        } else {
+            /* axis 1 on every row: low -> tmp[r][0..Mh), high -> tmp[r][Mh..M) */
+            for (int64_t r0 = 0; r0 < M; ++r0)
+                analysis_line(h, g, Lf, M, cur + r0 * M, 1, tmp + r0 * M, tmp + r0 * M + Mh, 1);
+            /* axis 0 on every column of both halves */
+            int64_t Nb = Mh * Mh;                       /* band size at level j */
+            double *LL = malloc(sizeof(double) * Nb);
+            for (int64_t q1 = 0; q1 < Mh; ++q1) {
+                /* low half column q1 (e1=0): axis0 low -> LL, axis0 high -> band (1,0) */
+                analysis_line(h, g, Lf, M, tmp + q1, M, LL + q1, c + Nb + 1 * Nb + q1, Mh);
+                /* high half column (e1=1): axis0 low -> band (0,1), high -> band (1,1) */
+                analysis_line(h, g, Lf, M, tmp + Mh + q1, M, c + Nb + 0 * Nb + q1, c + Nb + 2 * Nb + q1, Mh);
+            }
+            memcpy(cur, LL, sizeof(double) * Nb);
+            free(LL);
+        }
+    }
+    int64_t NL = (d == 1) ? (n >> L) : (int64_t)(n >> L) * (n >> L);
+    memcpy(c, cur, sizeof(double) * NL);
+    free(cur);
+    free(tmp);
+    return 0;
+}
+
+/* inverse transform Psi: c (canonical) -> f (pixels) */
+int or_idwt(int d, int n, int L, int delta, const double *c, double *f)
+{
+    double h[OR_MAXTAPS], g[OR_MAXTAPS];
+    int Lf = or_daubechies(delta, h);
+    if (Lf < 0 || (n >> L) < 1 || (d != 1 && d != 2)) return -1;
+    highpass(h, Lf, g);
+    int64_t N = (d == 1) ? n : (int64_t)n * n;
+    double *cur = malloc(sizeof(double) * N), *tmp = malloc(sizeof(double) * N);
+    int64_t NL = (d == 1) ? (n >> L) : (int64_t)(n >> L) * (n >> L);
+    memcpy(cur, c, sizeof(double) * NL);
+    for (int j = L; j >= 1; --j) {
+        int64_t M = n >> (j - 1), Mh = M / 2;
+        if (d == 1) {
+            synthesis_line(h, g, Lf, M, cur, c + Mh, 1, tmp, 1);
+            memcpy(cur, tmp, sizeof(double) * M);
+        } else {
+            int64_t Nb = Mh * Mh;
+            /* undo axis 0: columns of the low half from (LL, (1,0)), high half from ((0,1), (1,1)) */
+            for (int64_t q1 = 0; q1 < Mh; ++q1) {
+                synthesis_line(h, g, Lf, M, cur + q1, c + Nb + 1 * Nb + q1, Mh, tmp + q1, M);
+                synthesis_line(h, g, Lf, M, c + Nb + 0 * Nb + q1, c + Nb + 2 * Nb + q1, Mh, tmp + Mh + q1, M);
+            }
+            /* undo axis 1 on every row */
+            for (int64_t r0 = 0; r0 < M; ++r0)
+                synthesis_line(h, g, Lf, M, tmp + r0 * M, tmp + r0 * M + Mh, 1, cur + r0 * M, 1);
+            /* cur now holds the M x M LL of level j-1 (row stride M) */
+        }
+    }
+    memcpy(f, cur, sizeof(double) * N);
+    free(cur);
+    free(tmp);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Product-convolution operator applied to one signal (Eq. (2)), direct periodic
+ * convolution: (u * f)(y) = sum_t u(t) f(y - t), evaluated as the scatter
+ * w(x + t) += u(t) f(x) over the x where f(x) != 0.
+ * ---------------------------------------------------------------------------------- */
+static void scatter_conv(int d, int n, int r, const double *u, const double *f, double *w)
+{
+    int K = 2 * r + 1;
+    int64_t N = (d == 1) ? n : (int64_t)n * n;
+    for (int64_t x = 0; x < N; ++x) {
+        double fx = f[x];
+        if (fx == 0.0) continue;
+        if (d == 1) {
+            for (int t = -r; t <= r; ++t) w[pmod(x + t, n)] += u[t + r] * fx;
+        } else {
+            int64_t x0 = x / n, x1 = x % n;
+            for (int t0 = -r; t0 <= r; ++t0)
+                for (int t1 = -r; t1 <= r; ++t1)
+                    w[pmod(x0 + t0, n) * n + pmod(x1 + t1, n)] += u[(t0 + r) * K + (t1 + r)] * fx;
+        }
+    }
+}
+
+int or_pc_apply(int d, int n, int m, int r, int order, const double *u, const double *v,
+                const double *f, double *w)
+{
+    int64_t N = (d == 1) ? n : (int64_t)n * n;
+    int64_t Ku = (d == 1) ? (2 * r + 1) : (int64_t)(2 * r + 1) * (2 * r + 1);
+    double *t = malloc(sizeof(double) * N), *c = malloc(sizeof(double) * N);
+    for (int64_t x = 0; x < N; ++x) w[x] = 0.0;
+    for (int k = 0; k < m; ++k) {
+        const double *uk = u + k * Ku, *vk = v + k * N;
+        if (order == 0) {                    /* u_k * (v_k . f) */
+            for (int64_t x = 0; x < N; ++x) t[x] = vk[x] * f[x];
+            scatter_conv(d, n, r, uk, t, w);
+        } else {                             /* v_k . (u_k * f) */
+            for (int64_t x = 0; x < N; ++x) c[x] = 0.0;
+            scatter_conv(d, n, r, uk, f, c);
+            for (int64_t x = 0; x < N; ++x) w[x] += vk[x] * c[x];
+        }
+    }
+    free(t);
+    free(c);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Algorithm 2 (Section 4.2): for each requested lambda, psi_lambda = Psi e_lambda,
+ * w = H psi_lambda, column lambda of Theta = Psi^* w.  out is ncols x N (column-major
+ * by requested column: out[c*N + mu] = Theta[mu, cols[c]]).
+ * ---------------------------------------------------------------------------------- */
+int or_theta_columns(int d, int n, int L, int delta, int m, int r, int order,
+                     const double *u, const double *v, int64_t ncols, const int64_t *cols,
+                     double *out, int nthreads)
+{
+    int64_t N = (d == 1) ? n : (int64_t)n * n;
+    int bad = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+    {
+        double *e = calloc(N, sizeof(double)), *psi = malloc(sizeof(double) * N),
+               *w = malloc(sizeof(double) * N);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int64_t c = 0; c < ncols; ++c) {
+            int64_t lam = cols[c];
+            if (lam < 0 || lam >= N) { bad = 1; continue; }
+            e[lam] = 1.0;
+            or_idwt(d, n, L, delta, e, psi);
+            e[lam] = 0.0;
+            or_pc_apply(d, n, m, r, order, u, v, psi, w);
+            or_dwt(d, n, L, delta, w, out + c * N);
+        }
+        free(e);
+        free(psi);
+        free(w);
+    }
+    return bad ? -1 : 0;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Basis index <-> (level, band, translate) and the prescribed pattern.
+ * ---------------------------------------------------------------------------------- */
+/* returns level j (1..L; approximation band reported as level L) and e0, e1, l0, l1 */
+static void decode(int d, int n, int L, int64_t idx, int *j, int *e0, int *e1, int64_t *l0, int64_t *l1)
+{
+    int64_t nL = n >> L;
+    if (d == 1) {
+        *e0 = 0;
+        *l0 = 0;
+        if (idx < nL) { *j = L; *e1 = 0; *l1 = idx; return; }
+        for (int jj = L; jj >= 1; --jj) {
+            int64_t nj = n >> jj;
+            if (idx >= nj && idx < 2 * nj) { *j = jj; *e1 = 1; *l1 = idx - nj; return; }
+        }
+    } else {
+        if (idx < nL * nL) { *j = L; *e0 = 0; *e1 = 0; *l0 = idx / nL; *l1 = idx % nL; return; }
+        for (int jj = L; jj >= 1; --jj) {
+            int64_t nj = n >> jj, Nb = nj * nj;
+            if (idx >= Nb && idx < 4 * Nb) {
+                int64_t b = (idx - Nb) / Nb, l = (idx - Nb) % Nb;
+                *j = jj;
+                *e0 = (b >= 1) ? 1 : 0;
+                *e1 = (b == 1) ? 0 : 1;
+                *l0 = l / nj;
+                *l1 = l % nj;
+                return;
+            }
+        }
+    }
+    *j = -1;
+}
+
+/* closed support [lo, hi] (unwrapped) of the 1-D factor rho^e_{j,l}:
+ * phi_{j,l}: 2^j l + [0, (2^j-1)(Lf-1)],  psi_{j,l}: 2^j l + 2^(j-1)(2-Lf) + [0, (2^j-1)(Lf-1)] */
+static void support(int j, int e, int64_t l, int Lf, int64_t *lo, int64_t *hi)
+{
+    int64_t len = ((int64_t)1 << j) - 1;
+    len = len * (Lf - 1) + 1;
+    int64_t a = e ? ((int64_t)1 << (j - 1)) * (2 - Lf) : 0;
+    *lo = ((int64_t)1 << j) * l + a;
+    *hi = *lo + len - 1;
+}
+
+/* 1 if some periodic image of [B0,B1] meets [A0-r, A1+r] on the circle of length n */
+static int near_on_circle(int64_t A0, int64_t A1, int64_t B0, int64_t B1, int r, int n)
+{
+    int64_t span = (A1 - A0) + (B1 - B0) + 2 * r + llabs(A0) + llabs(B0);
+    int64_t P = span / n + 2;
+    for (int64_t p = -P; p <= P; ++p)
+        if (B0 + p * n <= A1 + r && B1 + p * n >= A0 - r) return 1;
+    return 0;
+}
+
+/* (mu, lambda) in P: gap < 0 keeps everything; otherwise | |mu| - |lambda| | <= gap and,
+ * on every axis, the supports of psi_mu and psi_lambda are within r of each other on the
+ * torus (entries failing this are exactly zero: the kernels have radius r). */
+int or_in_pattern(int d, int n, int L, int delta, int r, int gap, int64_t mu, int64_t lam)
+{
+    if (gap < 0) return 1;
+    int Lf = 2 * delta;
+    int jm, e0m, e1m, jl, e0l, e1l;
+    int64_t l0m, l1m, l0l, l1l;
+    decode(d, n, L, mu, &jm, &e0m, &e1m, &l0m, &l1m);
+    decode(d, n, L, lam, &jl, &e0l, &e1l, &l0l, &l1l);
+    if (jm < 0 || jl < 0) return -1;
+    if (abs(jm - jl) > gap) return 0;
+    int64_t A0, A1, B0, B1;
+    support(jm, e1m, l1m, Lf, &A0, &A1);
+    support(jl, e1l, l1l, Lf, &B0, &B1);
+    if (!near_on_circle(A0, A1, B0, B1, r, n)) return 0;
+    if (d == 2) {
+        support(jm, e0m, l0m, Lf, &A0, &A1);
+        support(jl, e0l, l0l, Lf, &B0, &B1);
+        if (!near_on_circle(A0, A1, B0, B1, r, n)) return 0;
+    }
+    return 1;
+}
+
+int or_pattern_mask(int d, int n, int L, int delta, int r, int gap, int64_t lam,
+                    unsigned char *mask)
+{
+    int64_t N = (d == 1) ? n : (int64_t)n * n;
+    for (int64_t mu = 0; mu < N; ++mu) mask[mu] = (unsigned char)or_in_pattern(d, n, L, delta, r, gap, mu, lam);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Gradient of a loss of Theta restricted to given columns.  G is ncols x N (caller has
+ * zeroed the entries outside the pattern).  With g = Psi G[:, lambda] (adjoint of the
+ * forward transform) and w = H psi_lambda:
+ *   order 0: dL/du_k(t) += sum_y g(y) (v_k psi)(y - t),  dL/dv_k(y) += psi(y) sum_t u_k(t) g(y + t)
+ *   order 1: dL/du_k(t) += sum_y g(y) v_k(y) psi(y - t), dL/dv_k(y) += g(y) (u_k * psi)(y)
+ * du (m x K) and dv (m x N) are overwritten.
+ * ---------------------------------------------------------------------------------- */
+int or_theta_grad(int d, int n, int L, int delta, int m, int r, int order,
+                  const double *u, const double *v, int64_t ncols, const int64_t *cols,
+                  const double *G, double *du, double *dv, int nthreads)
+{
+    int64_t N = (d == 1) ? n : (int64_t)n * n;
+    int K = 2 * r + 1;
+    int64_t Ku = (d == 1) ? K : (int64_t)K * K;
+    for (int64_t i = 0; i < m * Ku; ++i) du[i] = 0.0;
+    for (int64_t i = 0; i < m * N; ++i) dv[i] = 0.0;
+    int bad = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+    {
+        double *e = calloc(N, sizeof(double)), *psi = malloc(sizeof(double) * N),
+               *g = malloc(sizeof(double) * N), *c = malloc(sizeof(double) * N),
+               *du_t = calloc(m * Ku, sizeof(double)), *dv_t = calloc(m * N, sizeof(double));
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int64_t ci = 0; ci < ncols; ++ci) {
+            int64_t lam = cols[ci];
+            if (lam < 0 || lam >= N) { bad = 1; continue; }
+            e[lam] = 1.0;
+            or_idwt(d, n, L, delta, e, psi);
+            e[lam] = 0.0;
+            or_idwt(d, n, L, delta, G + ci * N, g);
+            for (int k = 0; k < m; ++k) {
+                const double *uk = u + k * Ku, *vk = v + k * N;
+                double *duk = du_t + k * Ku, *dvk = dv_t + k * N;
+                for (int64_t x = 0; x < N; ++x) {
+                    if (psi[x] == 0.0) continue;
+                    int64_t x0 = (d == 1) ? 0 : x / n, x1 = (d == 1) ? x : x % n;
+                    for (int t0 = (d == 1 ? 0 : -r); t0 <= (d == 1 ? 0 : r); ++t0)
+                        for (int t1 = -r; t1 <= r; ++t1) {
+                            int64_t y = (d == 1) ? pmod(x1 + t1, n) : pmod(x0 + t0, n) * n + pmod(x1 + t1, n);
+                            int64_t ti = (d == 1) ? (t1 + r) : (int64_t)(t0 + r) * K + (t1 + r);
+                            if (order == 0) {
+                                /* y = x + t: du(t) += g(x+t) v(x) psi(x);  dv(x) += psi(x) u(t) g(x+t) */
+                                duk[ti] += g[y] * vk[x] * psi[x];
+                                dvk[x] += psi[x] * uk[ti] * g[y];
+                            } else {
+                                /* du(t) += g(x+t) v(x+t) psi(x) */
+                                duk[ti] += g[y] * vk[y] * psi[x];
+                            }
+                        }
+                }
+                if (order == 1) {
+                    for (int64_t x = 0; x < N; ++x) c[x] = 0.0;
+                    scatter_conv(d, n, r, uk, psi, c);
+                    for (int64_t x = 0; x < N; ++x) dvk[x] += g[x] * c[x];
+                }
+            }
+        }
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+        {
+            for (int64_t i = 0; i < m * Ku; ++i) du[i] += du_t[i];
+            for (int64_t i = 0; i < m * N; ++i) dv[i] += dv_t[i];
+        }
+        free(e); free(psi); free(g); free(c); free(du_t); free(dv_t);
+    }
+    return bad ? -1 : 0;
+}
+
+int or_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
