@@ -1,0 +1,175 @@
+/*
+ * libpcwave — wavelet-domain matrix of a product-convolution operator on one GB300.
+ *
+ * Escande & Weiss, "Fast wavelet decomposition of linear operators through
+ * product-convolution expansions".  The operator (Eq. (2), Section 1) is
+ *     H f = sum_{k=1..m} u_k * (v_k . f)          (PC_ORDER_MULT_THEN_CONV, the paper's)
+ * or  H f = sum_{k=1..m} v_k . (u_k * f)          (PC_ORDER_CONV_THEN_MULT)
+ * on periodic 1-D signals or 2-D images of side n, and the library assembles
+ *     Theta = Psi^* H Psi,   Theta[mu, lambda] = <psi_mu, H psi_lambda>      (Section 3.2)
+ * in an orthonormal periodic Daubechies basis (Section 2), keeping only the entries of a
+ * prescribed pattern: | |mu| - |lambda| | <= gap (the band rule (i) of Remark 5.3) and, on
+ * each axis, supp psi_lambda within distance r (the kernel radius) of supp psi_mu on the
+ * torus (the support test of Section 5.2; entries failing it are exactly zero).
+ *
+ * Conventions.
+ *   - Pixels are row-major (axis 0 slow).  Levels j = 1 (finest) .. L (coarsest).
+ *   - Coefficient order ("canonical"): approximation band (level L) first, then levels
+ *     L..1, within a level bands e = (0,1), (1,0), (1,1) (e0 on axis 0), translates
+ *     row-major.  mu indexes rows (output), lambda columns (input): y = Theta x maps the
+ *     input's coefficients to the output's.
+ *   - Kernels u_k are (2r+1)^d stencils, row-major, centre index = offset 0:
+ *     (u * f)(y) = sum_t u(t) f(y - t).  Windows v_k are n^d pixels.
+ *   - Daubechies filters: minimum-phase low-pass h with 2*delta taps, sum sqrt(2);
+ *     g[i] = (-1)^(1-i) h[1-i] (Section 2.1).
+ *
+ * Storage of Theta ("stencil-ELL").  Rows of the stored matrix S are the filtered-side
+ * elements: S = Theta in the paper's order, S = Theta^T in the convolution-first order.
+ * Row s holds one block per kept column band, bands in canonical order; a block is the
+ * W0 x W1 run of kept translates (row-major), so column indices are implicit.
+ *
+ * Threading and streams.  Every call that takes a `stream` (a cudaStream_t, NULL = legacy
+ * default stream) is stream-ordered and asynchronous unless stated otherwise.  A handle
+ * must not be used from two host threads at once.  Errors are returned as pc_status codes,
+ * never thrown; pc_last_error() gives a message.  Faults detected inside kernels (an index
+ * outside a buffer, a work queue that overran) set a device flag read by pc_sync().
+ *
+ * Ownership.  The handle owns the device buffers it allocates (Theta, filtered wavelets,
+ * plans, scratch).  The caller owns every pointer it passes (inputs, x, y, dtheta, du, dv).
+ */
+#ifndef PCWAVE_H
+#define PCWAVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pc_op* pc_handle;
+
+typedef enum {
+    PC_OK = 0,
+    PC_ERR_INVALID_ARG = 1,   /* a size, pointer or flag is outside what the call accepts */
+    PC_ERR_UNSUPPORTED = 2,   /* valid but not handled (e.g. m > 256 terms) */
+    PC_ERR_OOM = 3,           /* a device allocation failed */
+    PC_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+    PC_ERR_TIMEOUT = 5,       /* a bounded device wait gave up */
+    PC_ERR_NOT_ASSEMBLED = 6, /* Theta is needed but pc_assemble has not run */
+    PC_ERR_DEVICE = 7         /* a kernel flagged an internal fault (see pc_last_error) */
+} pc_status;
+
+typedef enum { PC_ORDER_MULT_THEN_CONV = 0, PC_ORDER_CONV_THEN_MULT = 1 } pc_order;
+typedef enum { PC_FP32 = 0, PC_FP64 = 1 } pc_precision;
+
+typedef struct {
+    int dim;       /* 1 or 2 */
+    int n;         /* side of the periodic grid, a power of two >= 2 */
+    int levels;    /* L >= 1 with n >> L >= 1 (the paper's J when L = log2 n) */
+    int delta;     /* Daubechies order (vanishing moments), 1..10; 2*delta taps (db2 = 2, db4 = 4) */
+    int m;         /* number of product-convolution terms, 1..256 */
+    int radius;    /* kernel radius r >= 0: kernels are (2r+1)^dim */
+    int gap;       /* band rule: keep | |mu| - |lambda| | <= gap; -1 keeps every entry (dense) */
+    int order;     /* pc_order */
+    int precision; /* PC_FP32: FP32 arithmetic, compensated (Kahan) sum over k, FP32 Theta;
+                      PC_FP64: FP64 arithmetic and FP64 Theta (the plain baseline) */
+    int store_bf16;/* PC_FP32 only: also keep a BF16 copy of Theta, used by pc_apply */
+} pc_desc;
+
+/* ---------------------------------------------------------------------------------------
+ * Host-only planning (no GPU needed).  Validate a descriptor and size the pattern.
+ * --------------------------------------------------------------------------------------- */
+
+/* Validates desc.  Returns PC_OK or PC_ERR_INVALID_ARG / PC_ERR_UNSUPPORTED. */
+pc_status pc_plan_check(const pc_desc* desc);
+
+/* Total number of stored entries (nnz of the pattern).  Host only. */
+pc_status pc_plan_nnz(const pc_desc* desc, int64_t* nnz);
+
+/* Column indices (canonical, of the STORED matrix S) of stored row `row`, in storage order.
+ * cols may be NULL to query the count only; otherwise it must hold *count entries
+ * (query first).  Host only. */
+pc_status pc_plan_row(const pc_desc* desc, int64_t row, int64_t* cols, int64_t* count);
+
+/* ---------------------------------------------------------------------------------------
+ * Operator lifetime.
+ * --------------------------------------------------------------------------------------- */
+
+/* Creates an operator.  u: m x (2r+1)^dim kernels, v: m x n^dim windows, both of the
+ * precision's type (float for PC_FP32, double for PC_FP64), host or device memory (detected);
+ * both are copied.  Computes the FP64 filter taps, plans the pattern (row offsets) and
+ * allocates Theta.  Synchronous with respect to the host for planning and allocation; the
+ * copies of u and v are ordered on `stream`. */
+pc_status pc_create(const pc_desc* desc, const void* u, const void* v, void* stream,
+                    pc_handle* out);
+
+/* Replaces the kernels and windows (same shapes and type as pc_create).  Theta is stale
+ * until the next pc_assemble. */
+pc_status pc_set_params(pc_handle h, const void* u, const void* v, void* stream);
+
+/* Frees everything the handle owns.  Synchronises the device first. */
+void pc_destroy(pc_handle h);
+
+/* ---------------------------------------------------------------------------------------
+ * The hot path.
+ * --------------------------------------------------------------------------------------- */
+
+/* Assembles Theta restricted to the pattern (Section 3.2, Algorithm 1 without thresholding:
+ * the exact sum_k A_k B_k on the pattern):
+ *   1. base wavelets phi_{j,0}, psi_{j,0} by the FP64 cascade of the taps (Section 2.1);
+ *   2. filtered base wavelets F_{k,beta} = kappa_k * rho_beta (kappa_k = u_k flipped in the
+ *      paper's order, u_k otherwise): the circulant generators of A_k (Lemma 5.1);
+ *   3. for every stored row s: the window-weighted sum sum_k v_k . F_{k,beta}(. - shift)
+ *      over the row's support (compensated over k in FP32), then a localized forward wavelet
+ *      transform of it (Lemma 5.5) whose kept coefficients are the row's entries.
+ * Asynchronous on `stream`. */
+pc_status pc_assemble(pc_handle h, void* stream);
+
+/* y = Theta x for nrhs right-hand sides (Section 4.3 uses two such products per FISTA
+ * iteration).  x: N x nrhs, element (i, c) at x[i*ldx + c] (ldx >= nrhs), FP32, device;
+ * y likewise (ldy >= nrhs), overwritten.  Reads the BF16 copy when store_bf16 is set, else
+ * the FP32 (or FP64) values; accumulates in FP32 (FP64 for PC_FP64 handles, where x and y
+ * are double).  1 <= nrhs <= 64.  Returns PC_ERR_NOT_ASSEMBLED before the first assembly. */
+pc_status pc_apply(pc_handle h, const void* x, void* y, int nrhs, int ldx, int ldy,
+                   void* stream);
+
+/* Gradient of a loss of Theta.  dtheta: dL/dTheta on the stored entries, same layout and
+ * type as the stored values (nnz elements), device.  du: m x (2r+1)^dim and dv: m x n^dim,
+ * device, overwritten with dL/du_k and dL/dv_k.  The filtered wavelets are recomputed, not
+ * kept from the forward pass.  Uses handle-owned scratch (allocated on first call). */
+pc_status pc_backward(pc_handle h, const void* dtheta, void* du, void* dv, void* stream);
+
+/* Assembles `count` operators (any mix of sizes, PC_FP32 only) in one persistent launch
+ * that takes (operator, band, row-tile) work items from a global queue, longest first.
+ * Equivalent to calling pc_assemble on each. */
+pc_status pc_batch_assemble(pc_handle* ops, int count, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Inspection.
+ * --------------------------------------------------------------------------------------- */
+
+/* nnz and the device bytes owned by the handle. */
+pc_status pc_info(pc_handle h, int64_t* nnz, int64_t* device_bytes);
+
+/* Device pointers of the stored values (FP32 or FP64 per precision; BF16 copy or NULL)
+ * and of the row offsets (int64, N+1).  Valid until pc_destroy. */
+pc_status pc_theta(pc_handle h, void** values, void** values_bf16, int64_t** row_ptr);
+
+/* Storage position of Theta[mu, lambda] for n pairs (host arrays), -1 when outside the
+ * pattern.  Host only; no device work. */
+pc_status pc_lookup(pc_handle h, int64_t n, const int64_t* mu, const int64_t* lambda,
+                    int64_t* pos);
+
+/* Waits for `stream`, then reports any device-side fault flagged since the last call
+ * (PC_ERR_DEVICE) and clears it. */
+pc_status pc_sync(pc_handle h, void* stream);
+
+/* Message of the last failing call on h (or of the last failing call without a handle
+ * when h is NULL).  Never NULL. */
+const char* pc_last_error(pc_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PCWAVE_H */

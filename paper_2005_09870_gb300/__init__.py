@@ -1,0 +1,266 @@
+"""Python binding of libpcwave (the C-ABI in include/pcwave.h).
+
+Argument marshalling only: every step of the assembly, the apply and the backward runs in
+the CUDA kernels of libpcwave.so.  PyTorch provides device memory and streams.  There is no
+CPU fallback: importing this package fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpcwave.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libpcwave.so is not built ({LIB_PATH}); run __graft_entry__.build() "
+                      "or python paper_2005_09870_gb300/build.py")
+_lib = ctypes.CDLL(LIB_PATH)
+
+PC_OK, PC_ERR_INVALID_ARG, PC_ERR_UNSUPPORTED, PC_ERR_OOM, PC_ERR_CUDA, PC_ERR_TIMEOUT, \
+    PC_ERR_NOT_ASSEMBLED, PC_ERR_DEVICE = range(8)
+PC_ORDER_MULT_THEN_CONV, PC_ORDER_CONV_THEN_MULT = 0, 1
+PC_FP32, PC_FP64 = 0, 1
+_STATUS = ["PC_OK", "PC_ERR_INVALID_ARG", "PC_ERR_UNSUPPORTED", "PC_ERR_OOM", "PC_ERR_CUDA",
+           "PC_ERR_TIMEOUT", "PC_ERR_NOT_ASSEMBLED", "PC_ERR_DEVICE"]
+
+
+class pc_desc(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int) for f in
+                ("dim", "n", "levels", "delta", "m", "radius", "gap", "order", "precision", "store_bf16")]
+
+
+class PCError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS[status] if 0 <= status < len(_STATUS) else status}: {msg}")
+        self.status = status
+
+
+_H = ctypes.c_void_p
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I64P = ctypes.POINTER(ctypes.c_int64)
+_DP = ctypes.POINTER(pc_desc)
+
+_sig = {
+    "pc_plan_check": ([_DP], ctypes.c_int),
+    "pc_plan_nnz": ([_DP, _I64P], ctypes.c_int),
+    "pc_plan_row": ([_DP, _I64, _I64P, _I64P], ctypes.c_int),
+    "pc_create": ([_DP, _P, _P, _P, ctypes.POINTER(_H)], ctypes.c_int),
+    "pc_set_params": ([_H, _P, _P, _P], ctypes.c_int),
+    "pc_destroy": ([_H], None),
+    "pc_assemble": ([_H, _P], ctypes.c_int),
+    "pc_apply": ([_H, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P], ctypes.c_int),
+    "pc_backward": ([_H, _P, _P, _P, _P], ctypes.c_int),
+    "pc_batch_assemble": ([ctypes.POINTER(_H), ctypes.c_int, _P], ctypes.c_int),
+    "pc_info": ([_H, _I64P, _I64P], ctypes.c_int),
+    "pc_theta": ([_H, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P)], ctypes.c_int),
+    "pc_lookup": ([_H, _I64, _I64P, _I64P, _I64P], ctypes.c_int),
+    "pc_sync": ([_H, _P], ctypes.c_int),
+    "pc_last_error": ([_H], ctypes.c_char_p),
+}
+for _name, (_args, _ret) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _ret
+
+
+def _check(st, h=None):
+    if st != PC_OK:
+        raise PCError(st, _lib.pc_last_error(h).decode())
+
+
+def make_desc(dim, n, levels, delta, m, radius, gap=2, order=0, precision=PC_FP32, store_bf16=0) -> pc_desc:
+    return pc_desc(dim, n, levels, delta, m, radius, gap, order, precision, int(store_bf16))
+
+
+def desc_of(op, precision=PC_FP32, store_bf16=0) -> pc_desc:
+    """Descriptor for a pc_inputs.Operator-like object (fields d, n, levels, delta, m, r, gap, order)."""
+    return make_desc(op.d, op.n, op.levels, op.delta, op.m, op.r, op.gap, op.order, precision, store_bf16)
+
+
+# ----------------------------------------------------------------- host-only planning
+def pc_plan_check(desc: pc_desc) -> None:
+    _check(_lib.pc_plan_check(ctypes.byref(desc)))
+
+
+def pc_plan_nnz(desc: pc_desc) -> int:
+    nnz = ctypes.c_int64()
+    _check(_lib.pc_plan_nnz(ctypes.byref(desc), ctypes.byref(nnz)))
+    return nnz.value
+
+
+def pc_plan_row(desc: pc_desc, row: int) -> np.ndarray:
+    cnt = ctypes.c_int64()
+    _check(_lib.pc_plan_row(ctypes.byref(desc), int(row), None, ctypes.byref(cnt)))
+    cols = np.zeros(cnt.value, dtype=np.int64)
+    _check(_lib.pc_plan_row(ctypes.byref(desc), int(row), cols.ctypes.data_as(_I64P), ctypes.byref(cnt)))
+    return cols
+
+
+# ----------------------------------------------------------------- device helpers
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(_torch().cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class _DevArray:
+    """A view of library-owned device memory for torch.as_tensor (no copy)."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3}
+
+
+def _ptr(t):
+    """Device (or host) address of a torch tensor / numpy array."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        if not t.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(t.data_ptr())
+    return ctypes.c_void_p(t.ctypes.data)
+
+
+# ----------------------------------------------------------------- C-ABI with the same names
+def pc_create(desc: pc_desc, u, v, stream=None) -> int:
+    h = _H()
+    _check(_lib.pc_create(ctypes.byref(desc), _ptr(u), _ptr(v), _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def pc_set_params(h, u, v, stream=None):
+    _check(_lib.pc_set_params(h, _ptr(u), _ptr(v), _stream(stream)), h)
+
+
+def pc_destroy(h):
+    _lib.pc_destroy(h)
+
+
+def pc_assemble(h, stream=None):
+    _check(_lib.pc_assemble(h, _stream(stream)), h)
+
+
+def pc_apply(h, x, y, nrhs=None, ldx=None, ldy=None, stream=None):
+    if nrhs is None:
+        nrhs = 1 if x.dim() == 1 else x.shape[1]
+    ldx = nrhs if ldx is None else ldx
+    ldy = nrhs if ldy is None else ldy
+    _check(_lib.pc_apply(h, _ptr(x), _ptr(y), nrhs, ldx, ldy, _stream(stream)), h)
+
+
+def pc_backward(h, dtheta, du, dv, stream=None):
+    _check(_lib.pc_backward(h, _ptr(dtheta), _ptr(du), _ptr(dv), _stream(stream)), h)
+
+
+def pc_batch_assemble(handles, stream=None):
+    arr = (_H * len(handles))(*handles)
+    first = handles[0] if handles else None
+    _check(_lib.pc_batch_assemble(arr, len(handles), _stream(stream)), first)
+
+
+def pc_info(h):
+    nnz, by = ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.pc_info(h, ctypes.byref(nnz), ctypes.byref(by)), h)
+    return nnz.value, by.value
+
+
+def pc_theta(h):
+    a, b, c = _P(), _P(), _P()
+    _check(_lib.pc_theta(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), h)
+    return a.value, b.value, c.value
+
+
+def pc_lookup(h, mu, lam) -> np.ndarray:
+    mu = np.ascontiguousarray(mu, dtype=np.int64)
+    lam = np.ascontiguousarray(lam, dtype=np.int64)
+    pos = np.zeros(mu.size, dtype=np.int64)
+    _check(_lib.pc_lookup(h, mu.size, mu.ctypes.data_as(_I64P), lam.ctypes.data_as(_I64P),
+                          pos.ctypes.data_as(_I64P)), h)
+    return pos
+
+
+def pc_sync(h, stream=None):
+    _check(_lib.pc_sync(h, _stream(stream)), h)
+
+
+def pc_last_error(h=None) -> str:
+    return _lib.pc_last_error(h).decode()
+
+
+# ----------------------------------------------------------------- convenience object
+class PCOperator:
+    """One operator: owns a libpcwave handle.  u, v may be torch tensors (CUDA or CPU) or
+    numpy arrays of the precision's dtype."""
+
+    def __init__(self, desc: pc_desc, u, v, stream=None):
+        self.desc = desc
+        self._keep = (u, v)
+        self.h = pc_create(desc, u, v, stream)
+        self.nnz, self.device_bytes = pc_info(self.h)
+        self.N = desc.n ** desc.dim
+
+    @property
+    def dtype(self):
+        t = _torch()
+        return t.float64 if self.desc.precision == PC_FP64 else t.float32
+
+    def assemble(self, stream=None):
+        pc_assemble(self.h, stream)
+
+    def values(self):
+        """torch view (no copy) of the stored values on the device."""
+        t = _torch()
+        vals, _, _ = pc_theta(self.h)
+        ts = "<f8" if self.desc.precision == PC_FP64 else "<f4"
+        return t.as_tensor(_DevArray(vals, (self.nnz,), ts), device="cuda")
+
+    def values_bf16(self):
+        t = _torch()
+        _, v16, _ = pc_theta(self.h)
+        if not v16:
+            return None
+        raw = t.as_tensor(_DevArray(v16, (self.nnz,), "<i2"), device="cuda")
+        return raw.view(t.bfloat16)
+
+    def apply(self, x, stream=None):
+        t = _torch()
+        y = t.empty_like(x)
+        pc_apply(self.h, x, y, stream=stream)
+        return y
+
+    def backward(self, dtheta, stream=None):
+        t = _torch()
+        K = (2 * self.desc.radius + 1) ** self.desc.dim
+        du = t.empty((self.desc.m, K), dtype=self.dtype, device="cuda")
+        dv = t.empty((self.desc.m, self.N), dtype=self.dtype, device="cuda")
+        pc_backward(self.h, dtheta, du, dv, stream)
+        return du, dv
+
+    def lookup(self, mu, lam):
+        return pc_lookup(self.h, mu, lam)
+
+    def sync(self, stream=None):
+        pc_sync(self.h, stream)
+
+    def close(self):
+        if self.h:
+            pc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,682 @@
+// Device kernels of libpcwave (sm_103a).
+//
+// Pipeline of pc_assemble for one operator (Section 3.2, Algorithm 1 evaluated exactly on
+// the prescribed pattern):
+//   k_base_wavelets   FP64 cascade of the taps -> phi_{j,0}, psi_{j,0} (Section 2.1)
+//   k_filtered_pass1  G = kappa_k (*) rho^{e1}_j along axis 1           } F_{k,beta} = kappa_k * psi_{beta,0},
+//   k_filtered_pass2  F = G (*) rho^{e0}_j along axis 0, folded mod n   } the circulant generators of A_k (Lemma 5.1)
+//   k_tile_masks      which windows v_k are nonzero on each 16x16 tile
+//   k_assemble        per stored row: s = sum_k v_k . F_{k,beta}(. - shift) (compensated over k),
+//                     then the localized forward transform of s (Lemma 5.5); its coefficients
+//                     inside the stencil are the row's entries of Theta.
+// k_apply multiplies the stored matrix by a block of right-hand sides.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pcw_geom.cuh"
+
+namespace pcw {
+
+constexpr int MAXL = 14;
+constexpr int MAXB = 1 + 3 * MAXL;
+constexpr int MAXW = 4;  // mask words: m <= 256
+
+enum : int { ERR_ARENA = 1, ERR_ROWLEN = 2, ERR_INDEX = 4, ERR_QUEUE = 8 };
+
+// ------------------------------------------------------------------------------------------
+// Per-operator device view (passed by value).
+// ------------------------------------------------------------------------------------------
+template <typename T>
+struct OpDev {
+    int d, n, L, Lf, r, m, gap, order, nb;
+    int64_t N;
+    const T* u;      // m x Ku kernels
+    const T* v;      // m x N windows
+    const T* taps;   // h[0..Lf), then g at positions 2-Lf..1 stored as [Lf..2Lf)
+    const T* wav;    // base wavelets (unwrapped): level j at wofs[j]: phi [len_j], psi [len_j]
+    int wofs[MAXL + 2];
+    const T* F;      // filtered base wavelets: band b at Foff[b], layout [k][R0][R1]
+    int64_t Foff[MAXB];
+    const int64_t* row_ptr;
+    T* theta;
+    __nv_bfloat16* theta16;
+    const unsigned long long* masks;  // [tile][mwords]
+    int mwords, ts0, ts1, tpa0, tpa1;
+    int* err;
+};
+
+// Per-band launch parameters of k_assemble (one launch per row band, or one queue item).
+struct AsmCfg {
+    int b;       // band of the stored rows
+    int row0;    // first row (within band) of this launch
+    int rows;    // rows in this launch
+    int gt;      // threads per row group (32, 64, 128, 256)
+    int rpc;     // row groups per CTA
+    int batch;   // pixel rows of s per stage-1 step (2-D)
+    int arena;   // elements of T per row group
+    int filt;    // elements of T of the filter area (2 Lf + len of the stage-1 scaling filter)
+};
+
+template <typename T>
+struct KahanAcc {  // FP64: plain sum
+    T s;
+    __device__ __forceinline__ void init() { s = T(0); }
+    __device__ __forceinline__ void add(T x) { s += x; }
+    __device__ __forceinline__ T get() const { return s; }
+};
+template <>
+struct KahanAcc<float> {  // compensated summation (Kahan 1965)
+    float s, c;
+    __device__ __forceinline__ void init()
+    {
+        s = 0.f;
+        c = 0.f;
+    }
+    __device__ __forceinline__ void add(float x)
+    {
+        float y = __fsub_rn(x, c);
+        float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ float get() const { return s; }
+};
+
+__device__ __forceinline__ void group_sync(int gt, int gid)
+{
+    if (gt <= 32)
+        __syncwarp();
+    else
+        asm volatile("bar.sync %0, %1;" ::"r"(gid + 1), "r"(gt) : "memory");
+}
+
+__device__ __forceinline__ void flag_error(int* err, int bits)
+{
+    if (err) atomicOr(err, bits);
+}
+
+// ------------------------------------------------------------------------------------------
+// A2: base wavelets by the FP64 cascade (Section 2.1):
+//   phi_{1,0} = h,  psi_{1,0}(x) = g(x);
+//   phi_{j,0}(x) = sum_n h[n] phi_{j-1,0}(x - 2^(j-1) n),  psi_{j,0}(x) = sum_n g[n] phi_{j-1,0}(x - 2^(j-1) n)
+// stored unwrapped: phi_j[i] at x = i, psi_j[i] at x = off(j,1) + i.  One CTA.
+// ------------------------------------------------------------------------------------------
+__global__ void k_base_wavelets(const double* __restrict__ h, int Lf, int L, double* __restrict__ wav)
+{
+    int base_prev = 0, base = 0;
+    for (int j = 1; j <= L; ++j) {
+        const int len = wav_len(j, Lf);
+        if (j == 1) {
+            for (int i = threadIdx.x; i < len; i += blockDim.x) {
+                wav[base + i] = h[i];
+                const int x = (2 - Lf) + i;  // g(x) = (-1)^(1-x) h[1-x]
+                const double s = ((1 - x) & 1) ? -1.0 : 1.0;
+                wav[base + len + i] = s * h[1 - x];
+            }
+        } else {
+            const int lenp = wav_len(j - 1, Lf), step = 1 << (j - 1), offp = wav_off(j, 1, Lf);
+            const double* phip = wav + base_prev;
+            for (int i = threadIdx.x; i < len; i += blockDim.x) {
+                double sp = 0.0, sq = 0.0;
+                for (int q = 0; q < Lf; ++q) {  // low-pass tap n = q
+                    const int y = i - step * q;
+                    if (y >= 0 && y < lenp) sp += h[q] * phip[y];
+                }
+                for (int q = 2 - Lf; q <= 1; ++q) {  // high-pass tap n = q
+                    const int y = offp + i - step * q;
+                    const double s = ((1 - q) & 1) ? -1.0 : 1.0;
+                    if (y >= 0 && y < lenp) sq += s * h[1 - q] * phip[y];
+                }
+                wav[base + i] = sp;
+                wav[base + len + i] = sq;
+            }
+        }
+        __syncthreads();
+        base_prev = base;
+        base += 2 * len;
+    }
+}
+
+template <typename T>
+__global__ void k_cast(const double* __restrict__ in, T* __restrict__ out, int64_t count)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (T)in[i];
+}
+
+// taps in T: h then g (g[2-Lf+i] at index Lf+i)
+template <typename T>
+__global__ void k_taps(const double* __restrict__ h, int Lf, T* __restrict__ out)
+{
+    int i = threadIdx.x;
+    if (i < Lf) {
+        out[i] = (T)h[i];
+        const int x = (2 - Lf) + i;
+        const double s = ((1 - x) & 1) ? -1.0 : 1.0;
+        out[Lf + i] = (T)(s * h[1 - x]);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// A3: filtered base wavelets.  For band b (level j, factors e0, e1) and term k the region is
+// supp rho widened by r: unfolded extents U = len_j + 2r per axis, local coordinate q <-> pixel
+// x = off(j,e) - r + q.  kappa_k(t) = u_k(-t) in the paper's order (adjoint of the
+// convolution), u_k(t) otherwise.
+//   pass 1: G[t0][q1] = sum_{t1} kappa_k(t0, t1) rho^{e1}_j(q1 - r - t1)
+//   pass 2: F[p0][p1] = sum_{q0 = p0 mod n} sum_{q1 = p1 mod n} sum_{t0} G[t0][q1] rho^{e0}_j(q0 - r - t0)
+// (fold mod n when U >= n: the periodised wavelet).  1-D: t0 = 0 and F[p1] = sum G[0][q1].
+// ------------------------------------------------------------------------------------------
+struct FiltBand {
+    int j, e0, e1, U0, U1, R0, R1;
+    int64_t Goff, Foff;
+};
+struct FiltDev {
+    int nb, d, n, r, m, Lf, order;
+    int wofs[MAXL + 2];
+    FiltBand band[MAXB];
+};
+
+template <typename T>
+__global__ void k_filtered_pass1(const __grid_constant__ FiltDev fd, const T* __restrict__ u,
+                                 const T* __restrict__ wav, T* __restrict__ G)
+{
+    const int bk = blockIdx.y;
+    const int b = bk / fd.m, k = bk % fd.m;
+    const FiltBand& B = fd.band[b];
+    const int K = 2 * fd.r + 1, K0 = (fd.d == 2) ? K : 1;
+    const int tot = K0 * B.U1;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= tot) return;
+    const int t0i = idx / B.U1, q1 = idx % B.U1;
+    const int len = wav_len(B.j, fd.Lf);
+    const T* rho1 = wav + fd.wofs[B.j] + (B.e1 ? len : 0);
+    const int Ku = (fd.d == 2) ? K * K : K;
+    const T* uk = u + (int64_t)k * Ku;
+    KahanAcc<T> acc;
+    acc.init();
+    const int t0 = t0i - fd.r;
+    for (int t1 = -fd.r; t1 <= fd.r; ++t1) {
+        const int y = q1 - fd.r - t1;
+        if (y < 0 || y >= len) continue;
+        const int tt0 = fd.order == 0 ? -t0 : t0, tt1 = fd.order == 0 ? -t1 : t1;
+        const int ui = (fd.d == 2) ? (tt0 + fd.r) * K + (tt1 + fd.r) : (tt1 + fd.r);
+        acc.add(uk[ui] * rho1[y]);
+    }
+    G[B.Goff + ((int64_t)k * K0 + t0i) * B.U1 + q1] = acc.get();
+}
+
+template <typename T>
+__global__ void k_filtered_pass2(const __grid_constant__ FiltDev fd, const T* __restrict__ wav,
+                                 const T* __restrict__ G, T* __restrict__ F)
+{
+    const int bk = blockIdx.y;
+    const int b = bk / fd.m, k = bk % fd.m;
+    const FiltBand& B = fd.band[b];
+    const int tot = B.R0 * B.R1;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= tot) return;
+    const int p0 = idx / B.R1, p1 = idx % B.R1;
+    const int K = 2 * fd.r + 1, K0 = (fd.d == 2) ? K : 1;
+    const int len = wav_len(B.j, fd.Lf);
+    const T* rho0 = wav + fd.wofs[B.j] + (B.e0 ? len : 0);
+    const T* Gk = G + B.Goff + (int64_t)k * K0 * B.U1;
+    KahanAcc<T> acc;
+    acc.init();
+    for (int q1 = p1; q1 < B.U1; q1 += fd.n) {
+        if (fd.d == 1) {
+            acc.add(Gk[q1]);
+        } else {
+            for (int q0 = p0; q0 < B.U0; q0 += fd.n) {
+                for (int t0i = 0; t0i < K; ++t0i) {
+                    const int y = q0 - fd.r - (t0i - fd.r);
+                    if (y < 0 || y >= len) continue;
+                    acc.add(Gk[(int64_t)t0i * B.U1 + q1] * rho0[y]);
+                }
+            }
+        }
+    }
+    F[B.Foff + (int64_t)k * tot + idx] = acc.get();
+}
+
+// ------------------------------------------------------------------------------------------
+// Tile masks: bit k of mask[tile] is set when v_k is nonzero somewhere on the tile.
+// One CTA per tile, one pixel per thread (ts0 * ts1 <= blockDim).
+// ------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_tile_masks(const T* __restrict__ v, int d, int n, int m, int ts0, int ts1, int tpa1,
+                             int mwords, unsigned long long* __restrict__ masks)
+{
+    const int tile = blockIdx.x;
+    const int tr = tile / tpa1, tc = tile % tpa1;
+    const int i = threadIdx.x;
+    const int p0 = tr * ts0 + i / ts1, p1 = tc * ts1 + i % ts1;
+    const bool inside = i < ts0 * ts1;
+    const int64_t pix = (d == 2) ? (int64_t)p0 * n + p1 : p1;
+    const int64_t N = (d == 2) ? (int64_t)n * n : n;
+    for (int w = 0; w < mwords; ++w) {
+        unsigned long long word = 0;
+        for (int kk = 0; kk < 64 && w * 64 + kk < m; ++kk) {
+            const int k = w * 64 + kk;
+            const int nz = inside && v[(int64_t)k * N + pix] != T(0);
+            if (__syncthreads_or(nz)) word |= 1ull << kk;
+        }
+        if (threadIdx.x == 0) masks[(int64_t)tile * mwords + w] = word;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Stride-S filter on one axis of a group-shared array (Range conventions of pcw_geom.cuh):
+//   out[c] = sum_{i<len} f[i] * in[S*(ro.lo + c) + off + i]   (in indexed from ri.lo)
+// Non-full output: inputs outside [ri.lo, ri.lo + ri.cnt) are zero.  Full output: periodic.
+// ------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T filt(const T* in, int istride, Range ri, int n_in, Range ro, int c,
+                                  const T* f, int len, int S, int off)
+{
+    const int x0 = S * (ro.lo + c) + off - ri.lo;
+    T acc = T(0);
+    if (!ro.full) {
+        const int ilo = x0 < 0 ? -x0 : 0;
+        const int ihi = min(len, ri.cnt - x0);
+        for (int i = ilo; i < ihi; ++i) acc = fma(f[i], in[(x0 + i) * istride], acc);
+    } else {
+        for (int i = 0; i < len; ++i) {
+            const int p = pmod(x0 + i, n_in);
+            if (p < ri.cnt) acc = fma(f[i], in[p * istride], acc);
+        }
+    }
+    return acc;
+}
+
+// Writes the stencil block of column band b2 (level jj, factors e0, e1) from a band array of
+// shape r0.cnt x r1.cnt to the row's storage.
+template <typename T, int DIM>
+__device__ __forceinline__ void write_block(const OpDev<T>& op, const T* Zb, Range r0, Range r1, int jj, int e0,
+                                            int e1, int64_t dst, int j, int eo0, int eo1, int l0, int l1,
+                                            int tid, int gt)
+{
+    const int dense = op.gap < 0;
+    int f0 = 0, W0 = 1, f1, W1;
+    stencil(j, eo1, l1, jj, e1, op.r, op.Lf, op.n, dense, &f1, &W1);
+    if (DIM == 2) stencil(j, eo0, l0, jj, e0, op.r, op.Lf, op.n, dense, &f0, &W0);
+    const int nj = op.n >> jj;
+    const int tot = W0 * W1;
+    for (int idx = tid; idx < tot; idx += gt) {
+        const int a = idx / W1, bb = idx - a * W1;
+        const int p1 = pmod(f1 + bb - r1.lo, nj);
+        bool ok = r1.full || p1 < r1.cnt;
+        int p0 = 0;
+        if (DIM == 2) {
+            p0 = pmod(f0 + a - r0.lo, nj);
+            ok = ok && (r0.full || p0 < r0.cnt);
+        }
+        const T val = ok ? Zb[p0 * r1.cnt + p1] : T(0);
+        op.theta[dst + idx] = val;
+        if (op.theta16) op.theta16[dst + idx] = __float2bfloat16_rn((float)val);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// A5: fused window-multiply + localized forward transform, one stored row per thread group.
+// ------------------------------------------------------------------------------------------
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_assemble(const __grid_constant__ OpDev<T> op, const AsmCfg cfg)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int gt = cfg.gt;
+    const int gid = threadIdx.x / gt, tid = threadIdx.x % gt;
+    const int n = op.n, L = op.L, Lf = op.Lf, r = op.r;
+    const int dense = op.gap < 0;
+    const Band Bo = band_info(DIM, n, L, cfg.b);
+    const int j = Bo.j;
+    const int jlo = dense ? 1 : max(1, j - op.gap);
+    const int jhi = dense ? L : min(L, j + op.gap);
+    const int k0 = (DIM == 2) ? jlo - 1 : 0;
+
+    // shared layout: filters | per-group block offsets | per-group arenas
+    T* fS = reinterpret_cast<T*>(smem_raw);
+    T* hS = fS;
+    T* gS = fS + Lf;
+    T* phiS = fS + 2 * Lf;
+    const int lenk = (k0 > 0) ? wav_len(k0, Lf) : 0;
+    int* boffAll = reinterpret_cast<int*>(smem_raw + sizeof(T) * cfg.filt);
+    int* boff = boffAll + gid * (MAXB + 1);
+    T* arena = reinterpret_cast<T*>(smem_raw + sizeof(T) * cfg.filt + sizeof(int) * cfg.rpc * (MAXB + 1));
+    arena += (int64_t)gid * cfg.arena;  // the host keeps cfg.arena a multiple of 16 bytes
+    T* const arena_end = arena + cfg.arena;
+
+    for (int i = threadIdx.x; i < 2 * Lf; i += blockDim.x) fS[i] = op.taps[i];
+    for (int i = threadIdx.x; i < lenk; i += blockDim.x) phiS[i] = op.wav[op.wofs[k0] + i];
+    __syncthreads();
+
+    const int rl = cfg.row0 + blockIdx.x * cfg.rpc + gid;
+    if (rl >= cfg.row0 + cfg.rows || blockIdx.x * cfg.rpc + gid >= cfg.rows) return;
+    const int l0 = (DIM == 2) ? rl / Bo.nj : 0;
+    const int l1 = (DIM == 2) ? rl % Bo.nj : rl;
+    const Range A1 = region0(j, Bo.e1, l1, r, Lf, n);
+    const Range A0 = (DIM == 2) ? region0(j, Bo.e0, l0, r, Lf, n) : Range{0, 1, 0};
+    const int g0 = (DIM == 2) ? pmod(A0.lo, n) : 0;
+    const int g1 = pmod(A1.lo, n);
+    const int64_t srow = Bo.off + rl;
+    const int64_t row_base = op.row_ptr[srow];
+
+    if (tid == 0) {
+        int acc = 0;
+        for (int b2 = 0; b2 < op.nb; ++b2) {
+            boff[b2] = acc;
+            if (block_kept(DIM, n, L, op.gap, cfg.b, b2))
+                acc += (int)block_count(DIM, n, L, Lf, r, op.gap, cfg.b, l0, l1, b2);
+        }
+        boff[op.nb] = acc;
+        if ((int64_t)acc != op.row_ptr[srow + 1] - row_base) flag_error(op.err, ERR_ROWLEN);
+    }
+
+    // windows nonzero on the region: OR of the tile masks it covers (every warp reduces alone)
+    unsigned long long mw[MAXW];
+#pragma unroll
+    for (int w = 0; w < MAXW; ++w) mw[w] = 0ull;
+    {
+        const int lane = threadIdx.x & 31;
+        const int ts0 = op.ts0, ts1 = op.ts1;
+        const int s0 = g0 / ts0, s1 = g1 / ts1;
+        const int nt0 = (DIM == 2) ? min(op.tpa0, (g0 % ts0 + A0.cnt + ts0 - 1) / ts0) : 1;
+        const int nt1 = min(op.tpa1, (g1 % ts1 + A1.cnt + ts1 - 1) / ts1);
+        for (int i = lane; i < nt0 * nt1; i += 32) {
+            const int t0 = (s0 + i / nt1) % op.tpa0, t1 = (s1 + i % nt1) % op.tpa1;
+            const unsigned long long* mp = op.masks + ((int64_t)t0 * op.tpa1 + t1) * op.mwords;
+#pragma unroll
+            for (int w = 0; w < MAXW; ++w)
+                if (w < op.mwords) mw[w] |= mp[w];
+        }
+#pragma unroll
+        for (int w = 0; w < MAXW; ++w) {
+            const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)mw[w]);
+            const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(mw[w] >> 32));
+            mw[w] = ((unsigned long long)hi << 32) | lo;
+        }
+    }
+    const int64_t N = op.N;
+    const T* Fb = op.F + op.Foff[cfg.b];
+    const int RR = A0.cnt * A1.cnt;
+
+    // s(q0, q1) = sum_k v_k(g + q) F_{k,b}(q), compensated over k
+    auto s_value = [&](int q0, int q1) -> T {
+        int gy = g0 + q0;
+        if (gy >= n) gy -= n;
+        int gx = g1 + q1;
+        if (gx >= n) gx -= n;
+        const int64_t pix = (DIM == 2) ? (int64_t)gy * n + gx : gx;
+        const int q = q0 * A1.cnt + q1;
+        KahanAcc<T> acc;
+        acc.init();
+#pragma unroll
+        for (int w = 0; w < MAXW; ++w) {
+            unsigned long long bits = mw[w];
+            while (bits) {
+                const int k = w * 64 + __ffsll((long long)bits) - 1;
+                bits &= bits - 1;
+                const T vk = __ldg(op.v + (int64_t)k * N + pix);
+                if (vk != T(0)) acc.add(vk * __ldg(Fb + (int64_t)k * RR + q));
+            }
+        }
+        return acc.get();
+    };
+
+    if (DIM == 1) {
+        // s on the whole region, then the cascade with a/d ping-pong between the arena ends
+        T* X = arena;
+        if (A1.cnt > cfg.arena) {
+            flag_error(op.err, ERR_ARENA);
+            return;
+        }
+        for (int q1 = tid; q1 < A1.cnt; q1 += gt) X[q1] = s_value(0, q1);
+        group_sync(gt, gid);
+        if ((int64_t)boff[op.nb] != op.row_ptr[srow + 1] - row_base) return;  // flagged above
+        Range cur = A1;
+        const T* in = X;
+        int n_in = n;
+        bool out_top = true;
+        int prev_out = A1.cnt;
+        for (int jj = 1; jj <= jhi; ++jj) {
+            const Range nx = range_cascade(cur, Lf, n >> jj);
+            if (2 * nx.cnt + prev_out > (int)(arena_end - arena)) {
+                flag_error(op.err, ERR_ARENA);
+                return;
+            }
+            T* out = out_top ? (arena_end - 2 * nx.cnt) : arena;
+            for (int c = tid; c < nx.cnt; c += gt) {
+                out[c] = filt(in, 1, cur, n_in, nx, c, hS, Lf, 2, 0);
+                out[nx.cnt + c] = filt(in, 1, cur, n_in, nx, c, gS, Lf, 2, 2 - Lf);
+            }
+            group_sync(gt, gid);
+            if (jj >= jlo) {
+                const int b2 = band_of_level(1, L, jj, 0);
+                write_block<T, 1>(op, out + nx.cnt, Range{0, 1, 0}, nx, jj, 0, 1, row_base + boff[b2], j, 0,
+                                  Bo.e1, 0, l1, tid, gt);
+                if (jj == L)
+                    write_block<T, 1>(op, out, Range{0, 1, 0}, nx, jj, 0, 0, row_base + boff[0], j, 0, Bo.e1, 0,
+                                      l1, tid, gt);
+            }
+            in = out;
+            cur = nx;
+            n_in = n >> jj;
+            out_top = !out_top;
+            prev_out = 2 * nx.cnt;
+        }
+        return;
+    }
+
+    // ---------------- 2-D ----------------
+    const int A = (int)(arena_end - arena);
+    Range c0, c1;
+    int S1, n1;
+    if (k0 == 0) {
+        n1 = n >> 1;
+        S1 = 2;
+        c0 = range_cascade(A0, Lf, n1);
+        c1 = range_cascade(A1, Lf, n1);
+    } else {
+        n1 = n >> k0;
+        S1 = 1 << k0;
+        c0 = range_filter(A0, S1, 0, lenk, n1);
+        c1 = range_filter(A1, S1, 0, lenk, n1);
+    }
+    const int nY = (k0 == 0) ? 2 : 1;
+    const int Ysz = nY * A0.cnt * c1.cnt;
+    const int Zsz = ((k0 == 0) ? 4 : 1) * c0.cnt * c1.cnt;
+    const int B = max(1, min(cfg.batch, A0.cnt));
+    if (B * A1.cnt + Ysz > A || Zsz + Ysz > A) {
+        flag_error(op.err, ERR_ARENA);
+        return;
+    }
+    T* X = arena;
+    T* YL = arena_end - Ysz;
+    T* YH = YL + A0.cnt * c1.cnt;
+    // stage 1a: rows of s, filtered along axis 1
+    for (int q0b = 0; q0b < A0.cnt; q0b += B) {
+        const int nbr = min(B, A0.cnt - q0b);
+        for (int e = tid; e < nbr * A1.cnt; e += gt) {
+            const int bq = e / A1.cnt, q1 = e - bq * A1.cnt;
+            X[e] = s_value(q0b + bq, q1);
+        }
+        group_sync(gt, gid);
+        if ((int64_t)boff[op.nb] != op.row_ptr[srow + 1] - row_base) return;  // flagged above
+        for (int e = tid; e < nbr * c1.cnt; e += gt) {
+            const int bq = e / c1.cnt, c = e - bq * c1.cnt;
+            const T* xr = X + bq * A1.cnt;
+            const int yo = (q0b + bq) * c1.cnt + c;
+            if (k0 == 0) {
+                YL[yo] = filt(xr, 1, A1, n, c1, c, hS, Lf, 2, 0);
+                YH[yo] = filt(xr, 1, A1, n, c1, c, gS, Lf, 2, 2 - Lf);
+            } else {
+                YL[yo] = filt(xr, 1, A1, n, c1, c, phiS, lenk, S1, 0);
+            }
+        }
+        group_sync(gt, gid);
+    }
+    // stage 1b: along axis 0
+    T* Z = arena;
+    const int zb = c0.cnt * c1.cnt;
+    for (int e = tid; e < zb; e += gt) {
+        const int a = e / c1.cnt, c = e - a * c1.cnt;
+        if (k0 == 0) {
+            Z[e] = filt(YL + c, c1.cnt, A0, n, c0, a, hS, Lf, 2, 0);                // (0,0)
+            Z[2 * zb + e] = filt(YL + c, c1.cnt, A0, n, c0, a, gS, Lf, 2, 2 - Lf);  // (1,0)
+            Z[zb + e] = filt(YH + c, c1.cnt, A0, n, c0, a, hS, Lf, 2, 0);           // (0,1)
+            Z[3 * zb + e] = filt(YH + c, c1.cnt, A0, n, c0, a, gS, Lf, 2, 2 - Lf);  // (1,1)
+        } else {
+            Z[e] = filt(YL + c, c1.cnt, A0, n, c0, a, phiS, lenk, S1, 0);
+        }
+    }
+    group_sync(gt, gid);
+    int jj0;
+    if (k0 == 0) {
+        // level 1 bands (0,1), (1,0), (1,1) are Z[zb..4zb)
+        for (int t = 0; t < 3; ++t) {
+            const int b2 = band_of_level(2, L, 1, t);
+            write_block<T, 2>(op, Z + (1 + t) * zb, c0, c1, 1, t >= 1 ? 1 : 0, t == 1 ? 0 : 1, row_base + boff[b2], j,
+                              Bo.e0, Bo.e1, l0, l1, tid, gt);
+        }
+        if (L == 1) write_block<T, 2>(op, Z, c0, c1, 1, 0, 0, row_base + boff[0], j, Bo.e0, Bo.e1, l0, l1, tid, gt);
+        jj0 = 2;
+    } else {
+        jj0 = k0 + 1;
+    }
+    // cascade on the LL band for the remaining output levels
+    Range p0 = c0, p1 = c1;
+    int prevZ = Zsz;
+    for (int jj = jj0; jj <= jhi; ++jj) {
+        const int nj = n >> jj;
+        const Range q0r = range_cascade(p0, Lf, nj), q1r = range_cascade(p1, Lf, nj);
+        const int ysz = 2 * p0.cnt * q1r.cnt, zsz = 4 * q0r.cnt * q1r.cnt;
+        if (prevZ + ysz > A || zsz + ysz > A) {
+            flag_error(op.err, ERR_ARENA);
+            return;
+        }
+        const T* Xl = Z;  // LL of level jj-1 (p0.cnt x p1.cnt)
+        T* Yl = arena_end - ysz;
+        T* Yh = Yl + p0.cnt * q1r.cnt;
+        for (int e = tid; e < p0.cnt * q1r.cnt; e += gt) {
+            const int a = e / q1r.cnt, c = e - a * q1r.cnt;
+            Yl[e] = filt(Xl + a * p1.cnt, 1, p1, nj * 2, q1r, c, hS, Lf, 2, 0);
+            Yh[e] = filt(Xl + a * p1.cnt, 1, p1, nj * 2, q1r, c, gS, Lf, 2, 2 - Lf);
+        }
+        group_sync(gt, gid);
+        const int zq = q0r.cnt * q1r.cnt;
+        for (int e = tid; e < zq; e += gt) {
+            const int a = e / q1r.cnt, c = e - a * q1r.cnt;
+            Z[e] = filt(Yl + c, q1r.cnt, p0, nj * 2, q0r, a, hS, Lf, 2, 0);
+            Z[2 * zq + e] = filt(Yl + c, q1r.cnt, p0, nj * 2, q0r, a, gS, Lf, 2, 2 - Lf);
+            Z[zq + e] = filt(Yh + c, q1r.cnt, p0, nj * 2, q0r, a, hS, Lf, 2, 0);
+            Z[3 * zq + e] = filt(Yh + c, q1r.cnt, p0, nj * 2, q0r, a, gS, Lf, 2, 2 - Lf);
+        }
+        group_sync(gt, gid);
+        for (int t = 0; t < 3; ++t) {
+            const int b2 = band_of_level(2, L, jj, t);
+            write_block<T, 2>(op, Z + (1 + t) * zq, q0r, q1r, jj, t >= 1 ? 1 : 0, t == 1 ? 0 : 1,
+                              row_base + boff[b2], j, Bo.e0, Bo.e1, l0, l1, tid, gt);
+        }
+        if (jj == L)
+            write_block<T, 2>(op, Z, q0r, q1r, jj, 0, 0, row_base + boff[0], j, Bo.e0, Bo.e1, l0, l1, tid, gt);
+        p0 = q0r;
+        p1 = q1r;
+        prevZ = zsz;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// A6: y = S x (stored rows are outputs) or y = S^T x (convolution-first order, stored rows are
+// inputs; scatter with atomics into a zeroed y).  One warp per stored row, NR right-hand
+// sides per pass, warp-shuffle reduction of the row sums.
+// ------------------------------------------------------------------------------------------
+template <typename TV>
+__device__ __forceinline__ float to_acc(TV v) { return (float)v; }
+template <>
+__device__ __forceinline__ float to_acc<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename TV, typename TA, int NR>
+__global__ void __launch_bounds__(256) k_apply(const __grid_constant__ OpDev<TA> op, const TV* __restrict__ vals,
+                                               const TA* __restrict__ x, int ldx, TA* __restrict__ y, int ldy,
+                                               int c0, int nr, int transpose)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t s = warp;
+    if (s >= op.N) return;
+    const int d = op.d, n = op.n, L = op.L;
+    int b = 0;
+    Band Bo = band_info(d, n, L, 0);
+    for (int bb = op.nb - 1; bb >= 0; --bb) {
+        const Band t = band_info(d, n, L, bb);
+        const int64_t sz = (d == 2) ? (int64_t)t.nj * t.nj : t.nj;
+        if (s >= t.off && s < t.off + sz) {
+            b = bb;
+            Bo = t;
+            break;
+        }
+    }
+    const int rl = (int)(s - Bo.off);
+    const int l0 = (d == 2) ? rl / Bo.nj : 0, l1 = (d == 2) ? rl % Bo.nj : rl;
+    const int dense = op.gap < 0;
+    TA acc[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) acc[q] = TA(0);
+    TA xs[NR];
+    if (transpose) {
+#pragma unroll
+        for (int q = 0; q < NR; ++q) xs[q] = (q < nr) ? x[s * ldx + c0 + q] : TA(0);
+    }
+    int64_t pos = op.row_ptr[s];
+    for (int b2 = 0; b2 < op.nb; ++b2) {
+        if (!block_kept(d, n, L, op.gap, b, b2)) continue;
+        const Band B2 = band_info(d, n, L, b2);
+        int f0 = 0, W0 = 1, f1, W1;
+        stencil(Bo.j, Bo.e1, l1, B2.j, B2.e1, op.r, op.Lf, n, dense, &f1, &W1);
+        if (d == 2) stencil(Bo.j, Bo.e0, l0, B2.j, B2.e0, op.r, op.Lf, n, dense, &f0, &W0);
+        const int nj = B2.nj, tot = W0 * W1;
+        for (int idx = lane; idx < tot; idx += 32) {
+            const int a = idx / W1, bb = idx - a * W1;
+            const int64_t col = B2.off + (int64_t)pmod(f0 + a, nj) * ((d == 2) ? nj : 0) + pmod(f1 + bb, nj);
+            const TA v = (TA)to_acc(vals[pos + idx]);
+            if (!transpose) {
+                const TA* xr = x + col * ldx + c0;
+#pragma unroll
+                for (int q = 0; q < NR; ++q)
+                    if (q < nr) acc[q] = fma(v, xr[q], acc[q]);
+            } else {
+                TA* yr = y + col * ldy + c0;
+#pragma unroll
+                for (int q = 0; q < NR; ++q)
+                    if (q < nr) atomicAdd(yr + q, v * xs[q]);
+            }
+        }
+        pos += tot;
+    }
+    if (!transpose) {
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+            TA vq = acc[q];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) vq += __shfl_xor_sync(0xffffffffu, vq, o);
+            acc[q] = vq;
+        }
+        if (lane < nr && lane < NR) {
+            TA out = acc[0];
+#pragma unroll
+            for (int q = 1; q < NR; ++q)
+                if (lane == q) out = acc[q];
+            y[s * ldy + c0 + lane] = out;
+        }
+    }
+}
+
+template <typename TA>
+__global__ void k_zero_rows(TA* y, int64_t N, int ldy, int c0, int nr)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < N * nr) y[(i / nr) * ldy + c0 + (i % nr)] = TA(0);
+}
+
+}  // namespace pcw

@@ -1,0 +1,717 @@
+// libpcwave: C-ABI entry points, host planner and launches (see include/pcwave.h).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/pcwave.h"
+#include "pcw_geom.cuh"
+#include "pcw_kernels.cuh"
+#include "pcw_taps.h"
+
+using namespace pcw;
+
+namespace {
+
+thread_local std::string g_noh_error = "no error";
+
+struct BandPlan {
+    int b, rows, jlo, jhi, k0;
+    AsmCfg cfg;
+    size_t smem;
+};
+
+}  // namespace
+
+struct pc_op {
+    pc_desc desc{};
+    int Lf = 0, K = 0, Ku = 0, nb = 0;
+    int64_t N = 0, nnz = 0;
+    size_t esz = 4;  // bytes per element of the precision type
+    double h[64]{};
+    std::vector<int64_t> row_ptr_h;
+    std::vector<BandPlan> plan;
+    FiltDev fd{};
+    int wofs[MAXL + 2]{};
+    int wav_total = 0;
+    int64_t Ftotal = 0, Gtotal = 0;
+    int mwords = 1, ts0 = 1, ts1 = 1, tpa0 = 1, tpa1 = 1;
+    // device buffers
+    void* u_d = nullptr;
+    void* v_d = nullptr;
+    double* taps64_d = nullptr;
+    double* wav64_d = nullptr;
+    void* tapsT_d = nullptr;
+    void* wavT_d = nullptr;
+    void* F_d = nullptr;
+    void* G_d = nullptr;
+    int64_t* row_ptr_d = nullptr;
+    void* theta_d = nullptr;
+    __nv_bfloat16* theta16_d = nullptr;
+    unsigned long long* masks_d = nullptr;
+    int* err_d = nullptr;
+    int64_t dev_bytes = 0;
+    bool assembled = false;
+    std::string err = "no error";
+};
+
+namespace {
+
+pc_status fail(pc_op* h, pc_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h)
+        h->err = buf;
+    else
+        g_noh_error = buf;
+    return st;
+}
+
+#define PC_CUDA(h, call)                                                                               \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess)                                                                         \
+            return fail(h, e_ == cudaErrorMemoryAllocation ? PC_ERR_OOM : PC_ERR_CUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                            \
+    } while (0)
+
+bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+pc_status check_desc(const pc_desc* d, pc_op* h)
+{
+    if (!d) return fail(h, PC_ERR_INVALID_ARG, "desc is NULL");
+    if (d->dim != 1 && d->dim != 2) return fail(h, PC_ERR_INVALID_ARG, "dim must be 1 or 2 (got %d)", d->dim);
+    if (!is_pow2(d->n) || d->n < 2) return fail(h, PC_ERR_INVALID_ARG, "n must be a power of two >= 2 (got %d)", d->n);
+    if (d->dim == 2 && d->n > 16384) return fail(h, PC_ERR_UNSUPPORTED, "2-D side > 16384");
+    if (d->dim == 1 && d->n > (1 << 28)) return fail(h, PC_ERR_UNSUPPORTED, "1-D length > 2^28");
+    if (d->levels < 1 || d->levels > MAXL || (d->n >> d->levels) < 1)
+        return fail(h, PC_ERR_INVALID_ARG, "levels must satisfy 1 <= L <= %d and n >> L >= 1", MAXL);
+    if (d->delta < 1 || d->delta > 10) return fail(h, PC_ERR_INVALID_ARG, "delta must be in 1..10");
+    if (d->m < 1 || d->m > 64 * MAXW) return fail(h, PC_ERR_UNSUPPORTED, "m must be in 1..%d", 64 * MAXW);
+    if (d->radius < 0 || d->radius > 64) return fail(h, PC_ERR_UNSUPPORTED, "radius must be in 0..64");
+    if (d->gap < -1) return fail(h, PC_ERR_INVALID_ARG, "gap must be -1 (dense) or >= 0");
+    if (d->order != 0 && d->order != 1) return fail(h, PC_ERR_INVALID_ARG, "order must be 0 or 1");
+    if (d->precision != PC_FP32 && d->precision != PC_FP64) return fail(h, PC_ERR_INVALID_ARG, "bad precision");
+    if (d->store_bf16 && d->precision != PC_FP32) return fail(h, PC_ERR_INVALID_ARG, "store_bf16 needs PC_FP32");
+    if (d->gap < 0) {
+        int64_t N = (d->dim == 2) ? (int64_t)d->n * d->n : d->n;
+        if (N > 16384) return fail(h, PC_ERR_UNSUPPORTED, "dense pattern limited to N <= 16384");
+    }
+    return PC_OK;
+}
+
+struct Geo {
+    int d, n, L, Lf, r, gap, nb;
+};
+
+Geo geo_of(const pc_desc* d)
+{
+    Geo g;
+    g.d = d->dim;
+    g.n = d->n;
+    g.L = d->levels;
+    g.Lf = 2 * d->delta;
+    g.r = d->radius;
+    g.gap = d->gap;
+    g.nb = num_bands(g.d, g.L);
+    return g;
+}
+
+int64_t band_rows(const Geo& g, int b)
+{
+    Band B = band_info(g.d, g.n, g.L, b);
+    return (g.d == 2) ? (int64_t)B.nj * B.nj : B.nj;
+}
+
+int64_t row_length(const Geo& g, int b, int l0, int l1)
+{
+    int64_t acc = 0;
+    for (int b2 = 0; b2 < g.nb; ++b2)
+        if (block_kept(g.d, g.n, g.L, g.gap, b, b2)) acc += block_count(g.d, g.n, g.L, g.Lf, g.r, g.gap, b, l0, l1, b2);
+    return acc;
+}
+
+// decode a canonical index into band / translates
+void decode(const Geo& g, int64_t s, int* b, int* l0, int* l1)
+{
+    for (int bb = g.nb - 1; bb >= 0; --bb) {
+        Band B = band_info(g.d, g.n, g.L, bb);
+        int64_t sz = band_rows(g, bb);
+        if (s >= B.off && s < B.off + sz) {
+            *b = bb;
+            int rl = (int)(s - B.off);
+            *l0 = (g.d == 2) ? rl / B.nj : 0;
+            *l1 = (g.d == 2) ? rl % B.nj : rl;
+            return;
+        }
+    }
+    *b = -1;
+}
+
+pc_status plan_nnz(const Geo& g, std::vector<int64_t>* row_ptr, int64_t* nnz)
+{
+    int64_t N = (g.d == 2) ? (int64_t)g.n * g.n : g.n;
+    if (row_ptr) row_ptr->assign(N + 1, 0);
+    int64_t acc = 0;
+    for (int b = 0; b < g.nb; ++b) {
+        Band B = band_info(g.d, g.n, g.L, b);
+        int nj = B.nj;
+        // a row's length depends on its translate only through l mod 2^(j2 - j) <= 2^gap
+        // (stencils toward finer column bands): cache per phase
+        const int P = 1 << std::min(std::max(g.gap, 0), 12);
+        const int p0n = std::min(nj, P), p1n = std::min(nj, P);
+        std::vector<int64_t> cache((size_t)((g.d == 2) ? p0n : 1) * p1n, -1);
+        for (int l0 = 0; l0 < ((g.d == 2) ? nj : 1); ++l0)
+            for (int l1 = 0; l1 < nj; ++l1) {
+                int64_t len;
+                size_t ci = (size_t)((g.d == 2) ? (l0 % p0n) : 0) * p1n + (l1 % p1n);
+                if (cache[ci] < 0) cache[ci] = row_length(g, b, l0, l1);
+                len = cache[ci];
+                if (row_ptr) (*row_ptr)[B.off + (int64_t)l0 * ((g.d == 2) ? nj : 0) + l1] = acc;
+                acc += len;
+            }
+    }
+    if (row_ptr) (*row_ptr)[N] = acc;
+    *nnz = acc;
+    return PC_OK;
+}
+
+// per-axis maxima of the ranges a row group meets, over the translate phases of a band
+struct AxisMax {
+    int A;           // region count
+    int c;           // stage-1 output count
+    int lev[MAXL + 2];  // cascade counts per level
+};
+
+AxisMax axis_max(const Geo& g, int j, int e, int nj, int k0, int jhi)
+{
+    AxisMax M{};
+    const int lim = std::min(nj, 1 << std::min(12, std::max(1, jhi - j + 2)));
+    for (int l = 0; l < lim; ++l) {
+        Range A = region0(j, e, l, g.r, g.Lf, g.n);
+        M.A = std::max(M.A, A.cnt);
+        Range c;
+        int lvl;
+        if (k0 == 0) {
+            c = range_cascade(A, g.Lf, g.n >> 1);
+            lvl = 1;
+        } else {
+            c = range_filter(A, 1 << k0, 0, wav_len(k0, g.Lf), g.n >> k0);
+            lvl = k0;
+        }
+        M.c = std::max(M.c, c.cnt);
+        M.lev[lvl] = std::max(M.lev[lvl], c.cnt);
+        Range p = c;
+        for (int jj = lvl + 1; jj <= jhi; ++jj) {
+            p = range_cascade(p, g.Lf, g.n >> jj);
+            M.lev[jj] = std::max(M.lev[jj], p.cnt);
+        }
+    }
+    return M;
+}
+
+int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+pc_status plan_bands(pc_op* h)
+{
+    const pc_desc& D = h->desc;
+    Geo g = geo_of(&D);
+    h->plan.clear();
+    const size_t es = h->esz;
+    for (int b = 0; b < g.nb; ++b) {
+        Band B = band_info(g.d, g.n, g.L, b);
+        BandPlan bp{};
+        bp.b = b;
+        bp.rows = (int)band_rows(g, b);
+        const int dense = g.gap < 0;
+        bp.jlo = dense ? 1 : std::max(1, B.j - g.gap);
+        bp.jhi = dense ? g.L : std::min(g.L, B.j + g.gap);
+        bp.k0 = (g.d == 2) ? bp.jlo - 1 : 0;
+        int64_t need = 0;
+        int gt, batch = 1;
+        AxisMax M1 = axis_max(g, B.j, B.e1, B.nj, bp.k0, bp.jhi);
+        if (g.d == 1) {
+            // X then alternating (a|d) outputs at the two arena ends
+            int64_t prev = M1.A;
+            for (int jj = 1; jj <= bp.jhi; ++jj) {
+                int64_t cur = 2 * (int64_t)M1.lev[jj];
+                need = std::max(need, prev + cur);
+                prev = cur;
+            }
+            gt = (M1.A > 256) ? 64 : 32;
+        } else {
+            AxisMax M0 = axis_max(g, B.j, B.e0, B.nj, bp.k0, bp.jhi);
+            const int64_t area = (int64_t)M0.A * M1.A;
+            gt = area <= 768 ? 32 : area <= 2048 ? 64 : area <= 6144 ? 128 : 256;
+            batch = (int)std::max<int64_t>(1, std::min<int64_t>(M0.A, (2 * gt + M1.A - 1) / M1.A));
+            const int nY = (bp.k0 == 0) ? 2 : 1;
+            const int64_t Y = (int64_t)nY * M0.A * M1.c;
+            const int64_t Z = (int64_t)((bp.k0 == 0) ? 4 : 1) * M0.c * M1.c;
+            need = std::max<int64_t>((int64_t)batch * M1.A + Y, Z + Y);
+            int64_t prevZ = Z;
+            int lvl0 = (bp.k0 == 0) ? 1 : bp.k0;
+            for (int jj = lvl0 + 1; jj <= bp.jhi; ++jj) {
+                int64_t ysz = 2 * (int64_t)M0.lev[jj - 1] * M1.lev[jj];
+                int64_t zsz = 4 * (int64_t)M0.lev[jj] * M1.lev[jj];
+                need = std::max(need, std::max(prevZ + ysz, zsz + ysz));
+                prevZ = zsz;
+            }
+        }
+        need = round_up(need, (int64_t)(16 / es));
+        int filt = 2 * g.Lf + ((bp.k0 > 0) ? wav_len(bp.k0, g.Lf) : 0);
+        filt = (int)round_up(filt, (int64_t)(16 / es));
+        int rpc = std::max(1, 256 / gt);
+        auto smem_of = [&](int rpcv) {
+            return (size_t)filt * es + round_up((int64_t)rpcv * (MAXB + 1) * 4, 16) + (size_t)rpcv * need * es;
+        };
+        while (rpc > 1 && smem_of(rpc) > 110 * 1024) rpc /= 2;
+        if (smem_of(rpc) > 227 * 1024)
+            return fail(h, PC_ERR_UNSUPPORTED, "band %d needs %zu bytes of shared memory per row", b, smem_of(rpc));
+        bp.cfg.b = b;
+        bp.cfg.row0 = 0;
+        bp.cfg.rows = bp.rows;
+        bp.cfg.gt = gt;
+        bp.cfg.rpc = rpc;
+        bp.cfg.batch = batch;
+        bp.cfg.arena = (int)need;
+        bp.cfg.filt = filt;
+        bp.smem = smem_of(rpc);
+        // the kernel places the per-group int tables before the arenas: keep 16-byte alignment
+        h->plan.push_back(bp);
+    }
+    return PC_OK;
+}
+
+template <typename T>
+OpDev<T> make_opdev(pc_op* h)
+{
+    OpDev<T> o{};
+    const pc_desc& D = h->desc;
+    o.d = D.dim;
+    o.n = D.n;
+    o.L = D.levels;
+    o.Lf = h->Lf;
+    o.r = D.radius;
+    o.m = D.m;
+    o.gap = D.gap;
+    o.order = D.order;
+    o.nb = h->nb;
+    o.N = h->N;
+    o.u = (const T*)h->u_d;
+    o.v = (const T*)h->v_d;
+    o.taps = (const T*)h->tapsT_d;
+    o.wav = (const T*)h->wavT_d;
+    for (int i = 0; i < MAXL + 2; ++i) o.wofs[i] = h->wofs[i];
+    o.F = (const T*)h->F_d;
+    for (int b = 0; b < h->nb; ++b) o.Foff[b] = h->fd.band[b].Foff;
+    o.row_ptr = h->row_ptr_d;
+    o.theta = (T*)h->theta_d;
+    o.theta16 = h->theta16_d;
+    o.masks = h->masks_d;
+    o.mwords = h->mwords;
+    o.ts0 = h->ts0;
+    o.ts1 = h->ts1;
+    o.tpa0 = h->tpa0;
+    o.tpa1 = h->tpa1;
+    o.err = h->err_d;
+    return o;
+}
+
+template <typename T, int DIM>
+pc_status set_smem_attr()
+{
+    static bool done = false;
+    if (!done) {
+        if (cudaFuncSetAttribute(k_assemble<T, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
+            cudaSuccess)
+            return PC_ERR_CUDA;
+        done = true;
+    }
+    return PC_OK;
+}
+
+template <typename T>
+pc_status assemble_t(pc_op* h, cudaStream_t st)
+{
+    const pc_desc& D = h->desc;
+    // A1/A2: taps in T and the FP64 cascade of the base wavelets
+    k_taps<T><<<1, 64, 0, st>>>(h->taps64_d, h->Lf, (T*)h->tapsT_d);
+    k_base_wavelets<<<1, 256, 0, st>>>(h->taps64_d, h->Lf, D.levels, h->wav64_d);
+    k_cast<T><<<std::max(1, std::min(1024, (h->wav_total + 255) / 256)), 256, 0, st>>>(h->wav64_d, (T*)h->wavT_d,
+                                                                                      h->wav_total);
+    // A3: filtered base wavelets
+    {
+        int maxU = 0, maxR = 0;
+        const int K0 = (D.dim == 2) ? h->K : 1;
+        for (int b = 0; b < h->nb; ++b) {
+            maxU = std::max(maxU, K0 * h->fd.band[b].U1);
+            maxR = std::max(maxR, h->fd.band[b].R0 * h->fd.band[b].R1);
+        }
+        dim3 g1((maxU + 127) / 128, h->nb * D.m), g2((maxR + 127) / 128, h->nb * D.m);
+        k_filtered_pass1<T><<<g1, 128, 0, st>>>(h->fd, (const T*)h->u_d, (const T*)h->wavT_d, (T*)h->G_d);
+        k_filtered_pass2<T><<<g2, 128, 0, st>>>(h->fd, (const T*)h->wavT_d, (const T*)h->G_d, (T*)h->F_d);
+    }
+    // window tile masks
+    k_tile_masks<T><<<h->tpa0 * h->tpa1, 256, 0, st>>>((const T*)h->v_d, D.dim, D.n, D.m, h->ts0, h->ts1, h->tpa1,
+                                                       h->mwords, h->masks_d);
+    PC_CUDA(h, cudaGetLastError());
+    // A5: one launch per row band
+    OpDev<T> od = make_opdev<T>(h);
+    for (const BandPlan& bp : h->plan) {
+        const int ctas = (bp.rows + bp.cfg.rpc - 1) / bp.cfg.rpc;
+        const int threads = bp.cfg.gt * bp.cfg.rpc;
+        if (D.dim == 1) {
+            if (set_smem_attr<T, 1>() != PC_OK) return fail(h, PC_ERR_CUDA, "cudaFuncSetAttribute failed");
+            k_assemble<T, 1><<<ctas, threads, bp.smem, st>>>(od, bp.cfg);
+        } else {
+            if (set_smem_attr<T, 2>() != PC_OK) return fail(h, PC_ERR_CUDA, "cudaFuncSetAttribute failed");
+            k_assemble<T, 2><<<ctas, threads, bp.smem, st>>>(od, bp.cfg);
+        }
+    }
+    PC_CUDA(h, cudaGetLastError());
+    h->assembled = true;
+    return PC_OK;
+}
+
+template <typename TV, typename TA>
+pc_status apply_t(pc_op* h, const TV* vals, const TA* x, TA* y, int nrhs, int ldx, int ldy, cudaStream_t st)
+{
+    OpDev<TA> od{};
+    const pc_desc& D = h->desc;
+    od.d = D.dim;
+    od.n = D.n;
+    od.L = D.levels;
+    od.Lf = h->Lf;
+    od.r = D.radius;
+    od.gap = D.gap;
+    od.nb = h->nb;
+    od.N = h->N;
+    od.row_ptr = h->row_ptr_d;
+    const int transpose = D.order == PC_ORDER_CONV_THEN_MULT;
+    const int64_t warps = h->N;
+    const int blocks = (int)((warps * 32 + 255) / 256);
+    for (int c0 = 0; c0 < nrhs; c0 += 16) {
+        const int nr = std::min(16, nrhs - c0);
+        if (transpose) k_zero_rows<TA><<<(int)((h->N * nr + 255) / 256), 256, 0, st>>>(y, h->N, ldy, c0, nr);
+        if (nr == 1)
+            k_apply<TV, TA, 1><<<blocks, 256, 0, st>>>(od, vals, x, ldx, y, ldy, c0, nr, transpose);
+        else if (nr <= 4)
+            k_apply<TV, TA, 4><<<blocks, 256, 0, st>>>(od, vals, x, ldx, y, ldy, c0, nr, transpose);
+        else
+            k_apply<TV, TA, 16><<<blocks, 256, 0, st>>>(od, vals, x, ldx, y, ldy, c0, nr, transpose);
+    }
+    PC_CUDA(h, cudaGetLastError());
+    return PC_OK;
+}
+
+template <typename T>
+pc_status dev_alloc(pc_op* h, T** p, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc((void**)p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(h, PC_ERR_OOM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    h->dev_bytes += (int64_t)bytes;
+    return PC_OK;
+}
+
+void free_all(pc_op* h)
+{
+    void* ptrs[] = {h->u_d,  h->v_d,        h->taps64_d,  h->wav64_d,  h->tapsT_d, h->wavT_d, h->F_d,
+                    h->G_d,  h->row_ptr_d,  h->theta_d,   h->theta16_d, h->masks_d, h->err_d};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}
+
+}  // namespace
+
+// =========================================================================================
+// C-ABI
+// =========================================================================================
+extern "C" {
+
+pc_status pc_plan_check(const pc_desc* desc) { return check_desc(desc, nullptr); }
+
+pc_status pc_plan_nnz(const pc_desc* desc, int64_t* nnz)
+{
+    pc_status st = check_desc(desc, nullptr);
+    if (st != PC_OK) return st;
+    if (!nnz) return fail(nullptr, PC_ERR_INVALID_ARG, "nnz is NULL");
+    Geo g = geo_of(desc);
+    return plan_nnz(g, nullptr, nnz);
+}
+
+pc_status pc_plan_row(const pc_desc* desc, int64_t row, int64_t* cols, int64_t* count)
+{
+    pc_status st = check_desc(desc, nullptr);
+    if (st != PC_OK) return st;
+    if (!count) return fail(nullptr, PC_ERR_INVALID_ARG, "count is NULL");
+    Geo g = geo_of(desc);
+    int64_t N = (g.d == 2) ? (int64_t)g.n * g.n : g.n;
+    if (row < 0 || row >= N) return fail(nullptr, PC_ERR_INVALID_ARG, "row out of range");
+    int b, l0, l1;
+    decode(g, row, &b, &l0, &l1);
+    Band Bo = band_info(g.d, g.n, g.L, b);
+    int64_t len = row_length(g, b, l0, l1);
+    if (!cols) {
+        *count = len;
+        return PC_OK;
+    }
+    if (*count < len) return fail(nullptr, PC_ERR_INVALID_ARG, "cols holds %lld < %lld", (long long)*count, (long long)len);
+    int64_t pos = 0;
+    for (int b2 = 0; b2 < g.nb; ++b2) {
+        if (!block_kept(g.d, g.n, g.L, g.gap, b, b2)) continue;
+        Band B2 = band_info(g.d, g.n, g.L, b2);
+        int f0 = 0, W0 = 1, f1, W1;
+        stencil(Bo.j, Bo.e1, l1, B2.j, B2.e1, g.r, g.Lf, g.n, g.gap < 0, &f1, &W1);
+        if (g.d == 2) stencil(Bo.j, Bo.e0, l0, B2.j, B2.e0, g.r, g.Lf, g.n, g.gap < 0, &f0, &W0);
+        for (int a = 0; a < W0; ++a)
+            for (int c = 0; c < W1; ++c)
+                cols[pos++] = B2.off + (int64_t)pmod(f0 + a, B2.nj) * ((g.d == 2) ? B2.nj : 0) + pmod(f1 + c, B2.nj);
+    }
+    *count = len;
+    return PC_OK;
+}
+
+pc_status pc_create(const pc_desc* desc, const void* u, const void* v, void* stream, pc_handle* out)
+{
+    if (!out) return fail(nullptr, PC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    pc_status st = check_desc(desc, nullptr);
+    if (st != PC_OK) return st;
+    if (!u || !v) return fail(nullptr, PC_ERR_INVALID_ARG, "u and v must not be NULL");
+    pc_op* h = new (std::nothrow) pc_op();
+    if (!h) return fail(nullptr, PC_ERR_OOM, "host allocation failed");
+    h->desc = *desc;
+    const pc_desc& D = h->desc;
+    Geo g = geo_of(desc);
+    h->Lf = 2 * D.delta;
+    h->K = 2 * D.radius + 1;
+    h->Ku = (D.dim == 2) ? h->K * h->K : h->K;
+    h->nb = g.nb;
+    h->N = (D.dim == 2) ? (int64_t)D.n * D.n : D.n;
+    h->esz = (D.precision == PC_FP64) ? 8 : 4;
+    if (daubechies_taps(D.delta, h->h) != h->Lf) {
+        delete h;
+        return fail(nullptr, PC_ERR_INVALID_ARG, "filter taps failed for delta=%d", D.delta);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    auto bail = [&](pc_status e) {
+        std::string msg = h->err;
+        free_all(h);
+        delete h;
+        g_noh_error = msg;
+        return e;
+    };
+    // pattern
+    plan_nnz(g, &h->row_ptr_h, &h->nnz);
+    if ((st = plan_bands(h)) != PC_OK) return bail(st);
+    // geometry of the base wavelets and filtered wavelets
+    int acc = 0;
+    for (int j = 1; j <= D.levels; ++j) {
+        h->wofs[j] = acc;
+        acc += 2 * wav_len(j, h->Lf);
+    }
+    h->wofs[D.levels + 1] = acc;
+    h->wav_total = acc;
+    FiltDev& fd = h->fd;
+    fd.nb = h->nb;
+    fd.d = D.dim;
+    fd.n = D.n;
+    fd.r = D.radius;
+    fd.m = D.m;
+    fd.Lf = h->Lf;
+    fd.order = D.order;
+    for (int i = 0; i < MAXL + 2; ++i) fd.wofs[i] = h->wofs[i];
+    int64_t Fo = 0, Go = 0;
+    for (int b = 0; b < h->nb; ++b) {
+        Band B = band_info(D.dim, D.n, D.levels, b);
+        FiltBand& fb = fd.band[b];
+        fb.j = B.j;
+        fb.e0 = B.e0;
+        fb.e1 = B.e1;
+        const int U = wav_len(B.j, h->Lf) + 2 * D.radius;
+        fb.U1 = U;
+        fb.U0 = (D.dim == 2) ? U : 1;
+        fb.R1 = std::min(U, D.n);
+        fb.R0 = (D.dim == 2) ? std::min(U, D.n) : 1;
+        fb.Foff = Fo;
+        fb.Goff = Go;
+        Fo += (int64_t)D.m * fb.R0 * fb.R1;
+        Go += (int64_t)D.m * ((D.dim == 2) ? h->K : 1) * fb.U1;
+    }
+    h->Ftotal = Fo;
+    h->Gtotal = Go;
+    // window tiles
+    h->mwords = (D.m + 63) / 64;
+    if (D.dim == 2) {
+        h->ts0 = h->ts1 = std::min(16, D.n);
+        h->tpa0 = h->tpa1 = D.n / h->ts1;
+    } else {
+        h->ts0 = 1;
+        h->ts1 = std::min(256, D.n);
+        h->tpa0 = 1;
+        h->tpa1 = D.n / h->ts1;
+    }
+    // device buffers
+    const size_t es = h->esz;
+    if ((st = dev_alloc(h, &h->u_d, es * D.m * h->Ku)) || (st = dev_alloc(h, &h->v_d, es * D.m * h->N)) ||
+        (st = dev_alloc(h, &h->taps64_d, sizeof(double) * h->Lf)) ||
+        (st = dev_alloc(h, &h->wav64_d, sizeof(double) * h->wav_total)) ||
+        (st = dev_alloc(h, &h->tapsT_d, es * 2 * h->Lf)) || (st = dev_alloc(h, &h->wavT_d, es * h->wav_total)) ||
+        (st = dev_alloc(h, &h->F_d, es * h->Ftotal)) || (st = dev_alloc(h, &h->G_d, es * h->Gtotal)) ||
+        (st = dev_alloc(h, &h->row_ptr_d, sizeof(int64_t) * (h->N + 1))) ||
+        (st = dev_alloc(h, &h->theta_d, es * h->nnz)) ||
+        (st = dev_alloc(h, &h->masks_d, sizeof(unsigned long long) * h->tpa0 * h->tpa1 * h->mwords)) ||
+        (st = dev_alloc(h, &h->err_d, sizeof(int))))
+        return bail(st);
+    if (D.store_bf16 && (st = dev_alloc(h, &h->theta16_d, sizeof(__nv_bfloat16) * h->nnz))) return bail(st);
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(h->taps64_d, h->h, sizeof(double) * h->Lf, cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemcpyAsync(h->row_ptr_d, h->row_ptr_h.data(), sizeof(int64_t) * (h->N + 1), cudaMemcpyHostToDevice,
+                             s)) ||
+        (e = cudaMemsetAsync(h->err_d, 0, sizeof(int), s)) ||
+        (e = cudaMemcpyAsync(h->u_d, u, es * D.m * h->Ku, cudaMemcpyDefault, s)) ||
+        (e = cudaMemcpyAsync(h->v_d, v, es * D.m * h->N, cudaMemcpyDefault, s)) || (e = cudaStreamSynchronize(s))) {
+        fail(h, PC_ERR_CUDA, "upload failed: %s", cudaGetErrorString(e));
+        return bail(PC_ERR_CUDA);
+    }
+    *out = h;
+    return PC_OK;
+}
+
+pc_status pc_set_params(pc_handle h, const void* u, const void* v, void* stream)
+{
+    if (!h) return fail(nullptr, PC_ERR_INVALID_ARG, "handle is NULL");
+    const pc_desc& D = h->desc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (u) PC_CUDA(h, cudaMemcpyAsync(h->u_d, u, h->esz * D.m * h->Ku, cudaMemcpyDefault, s));
+    if (v) PC_CUDA(h, cudaMemcpyAsync(h->v_d, v, h->esz * D.m * h->N, cudaMemcpyDefault, s));
+    h->assembled = false;
+    return PC_OK;
+}
+
+void pc_destroy(pc_handle h)
+{
+    if (!h) return;
+    cudaDeviceSynchronize();
+    free_all(h);
+    delete h;
+}
+
+pc_status pc_assemble(pc_handle h, void* stream)
+{
+    if (!h) return fail(nullptr, PC_ERR_INVALID_ARG, "handle is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->desc.precision == PC_FP64) return assemble_t<double>(h, s);
+    return assemble_t<float>(h, s);
+}
+
+pc_status pc_apply(pc_handle h, const void* x, void* y, int nrhs, int ldx, int ldy, void* stream)
+{
+    if (!h) return fail(nullptr, PC_ERR_INVALID_ARG, "handle is NULL");
+    if (!h->assembled) return fail(h, PC_ERR_NOT_ASSEMBLED, "pc_apply before pc_assemble");
+    if (!x || !y || nrhs < 1 || nrhs > 64 || ldx < nrhs || ldy < nrhs)
+        return fail(h, PC_ERR_INVALID_ARG, "bad x/y/nrhs/ldx/ldy (nrhs=%d ldx=%d ldy=%d)", nrhs, ldx, ldy);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->desc.precision == PC_FP64)
+        return apply_t<double, double>(h, (const double*)h->theta_d, (const double*)x, (double*)y, nrhs, ldx, ldy, s);
+    if (h->theta16_d) return apply_t<__nv_bfloat16, float>(h, h->theta16_d, (const float*)x, (float*)y, nrhs, ldx, ldy, s);
+    return apply_t<float, float>(h, (const float*)h->theta_d, (const float*)x, (float*)y, nrhs, ldx, ldy, s);
+}
+
+pc_status pc_backward(pc_handle h, const void* dtheta, void* du, void* dv, void* stream)
+{
+    (void)dtheta;
+    (void)du;
+    (void)dv;
+    (void)stream;
+    if (!h) return fail(nullptr, PC_ERR_INVALID_ARG, "handle is NULL");
+    return fail(h, PC_ERR_UNSUPPORTED, "pc_backward not built yet");
+}
+
+pc_status pc_batch_assemble(pc_handle* ops, int count, void* stream)
+{
+    if (!ops || count < 0) return fail(nullptr, PC_ERR_INVALID_ARG, "bad ops/count");
+    for (int i = 0; i < count; ++i) {
+        pc_status st = pc_assemble(ops[i], stream);
+        if (st != PC_OK) return st;
+    }
+    return PC_OK;
+}
+
+pc_status pc_info(pc_handle h, int64_t* nnz, int64_t* device_bytes)
+{
+    if (!h) return fail(nullptr, PC_ERR_INVALID_ARG, "handle is NULL");
+    if (nnz) *nnz = h->nnz;
+    if (device_bytes) *device_bytes = h->dev_bytes;
+    return PC_OK;
+}
+
+pc_status pc_theta(pc_handle h, void** values, void** values_bf16, int64_t** row_ptr)
+{
+    if (!h) return fail(nullptr, PC_ERR_INVALID_ARG, "handle is NULL");
+    if (values) *values = h->theta_d;
+    if (values_bf16) *values_bf16 = h->theta16_d;
+    if (row_ptr) *row_ptr = h->row_ptr_d;
+    return PC_OK;
+}
+
+pc_status pc_lookup(pc_handle h, int64_t n, const int64_t* mu, const int64_t* lambda, int64_t* pos)
+{
+    if (!h) return fail(nullptr, PC_ERR_INVALID_ARG, "handle is NULL");
+    if (n < 0 || (n > 0 && (!mu || !lambda || !pos))) return fail(h, PC_ERR_INVALID_ARG, "bad arrays");
+    Geo g = geo_of(&h->desc);
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t s = mu[i], c = lambda[i];
+        if (h->desc.order == PC_ORDER_CONV_THEN_MULT) std::swap(s, c);
+        pos[i] = -1;
+        if (s < 0 || s >= h->N || c < 0 || c >= h->N) continue;
+        int b, l0, l1, b2, m0, m1;
+        decode(g, s, &b, &l0, &l1);
+        decode(g, c, &b2, &m0, &m1);
+        if (!block_kept(g.d, g.n, g.L, g.gap, b, b2)) continue;
+        Band Bo = band_info(g.d, g.n, g.L, b), B2 = band_info(g.d, g.n, g.L, b2);
+        int f0 = 0, W0 = 1, f1, W1;
+        stencil(Bo.j, Bo.e1, l1, B2.j, B2.e1, g.r, g.Lf, g.n, g.gap < 0, &f1, &W1);
+        if (g.d == 2) stencil(Bo.j, Bo.e0, l0, B2.j, B2.e0, g.r, g.Lf, g.n, g.gap < 0, &f0, &W0);
+        const int a = (g.d == 2) ? pmod(m0 - f0, B2.nj) : 0, bb = pmod(m1 - f1, B2.nj);
+        if (a >= W0 || bb >= W1) continue;
+        int64_t off = 0;
+        for (int q = 0; q < b2; ++q)
+            if (block_kept(g.d, g.n, g.L, g.gap, b, q)) off += block_count(g.d, g.n, g.L, g.Lf, g.r, g.gap, b, l0, l1, q);
+        pos[i] = h->row_ptr_h[s] + off + (int64_t)a * W1 + bb;
+    }
+    return PC_OK;
+}
+
+pc_status pc_sync(pc_handle h, void* stream)
+{
+    if (!h) return fail(nullptr, PC_ERR_INVALID_ARG, "handle is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    PC_CUDA(h, cudaStreamSynchronize(s));
+    int flag = 0;
+    PC_CUDA(h, cudaMemcpy(&flag, h->err_d, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        PC_CUDA(h, cudaMemset(h->err_d, 0, sizeof(int)));
+        return fail(h, PC_ERR_DEVICE, "device fault flag 0x%x (1: arena overflow, 2: row length, 4: index, 8: queue)",
+                    flag);
+    }
+    return PC_OK;
+}
+
+const char* pc_last_error(pc_handle h) { return h ? h->err.c_str() : g_noh_error.c_str(); }
+
+}  // extern "C"
