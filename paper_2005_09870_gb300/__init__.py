@@ -264,3 +264,40 @@ class PCOperator:
             self.close()
         except Exception:
             pass
+
+
+# ----------------------------------------------------------------- autograd
+def theta(u, v, op: "PCOperator"):
+    """Differentiable Theta: the stored values (nnz,) as a function of kernels u (m, K) and
+    windows v (m, N).  Backward runs pc_backward (the adjoint kernels)."""
+    return _theta_fn().apply(u, v, op)
+
+
+_THETA_FN = None
+
+
+def _theta_fn():
+    global _THETA_FN
+    if _THETA_FN is None:
+        torch = _torch()
+
+        class PCTheta(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, u, v, op):
+                u = u.detach().contiguous()
+                v = v.detach().contiguous()
+                pc_set_params(op.h, u, v)
+                op.assemble()
+                ctx.op = op
+                ctx.save_for_backward(u, v)
+                return op.values().clone()
+
+            @staticmethod
+            def backward(ctx, g):
+                u, v = ctx.saved_tensors
+                pc_set_params(ctx.op.h, u, v)
+                du, dv = ctx.op.backward(g.contiguous())
+                return du, dv, None
+
+        _THETA_FN = PCTheta
+    return _THETA_FN

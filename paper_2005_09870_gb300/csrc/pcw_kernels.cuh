@@ -587,6 +587,349 @@ __global__ void __launch_bounds__(256) k_assemble(const __grid_constant__ OpDev<
 }
 
 // ------------------------------------------------------------------------------------------
+// A7: adjoint (backward).  The transpose of filt(): for an input position p,
+//   in_bar[p] = sum over (c, i) with S*(ro.lo + c) + off + i = ri.lo + p (mod n_in when the
+//   output is full) of f[i] * out_bar[c].
+// ------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T filt_adj(const T* outb, int ostride, Range ri, Range ro, int n_out, int p, const T* f,
+                                      int len, int S, int off)
+{
+    const int x = ri.lo + p - off;  // = S*y + i
+    T acc = T(0);
+    for (int i = pmod(x, S); i < len; i += S) {
+        const int y = (x - i) / S;  // exact
+        int c = y - ro.lo;
+        if (!ro.full) {
+            if ((unsigned)c >= (unsigned)ro.cnt) continue;
+        } else {
+            c = pmod(c, n_out);
+        }
+        acc = fma(f[i], outb[c * ostride], acc);
+    }
+    return acc;
+}
+
+// Scatters the row's dL/dTheta entries of column band b2 into a zeroed band array (transpose
+// of write_block).
+template <typename T, int DIM>
+__device__ __forceinline__ void read_block(const OpDev<T>& op, const T* __restrict__ Gr, T* Zb, Range r0, Range r1,
+                                           int jj, int e0, int e1, int64_t src, int j, int eo0, int eo1, int l0,
+                                           int l1, int tid, int gt)
+{
+    const int dense = op.gap < 0;
+    int f0 = 0, W0 = 1, f1, W1;
+    stencil(j, eo1, l1, jj, e1, op.r, op.Lf, op.n, dense, &f1, &W1);
+    if (DIM == 2) stencil(j, eo0, l0, jj, e0, op.r, op.Lf, op.n, dense, &f0, &W0);
+    const int nj = op.n >> jj;
+    const int tot = W0 * W1;
+    for (int idx = tid; idx < tot; idx += gt) {
+        const int a = idx / W1, bb = idx - a * W1;
+        const int p1 = pmod(f1 + bb - r1.lo, nj);
+        bool ok = r1.full || p1 < r1.cnt;
+        int p0 = 0;
+        if (DIM == 2) {
+            p0 = pmod(f0 + a - r0.lo, nj);
+            ok = ok && (r0.full || p0 < r0.cnt);
+        }
+        if (ok) Zb[p0 * r1.cnt + p1] = Gr[src + idx];
+    }
+}
+
+// One stored row per thread group: dL/ds on the row's region by the transposed localized
+// transform of the row's dL/dTheta, then
+//   dL/dv_k(x) += F_{k,b}(x - shift) dL/ds(x)   (every k)
+//   dL/dF_{k,b}(q) += v_k(q + shift) dL/ds(q)   (k with v_k nonzero on the region)
+// with atomics into dv (m x N) and dF (layout of F).
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_backward(const __grid_constant__ OpDev<T> op, const AsmCfg cfg,
+                                                  const T* __restrict__ Gth, T* __restrict__ dv, T* __restrict__ dF)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int gt = cfg.gt;
+    const int gid = threadIdx.x / gt, tid = threadIdx.x % gt;
+    const int n = op.n, L = op.L, Lf = op.Lf, r = op.r;
+    const int dense = op.gap < 0;
+    const Band Bo = band_info(DIM, n, L, cfg.b);
+    const int j = Bo.j;
+    const int jlo = dense ? 1 : max(1, j - op.gap);
+    const int jhi = dense ? L : min(L, j + op.gap);
+    const int k0 = (DIM == 2) ? jlo - 1 : 0;
+
+    T* fS = reinterpret_cast<T*>(smem_raw);
+    T* hS = fS;
+    T* gS = fS + Lf;
+    T* phiS = fS + 2 * Lf;
+    const int lenk = (k0 > 0) ? wav_len(k0, Lf) : 0;
+    int* boffAll = reinterpret_cast<int*>(smem_raw + sizeof(T) * cfg.filt);
+    int* boff = boffAll + gid * (MAXB + 1);
+    T* arena = reinterpret_cast<T*>(smem_raw + sizeof(T) * cfg.filt + sizeof(int) * cfg.rpc * (MAXB + 1));
+    arena += (int64_t)gid * cfg.arena;
+    T* const arena_end = arena + cfg.arena;
+    const int A = cfg.arena;
+
+    for (int i = threadIdx.x; i < 2 * Lf; i += blockDim.x) fS[i] = op.taps[i];
+    for (int i = threadIdx.x; i < lenk; i += blockDim.x) phiS[i] = op.wav[op.wofs[k0] + i];
+    __syncthreads();
+
+    const int rl = cfg.row0 + blockIdx.x * cfg.rpc + gid;
+    if (blockIdx.x * cfg.rpc + gid >= cfg.rows) return;
+    const int l0 = (DIM == 2) ? rl / Bo.nj : 0;
+    const int l1 = (DIM == 2) ? rl % Bo.nj : rl;
+    const Range A1 = region0(j, Bo.e1, l1, r, Lf, n);
+    const Range A0 = (DIM == 2) ? region0(j, Bo.e0, l0, r, Lf, n) : Range{0, 1, 0};
+    const int g0 = (DIM == 2) ? pmod(A0.lo, n) : 0;
+    const int g1 = pmod(A1.lo, n);
+    const int64_t srow = Bo.off + rl;
+    const int64_t row_base = op.row_ptr[srow];
+    if (tid == 0) {
+        int acc = 0;
+        for (int b2 = 0; b2 < op.nb; ++b2) {
+            boff[b2] = acc;
+            if (block_kept(DIM, n, L, op.gap, cfg.b, b2))
+                acc += (int)block_count(DIM, n, L, Lf, r, op.gap, cfg.b, l0, l1, b2);
+        }
+        boff[op.nb] = acc;
+        if ((int64_t)acc != op.row_ptr[srow + 1] - row_base) flag_error(op.err, ERR_ROWLEN);
+    }
+    unsigned long long mw[MAXW];
+#pragma unroll
+    for (int w = 0; w < MAXW; ++w) mw[w] = 0ull;
+    {
+        const int lane = threadIdx.x & 31;
+        const int ts0 = op.ts0, ts1 = op.ts1;
+        const int s0 = g0 / ts0, s1 = g1 / ts1;
+        const int nt0 = (DIM == 2) ? min(op.tpa0, (g0 % ts0 + A0.cnt + ts0 - 1) / ts0) : 1;
+        const int nt1 = min(op.tpa1, (g1 % ts1 + A1.cnt + ts1 - 1) / ts1);
+        for (int i = lane; i < nt0 * nt1; i += 32) {
+            const int t0 = (s0 + i / nt1) % op.tpa0, t1 = (s1 + i % nt1) % op.tpa1;
+            const unsigned long long* mp = op.masks + ((int64_t)t0 * op.tpa1 + t1) * op.mwords;
+#pragma unroll
+            for (int w = 0; w < MAXW; ++w)
+                if (w < op.mwords) mw[w] |= mp[w];
+        }
+#pragma unroll
+        for (int w = 0; w < MAXW; ++w) {
+            const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)mw[w]);
+            const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(mw[w] >> 32));
+            mw[w] = ((unsigned long long)hi << 32) | lo;
+        }
+    }
+    group_sync(gt, gid);
+    if ((int64_t)boff[op.nb] != op.row_ptr[srow + 1] - row_base) return;
+    const int64_t N = op.N;
+    const int64_t Fo = op.Foff[cfg.b];
+    const int RR = A0.cnt * A1.cnt;
+
+    // dL/ds(q) -> dv, dF
+    auto scatter = [&](int q0, int q1, T sb) {
+        int gy = g0 + q0;
+        if (gy >= n) gy -= n;
+        int gx = g1 + q1;
+        if (gx >= n) gx -= n;
+        const int64_t pix = (DIM == 2) ? (int64_t)gy * n + gx : gx;
+        const int q = q0 * A1.cnt + q1;
+        if (sb == T(0)) return;
+        for (int k = 0; k < op.m; ++k) {
+            const int64_t fi = Fo + (int64_t)k * RR + q;
+            atomicAdd(dv + (int64_t)k * N + pix, __ldg(op.F + fi) * sb);
+            if ((mw[k >> 6] >> (k & 63)) & 1ull) {
+                const T vk = __ldg(op.v + (int64_t)k * N + pix);
+                if (vk != T(0)) atomicAdd(dF + fi, vk * sb);
+            }
+        }
+    };
+
+    if (DIM == 1) {
+        // ranges of the forward cascade: R(0) = A1, R(jj) = cascade of R(jj-1)
+        // level jj's [a|d] sits at the top for odd jj, at the bottom for even jj (forward layout)
+        Range Rj = A1;
+        Range Rs[MAXL + 2];
+        Rs[0] = A1;
+        for (int jj = 1; jj <= jhi; ++jj) {
+            Rj = range_cascade(Rj, Lf, n >> jj);
+            Rs[jj] = Rj;
+        }
+        for (int jj = jhi; jj >= 1; --jj) {
+            const Range R = Rs[jj], P = Rs[jj - 1];
+            if (2 * R.cnt + ((jj == 1) ? P.cnt : 2 * P.cnt) > A) {
+                flag_error(op.err, ERR_ARENA);
+                return;
+            }
+            T* buf = (jj & 1) ? (arena_end - 2 * R.cnt) : arena;
+            T* prev = (jj & 1) ? arena : (arena_end - 2 * P.cnt);  // level jj-1 (a part first), or X
+            for (int c = tid; c < R.cnt; c += gt) {
+                if (jj == jhi) buf[c] = T(0);
+                buf[R.cnt + c] = T(0);
+            }
+            group_sync(gt, gid);
+            if (jj >= jlo) read_block<T, 1>(op, Gth, buf + R.cnt, Range{0, 1, 0}, R, jj, 0, 1,
+                                           row_base + boff[band_of_level(1, L, jj, 0)], j, 0, Bo.e1, 0, l1, tid, gt);
+            if (jj == jhi && jj == L)
+                read_block<T, 1>(op, Gth, buf, Range{0, 1, 0}, R, jj, 0, 0, row_base + boff[0], j, 0, Bo.e1, 0, l1,
+                                 tid, gt);
+            group_sync(gt, gid);
+            for (int p = tid; p < P.cnt; p += gt)
+                prev[p] = filt_adj(buf, 1, P, R, n >> jj, p, hS, Lf, 2, 0) +
+                          filt_adj(buf + R.cnt, 1, P, R, n >> jj, p, gS, Lf, 2, 2 - Lf);
+            group_sync(gt, gid);
+        }
+        for (int q1 = tid; q1 < A1.cnt; q1 += gt) scatter(0, q1, arena[q1]);
+        return;
+    }
+
+    // ---------------- 2-D ----------------
+    Range c0, c1;
+    int S1, n1;
+    if (k0 == 0) {
+        n1 = n >> 1;
+        S1 = 2;
+        c0 = range_cascade(A0, Lf, n1);
+        c1 = range_cascade(A1, Lf, n1);
+    } else {
+        n1 = n >> k0;
+        S1 = 1 << k0;
+        c0 = range_filter(A0, S1, 0, lenk, n1);
+        c1 = range_filter(A1, S1, 0, lenk, n1);
+    }
+    const int lvl0 = (k0 == 0) ? 1 : k0;
+    Range Q0[MAXL + 2], Q1[MAXL + 2];
+    Q0[lvl0] = c0;
+    Q1[lvl0] = c1;
+    for (int jj = lvl0 + 1; jj <= jhi; ++jj) {
+        Q0[jj] = range_cascade(Q0[jj - 1], Lf, n >> jj);
+        Q1[jj] = range_cascade(Q1[jj - 1], Lf, n >> jj);
+    }
+    T* Z = arena;
+    // cascade levels, coarse to fine
+    for (int jj = jhi; jj >= lvl0 + 1; --jj) {
+        const int nj = n >> jj;
+        const Range q0r = Q0[jj], q1r = Q1[jj], p0 = Q0[jj - 1], p1 = Q1[jj - 1];
+        const int zq = q0r.cnt * q1r.cnt, ysz = 2 * p0.cnt * q1r.cnt;
+        if (4 * zq + ysz > A || p0.cnt * p1.cnt + ysz > A) {
+            flag_error(op.err, ERR_ARENA);
+            return;
+        }
+        for (int e = tid; e < ((jj == jhi) ? 4 : 3) * zq; e += gt) Z[((jj == jhi) ? 0 : zq) + e] = T(0);
+        group_sync(gt, gid);
+        for (int t = 0; t < 3; ++t)
+            read_block<T, 2>(op, Gth, Z + (1 + t) * zq, q0r, q1r, jj, t >= 1 ? 1 : 0, t == 1 ? 0 : 1,
+                             row_base + boff[band_of_level(2, L, jj, t)], j, Bo.e0, Bo.e1, l0, l1, tid, gt);
+        if (jj == jhi && jj == L)
+            read_block<T, 2>(op, Gth, Z, q0r, q1r, jj, 0, 0, row_base + boff[0], j, Bo.e0, Bo.e1, l0, l1, tid, gt);
+        group_sync(gt, gid);
+        T* Yl = arena_end - ysz;
+        T* Yh = Yl + p0.cnt * q1r.cnt;
+        for (int e = tid; e < p0.cnt * q1r.cnt; e += gt) {
+            const int a = e / q1r.cnt, c = e - a * q1r.cnt;
+            Yl[e] = filt_adj(Z + c, q1r.cnt, p0, q0r, nj, a, hS, Lf, 2, 0) +
+                    filt_adj(Z + 2 * zq + c, q1r.cnt, p0, q0r, nj, a, gS, Lf, 2, 2 - Lf);
+            Yh[e] = filt_adj(Z + zq + c, q1r.cnt, p0, q0r, nj, a, hS, Lf, 2, 0) +
+                    filt_adj(Z + 3 * zq + c, q1r.cnt, p0, q0r, nj, a, gS, Lf, 2, 2 - Lf);
+        }
+        group_sync(gt, gid);
+        for (int e = tid; e < p0.cnt * p1.cnt; e += gt) {
+            const int a = e / p1.cnt, b = e - a * p1.cnt;
+            Z[e] = filt_adj(Yl + a * q1r.cnt, 1, p1, q1r, nj, b, hS, Lf, 2, 0) +
+                   filt_adj(Yh + a * q1r.cnt, 1, p1, q1r, nj, b, gS, Lf, 2, 2 - Lf);
+        }
+        group_sync(gt, gid);
+    }
+    // stage 1 (level 1 with its detail bands, or LL of level k0)
+    const int zb = c0.cnt * c1.cnt;
+    const int nY = (k0 == 0) ? 2 : 1;
+    const int Ysz = nY * A0.cnt * c1.cnt;
+    if (((k0 == 0) ? 4 : 1) * zb + Ysz > A) {
+        flag_error(op.err, ERR_ARENA);
+        return;
+    }
+    if (k0 == 0) {
+        const bool top = (jhi == 1);
+        for (int e = tid; e < (top ? 4 : 3) * zb; e += gt) Z[(top ? 0 : zb) + e] = T(0);
+        group_sync(gt, gid);
+        for (int t = 0; t < 3; ++t)
+            read_block<T, 2>(op, Gth, Z + (1 + t) * zb, c0, c1, 1, t >= 1 ? 1 : 0, t == 1 ? 0 : 1,
+                             row_base + boff[band_of_level(2, L, 1, t)], j, Bo.e0, Bo.e1, l0, l1, tid, gt);
+        if (L == 1) read_block<T, 2>(op, Gth, Z, c0, c1, 1, 0, 0, row_base + boff[0], j, Bo.e0, Bo.e1, l0, l1, tid, gt);
+        group_sync(gt, gid);
+    }
+    T* YL = arena_end - Ysz;
+    T* YH = YL + A0.cnt * c1.cnt;
+    for (int e = tid; e < A0.cnt * c1.cnt; e += gt) {
+        const int q0 = e / c1.cnt, c = e - q0 * c1.cnt;
+        if (k0 == 0) {
+            YL[e] = filt_adj(Z + c, c1.cnt, A0, c0, n1, q0, hS, Lf, 2, 0) +
+                    filt_adj(Z + 2 * zb + c, c1.cnt, A0, c0, n1, q0, gS, Lf, 2, 2 - Lf);
+            YH[e] = filt_adj(Z + zb + c, c1.cnt, A0, c0, n1, q0, hS, Lf, 2, 0) +
+                    filt_adj(Z + 3 * zb + c, c1.cnt, A0, c0, n1, q0, gS, Lf, 2, 2 - Lf);
+        } else {
+            YL[e] = filt_adj(Z + c, c1.cnt, A0, c0, n1, q0, phiS, lenk, S1, 0);
+        }
+    }
+    group_sync(gt, gid);
+    for (int e = tid; e < RR; e += gt) {
+        const int q0 = e / A1.cnt, q1 = e - q0 * A1.cnt;
+        T sb;
+        if (k0 == 0)
+            sb = filt_adj(YL + q0 * c1.cnt, 1, A1, c1, n1, q1, hS, Lf, 2, 0) +
+                 filt_adj(YH + q0 * c1.cnt, 1, A1, c1, n1, q1, gS, Lf, 2, 2 - Lf);
+        else
+            sb = filt_adj(YL + q0 * c1.cnt, 1, A1, c1, n1, q1, phiS, lenk, S1, 0);
+        scatter(q0, q1, sb);
+    }
+}
+
+// Adjoint of A3.  pass 2^T: dG[t0][q1] = sum_{q0 < U0} dF[q0 mod n][q1 mod n] rho^{e0}_j(q0 - r - t0)
+template <typename T>
+__global__ void k_dfilt_pass2(const __grid_constant__ FiltDev fd, const T* __restrict__ wav,
+                              const T* __restrict__ dF, T* __restrict__ dG)
+{
+    const int bk = blockIdx.y;
+    const int b = bk / fd.m, k = bk % fd.m;
+    const FiltBand& B = fd.band[b];
+    const int K = 2 * fd.r + 1, K0 = (fd.d == 2) ? K : 1;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= K0 * B.U1) return;
+    const int t0i = idx / B.U1, q1 = idx % B.U1;
+    const int len = wav_len(B.j, fd.Lf);
+    const T* dFk = dF + B.Foff + (int64_t)k * B.R0 * B.R1;
+    const int p1 = q1 % fd.n;
+    T acc = T(0);
+    if (fd.d == 1) {
+        acc = dFk[p1];
+    } else {
+        const T* rho0 = wav + fd.wofs[B.j] + (B.e0 ? len : 0);
+        const int qlo = t0i, qhi = min(B.U0, t0i + len);  // rho index q0 - t0i in [0, len)
+        for (int q0 = qlo; q0 < qhi; ++q0) acc = fma(dFk[(int64_t)(q0 % fd.n) * B.R1 + p1], rho0[q0 - t0i], acc);
+    }
+    dG[B.Goff + ((int64_t)k * K0 + t0i) * B.U1 + q1] = acc;
+}
+
+// pass 1^T summed over bands: dkappa_k(t0, t1) = sum_b sum_q1 dG_b[t0][q1] rho^{e1}_j(q1 - r - t1);
+// du_k(t) = dkappa_k(-t) in the paper's order, dkappa_k(t) otherwise.  One thread per (k, t).
+template <typename T>
+__global__ void k_dfilt_pass1(const __grid_constant__ FiltDev fd, const T* __restrict__ wav,
+                              const T* __restrict__ dG, T* __restrict__ du)
+{
+    const int K = 2 * fd.r + 1, K0 = (fd.d == 2) ? K : 1, Ku = K0 * K;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= fd.m * Ku) return;
+    const int k = idx / Ku, t = idx % Ku;
+    const int t0i = t / K, t1i = t % K;
+    T acc = T(0);
+    for (int b = 0; b < fd.nb; ++b) {
+        const FiltBand& B = fd.band[b];
+        const int len = wav_len(B.j, fd.Lf);
+        const T* rho1 = wav + fd.wofs[B.j] + (B.e1 ? len : 0);
+        const T* g = dG + B.Goff + ((int64_t)k * K0 + t0i) * B.U1;
+        const int qlo = t1i, qhi = min(B.U1, t1i + len);
+        for (int q1 = qlo; q1 < qhi; ++q1) acc = fma(g[q1], rho1[q1 - t1i], acc);
+    }
+    const int o = (fd.order == 0) ? (Ku - 1 - t) : t;  // flip: index of -t
+    du[(int64_t)k * Ku + o] = acc;
+}
+
+// ------------------------------------------------------------------------------------------
 // A6: y = S x (stored rows are outputs) or y = S^T x (convolution-first order, stored rows are
 // inputs; scatter with atomics into a zeroed y).  One warp per stored row, NR right-hand
 // sides per pass, warp-shuffle reduction of the row sums.

@@ -51,6 +51,8 @@ struct pc_op {
     void* wavT_d = nullptr;
     void* F_d = nullptr;
     void* G_d = nullptr;
+    void* dF_d = nullptr;  // backward scratch: dL/dF
+    void* dG_d = nullptr;  // backward scratch: dL/dG
     int64_t* row_ptr_d = nullptr;
     void* theta_d = nullptr;
     __nv_bfloat16* theta16_d = nullptr;
@@ -333,7 +335,9 @@ pc_status set_smem_attr()
     static bool done = false;
     if (!done) {
         if (cudaFuncSetAttribute(k_assemble<T, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
-            cudaSuccess)
+                cudaSuccess ||
+            cudaFuncSetAttribute(k_backward<T, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
+                cudaSuccess)
             return PC_ERR_CUDA;
         done = true;
     }
@@ -341,7 +345,7 @@ pc_status set_smem_attr()
 }
 
 template <typename T>
-pc_status assemble_t(pc_op* h, cudaStream_t st)
+pc_status prepare_t(pc_op* h, cudaStream_t st)
 {
     const pc_desc& D = h->desc;
     // A1/A2: taps in T and the FP64 cascade of the base wavelets
@@ -365,6 +369,15 @@ pc_status assemble_t(pc_op* h, cudaStream_t st)
     k_tile_masks<T><<<h->tpa0 * h->tpa1, 256, 0, st>>>((const T*)h->v_d, D.dim, D.n, D.m, h->ts0, h->ts1, h->tpa1,
                                                        h->mwords, h->masks_d);
     PC_CUDA(h, cudaGetLastError());
+    return PC_OK;
+}
+
+template <typename T>
+pc_status assemble_t(pc_op* h, cudaStream_t st)
+{
+    const pc_desc& D = h->desc;
+    pc_status ps = prepare_t<T>(h, st);
+    if (ps != PC_OK) return ps;
     // A5: one launch per row band
     OpDev<T> od = make_opdev<T>(h);
     for (const BandPlan& bp : h->plan) {
@@ -427,10 +440,45 @@ pc_status dev_alloc(pc_op* h, T** p, size_t bytes)
     return PC_OK;
 }
 
+template <typename T>
+pc_status backward_t(pc_op* h, const T* G, T* du, T* dv, cudaStream_t st)
+{
+    const pc_desc& D = h->desc;
+    if (!h->dF_d) {
+        pc_status a;
+        if ((a = dev_alloc(h, &h->dF_d, h->esz * h->Ftotal)) != PC_OK) return a;
+        if ((a = dev_alloc(h, &h->dG_d, h->esz * h->Gtotal)) != PC_OK) return a;
+    }
+    pc_status ps = prepare_t<T>(h, st);  // filtered wavelets recomputed from the current u
+    if (ps != PC_OK) return ps;
+    PC_CUDA(h, cudaMemsetAsync(dv, 0, h->esz * D.m * h->N, st));
+    PC_CUDA(h, cudaMemsetAsync(h->dF_d, 0, h->esz * h->Ftotal, st));
+    OpDev<T> od = make_opdev<T>(h);
+    for (const BandPlan& bp : h->plan) {
+        const int ctas = (bp.rows + bp.cfg.rpc - 1) / bp.cfg.rpc;
+        const int threads = bp.cfg.gt * bp.cfg.rpc;
+        if (D.dim == 1) {
+            if (set_smem_attr<T, 1>() != PC_OK) return fail(h, PC_ERR_CUDA, "cudaFuncSetAttribute failed");
+            k_backward<T, 1><<<ctas, threads, bp.smem, st>>>(od, bp.cfg, G, dv, (T*)h->dF_d);
+        } else {
+            if (set_smem_attr<T, 2>() != PC_OK) return fail(h, PC_ERR_CUDA, "cudaFuncSetAttribute failed");
+            k_backward<T, 2><<<ctas, threads, bp.smem, st>>>(od, bp.cfg, G, dv, (T*)h->dF_d);
+        }
+    }
+    int maxU = 0;
+    const int K0 = (D.dim == 2) ? h->K : 1;
+    for (int b = 0; b < h->nb; ++b) maxU = std::max(maxU, K0 * h->fd.band[b].U1);
+    k_dfilt_pass2<T><<<dim3((maxU + 127) / 128, h->nb * D.m), 128, 0, st>>>(h->fd, (const T*)h->wavT_d,
+                                                                           (const T*)h->dF_d, (T*)h->dG_d);
+    k_dfilt_pass1<T><<<(D.m * h->Ku + 127) / 128, 128, 0, st>>>(h->fd, (const T*)h->wavT_d, (const T*)h->dG_d, du);
+    PC_CUDA(h, cudaGetLastError());
+    return PC_OK;
+}
+
 void free_all(pc_op* h)
 {
     void* ptrs[] = {h->u_d,  h->v_d,        h->taps64_d,  h->wav64_d,  h->tapsT_d, h->wavT_d, h->F_d,
-                    h->G_d,  h->row_ptr_d,  h->theta_d,   h->theta16_d, h->masks_d, h->err_d};
+                    h->G_d,  h->dF_d, h->dG_d, h->row_ptr_d,  h->theta_d,   h->theta16_d, h->masks_d, h->err_d};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -634,12 +682,11 @@ pc_status pc_apply(pc_handle h, const void* x, void* y, int nrhs, int ldx, int l
 
 pc_status pc_backward(pc_handle h, const void* dtheta, void* du, void* dv, void* stream)
 {
-    (void)dtheta;
-    (void)du;
-    (void)dv;
-    (void)stream;
     if (!h) return fail(nullptr, PC_ERR_INVALID_ARG, "handle is NULL");
-    return fail(h, PC_ERR_UNSUPPORTED, "pc_backward not built yet");
+    if (!dtheta || !du || !dv) return fail(h, PC_ERR_INVALID_ARG, "dtheta, du and dv must not be NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->desc.precision == PC_FP64) return backward_t<double>(h, (const double*)dtheta, (double*)du, (double*)dv, s);
+    return backward_t<float>(h, (const float*)dtheta, (float*)du, (float*)dv, s);
 }
 
 pc_status pc_batch_assemble(pc_handle* ops, int count, void* stream)
