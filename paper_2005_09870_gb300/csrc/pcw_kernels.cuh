@@ -934,10 +934,10 @@ __global__ void k_dfilt_pass1(const __grid_constant__ FiltDev fd, const T* __res
 // inputs; scatter with atomics into a zeroed y).  One warp per stored row, NR right-hand
 // sides per pass, warp-shuffle reduction of the row sums.
 // ------------------------------------------------------------------------------------------
-template <typename TV>
-__device__ __forceinline__ float to_acc(TV v) { return (float)v; }
+template <typename TA, typename TV>
+__device__ __forceinline__ TA to_acc(TV v) { return (TA)v; }
 template <>
-__device__ __forceinline__ float to_acc<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_acc<float, __nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
 
 template <typename TV, typename TA, int NR>
 __global__ void __launch_bounds__(256) k_apply(const __grid_constant__ OpDev<TA> op, const TV* __restrict__ vals,
@@ -982,7 +982,7 @@ __global__ void __launch_bounds__(256) k_apply(const __grid_constant__ OpDev<TA>
         for (int idx = lane; idx < tot; idx += 32) {
             const int a = idx / W1, bb = idx - a * W1;
             const int64_t col = B2.off + (int64_t)pmod(f0 + a, nj) * ((d == 2) ? nj : 0) + pmod(f1 + bb, nj);
-            const TA v = (TA)to_acc(vals[pos + idx]);
+            const TA v = to_acc<TA, TV>(vals[pos + idx]);
             if (!transpose) {
                 const TA* xr = x + col * ldx + c0;
 #pragma unroll

@@ -122,4 +122,6 @@ def test_autograd_function(pw):
     w = torch.linspace(-1, 1, th.numel(), device="cuda")
     (th * w).sum().backward()
     du, dv = g.backward(w.contiguous())
-    assert torch.allclose(u.grad, du) and torch.allclose(v.grad, dv)
+    # dv is accumulated with FP32 atomics, so two runs agree up to summation order
+    for a, b in ((u.grad, du), (v.grad, dv)):
+        assert (a - b).abs().max() <= 1e-5 * b.abs().max()
