@@ -1,0 +1,355 @@
+"""Benchmark of the hot path on one GB300 (or N, one process per GPU).
+
+Workload (default): 2-D periodic image 256x256, db4 (8 taps), L = 4 levels, m = 16 terms
+(4x4 bilinear hat windows), 15x15 Gaussian kernels sigma_k = 0.5 + 2.5 k/15, pattern
+| |mu| - |lambda| | <= 2 with the support rule (nnz = 123,896,832).  One step is one pass
+of the whole hot path:
+  pc_assemble  (FP64 base wavelets, filtered wavelets, fused window-multiply + localized
+                transform, FP32 Theta + BF16 copy)
+  pc_apply     (y = Theta x, 16 right-hand sides, BF16 Theta, FP32 accumulation)
+  pc_backward  (dL/du, dL/dv for L = 1/2 ||Theta||^2, i.e. dL/dTheta = Theta)
+`value` = Theta entries per second of the whole step (nnz / step time, summed over ranks).
+
+--impl reference times the FP64 CPU oracle (the paper's Algorithm 2) on the machine's host
+cores, on a bounded sample of columns of the same workload, in the same unit.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Theta entries/s + HBM GB/s, batched FP32 vs plain FP64 on 1 GB300 @1e-5; bwd ms"
+UNIT = "Theta entries/s"
+WORKLOAD = ("c2: 2-D periodic 256x256, db4 J=4, m=16 (4x4 bilinear hats), 15x15 Gaussians "
+            "sigma 0.5->3, pattern |j-j'|<=2 + support distance <= kernel radius; step = "
+            "assemble (FP32 Kahan + BF16 copy) + apply (16 RHS, BF16) + backward")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}",
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_rate(op, seconds, seed=5, max_cols=4096):
+    """Algorithm 2 (FP64 oracle, OpenMP over columns) on uniformly drawn columns until about
+    `seconds` of oracle time: returns (entries/s counted on the pattern, columns, threads, wall)."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    threads = oracle.max_threads()
+    batch = max(threads, 8)
+    done = entries = 0
+    wall = 0.0
+    while wall < seconds and done < max_cols:
+        cols = rng.integers(0, op.N, size=batch)
+        t0 = time.perf_counter()
+        oracle.theta_columns(op, cols)
+        wall += time.perf_counter() - t0
+        entries += sum(int(oracle.pattern_column(op, c).sum()) for c in cols)   # untimed
+        done += batch
+    return entries / wall, done, threads, wall
+
+
+def run_reference(args, rank, world):
+    """The oracle arm: FP64 CPU Algorithm 2 on the host cores, rank 0 only."""
+    if rank != 0:
+        return
+    import oracle
+    import pc_inputs as P
+    oracle.build()
+    op = P.workload(args.workload)
+    import paper_2005_09870_gb300 as pw  # noqa: F401  (nnz from the planner for the unit only)
+    rng = np.random.default_rng(7)
+    threads = oracle.max_threads()
+    ncols = max(threads, 16)
+    for _ in range(args.warmup):
+        oracle.theta_columns(op, rng.integers(0, op.N, size=ncols))
+    times, entries = [], 0
+    for _ in range(args.steps):
+        cols = rng.integers(0, op.N, size=ncols)
+        t0 = time.perf_counter()
+        oracle.theta_columns(op, cols)
+        times.append(time.perf_counter() - t0)
+        entries += sum(int(oracle.pattern_column(op, c).sum()) for c in cols)
+    wall = sum(times)
+    rate = entries / wall
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{ncols} uniformly drawn columns per step, Algorithm 2 in FP64"},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2005_09870_gb300 as pw
+    import pc_inputs as P
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    op = P.workload(args.workload, seed_offset=rank)
+    u = torch.tensor(op.u, dtype=torch.float32, device=dev)
+    v = torch.tensor(op.v, dtype=torch.float32, device=dev)
+    g = pw.PCOperator(pw.desc_of(op, pw.PC_FP32, 1), u, v)
+    nnz = g.nnz
+    nrhs = 16
+    x = torch.tensor(P.normal(P.BASE_SEED + 99 + rank, op.N * nrhs), dtype=torch.float32,
+                     device=dev).reshape(op.N, nrhs)
+    y = torch.empty_like(x)
+    K = (2 * op.r + 1) ** op.d
+    du = torch.empty((op.m, K), dtype=torch.float32, device=dev)
+    dv = torch.empty((op.m, op.N), dtype=torch.float32, device=dev)
+    theta_vals = g.values()                # dL/dTheta = Theta for L = 1/2 ||Theta||^2
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+
+    def step(e=None):
+        if e: e[0].record(stream)
+        pw.pc_assemble_stage(g.h, 0)
+        if e: e[1].record(stream)
+        pw.pc_assemble_stage(g.h, 1)
+        if e: e[2].record(stream)
+        pw.pc_apply(g.h, x, y, nrhs)
+        if e: e[3].record(stream)
+        pw.pc_backward(g.h, theta_vals, du, dv)
+        if e: e[4].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    g.sync()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = pw.pc_launch_counter()
+    with Clocks(local_rank) as clk:
+        for i in range(args.steps):
+            flush.zero_()                   # L2 flush between steps (not inside the timed events)
+            step(ev[i])
+        torch.cuda.synchronize()
+    launches = pw.pc_launch_counter() - launches0
+    if world > 1:
+        torch.distributed.barrier()
+    g.sync()
+    ph = np.array([[ev[i][k].elapsed_time(ev[i][k + 1]) for k in range(4)] for i in range(args.steps)])
+    step_ms = ph.sum(axis=1)
+    ms = float(step_ms.mean())
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    prep_ms, rows_ms, apply_ms, bwd_ms = (float(a) for a in ph.mean(axis=0))
+    value = world * nnz / (ms * 1e-3)
+
+    # ---------------- end to end through the C-ABI with host buffers ----------------
+    u_h = torch.tensor(op.u, dtype=torch.float32).pin_memory()
+    v_h = torch.tensor(op.v, dtype=torch.float32).pin_memory()
+    x_h = x.cpu().pin_memory()
+    y_h = torch.empty_like(x_h).pin_memory()
+    du_h = torch.empty(du.shape, dtype=torch.float32).pin_memory()
+    dv_h = torch.empty(dv.shape, dtype=torch.float32).pin_memory()
+    h2d = (u_h.numel() + v_h.numel() + x_h.numel()) * 4
+    d2h = (y_h.numel() + du_h.numel() + dv_h.numel()) * 4
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    for i in range(args.steps + args.warmup):
+        flush.zero_()
+        e = e2e_ev[i - args.warmup] if i >= args.warmup else None
+        if e: e[0].record(stream)
+        pw.pc_set_params(g.h, u_h, v_h)     # H2D from pinned host memory
+        x.copy_(x_h, non_blocking=True)
+        step()
+        y_h.copy_(y, non_blocking=True)
+        du_h.copy_(du, non_blocking=True)
+        dv_h.copy_(dv, non_blocking=True)
+        if e: e[1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = float(np.mean([a.elapsed_time(b) for a, b in e2e_ev]))
+    e2e_value = world * nnz / (e2e_ms * 1e-3)
+
+    # ---------------- plain FP64 single-operator baseline (same kernels in FP64) ----------------
+    u64 = torch.tensor(op.u, dtype=torch.float64, device=dev)
+    v64 = torch.tensor(op.v, dtype=torch.float64, device=dev)
+    g64 = pw.PCOperator(pw.desc_of(op, pw.PC_FP64, 0), u64, v64)
+    for _ in range(2):
+        g64.assemble()
+    f64_ms = []
+    for _ in range(3):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g64.assemble()
+        b.record(stream)
+        torch.cuda.synchronize()
+        f64_ms.append(a.elapsed_time(b))
+    fp32_asm_ms = prep_ms + rows_ms
+    fp64_asm_ms = float(np.mean(f64_ms))
+    # accuracy of both on seeded columns against the oracle (outside the timed region)
+    acc = {}
+    if rank == 0 and not args.no_check:
+        import oracle
+        cols = np.random.default_rng(3).integers(0, op.N, size=8)
+        T = oracle.theta_columns(op, cols)
+        mus = np.arange(op.N, dtype=np.int64)
+        v32 = g.values().double().cpu().numpy()
+        v64h = g64.values().cpu().numpy()
+        e32 = e64 = ref = 0.0
+        for c, lam in enumerate(cols):
+            pos = g.lookup(mus, np.full(op.N, lam, dtype=np.int64))
+            m = pos >= 0
+            e32 = max(e32, np.abs(v32[pos[m]] - T[c][mus[m]]).max())
+            e64 = max(e64, np.abs(v64h[pos[m]] - T[c][mus[m]]).max())
+            ref = max(ref, np.abs(T[c][mus[m]]).max())
+        acc = {"fp32_max_rel_err": e32 / ref, "fp64_max_rel_err": e64 / ref, "columns_checked": 8}
+    g64.close()
+
+    # ---------------- roofline of the dominant kernel (fused row assembly) ----------------
+    peak, peak_kind = _peaks()
+    alg_bytes = nnz * (4 + 2) + op.m * op.N * 4     # Theta FP32 + BF16 written once, windows read once
+    achieved = alg_bytes / (rows_ms * 1e-3) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "assemble_c2_traffic.json")
+    if os.path.exists(tpath):
+        try:
+            traffic = json.load(open(tpath)).get("bytes_per_launch_set")
+        except Exception:
+            traffic = None
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": "k_assemble (13 launches per step, one per row band)",
+            "peak_kind": peak_kind}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, cols, threads, wall = cpu_oracle_rate(op, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{cols} uniformly drawn columns of the workload, Algorithm 2 in FP64, {wall:.1f} s"}
+
+    clocks = clk.summary()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nnz": nnz, "nrhs": nrhs, "l2": "flushed between steps (256 MB write, untimed)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+            "phases_ms": {"prepare": prep_ms, "assemble_rows": rows_ms, "apply_16rhs": apply_ms, "backward": bwd_ms},
+            "assembly": {"entries_per_s": nnz / (fp32_asm_ms * 1e-3), "ms": fp32_asm_ms,
+                         "fp64_ms": fp64_asm_ms, "fp64_entries_per_s": nnz / (fp64_asm_ms * 1e-3),
+                         "fp32_vs_fp64_factor": fp64_asm_ms / fp32_asm_ms, **acc},
+            "bwd_ms": bwd_ms,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": e2e_ms},
+            "gpu_launches": int(launches),
+            "gpu_launches_per_step": launches / args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    g.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-check", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if world > 1 and rank != 0:
+            return
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -134,6 +134,12 @@ pc_status pc_assemble(pc_handle h, void* stream);
 pc_status pc_apply(pc_handle h, const void* x, void* y, int nrhs, int ldx, int ldy,
                    void* stream);
 
+/* The two stages of pc_assemble, for callers that time or overlap them separately:
+ * stage 0 = base wavelets, filtered wavelets and window tile masks (steps 1-2 above);
+ * stage 1 = the per-row fused window-multiply + localized transform (step 3), which needs a
+ * stage 0 for the current parameters before it.  pc_assemble(h, s) equals stage 0 then 1. */
+pc_status pc_assemble_stage(pc_handle h, int stage, void* stream);
+
 /* Gradient of a loss of Theta.  dtheta: dL/dTheta on the stored entries, same layout and
  * type as the stored values (nnz elements), device.  du: m x (2r+1)^dim and dv: m x n^dim,
  * device, overwritten with dL/du_k and dL/dv_k.  The filtered wavelets are recomputed, not
@@ -160,6 +166,10 @@ pc_status pc_theta(pc_handle h, void** values, void** values_bf16, int64_t** row
  * pattern.  Host only; no device work. */
 pc_status pc_lookup(pc_handle h, int64_t n, const int64_t* mu, const int64_t* lambda,
                     int64_t* pos);
+
+/* Number of kernel launches this library has issued in the process so far (all handles),
+ * for counting the launches inside a timed region. */
+int64_t pc_launch_counter(void);
 
 /* Waits for `stream`, then reports any device-side fault flagged since the last call
  * (PC_ERR_DEVICE) and clears it. */

@@ -53,7 +53,9 @@ _sig = {
     "pc_destroy": ([_H], None),
     "pc_assemble": ([_H, _P], ctypes.c_int),
     "pc_apply": ([_H, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P], ctypes.c_int),
+    "pc_assemble_stage": ([_H, ctypes.c_int, _P], ctypes.c_int),
     "pc_backward": ([_H, _P, _P, _P, _P], ctypes.c_int),
+    "pc_launch_counter": ([], ctypes.c_int64),
     "pc_batch_assemble": ([ctypes.POINTER(_H), ctypes.c_int, _P], ctypes.c_int),
     "pc_info": ([_H, _I64P, _I64P], ctypes.c_int),
     "pc_theta": ([_H, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P)], ctypes.c_int),
@@ -150,6 +152,14 @@ def pc_destroy(h):
 
 def pc_assemble(h, stream=None):
     _check(_lib.pc_assemble(h, _stream(stream)), h)
+
+
+def pc_assemble_stage(h, stage, stream=None):
+    _check(_lib.pc_assemble_stage(h, int(stage), _stream(stream)), h)
+
+
+def pc_launch_counter() -> int:
+    return int(_lib.pc_launch_counter())
 
 
 def pc_apply(h, x, y, nrhs=None, ldx=None, ldy=None, stream=None):

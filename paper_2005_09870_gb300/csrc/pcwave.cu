@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -20,6 +21,8 @@ using namespace pcw;
 namespace {
 
 thread_local std::string g_noh_error = "no error";
+std::atomic<long long> g_launches{0};
+inline void count_launch(long long k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 struct BandPlan {
     int b, rows, jlo, jhi, k0;
@@ -60,6 +63,7 @@ struct pc_op {
     int* err_d = nullptr;
     int64_t dev_bytes = 0;
     bool assembled = false;
+    bool prepared = false;  // stage 0 ran for the current parameters
     std::string err = "no error";
 };
 
@@ -368,16 +372,22 @@ pc_status prepare_t(pc_op* h, cudaStream_t st)
     // window tile masks
     k_tile_masks<T><<<h->tpa0 * h->tpa1, 256, 0, st>>>((const T*)h->v_d, D.dim, D.n, D.m, h->ts0, h->ts1, h->tpa1,
                                                        h->mwords, h->masks_d);
+    count_launch(6);
     PC_CUDA(h, cudaGetLastError());
     return PC_OK;
 }
 
 template <typename T>
-pc_status assemble_t(pc_op* h, cudaStream_t st)
+pc_status assemble_t(pc_op* h, cudaStream_t st, int stage_mask)
 {
     const pc_desc& D = h->desc;
-    pc_status ps = prepare_t<T>(h, st);
-    if (ps != PC_OK) return ps;
+    if (stage_mask & 1) {
+        pc_status ps = prepare_t<T>(h, st);
+        if (ps != PC_OK) return ps;
+        h->prepared = true;
+    }
+    if (!(stage_mask & 2)) return PC_OK;
+    if (!h->prepared) return fail(h, PC_ERR_INVALID_ARG, "assembly stage 1 before stage 0");
     // A5: one launch per row band
     OpDev<T> od = make_opdev<T>(h);
     for (const BandPlan& bp : h->plan) {
@@ -390,6 +400,7 @@ pc_status assemble_t(pc_op* h, cudaStream_t st)
             if (set_smem_attr<T, 2>() != PC_OK) return fail(h, PC_ERR_CUDA, "cudaFuncSetAttribute failed");
             k_assemble<T, 2><<<ctas, threads, bp.smem, st>>>(od, bp.cfg);
         }
+        count_launch();
     }
     PC_CUDA(h, cudaGetLastError());
     h->assembled = true;
@@ -415,7 +426,11 @@ pc_status apply_t(pc_op* h, const TV* vals, const TA* x, TA* y, int nrhs, int ld
     const int blocks = (int)((warps * 32 + 255) / 256);
     for (int c0 = 0; c0 < nrhs; c0 += 16) {
         const int nr = std::min(16, nrhs - c0);
-        if (transpose) k_zero_rows<TA><<<(int)((h->N * nr + 255) / 256), 256, 0, st>>>(y, h->N, ldy, c0, nr);
+        if (transpose) {
+            k_zero_rows<TA><<<(int)((h->N * nr + 255) / 256), 256, 0, st>>>(y, h->N, ldy, c0, nr);
+            count_launch();
+        }
+        count_launch();
         if (nr == 1)
             k_apply<TV, TA, 1><<<blocks, 256, 0, st>>>(od, vals, x, ldx, y, ldy, c0, nr, transpose);
         else if (nr <= 4)
@@ -464,6 +479,7 @@ pc_status backward_t(pc_op* h, const T* G, T* du, T* dv, cudaStream_t st)
             if (set_smem_attr<T, 2>() != PC_OK) return fail(h, PC_ERR_CUDA, "cudaFuncSetAttribute failed");
             k_backward<T, 2><<<ctas, threads, bp.smem, st>>>(od, bp.cfg, G, dv, (T*)h->dF_d);
         }
+        count_launch();
     }
     int maxU = 0;
     const int K0 = (D.dim == 2) ? h->K : 1;
@@ -471,6 +487,7 @@ pc_status backward_t(pc_op* h, const T* G, T* du, T* dv, cudaStream_t st)
     k_dfilt_pass2<T><<<dim3((maxU + 127) / 128, h->nb * D.m), 128, 0, st>>>(h->fd, (const T*)h->wavT_d,
                                                                            (const T*)h->dF_d, (T*)h->dG_d);
     k_dfilt_pass1<T><<<(D.m * h->Ku + 127) / 128, 128, 0, st>>>(h->fd, (const T*)h->wavT_d, (const T*)h->dG_d, du);
+    count_launch(2);
     PC_CUDA(h, cudaGetLastError());
     return PC_OK;
 }
@@ -648,6 +665,7 @@ pc_status pc_set_params(pc_handle h, const void* u, const void* v, void* stream)
     if (u) PC_CUDA(h, cudaMemcpyAsync(h->u_d, u, h->esz * D.m * h->Ku, cudaMemcpyDefault, s));
     if (v) PC_CUDA(h, cudaMemcpyAsync(h->v_d, v, h->esz * D.m * h->N, cudaMemcpyDefault, s));
     h->assembled = false;
+    h->prepared = false;
     return PC_OK;
 }
 
@@ -663,9 +681,21 @@ pc_status pc_assemble(pc_handle h, void* stream)
 {
     if (!h) return fail(nullptr, PC_ERR_INVALID_ARG, "handle is NULL");
     cudaStream_t s = (cudaStream_t)stream;
-    if (h->desc.precision == PC_FP64) return assemble_t<double>(h, s);
-    return assemble_t<float>(h, s);
+    if (h->desc.precision == PC_FP64) return assemble_t<double>(h, s, 3);
+    return assemble_t<float>(h, s, 3);
 }
+
+pc_status pc_assemble_stage(pc_handle h, int stage, void* stream)
+{
+    if (!h) return fail(nullptr, PC_ERR_INVALID_ARG, "handle is NULL");
+    if (stage != 0 && stage != 1) return fail(h, PC_ERR_INVALID_ARG, "stage must be 0 or 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int mask = stage == 0 ? 1 : 2;
+    if (h->desc.precision == PC_FP64) return assemble_t<double>(h, s, mask);
+    return assemble_t<float>(h, s, mask);
+}
+
+int64_t pc_launch_counter(void) { return (int64_t)g_launches.load(); }
 
 pc_status pc_apply(pc_handle h, const void* x, void* y, int nrhs, int ldx, int ldy, void* stream)
 {
