@@ -455,41 +455,49 @@ pc_status dev_alloc(pc_op* h, T** p, size_t bytes)
     return PC_OK;
 }
 
+// Backward kernels with caller-chosen scratch: dF (Ftotal elements, zeroed here) and dG
+// (Gtotal elements, fully overwritten).
 template <typename T>
-pc_status backward_t(pc_op* h, const T* G, T* du, T* dv, cudaStream_t st)
+pc_status backward_core(pc_op* h, const T* G, T* du, T* dv, T* dF, T* dG, cudaStream_t st)
 {
     const pc_desc& D = h->desc;
-    if (!h->dF_d) {
-        pc_status a;
-        if ((a = dev_alloc(h, &h->dF_d, h->esz * h->Ftotal)) != PC_OK) return a;
-        if ((a = dev_alloc(h, &h->dG_d, h->esz * h->Gtotal)) != PC_OK) return a;
-    }
     pc_status ps = prepare_t<T>(h, st);  // filtered wavelets recomputed from the current u
     if (ps != PC_OK) return ps;
     PC_CUDA(h, cudaMemsetAsync(dv, 0, h->esz * D.m * h->N, st));
-    PC_CUDA(h, cudaMemsetAsync(h->dF_d, 0, h->esz * h->Ftotal, st));
+    PC_CUDA(h, cudaMemsetAsync(dF, 0, h->esz * h->Ftotal, st));
     OpDev<T> od = make_opdev<T>(h);
     for (const BandPlan& bp : h->plan) {
         const int ctas = (bp.rows + bp.cfg.rpc - 1) / bp.cfg.rpc;
         const int threads = bp.cfg.gt * bp.cfg.rpc;
         if (D.dim == 1) {
             if (set_smem_attr<T, 1>() != PC_OK) return fail(h, PC_ERR_CUDA, "cudaFuncSetAttribute failed");
-            k_backward<T, 1><<<ctas, threads, bp.smem, st>>>(od, bp.cfg, G, dv, (T*)h->dF_d);
+            k_backward<T, 1><<<ctas, threads, bp.smem, st>>>(od, bp.cfg, G, dv, dF);
         } else {
             if (set_smem_attr<T, 2>() != PC_OK) return fail(h, PC_ERR_CUDA, "cudaFuncSetAttribute failed");
-            k_backward<T, 2><<<ctas, threads, bp.smem, st>>>(od, bp.cfg, G, dv, (T*)h->dF_d);
+            k_backward<T, 2><<<ctas, threads, bp.smem, st>>>(od, bp.cfg, G, dv, dF);
         }
         count_launch();
     }
     int maxU = 0;
     const int K0 = (D.dim == 2) ? h->K : 1;
     for (int b = 0; b < h->nb; ++b) maxU = std::max(maxU, K0 * h->fd.band[b].U1);
-    k_dfilt_pass2<T><<<dim3((maxU + 127) / 128, h->nb * D.m), 128, 0, st>>>(h->fd, (const T*)h->wavT_d,
-                                                                           (const T*)h->dF_d, (T*)h->dG_d);
-    k_dfilt_pass1<T><<<(D.m * h->Ku + 127) / 128, 128, 0, st>>>(h->fd, (const T*)h->wavT_d, (const T*)h->dG_d, du);
+    k_dfilt_pass2<T><<<dim3((maxU + 127) / 128, h->nb * D.m), 128, 0, st>>>(h->fd, (const T*)h->wavT_d, dF, dG);
+    k_dfilt_pass1<T><<<(D.m * h->Ku + 127) / 128, 128, 0, st>>>(h->fd, (const T*)h->wavT_d, dG, du);
     count_launch(2);
     PC_CUDA(h, cudaGetLastError());
     return PC_OK;
+}
+
+// pc_backward: scratch owned by the handle, allocated on first use.
+template <typename T>
+pc_status backward_t(pc_op* h, const T* G, T* du, T* dv, cudaStream_t st)
+{
+    if (!h->dF_d) {
+        pc_status a;
+        if ((a = dev_alloc(h, &h->dF_d, h->esz * h->Ftotal)) != PC_OK) return a;
+        if ((a = dev_alloc(h, &h->dG_d, h->esz * h->Gtotal)) != PC_OK) return a;
+    }
+    return backward_core<T>(h, G, du, dv, (T*)h->dF_d, (T*)h->dG_d, st);
 }
 
 void free_all(pc_op* h)
