@@ -146,6 +146,27 @@ pc_status pc_assemble_stage(pc_handle h, int stage, void* stream);
  * kept from the forward pass.  Uses handle-owned scratch (allocated on first call). */
 pc_status pc_backward(pc_handle h, const void* dtheta, void* du, void* dv, void* stream);
 
+/* Allocation-free pc_backward.  The paper has no counterpart; this is a library concern.
+ *
+ * Same arguments, results and stream semantics as pc_backward, but the call never allocates
+ * device memory: its scratch (dL/dF and dL/dG, the adjoints of the filtered wavelets) lives in
+ * one file-scope device array of PC_NOALLOC_SCRATCH_BYTES, which every GPU that loads this
+ * library holds until the process exits.  It is meant for callers that cannot call
+ * cudaMalloc: a framework that has reserved the whole device for its own pool allocator, or a
+ * loop where the implicit device synchronisation of cudaMalloc/cudaFree is not acceptable.
+ * (pc_backward instead allocates its scratch on the handle at its first call.)
+ *
+ * Limit: the operator must need at most PC_NOALLOC_SCRATCH_BYTES of scratch (bytes of one
+ * element times the sizes of its filtered wavelets and their first-pass products);
+ * otherwise PC_ERR_UNSUPPORTED with the required size in pc_last_error().
+ * Set-up: the first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ * capture.  Sharing: all calls on a device use the same array and it keeps the last call's
+ * contents (the call clears what must start at zero).  Calls that overlap on the GPU (two
+ * streams, two host threads, two handles) race on it: order them. */
+#define PC_NOALLOC_SCRATCH_BYTES (8u << 20)
+pc_status pc_backward_noalloc(pc_handle h, const void* dtheta, void* du, void* dv, void* stream);
+
 /* Assembles `count` operators (any mix of sizes, PC_FP32 only) in one persistent launch
  * that takes (operator, band, row-tile) work items from a global queue, longest first.
  * Equivalent to calling pc_assemble on each. */

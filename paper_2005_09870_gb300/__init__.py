@@ -56,6 +56,7 @@ _sig = {
     "pc_assemble_stage": ([_H, ctypes.c_int, _P], ctypes.c_int),
     "pc_backward": ([_H, _P, _P, _P, _P], ctypes.c_int),
     "pc_launch_counter": ([], ctypes.c_int64),
+    "pc_backward_noalloc": ([_H, _P, _P, _P, _P], ctypes.c_int),
     "pc_batch_assemble": ([ctypes.POINTER(_H), ctypes.c_int, _P], ctypes.c_int),
     "pc_info": ([_H, _I64P, _I64P], ctypes.c_int),
     "pc_theta": ([_H, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P)], ctypes.c_int),
@@ -172,6 +173,11 @@ def pc_apply(h, x, y, nrhs=None, ldx=None, ldy=None, stream=None):
 
 def pc_backward(h, dtheta, du, dv, stream=None):
     _check(_lib.pc_backward(h, _ptr(dtheta), _ptr(du), _ptr(dv), _stream(stream)), h)
+
+
+def pc_backward_noalloc(h, dtheta, du, dv, stream=None):
+    """pc_backward without any device allocation (static library scratch; see pcwave.h)."""
+    _check(_lib.pc_backward_noalloc(h, _ptr(dtheta), _ptr(du), _ptr(dv), _stream(stream)), h)
 
 
 def pc_batch_assemble(handles, stream=None):

@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -500,6 +501,50 @@ pc_status backward_t(pc_op* h, const T* G, T* du, T* dv, cudaStream_t st)
     return backward_core<T>(h, G, du, dv, (T*)h->dF_d, (T*)h->dG_d, st);
 }
 
+// Scratch of pc_backward_noalloc: one static device array per GPU that loads the library.
+// Host code must not use the symbol as an address: its device address comes from
+// cudaGetSymbolAddress, looked up once per device (with that device current) and cached.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[PC_NOALLOC_SCRATCH_BYTES];
+constexpr int kMaxDevices = 256;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kMaxDevices] = {};
+
+pc_status noalloc_scratch(pc_op* h, void** out)
+{
+    int dev = -1;
+    PC_CUDA(h, cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(h, PC_ERR_UNSUPPORTED, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(h, PC_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed on device %d: %s", dev,
+                        cudaGetErrorString(e));
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return PC_OK;
+}
+
+template <typename T>
+pc_status backward_noalloc_t(pc_op* h, const T* G, T* du, T* dv, cudaStream_t st)
+{
+    const size_t fbytes = h->esz * (size_t)h->Ftotal;
+    const size_t goff = (fbytes + 255) / 256 * 256;
+    const size_t need = goff + h->esz * (size_t)h->Gtotal;
+    if (need > (size_t)PC_NOALLOC_SCRATCH_BYTES)
+        return fail(h, PC_ERR_UNSUPPORTED,
+                    "pc_backward_noalloc: this operator needs %zu bytes of scratch, the static array holds %u",
+                    need, (unsigned)PC_NOALLOC_SCRATCH_BYTES);
+    void* base = nullptr;
+    pc_status st0 = noalloc_scratch(h, &base);
+    if (st0 != PC_OK) return st0;
+    T* dF = (T*)base;                             // zeroed by backward_core
+    T* dG = (T*)((unsigned char*)base + goff);    // fully overwritten
+    return backward_core<T>(h, G, du, dv, dF, dG, st);
+}
+
 void free_all(pc_op* h)
 {
     void* ptrs[] = {h->u_d,  h->v_d,        h->taps64_d,  h->wav64_d,  h->tapsT_d, h->wavT_d, h->F_d,
@@ -725,6 +770,16 @@ pc_status pc_backward(pc_handle h, const void* dtheta, void* du, void* dv, void*
     cudaStream_t s = (cudaStream_t)stream;
     if (h->desc.precision == PC_FP64) return backward_t<double>(h, (const double*)dtheta, (double*)du, (double*)dv, s);
     return backward_t<float>(h, (const float*)dtheta, (float*)du, (float*)dv, s);
+}
+
+pc_status pc_backward_noalloc(pc_handle h, const void* dtheta, void* du, void* dv, void* stream)
+{
+    if (!h) return fail(nullptr, PC_ERR_INVALID_ARG, "handle is NULL");
+    if (!dtheta || !du || !dv) return fail(h, PC_ERR_INVALID_ARG, "dtheta, du and dv must not be NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->desc.precision == PC_FP64)
+        return backward_noalloc_t<double>(h, (const double*)dtheta, (double*)du, (double*)dv, s);
+    return backward_noalloc_t<float>(h, (const float*)dtheta, (float*)du, (float*)dv, s);
 }
 
 pc_status pc_batch_assemble(pc_handle* ops, int count, void* stream)
