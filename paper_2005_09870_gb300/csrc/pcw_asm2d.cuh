@@ -1,0 +1,432 @@
+// 2-D row assembly (A5) and its adjoint (A7), register-blocked.
+//
+// One stored row per thread group (gt threads; several groups per CTA).  Per row:
+//   s(q) = sum_{k active} v_k(g + q) F_{k,b}(q)            compensated over k (FP32)
+//   level 1 (or LL of level k0 by the scaling filter phi_{k0} at stride 2^k0 for rows whose
+//   finest kept level is k0 + 1), then the cascade on LL up to the coarsest kept level; the
+//   coefficients inside the row's stencil windows are written to its storage segment.
+// The low/high-pass passes hold a sliding window of 2*CH + 2*LF - 4 inputs in registers and
+// produce CH low-pass and CH high-pass outputs per work item (taps unrolled, LF = filter
+// length as a template parameter; shorter filters run zero-padded).
+#pragma once
+#include "pcw_kernels.cuh"
+
+namespace pcw {
+
+constexpr int META_INTS = 112;  // per group: block offsets [MAXB+1], active terms [64], count
+constexpr int ACT_OFF = MAXB + 1;
+constexpr int NACT_OFF = ACT_OFF + 64;
+static_assert(NACT_OFF < META_INTS, "meta layout");
+
+template <typename T>
+__device__ __forceinline__ void kahan_add(T& s, T& c, T x)
+{
+    s += x;
+}
+template <>
+__device__ __forceinline__ void kahan_add<float>(float& s, float& c, float x)
+{
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}
+
+// s over pixel rows [q0b, q0b + nrows) of the region into X (row pitch px)
+template <typename T, int P>
+__device__ __forceinline__ void s_stage(const OpDev<T>& op, const T* __restrict__ Fb, int RR, int R1, int q0b,
+                                        int nrows, int g0, int g1, const int* act, int nact, T* X, int px, int tid,
+                                        int gt)
+{
+    const int tot = nrows * R1;
+    const int n = op.n;
+    const int64_t N = op.N;
+    for (int e0 = tid; e0 < tot; e0 += gt * P) {
+        int pix[P], q[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const int e = e0 + p * gt;
+            const int ee = e < tot ? e : 0;
+            const int bq = ee / R1, q1 = ee - bq * R1;
+            int gy = g0 + q0b + bq;
+            if (gy >= n) gy -= n;
+            int gx = g1 + q1;
+            if (gx >= n) gx -= n;
+            pix[p] = gy * n + gx;
+            q[p] = (q0b + bq) * R1 + q1;
+        }
+        T s[P], c[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) s[p] = c[p] = T(0);
+        for (int t = 0; t < nact; ++t) {
+            const int k = act[t];
+            const T* vk = op.v + (int64_t)k * N;
+            const T* Fk = Fb + (int64_t)k * RR;
+            T vv[P], ff[P];
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                vv[p] = __ldg(vk + pix[p]);
+                ff[p] = __ldg(Fk + q[p]);
+            }
+#pragma unroll
+            for (int p = 0; p < P; ++p) kahan_add(s[p], c[p], vv[p] * ff[p]);
+        }
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const int e = e0 + p * gt;
+            if (e < tot) {
+                const int bq = e / R1;
+                X[bq * px + (e - bq * R1)] = s[p];
+            }
+        }
+    }
+}
+
+// Fills w[0..WN) with in[base + i] (zero outside the stored range; periodic when full).
+template <typename T, int WN>
+__device__ __forceinline__ void load_window(T (&w)[WN], const T* in, int stride, int base, Range ri, int n_in,
+                                            bool out_full)
+{
+    if (!out_full && base >= 0 && base + WN <= ri.cnt) {
+#pragma unroll
+        for (int i = 0; i < WN; ++i) w[i] = in[(base + i) * stride];
+    } else {
+#pragma unroll
+        for (int i = 0; i < WN; ++i) {
+            int p = base + i;
+            if (out_full) p = pmod(p, n_in);
+            w[i] = (p >= 0 && p < ri.cnt) ? in[p * stride] : T(0);
+        }
+    }
+}
+
+// Low/high-pass pass along one axis.  nlines lines; line l of the input starts at
+// in + l*lstride and its samples are `stride` apart; outputs go to outL/outH at
+// line*olstride + c*ostride.  Output c (unwrapped ro.lo + c) reads inputs
+// 2(ro.lo + c) + [2 - LF, LF - 1].
+template <typename T, int LF, int CH>
+__device__ __forceinline__ void pass_hg(const T* in, int lstride, int stride, Range ri, int n_in, T* outL, T* outH,
+                                        int olstride, int ostride, Range ro, int nlines, const T (&hr)[LF],
+                                        const T (&gr)[LF], int tid, int gt)
+{
+    constexpr int WN = 2 * CH + 2 * LF - 4;
+    const int nch = (ro.cnt + CH - 1) / CH;
+    const int items = nlines * nch;
+    for (int it = tid; it < items; it += gt) {
+        const int line = it % nlines;  // consecutive lanes walk lines: contiguous when stride > 1
+        const int c0 = (it / nlines) * CH;
+        const int base = 2 * (ro.lo + c0) + (2 - LF) - ri.lo;
+        T w[WN];
+        load_window<T, WN>(w, in + line * lstride, stride, base, ri, n_in, ro.full);
+#pragma unroll
+        for (int o = 0; o < CH; ++o) {
+            T a = T(0), d = T(0);
+#pragma unroll
+            for (int i = 0; i < LF; ++i) {
+                a = fma(hr[i], w[2 * o + LF - 2 + i], a);
+                d = fma(gr[i], w[2 * o + i], d);
+            }
+            if (c0 + o < ro.cnt) {
+                outL[line * olstride + (c0 + o) * ostride] = a;
+                outH[line * olstride + (c0 + o) * ostride] = d;
+            }
+        }
+    }
+}
+
+// Low-pass only (scaling filter f of length len at stride S, taps at offsets [0, len)).
+template <typename T>
+__device__ __forceinline__ void pass_lo(const T* in, int lstride, int stride, Range ri, int n_in, T* out,
+                                        int olstride, int ostride, Range ro, int nlines, const T* f, int len, int S,
+                                        int tid, int gt)
+{
+    const int items = nlines * ro.cnt;
+    for (int it = tid; it < items; it += gt) {
+        const int line = it % nlines, c = it / nlines;
+        const T* x = in + line * lstride;
+        const int x0 = S * (ro.lo + c) - ri.lo;
+        T acc = T(0), acc2 = T(0);
+        if (!ro.full) {
+            const int ilo = x0 < 0 ? -x0 : 0;
+            const int ihi = min(len, ri.cnt - x0);
+            int i = ilo;
+            for (; i + 1 < ihi; i += 2) {
+                acc = fma(f[i], x[(x0 + i) * stride], acc);
+                acc2 = fma(f[i + 1], x[(x0 + i + 1) * stride], acc2);
+            }
+            if (i < ihi) acc = fma(f[i], x[(x0 + i) * stride], acc);
+        } else {
+            for (int i = 0; i < len; ++i) {
+                const int p = pmod(x0 + i, n_in);
+                if (p < ri.cnt) acc = fma(f[i], x[p * stride], acc);
+            }
+        }
+        out[line * olstride + c * ostride] = acc + acc2;
+    }
+}
+
+// Copies the stencil window of one column band from its coefficient array (pitch pz) to the
+// row's storage (and the BF16 copy).
+template <typename T>
+__device__ __forceinline__ void write_win(const OpDev<T>& op, const T* Zb, int pz, Range r0, Range r1, int nj, int f0,
+                                          int W0, int f1, int W1, int64_t dst, int tid, int gt)
+{
+    const int tot = W0 * W1;
+    if (tot <= 0) return;
+    T* th = op.theta + dst;
+    __nv_bfloat16* t16 = op.theta16 ? op.theta16 + dst : nullptr;
+    if (!r0.full && !r1.full && op.gap >= 0) {
+        const int p0s = f0 - r0.lo, p1s = f1 - r1.lo;  // inside the array (checked by the planner)
+        int a = tid / W1, b = tid - (tid / W1) * W1;
+        const int da = gt / W1, db = gt - da * W1;
+        for (int idx = tid; idx < tot; idx += gt) {
+            const T val = Zb[(p0s + a) * pz + p1s + b];
+            th[idx] = val;
+            if (t16) t16[idx] = __float2bfloat16_rn((float)val);
+            a += da;
+            b += db;
+            if (b >= W1) {
+                b -= W1;
+                ++a;
+            }
+        }
+    } else {
+        for (int idx = tid; idx < tot; idx += gt) {
+            const int a = idx / W1, b = idx - a * W1;
+            const int p0 = pmod(f0 + a - r0.lo, nj), p1 = pmod(f1 + b - r1.lo, nj);
+            const bool ok = (r0.full || p0 < r0.cnt) && (r1.full || p1 < r1.cnt);
+            const T val = ok ? Zb[p0 * pz + p1] : T(0);
+            th[idx] = val;
+            if (t16) t16[idx] = __float2bfloat16_rn((float)val);
+        }
+    }
+}
+
+// Per-row constants of a 2-D row.
+struct Row2 {
+    Band Bo;
+    int j, jlo, jhi, k0, l0, l1, g0, g1;
+    Range A0, A1;
+    int64_t srow, row_base;
+};
+
+template <typename T>
+__device__ __forceinline__ Row2 row2_setup(const OpDev<T>& op, int b, int rl)
+{
+    Row2 R;
+    const int n = op.n, L = op.L;
+    const int dense = op.gap < 0;
+    R.Bo = band_info(2, n, L, b);
+    R.j = R.Bo.j;
+    R.jlo = dense ? 1 : max(1, R.j - op.gap);
+    R.jhi = dense ? L : min(L, R.j + op.gap);
+    R.k0 = R.jlo - 1;
+    R.l0 = rl / R.Bo.nj;
+    R.l1 = rl % R.Bo.nj;
+    R.A0 = region0(R.j, R.Bo.e0, R.l0, op.r, op.Lf, n);
+    R.A1 = region0(R.j, R.Bo.e1, R.l1, op.r, op.Lf, n);
+    R.g0 = pmod(R.A0.lo, n);
+    R.g1 = pmod(R.A1.lo, n);
+    R.srow = R.Bo.off + rl;
+    R.row_base = op.row_ptr[R.srow];
+    return R;
+}
+
+// Block offsets and the active term list of a row (meta area of its group).  Ends with a
+// group barrier; returns false (uniformly) when the row length disagrees with row_ptr.
+template <typename T>
+__device__ __forceinline__ bool row2_meta(const OpDev<T>& op, const Row2& R, int b, int* meta, int tid, int gt,
+                                          int gid)
+{
+    const int n = op.n, L = op.L;
+    // OR of the tile masks over the region (every warp of the group reduces the same set)
+    unsigned long long mw[MAXW];
+#pragma unroll
+    for (int w = 0; w < MAXW; ++w) mw[w] = 0ull;
+    const int lane = threadIdx.x & 31;
+    const int ts0 = op.ts0, ts1 = op.ts1;
+    const int s0 = R.g0 / ts0, s1 = R.g1 / ts1;
+    const int nt0 = min(op.tpa0, (R.g0 % ts0 + R.A0.cnt + ts0 - 1) / ts0);
+    const int nt1 = min(op.tpa1, (R.g1 % ts1 + R.A1.cnt + ts1 - 1) / ts1);
+    for (int i = lane; i < nt0 * nt1; i += 32) {
+        const int t0 = (s0 + i / nt1) % op.tpa0, t1 = (s1 + i % nt1) % op.tpa1;
+        const unsigned long long* mp = op.masks + ((int64_t)t0 * op.tpa1 + t1) * op.mwords;
+#pragma unroll
+        for (int w = 0; w < MAXW; ++w)
+            if (w < op.mwords) mw[w] |= mp[w];
+    }
+#pragma unroll
+    for (int w = 0; w < MAXW; ++w) {
+        const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)mw[w]);
+        const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(mw[w] >> 32));
+        mw[w] = ((unsigned long long)hi << 32) | lo;
+    }
+    if (tid == 0) {
+        int acc = 0;
+        for (int b2 = 0; b2 < op.nb; ++b2) {
+            meta[b2] = acc;
+            if (block_kept(2, n, L, op.gap, b, b2))
+                acc += (int)block_count(2, n, L, op.Lf, op.r, op.gap, b, R.l0, R.l1, b2);
+        }
+        meta[op.nb] = acc;
+        if ((int64_t)acc != op.row_ptr[R.srow + 1] - R.row_base) flag_error(op.err, ERR_ROWLEN);
+        int na = 0;
+#pragma unroll
+        for (int w = 0; w < MAXW; ++w) {
+            unsigned long long bits = mw[w];
+            while (bits) {
+                const int k = w * 64 + __ffsll((long long)bits) - 1;
+                bits &= bits - 1;
+                if (na < 64) meta[ACT_OFF + na] = k;
+                ++na;
+            }
+        }
+        meta[NACT_OFF] = na;
+    }
+    group_sync(gt, gid);
+    return (int64_t)meta[op.nb] == op.row_ptr[R.srow + 1] - R.row_base;
+}
+
+// Writes the three detail bands of level jj (and the approximation band when jj == L) from
+// Z = [LL | (0,1) | (1,0) | (1,1)], each q0r.cnt x q1r.cnt.
+template <typename T>
+__device__ __forceinline__ void write_level(const OpDev<T>& op, const Row2& R, const int* meta, const T* Z, Range q0r,
+                                            Range q1r, int jj, int tid, int gt)
+{
+    const int n = op.n, L = op.L, dense = op.gap < 0;
+    const int zq = q0r.cnt * q1r.cnt, nj = n >> jj;
+    const int tmax = (jj == L) ? 4 : 3;
+    for (int t = 0; t < tmax; ++t) {
+        // t < 3: detail band t at Z + (1 + t) * zq; t == 3: approximation band at Z
+        const int e0 = (t == 3) ? 0 : (t >= 1 ? 1 : 0), e1 = (t == 3) ? 0 : (t == 1 ? 0 : 1);
+        const int b2 = (t == 3) ? 0 : band_of_level(2, L, jj, t);
+        int f0, W0, f1, W1;
+        stencil(R.j, R.Bo.e0, R.l0, jj, e0, op.r, op.Lf, n, dense, &f0, &W0);
+        stencil(R.j, R.Bo.e1, R.l1, jj, e1, op.r, op.Lf, n, dense, &f1, &W1);
+        write_win(op, Z + ((t == 3) ? 0 : (1 + t) * zq), q1r.cnt, q0r, q1r, nj, f0, W0, f1, W1,
+                  R.row_base + meta[b2], tid, gt);
+    }
+}
+
+template <typename T, int LF>
+__global__ void __launch_bounds__(256, 2) k_assemble2d(const __grid_constant__ OpDev<T> op, const AsmCfg cfg)
+{
+    constexpr int CH = 4;
+    constexpr int P = 4;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int gt = cfg.gt;
+    const int gid = threadIdx.x / gt, tid = threadIdx.x % gt;
+    const int n = op.n, L = op.L, Lf = op.Lf;
+
+    T* fS = reinterpret_cast<T*>(smem_raw);  // h padded to LF | g padded to LF | phi_k0
+    int* meta = reinterpret_cast<int*>(smem_raw + sizeof(T) * cfg.filt) + gid * META_INTS;
+    T* arena = reinterpret_cast<T*>(smem_raw + sizeof(T) * cfg.filt + sizeof(int) * cfg.rpc * META_INTS) +
+               (int64_t)gid * cfg.arena;
+    T* const arena_end = arena + cfg.arena;
+    const int A = cfg.arena;
+
+    const Band Bo = band_info(2, n, L, cfg.b);
+    const int dense = op.gap < 0;
+    const int jlo = dense ? 1 : max(1, Bo.j - op.gap);
+    const int k0 = jlo - 1;
+    const int lenk = (k0 > 0) ? wav_len(k0, Lf) : 0;
+    // zero-padded taps: h at [0, Lf) then zeros; g right-aligned so that tap i sits at 2 - LF + i
+    for (int i = threadIdx.x; i < LF; i += blockDim.x) {
+        fS[i] = (i < Lf) ? op.taps[i] : T(0);
+        fS[LF + i] = (i >= LF - Lf) ? op.taps[Lf + i - (LF - Lf)] : T(0);
+    }
+    for (int i = threadIdx.x; i < lenk; i += blockDim.x) fS[2 * LF + i] = op.wav[op.wofs[k0] + i];
+    __syncthreads();
+
+    const int rloc = blockIdx.x * cfg.rpc + gid;
+    if (rloc >= cfg.rows) return;
+    const int rl = cfg.row0 + rloc;
+    const Row2 R = row2_setup(op, cfg.b, rl);
+    if (!row2_meta(op, R, cfg.b, meta, tid, gt, gid)) return;
+
+    T hr[LF], gr[LF];
+#pragma unroll
+    for (int i = 0; i < LF; ++i) {
+        hr[i] = fS[i];
+        gr[i] = fS[LF + i];
+    }
+    const T* phiS = fS + 2 * LF;
+    const int* act = meta + ACT_OFF;
+    const int nact = min(meta[NACT_OFF], 64);
+    const T* Fb = op.F + op.Foff[cfg.b];
+    const Range A0 = R.A0, A1 = R.A1;
+    const int RR = A0.cnt * A1.cnt;
+
+    Range c0, c1;
+    int S1, n1;
+    if (k0 == 0) {
+        n1 = n >> 1;
+        S1 = 2;
+        c0 = range_cascade(A0, Lf, n1);
+        c1 = range_cascade(A1, Lf, n1);
+    } else {
+        n1 = n >> k0;
+        S1 = 1 << k0;
+        c0 = range_filter(A0, S1, 0, lenk, n1);
+        c1 = range_filter(A1, S1, 0, lenk, n1);
+    }
+    const int nY = (k0 == 0) ? 2 : 1;
+    const int Ysz = nY * A0.cnt * c1.cnt;
+    const int zb = c0.cnt * c1.cnt;
+    const int Zsz = ((k0 == 0) ? 4 : 1) * zb;
+    const int B = max(1, min(cfg.batch, A0.cnt));
+    if (B * A1.cnt + Ysz > A || Zsz + Ysz > A) {
+        flag_error(op.err, ERR_ARENA);
+        return;
+    }
+    T* X = arena;
+    T* YL = arena_end - Ysz;
+    T* YH = YL + A0.cnt * c1.cnt;
+    // stage 1a: s rows, then the axis-1 pass
+    for (int q0b = 0; q0b < A0.cnt; q0b += B) {
+        const int nbr = min(B, A0.cnt - q0b);
+        s_stage<T, P>(op, Fb, RR, A1.cnt, q0b, nbr, R.g0, R.g1, act, nact, X, A1.cnt, tid, gt);
+        group_sync(gt, gid);
+        if (k0 == 0)
+            pass_hg<T, LF, CH>(X, A1.cnt, 1, A1, n, YL + q0b * c1.cnt, YH + q0b * c1.cnt, c1.cnt, 1, c1, nbr, hr, gr,
+                               tid, gt);
+        else
+            pass_lo<T>(X, A1.cnt, 1, A1, n, YL + q0b * c1.cnt, c1.cnt, 1, c1, nbr, phiS, lenk, S1, tid, gt);
+        group_sync(gt, gid);
+    }
+    // stage 1b: axis 0 (lines = columns of Y)
+    T* Z = arena;
+    if (k0 == 0) {
+        pass_hg<T, LF, CH>(YL, 1, c1.cnt, A0, n, Z, Z + 2 * zb, 1, c1.cnt, c0, c1.cnt, hr, gr, tid, gt);
+        pass_hg<T, LF, CH>(YH, 1, c1.cnt, A0, n, Z + zb, Z + 3 * zb, 1, c1.cnt, c0, c1.cnt, hr, gr, tid, gt);
+    } else {
+        pass_lo<T>(YL, 1, c1.cnt, A0, n, Z, 1, c1.cnt, c0, c1.cnt, phiS, lenk, S1, tid, gt);
+    }
+    group_sync(gt, gid);
+    if (k0 == 0) write_level(op, R, meta, Z, c0, c1, 1, tid, gt);
+    // cascade
+    Range p0 = c0, p1 = c1;
+    int prevZ = Zsz;
+    for (int jj = (k0 == 0 ? 2 : k0 + 1); jj <= R.jhi; ++jj) {
+        const int nj = n >> jj;
+        const Range q0r = range_cascade(p0, Lf, nj), q1r = range_cascade(p1, Lf, nj);
+        const int ysz = 2 * p0.cnt * q1r.cnt, zq = q0r.cnt * q1r.cnt;
+        if (prevZ + ysz > A || 4 * zq + ysz > A) {
+            flag_error(op.err, ERR_ARENA);
+            return;
+        }
+        T* Yl = arena_end - ysz;
+        T* Yh = Yl + p0.cnt * q1r.cnt;
+        pass_hg<T, LF, CH>(Z, p1.cnt, 1, p1, 2 * nj, Yl, Yh, q1r.cnt, 1, q1r, p0.cnt, hr, gr, tid, gt);
+        group_sync(gt, gid);
+        pass_hg<T, LF, CH>(Yl, 1, q1r.cnt, p0, 2 * nj, Z, Z + 2 * zq, 1, q1r.cnt, q0r, q1r.cnt, hr, gr, tid, gt);
+        pass_hg<T, LF, CH>(Yh, 1, q1r.cnt, p0, 2 * nj, Z + zq, Z + 3 * zq, 1, q1r.cnt, q0r, q1r.cnt, hr, gr, tid, gt);
+        group_sync(gt, gid);
+        write_level(op, R, meta, Z, q0r, q1r, jj, tid, gt);
+        p0 = q0r;
+        p1 = q1r;
+        prevZ = 4 * zq;
+    }
+}
+
+}  // namespace pcw

@@ -7,6 +7,7 @@
 #include <mutex>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -15,6 +16,7 @@
 #include "../../include/pcwave.h"
 #include "pcw_geom.cuh"
 #include "pcw_kernels.cuh"
+#include "pcw_asm2d.cuh"
 #include "pcw_taps.h"
 
 using namespace pcw;
@@ -229,6 +231,45 @@ AxisMax axis_max(const Geo& g, int j, int e, int nj, int k0, int jhi)
 
 int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
+// filter-length template of the 2-D kernels (shorter filters run zero-padded)
+int lf_template(int Lf) { return Lf <= 2 ? 2 : Lf <= 4 ? 4 : Lf <= 8 ? 8 : 20; }
+
+// Checks, for every translate phase of band b, that each kept stencil window lies inside the
+// coefficient range the row's localized transform computes at that level (the kernels copy
+// windows without bounds checks when the range does not wrap).
+bool stencils_inside(const Geo& g, int b, int k0, int jhi)
+{
+    Band B = band_info(g.d, g.n, g.L, b);
+    const int lim = std::min(B.nj, 1 << std::min(12, std::max(1, jhi - B.j + 2)));
+    for (int axis = (g.d == 2 ? 0 : 1); axis < 2; ++axis) {
+        const int e = axis == 0 ? B.e0 : B.e1;
+        for (int l = 0; l < lim; ++l) {
+            Range rng[MAXL + 2];
+            Range A = region0(B.j, e, l, g.r, g.Lf, g.n);
+            int lvl0;
+            if (k0 == 0) {
+                rng[1] = range_cascade(A, g.Lf, g.n >> 1);
+                lvl0 = 1;
+            } else {
+                rng[k0] = range_filter(A, 1 << k0, 0, wav_len(k0, g.Lf), g.n >> k0);
+                lvl0 = k0;
+            }
+            for (int jj = lvl0 + 1; jj <= jhi; ++jj) rng[jj] = range_cascade(rng[jj - 1], g.Lf, g.n >> jj);
+            for (int b2 = 0; b2 < g.nb; ++b2) {
+                if (!block_kept(g.d, g.n, g.L, g.gap, b, b2)) continue;
+                Band B2 = band_info(g.d, g.n, g.L, b2);
+                if (B2.j < lvl0 || (k0 > 0 && B2.j == k0)) return false;  // level not produced
+                const int e2 = axis == 0 ? B2.e0 : B2.e1;
+                int f, W;
+                stencil(B.j, e, l, B2.j, e2, g.r, g.Lf, g.n, g.gap < 0, &f, &W);
+                const Range& R = rng[B2.j];
+                if (!R.full && g.gap >= 0 && (f < R.lo || f + W > R.lo + R.cnt)) return false;
+            }
+        }
+    }
+    return true;
+}
+
 pc_status plan_bands(pc_op* h)
 {
     const pc_desc& D = h->desc;
@@ -274,12 +315,16 @@ pc_status plan_bands(pc_op* h)
                 prevZ = zsz;
             }
         }
+        if (!stencils_inside(g, b, bp.k0, bp.jhi))
+            return fail(h, PC_ERR_UNSUPPORTED, "internal: stencil of band %d outside its transform range", b);
         need = round_up(need, (int64_t)(16 / es));
-        int filt = 2 * g.Lf + ((bp.k0 > 0) ? wav_len(bp.k0, g.Lf) : 0);
+        const int lft = (g.d == 2) ? lf_template(g.Lf) : g.Lf;
+        int filt = 2 * lft + ((bp.k0 > 0) ? wav_len(bp.k0, g.Lf) : 0);
         filt = (int)round_up(filt, (int64_t)(16 / es));
+        const int meta_ints = (g.d == 2) ? META_INTS : (MAXB + 1);
         int rpc = std::max(1, 256 / gt);
         auto smem_of = [&](int rpcv) {
-            return (size_t)filt * es + round_up((int64_t)rpcv * (MAXB + 1) * 4, 16) + (size_t)rpcv * need * es;
+            return (size_t)filt * es + round_up((int64_t)rpcv * meta_ints * 4, 16) + (size_t)rpcv * need * es;
         };
         while (rpc > 1 && smem_of(rpc) > 110 * 1024) rpc /= 2;
         if (smem_of(rpc) > 227 * 1024)
@@ -349,6 +394,31 @@ pc_status set_smem_attr()
     return PC_OK;
 }
 
+template <typename T, int LF>
+pc_status launch_asm2d_lf(pc_op* h, const OpDev<T>& od, const BandPlan& bp, int ctas, int threads, cudaStream_t st)
+{
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_assemble2d<T, LF>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
+            cudaSuccess)
+            return fail(h, PC_ERR_CUDA, "cudaFuncSetAttribute failed");
+        attr = true;
+    }
+    k_assemble2d<T, LF><<<ctas, threads, bp.smem, st>>>(od, bp.cfg);
+    return PC_OK;
+}
+
+template <typename T>
+pc_status launch_asm2d(pc_op* h, const OpDev<T>& od, const BandPlan& bp, int ctas, int threads, cudaStream_t st)
+{
+    switch (lf_template(h->Lf)) {
+        case 2: return launch_asm2d_lf<T, 2>(h, od, bp, ctas, threads, st);
+        case 4: return launch_asm2d_lf<T, 4>(h, od, bp, ctas, threads, st);
+        case 8: return launch_asm2d_lf<T, 8>(h, od, bp, ctas, threads, st);
+        default: return launch_asm2d_lf<T, 20>(h, od, bp, ctas, threads, st);
+    }
+}
+
 template <typename T>
 pc_status prepare_t(pc_op* h, cudaStream_t st)
 {
@@ -398,8 +468,8 @@ pc_status assemble_t(pc_op* h, cudaStream_t st, int stage_mask)
             if (set_smem_attr<T, 1>() != PC_OK) return fail(h, PC_ERR_CUDA, "cudaFuncSetAttribute failed");
             k_assemble<T, 1><<<ctas, threads, bp.smem, st>>>(od, bp.cfg);
         } else {
-            if (set_smem_attr<T, 2>() != PC_OK) return fail(h, PC_ERR_CUDA, "cudaFuncSetAttribute failed");
-            k_assemble<T, 2><<<ctas, threads, bp.smem, st>>>(od, bp.cfg);
+            pc_status ls = launch_asm2d<T>(h, od, bp, ctas, threads, st);
+            if (ls != PC_OK) return ls;
         }
         count_launch();
     }
@@ -636,6 +706,10 @@ pc_status pc_create(const pc_desc* desc, const void* u, const void* v, void* str
     // pattern
     plan_nnz(g, &h->row_ptr_h, &h->nnz);
     if ((st = plan_bands(h)) != PC_OK) return bail(st);
+    if (getenv("PCW_DEBUG"))
+        for (const BandPlan& bp : h->plan)
+            fprintf(stderr, "band %2d rows %7d j[%d..%d] k0 %d gt %3d rpc %2d batch %3d arena %7d smem %7zu\n", bp.b,
+                    bp.rows, bp.jlo, bp.jhi, bp.k0, bp.cfg.gt, bp.cfg.rpc, bp.cfg.batch, bp.cfg.arena, bp.smem);
     // geometry of the base wavelets and filtered wavelets
     int acc = 0;
     for (int j = 1; j <= D.levels; ++j) {
