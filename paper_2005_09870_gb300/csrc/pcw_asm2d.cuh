@@ -58,6 +58,7 @@ __device__ __forceinline__ void s_stage(const OpDev<T>& op, const T* __restrict_
         T s[P], c[P];
 #pragma unroll
         for (int p = 0; p < P; ++p) s[p] = c[p] = T(0);
+#pragma unroll 2
         for (int t = 0; t < nact; ++t) {
             const int k = act[t];
             const T* vk = op.v + (int64_t)k * N;

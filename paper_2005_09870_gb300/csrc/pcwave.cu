@@ -301,10 +301,14 @@ pc_status plan_bands(pc_op* h)
             AxisMax M0 = axis_max(g, B.j, B.e0, B.nj, bp.k0, bp.jhi);
             const int64_t area = (int64_t)M0.A * M1.A;
             gt = area <= 768 ? 32 : area <= 2048 ? 64 : area <= 6144 ? 128 : 256;
-            batch = (int)std::max<int64_t>(1, std::min<int64_t>(M0.A, (2 * gt + M1.A - 1) / M1.A));
             const int nY = (bp.k0 == 0) ? 2 : 1;
             const int64_t Y = (int64_t)nY * M0.A * M1.c;
             const int64_t Z = (int64_t)((bp.k0 == 0) ? 4 : 1) * M0.c * M1.c;
+            // s rows per stage-1 step: the whole region when it fits a ~96 KB-per-CTA budget,
+            // else as many rows as the budget allows (at least 8 pixels per thread)
+            const int64_t budget = (96 * 1024 / (int64_t)es) / std::max(1, 256 / gt);
+            const int64_t room = std::max<int64_t>(budget - Y, (int64_t)8 * gt);
+            batch = (int)std::max<int64_t>(1, std::min<int64_t>(M0.A, room / M1.A));
             need = std::max<int64_t>((int64_t)batch * M1.A + Y, Z + Y);
             int64_t prevZ = Z;
             int lvl0 = (bp.k0 == 0) ? 1 : bp.k0;
