@@ -32,79 +32,77 @@ __device__ __forceinline__ void kahan_add<float>(float& s, float& c, float x)
     s = t;
 }
 
-// s over pixel rows [q0b, q0b + nrows) of the region into X (row pitch px)
+// Steps (a, b) through a row-major count x W grid by gt per iteration (no divisions in loops).
+struct Stepper {
+    int a, b, da, db, W;
+    __device__ __forceinline__ void init(int start, int step, int w)
+    {
+        W = w;
+        a = start / w;
+        b = start - a * w;
+        da = step / w;
+        db = step - da * w;
+    }
+    __device__ __forceinline__ void next()
+    {
+        a += da;
+        b += db;
+        if (b >= W) {
+            b -= W;
+            ++a;
+        }
+    }
+};
+
+// s over pixel rows [q0b, q0b + nrows) of the region into X (row pitch R1)
 template <typename T, int P>
 __device__ __forceinline__ void s_stage(const OpDev<T>& op, const T* __restrict__ Fb, int RR, int R1, int q0b,
-                                        int nrows, int g0, int g1, const int* act, int nact, T* X, int px, int tid,
+                                        int nrows, int g0, int g1, const unsigned char* act, int nact, T* X, int tid,
                                         int gt)
 {
     const int tot = nrows * R1;
-    const int n = op.n;
+    const int n = op.n, nm = n - 1;
     const int64_t N = op.N;
+    Stepper st;
+    st.init(tid, gt, R1);
     for (int e0 = tid; e0 < tot; e0 += gt * P) {
-        int pix[P], q[P];
+        int pix[P], xo[P];
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-            const int e = e0 + p * gt;
-            const int ee = e < tot ? e : 0;
-            const int bq = ee / R1, q1 = ee - bq * R1;
-            int gy = g0 + q0b + bq;
-            if (gy >= n) gy -= n;
-            int gx = g1 + q1;
-            if (gx >= n) gx -= n;
+            const bool ok = e0 + p * gt < tot;
+            const int bq = ok ? st.a : 0, q1 = ok ? st.b : 0;
+            const int gy = (g0 + q0b + bq) & nm, gx = (g1 + q1) & nm;
             pix[p] = gy * n + gx;
-            q[p] = (q0b + bq) * R1 + q1;
+            xo[p] = bq * R1 + q1;
+            st.next();
         }
         T s[P], c[P];
 #pragma unroll
         for (int p = 0; p < P; ++p) s[p] = c[p] = T(0);
+        const T* F0 = Fb + q0b * R1;
 #pragma unroll 2
         for (int t = 0; t < nact; ++t) {
             const int k = act[t];
             const T* vk = op.v + (int64_t)k * N;
-            const T* Fk = Fb + (int64_t)k * RR;
+            const T* Fk = F0 + (int64_t)k * RR;
             T vv[P], ff[P];
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 vv[p] = __ldg(vk + pix[p]);
-                ff[p] = __ldg(Fk + q[p]);
+                ff[p] = __ldg(Fk + xo[p]);
             }
 #pragma unroll
             for (int p = 0; p < P; ++p) kahan_add(s[p], c[p], vv[p] * ff[p]);
         }
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
-            const int e = e0 + p * gt;
-            if (e < tot) {
-                const int bq = e / R1;
-                X[bq * px + (e - bq * R1)] = s[p];
-            }
-        }
-    }
-}
-
-// Fills w[0..WN) with in[base + i] (zero outside the stored range; periodic when full).
-template <typename T, int WN>
-__device__ __forceinline__ void load_window(T (&w)[WN], const T* in, int stride, int base, Range ri, int n_in,
-                                            bool out_full)
-{
-    if (!out_full && base >= 0 && base + WN <= ri.cnt) {
-#pragma unroll
-        for (int i = 0; i < WN; ++i) w[i] = in[(base + i) * stride];
-    } else {
-#pragma unroll
-        for (int i = 0; i < WN; ++i) {
-            int p = base + i;
-            if (out_full) p = pmod(p, n_in);
-            w[i] = (p >= 0 && p < ri.cnt) ? in[p * stride] : T(0);
-        }
+        for (int p = 0; p < P; ++p)
+            if (e0 + p * gt < tot) X[xo[p]] = s[p];
     }
 }
 
 // Low/high-pass pass along one axis.  nlines lines; line l of the input starts at
-// in + l*lstride and its samples are `stride` apart; outputs go to outL/outH at
-// line*olstride + c*ostride.  Output c (unwrapped ro.lo + c) reads inputs
-// 2(ro.lo + c) + [2 - LF, LF - 1].
+// in + l*lstride with samples `stride` apart; outputs at line*olstride + c*ostride.
+// Output c (unwrapped ro.lo + c) reads inputs 2(ro.lo + c) + [2 - LF, LF - 1].
 template <typename T, int LF, int CH>
 __device__ __forceinline__ void pass_hg(const T* in, int lstride, int stride, Range ri, int n_in, T* outL, T* outH,
                                         int olstride, int ostride, Range ro, int nlines, const T (&hr)[LF],
@@ -113,12 +111,32 @@ __device__ __forceinline__ void pass_hg(const T* in, int lstride, int stride, Ra
     constexpr int WN = 2 * CH + 2 * LF - 4;
     const int nch = (ro.cnt + CH - 1) / CH;
     const int items = nlines * nch;
-    for (int it = tid; it < items; it += gt) {
-        const int line = it % nlines;  // consecutive lanes walk lines: contiguous when stride > 1
-        const int c0 = (it / nlines) * CH;
+    Stepper st;  // a = chunk, b = line: consecutive lanes walk lines
+    st.init(tid, gt, nlines);
+    const int nim = n_in - 1;
+    for (int it = tid; it < items; it += gt, st.next()) {
+        const int line = st.b, c0 = st.a * CH;
         const int base = 2 * (ro.lo + c0) + (2 - LF) - ri.lo;
+        const T* src = in + line * lstride;
         T w[WN];
-        load_window<T, WN>(w, in + line * lstride, stride, base, ri, n_in, ro.full);
+        if (!ro.full) {
+            if (base >= 0 && base + WN <= ri.cnt) {
+#pragma unroll
+                for (int i = 0; i < WN; ++i) w[i] = src[(base + i) * stride];
+            } else {
+#pragma unroll
+                for (int i = 0; i < WN; ++i) {
+                    const int p = base + i;
+                    w[i] = ((unsigned)p < (unsigned)ri.cnt) ? src[p * stride] : T(0);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < WN; ++i) {
+                const int p = (base + i) & nim;
+                w[i] = (p < ri.cnt) ? src[p * stride] : T(0);
+            }
+        }
 #pragma unroll
         for (int o = 0; o < CH; ++o) {
             T a = T(0), d = T(0);
@@ -142,8 +160,11 @@ __device__ __forceinline__ void pass_lo(const T* in, int lstride, int stride, Ra
                                         int tid, int gt)
 {
     const int items = nlines * ro.cnt;
-    for (int it = tid; it < items; it += gt) {
-        const int line = it % nlines, c = it / nlines;
+    Stepper st;
+    st.init(tid, gt, nlines);
+    const int nim = n_in - 1;
+    for (int it = tid; it < items; it += gt, st.next()) {
+        const int line = st.b, c = st.a;
         const T* x = in + line * lstride;
         const int x0 = S * (ro.lo + c) - ri.lo;
         T acc = T(0), acc2 = T(0);
@@ -158,7 +179,7 @@ __device__ __forceinline__ void pass_lo(const T* in, int lstride, int stride, Ra
             if (i < ihi) acc = fma(f[i], x[(x0 + i) * stride], acc);
         } else {
             for (int i = 0; i < len; ++i) {
-                const int p = pmod(x0 + i, n_in);
+                const int p = (x0 + i) & nim;
                 if (p < ri.cnt) acc = fma(f[i], x[p * stride], acc);
             }
         }
@@ -176,25 +197,18 @@ __device__ __forceinline__ void write_win(const OpDev<T>& op, const T* Zb, int p
     if (tot <= 0) return;
     T* th = op.theta + dst;
     __nv_bfloat16* t16 = op.theta16 ? op.theta16 + dst : nullptr;
+    Stepper st;
+    st.init(tid, gt, W1);
     if (!r0.full && !r1.full && op.gap >= 0) {
-        const int p0s = f0 - r0.lo, p1s = f1 - r1.lo;  // inside the array (checked by the planner)
-        int a = tid / W1, b = tid - (tid / W1) * W1;
-        const int da = gt / W1, db = gt - da * W1;
-        for (int idx = tid; idx < tot; idx += gt) {
-            const T val = Zb[(p0s + a) * pz + p1s + b];
+        const T* z = Zb + (f0 - r0.lo) * pz + (f1 - r1.lo);  // inside the array (checked by the planner)
+        for (int idx = tid; idx < tot; idx += gt, st.next()) {
+            const T val = z[st.a * pz + st.b];
             th[idx] = val;
             if (t16) t16[idx] = __float2bfloat16_rn((float)val);
-            a += da;
-            b += db;
-            if (b >= W1) {
-                b -= W1;
-                ++a;
-            }
         }
     } else {
-        for (int idx = tid; idx < tot; idx += gt) {
-            const int a = idx / W1, b = idx - a * W1;
-            const int p0 = pmod(f0 + a - r0.lo, nj), p1 = pmod(f1 + b - r1.lo, nj);
+        for (int idx = tid; idx < tot; idx += gt, st.next()) {
+            const int p0 = pmod(f0 + st.a - r0.lo, nj), p1 = pmod(f1 + st.b - r1.lo, nj);
             const bool ok = (r0.full || p0 < r0.cnt) && (r1.full || p1 < r1.cnt);
             const T val = ok ? Zb[p0 * pz + p1] : T(0);
             th[idx] = val;
@@ -222,8 +236,9 @@ __device__ __forceinline__ Row2 row2_setup(const OpDev<T>& op, int b, int rl)
     R.jlo = dense ? 1 : max(1, R.j - op.gap);
     R.jhi = dense ? L : min(L, R.j + op.gap);
     R.k0 = R.jlo - 1;
-    R.l0 = rl / R.Bo.nj;
-    R.l1 = rl % R.Bo.nj;
+    const int lg = log2i(R.Bo.nj);
+    R.l0 = rl >> lg;
+    R.l1 = rl & (R.Bo.nj - 1);
     R.A0 = region0(R.j, R.Bo.e0, R.l0, op.r, op.Lf, n);
     R.A1 = region0(R.j, R.Bo.e1, R.l1, op.r, op.Lf, n);
     R.g0 = pmod(R.A0.lo, n);
@@ -233,56 +248,70 @@ __device__ __forceinline__ Row2 row2_setup(const OpDev<T>& op, int b, int rl)
     return R;
 }
 
-// Block offsets and the active term list of a row (meta area of its group).  Ends with a
-// group barrier; returns false (uniformly) when the row length disagrees with row_ptr.
+// Block offsets and the active term list of a row (meta area of its group), computed by the
+// group's first warp with lane-parallel counts and warp scans.  Ends with a group barrier;
+// returns false (uniformly) when the row length disagrees with row_ptr.
 template <typename T>
 __device__ __forceinline__ bool row2_meta(const OpDev<T>& op, const Row2& R, int b, int* meta, int tid, int gt,
                                           int gid)
 {
     const int n = op.n, L = op.L;
-    // OR of the tile masks over the region (every warp of the group reduces the same set)
-    unsigned long long mw[MAXW];
-#pragma unroll
-    for (int w = 0; w < MAXW; ++w) mw[w] = 0ull;
     const int lane = threadIdx.x & 31;
-    const int ts0 = op.ts0, ts1 = op.ts1;
-    const int s0 = R.g0 / ts0, s1 = R.g1 / ts1;
-    const int nt0 = min(op.tpa0, (R.g0 % ts0 + R.A0.cnt + ts0 - 1) / ts0);
-    const int nt1 = min(op.tpa1, (R.g1 % ts1 + R.A1.cnt + ts1 - 1) / ts1);
-    for (int i = lane; i < nt0 * nt1; i += 32) {
-        const int t0 = (s0 + i / nt1) % op.tpa0, t1 = (s1 + i % nt1) % op.tpa1;
-        const unsigned long long* mp = op.masks + ((int64_t)t0 * op.tpa1 + t1) * op.mwords;
+    if (tid < 32) {
+        // OR of the tile masks over the region
+        unsigned long long mw[MAXW];
 #pragma unroll
-        for (int w = 0; w < MAXW; ++w)
-            if (w < op.mwords) mw[w] |= mp[w];
-    }
+        for (int w = 0; w < MAXW; ++w) mw[w] = 0ull;
+        const int ts0 = op.ts0, ts1 = op.ts1;
+        const int s0 = R.g0 / ts0, s1 = R.g1 / ts1;
+        const int nt0 = min(op.tpa0, (R.g0 % ts0 + R.A0.cnt + ts0 - 1) / ts0);
+        const int nt1 = min(op.tpa1, (R.g1 % ts1 + R.A1.cnt + ts1 - 1) / ts1);
+        for (int i = lane; i < nt0 * nt1; i += 32) {
+            const int i0 = i / nt1;
+            const int t0 = (s0 + i0) % op.tpa0, t1 = (s1 + i - i0 * nt1) % op.tpa1;
+            const unsigned long long* mp = op.masks + ((int64_t)t0 * op.tpa1 + t1) * op.mwords;
 #pragma unroll
-    for (int w = 0; w < MAXW; ++w) {
-        const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)mw[w]);
-        const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(mw[w] >> 32));
-        mw[w] = ((unsigned long long)hi << 32) | lo;
-    }
-    if (tid == 0) {
-        int acc = 0;
-        for (int b2 = 0; b2 < op.nb; ++b2) {
-            meta[b2] = acc;
-            if (block_kept(2, n, L, op.gap, b, b2))
-                acc += (int)block_count(2, n, L, op.Lf, op.r, op.gap, b, R.l0, R.l1, b2);
+            for (int w = 0; w < MAXW; ++w)
+                if (w < op.mwords) mw[w] |= mp[w];
         }
-        meta[op.nb] = acc;
-        if ((int64_t)acc != op.row_ptr[R.srow + 1] - R.row_base) flag_error(op.err, ERR_ROWLEN);
+        // block counts: lane b2 (and b2 + 32); exclusive scan in canonical band order
+        int total = 0;
+        for (int base = 0; base < op.nb; base += 32) {
+            const int b2 = base + lane;
+            int cnt = 0;
+            if (b2 < op.nb && block_kept(2, n, L, op.gap, b, b2))
+                cnt = (int)block_count(2, n, L, op.Lf, op.r, op.gap, b, R.l0, R.l1, b2);
+            int x = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (b2 < op.nb) meta[b2] = total + x - cnt;
+            total += __shfl_sync(0xffffffffu, x, 31);
+        }
+        // active terms: ballot over the OR-reduced mask bits
+        unsigned char* act = reinterpret_cast<unsigned char*>(meta + ACT_OFF);
         int na = 0;
 #pragma unroll
         for (int w = 0; w < MAXW; ++w) {
-            unsigned long long bits = mw[w];
-            while (bits) {
-                const int k = w * 64 + __ffsll((long long)bits) - 1;
-                bits &= bits - 1;
-                if (na < 64) meta[ACT_OFF + na] = k;
-                ++na;
+            if (w >= op.mwords) break;
+            const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)mw[w]);
+            const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(mw[w] >> 32));
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const unsigned word = half ? hi : lo;
+                const bool bit = (word >> lane) & 1u;
+                const unsigned ball = __ballot_sync(0xffffffffu, bit);
+                if (bit) act[na + __popc(ball & ((1u << lane) - 1u))] = (unsigned char)(w * 64 + half * 32 + lane);
+                na += __popc(ball);
             }
         }
-        meta[NACT_OFF] = na;
+        if (lane == 0) {
+            meta[op.nb] = total;
+            meta[NACT_OFF] = na;
+            if ((int64_t)total != op.row_ptr[R.srow + 1] - R.row_base) flag_error(op.err, ERR_ROWLEN);
+        }
     }
     group_sync(gt, gid);
     return (int64_t)meta[op.nb] == op.row_ptr[R.srow + 1] - R.row_base;
@@ -316,7 +345,7 @@ __global__ void __launch_bounds__(256, 2) k_assemble2d(const __grid_constant__ O
     constexpr int P = 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int gt = cfg.gt;
-    const int gid = threadIdx.x / gt, tid = threadIdx.x % gt;
+    const int gid = threadIdx.x / gt, tid = threadIdx.x - gid * gt;
     const int n = op.n, L = op.L, Lf = op.Lf;
 
     T* fS = reinterpret_cast<T*>(smem_raw);  // h padded to LF | g padded to LF | phi_k0
@@ -341,8 +370,7 @@ __global__ void __launch_bounds__(256, 2) k_assemble2d(const __grid_constant__ O
 
     const int rloc = blockIdx.x * cfg.rpc + gid;
     if (rloc >= cfg.rows) return;
-    const int rl = cfg.row0 + rloc;
-    const Row2 R = row2_setup(op, cfg.b, rl);
+    const Row2 R = row2_setup(op, cfg.b, cfg.row0 + rloc);
     if (!row2_meta(op, R, cfg.b, meta, tid, gt, gid)) return;
 
     T hr[LF], gr[LF];
@@ -352,81 +380,67 @@ __global__ void __launch_bounds__(256, 2) k_assemble2d(const __grid_constant__ O
         gr[i] = fS[LF + i];
     }
     const T* phiS = fS + 2 * LF;
-    const int* act = meta + ACT_OFF;
-    const int nact = min(meta[NACT_OFF], 64);
+    const unsigned char* act = reinterpret_cast<const unsigned char*>(meta + ACT_OFF);
+    const int nact = meta[NACT_OFF];
     const T* Fb = op.F + op.Foff[cfg.b];
     const Range A0 = R.A0, A1 = R.A1;
     const int RR = A0.cnt * A1.cnt;
-
-    Range c0, c1;
-    int S1, n1;
-    if (k0 == 0) {
-        n1 = n >> 1;
-        S1 = 2;
-        c0 = range_cascade(A0, Lf, n1);
-        c1 = range_cascade(A1, Lf, n1);
-    } else {
-        n1 = n >> k0;
-        S1 = 1 << k0;
-        c0 = range_filter(A0, S1, 0, lenk, n1);
-        c1 = range_filter(A1, S1, 0, lenk, n1);
-    }
-    const int nY = (k0 == 0) ? 2 : 1;
-    const int Ysz = nY * A0.cnt * c1.cnt;
-    const int zb = c0.cnt * c1.cnt;
-    const int Zsz = ((k0 == 0) ? 4 : 1) * zb;
     const int B = max(1, min(cfg.batch, A0.cnt));
-    if (B * A1.cnt + Ysz > A || Zsz + Ysz > A) {
-        flag_error(op.err, ERR_ARENA);
-        return;
-    }
-    T* X = arena;
-    T* YL = arena_end - Ysz;
-    T* YH = YL + A0.cnt * c1.cnt;
-    // stage 1a: s rows, then the axis-1 pass
-    for (int q0b = 0; q0b < A0.cnt; q0b += B) {
-        const int nbr = min(B, A0.cnt - q0b);
-        s_stage<T, P>(op, Fb, RR, A1.cnt, q0b, nbr, R.g0, R.g1, act, nact, X, A1.cnt, tid, gt);
-        group_sync(gt, gid);
-        if (k0 == 0)
-            pass_hg<T, LF, CH>(X, A1.cnt, 1, A1, n, YL + q0b * c1.cnt, YH + q0b * c1.cnt, c1.cnt, 1, c1, nbr, hr, gr,
-                               tid, gt);
-        else
-            pass_lo<T>(X, A1.cnt, 1, A1, n, YL + q0b * c1.cnt, c1.cnt, 1, c1, nbr, phiS, lenk, S1, tid, gt);
-        group_sync(gt, gid);
-    }
-    // stage 1b: axis 0 (lines = columns of Y)
-    T* Z = arena;
-    if (k0 == 0) {
-        pass_hg<T, LF, CH>(YL, 1, c1.cnt, A0, n, Z, Z + 2 * zb, 1, c1.cnt, c0, c1.cnt, hr, gr, tid, gt);
-        pass_hg<T, LF, CH>(YH, 1, c1.cnt, A0, n, Z + zb, Z + 3 * zb, 1, c1.cnt, c0, c1.cnt, hr, gr, tid, gt);
-    } else {
-        pass_lo<T>(YL, 1, c1.cnt, A0, n, Z, 1, c1.cnt, c0, c1.cnt, phiS, lenk, S1, tid, gt);
-    }
-    group_sync(gt, gid);
-    if (k0 == 0) write_level(op, R, meta, Z, c0, c1, 1, tid, gt);
-    // cascade
-    Range p0 = c0, p1 = c1;
-    int prevZ = Zsz;
-    for (int jj = (k0 == 0 ? 2 : k0 + 1); jj <= R.jhi; ++jj) {
+
+    // Level loop.  The first produced level is 1 (cascade step on s), or k0 when the row's
+    // finest kept level is k0 + 1 > 1 (LL of level k0 directly by phi_k0 at stride 2^k0).
+    const int lv0 = (k0 == 0) ? 1 : k0;
+    Range p0 = A0, p1 = A1;
+    int n_in = n;
+    int prevZ = 0;
+    for (int jj = lv0; jj <= R.jhi; ++jj) {
+        const bool first = (jj == lv0);
+        const bool lo_only = first && k0 > 0;
         const int nj = n >> jj;
-        const Range q0r = range_cascade(p0, Lf, nj), q1r = range_cascade(p1, Lf, nj);
-        const int ysz = 2 * p0.cnt * q1r.cnt, zq = q0r.cnt * q1r.cnt;
-        if (prevZ + ysz > A || 4 * zq + ysz > A) {
+        const int S = lo_only ? (1 << k0) : 2;
+        const Range q0r = lo_only ? range_filter(A0, S, 0, lenk, nj) : range_cascade(p0, Lf, nj);
+        const Range q1r = lo_only ? range_filter(A1, S, 0, lenk, nj) : range_cascade(p1, Lf, nj);
+        const int ysz = (lo_only ? 1 : 2) * p0.cnt * q1r.cnt;
+        const int zq = q0r.cnt * q1r.cnt;
+        const int zsz = (lo_only ? 1 : 4) * zq;
+        const int xsz = first ? B * A1.cnt : prevZ;
+        if (xsz + ysz > A || zsz + ysz > A) {
             flag_error(op.err, ERR_ARENA);
             return;
         }
         T* Yl = arena_end - ysz;
         T* Yh = Yl + p0.cnt * q1r.cnt;
-        pass_hg<T, LF, CH>(Z, p1.cnt, 1, p1, 2 * nj, Yl, Yh, q1r.cnt, 1, q1r, p0.cnt, hr, gr, tid, gt);
+        // axis 1 (batched over pixel rows of s on the first level)
+        const int nbatch = first ? (A0.cnt + B - 1) / B : 1;
+        for (int bi = 0; bi < nbatch; ++bi) {
+            const int r0 = bi * B;
+            const int nr = first ? min(B, A0.cnt - r0) : p0.cnt;
+            if (first) {
+                s_stage<T, P>(op, Fb, RR, A1.cnt, r0, nr, R.g0, R.g1, act, nact, arena, tid, gt);
+                group_sync(gt, gid);
+            }
+            if (lo_only)
+                pass_lo<T>(arena, A1.cnt, 1, A1, n, Yl + r0 * q1r.cnt, q1r.cnt, 1, q1r, nr, phiS, lenk, S, tid, gt);
+            else
+                pass_hg<T, LF, CH>(arena, p1.cnt, 1, p1, n_in, Yl + r0 * q1r.cnt, Yh + r0 * q1r.cnt, q1r.cnt, 1, q1r,
+                                   nr, hr, gr, tid, gt);
+            group_sync(gt, gid);
+        }
+        // axis 0: lines are the columns of Y
+        if (lo_only) {
+            pass_lo<T>(Yl, 1, q1r.cnt, A0, n, arena, 1, q1r.cnt, q0r, q1r.cnt, phiS, lenk, S, tid, gt);
+        } else {
+#pragma unroll 1
+            for (int h2 = 0; h2 < 2; ++h2)
+                pass_hg<T, LF, CH>(h2 ? Yh : Yl, 1, q1r.cnt, p0, n_in, arena + (h2 ? zq : 0),
+                                   arena + (h2 ? 3 * zq : 2 * zq), 1, q1r.cnt, q0r, q1r.cnt, hr, gr, tid, gt);
+        }
         group_sync(gt, gid);
-        pass_hg<T, LF, CH>(Yl, 1, q1r.cnt, p0, 2 * nj, Z, Z + 2 * zq, 1, q1r.cnt, q0r, q1r.cnt, hr, gr, tid, gt);
-        pass_hg<T, LF, CH>(Yh, 1, q1r.cnt, p0, 2 * nj, Z + zq, Z + 3 * zq, 1, q1r.cnt, q0r, q1r.cnt, hr, gr, tid, gt);
-        group_sync(gt, gid);
-        write_level(op, R, meta, Z, q0r, q1r, jj, tid, gt);
+        if (!lo_only) write_level(op, R, meta, arena, q0r, q1r, jj, tid, gt);
         p0 = q0r;
         p1 = q1r;
-        prevZ = 4 * zq;
+        n_in = nj;
+        prevZ = zsz;
     }
 }
 

@@ -28,18 +28,19 @@
 
 namespace pcw {
 
-PCW_HD int floor_div(int a, int b)
-{  // b > 0
-    int q = a / b;
-    if ((a % b) != 0 && (a < 0)) --q;
-    return q;
-}
-PCW_HD int ceil_div(int a, int b) { return -floor_div(-a, b); }
-PCW_HD int pmod(int a, int b)
+// Every divisor in this geometry is a power of two (grid sides, level lengths, strides 2^k):
+// floor/ceil division are arithmetic shifts and the periodic residue is a mask.
+PCW_HD int log2i(int b)
 {
-    int r = a % b;
-    return r < 0 ? r + b : r;
+#ifdef __CUDA_ARCH__
+    return __ffs(b) - 1;
+#else
+    return __builtin_ctz((unsigned)b);
+#endif
 }
+PCW_HD int floor_div(int a, int b) { return a >> log2i(b); }     // b = 2^k
+PCW_HD int ceil_div(int a, int b) { return -((-a) >> log2i(b)); }
+PCW_HD int pmod(int a, int b) { return a & (b - 1); }            // b = 2^k, result in [0, b)
 
 PCW_HD int wav_len(int j, int Lf) { return ((1 << j) - 1) * (Lf - 1) + 1; }
 PCW_HD int wav_off(int j, int e, int Lf) { return e ? (1 << (j - 1)) * (2 - Lf) : 0; }
