@@ -1,0 +1,346 @@
+// 2-D backward (A7): adjoint of the row assembly, in three phases.
+//
+//   phase 1 (k_backward2d): per stored row s, dL/ds on the row's region by the transposed
+//           localized transform of the row's dL/dTheta entries, written to the scratch S
+//           (band b at Soff[b], row rl at + rl * RR_b, region row-major);
+//   phase 2 (k_bwd_dv):     dL/dv_k(x) = sum_b sum_{rows l covering x} F_{k,b}(x - t_l) S_{b,l}(x - t_l),
+//           one thread per pixel, no atomics;
+//   phase 3 (k_bwd_dF):     dL/dF_{k,b}(q) = sum_l v_k(t_l + q) S_{b,l}(q), chunks of rows per CTA,
+//           one atomic per (k, q, chunk).
+// The adjoint of F = kappa_k * rho_b (dL/dkappa_k) then runs in k_dfilt_pass2 / pass1.
+#pragma once
+#include "pcw_asm2d.cuh"
+
+namespace pcw {
+
+// Transpose of pass_hg along one axis: for every input position p (unwrapped ri.lo + p),
+//   in_bar[p] = sum_i h[i] yl_bar(C) [2C + i = X]  +  sum_i g[i] yh_bar(C) [2C + 2 - LF + i = X]
+// with C - ro.lo in [0, ro.cnt) (or modulo the output length when the output is full).
+// Work items are chunks of 2*CH inputs starting at an even unwrapped position.
+template <typename T, int LF, int CH>
+__device__ __forceinline__ void pass_hg_adj(const T* yl, const T* yh, int olstride, int ostride, Range ro, int n_out,
+                                            T* out, int lstride, int stride, Range ri, int nlines,
+                                            const T (&hr)[LF], const T (&gr)[LF], int tid, int gt)
+{
+    constexpr int WL = CH + LF / 2 - 1;
+    const int xs = ri.lo & ~1;               // first chunk start (even, unwrapped)
+    const int nch = (ri.lo + ri.cnt - xs + 2 * CH - 1) / (2 * CH);
+    const int items = nlines * nch;
+    Stepper st;
+    st.init(tid, gt, nlines);
+    const int nom = n_out - 1;
+    for (int it = tid; it < items; it += gt, st.next()) {
+        const int line = st.b;
+        const int X0 = xs + st.a * 2 * CH;
+        const int h0 = (X0 >> 1) - LF / 2 + 1 - ro.lo;  // window of yl_bar starts at C = X0/2 - LF/2 + 1
+        const int g0 = (X0 >> 1) - ro.lo;               // window of yh_bar starts at C = X0/2
+        const T* ylr = yl + line * olstride;
+        const T* yhr = yh + line * olstride;
+        T wl[WL], wh[WL];
+#pragma unroll
+        for (int t = 0; t < WL; ++t) {
+            int cl = h0 + t, ch = g0 + t;
+            if (ro.full) {
+                cl &= nom;
+                ch &= nom;
+                wl[t] = ylr[cl * ostride];
+                wh[t] = yhr[ch * ostride];
+            } else {
+                wl[t] = ((unsigned)cl < (unsigned)ro.cnt) ? ylr[cl * ostride] : T(0);
+                wh[t] = ((unsigned)ch < (unsigned)ro.cnt) ? yhr[ch * ostride] : T(0);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+#pragma unroll
+            for (int par = 0; par < 2; ++par) {
+                T acc = T(0);
+#pragma unroll
+                for (int m = 0; m < LF / 2; ++m) {
+                    acc = fma(hr[2 * m + par], wl[u - m + LF / 2 - 1], acc);
+                    acc = fma(gr[2 * m + par], wh[u + LF / 2 - 1 - m], acc);
+                }
+                const int p = X0 + 2 * u + par - ri.lo;
+                if ((unsigned)p < (unsigned)ri.cnt) out[line * lstride + p * stride] = acc;
+            }
+        }
+    }
+}
+
+// Transpose of pass_lo (scaling filter f of length len at stride S, offsets [0, len)).
+template <typename T>
+__device__ __forceinline__ void pass_lo_adj(const T* y, int olstride, int ostride, Range ro, int n_out, T* out,
+                                            int lstride, int stride, Range ri, int nlines, const T* f, int len, int S,
+                                            int tid, int gt)
+{
+    const int items = nlines * ri.cnt;
+    Stepper st;
+    st.init(tid, gt, nlines);
+    const int nom = n_out - 1;
+    for (int it = tid; it < items; it += gt, st.next()) {
+        const int line = st.b, p = st.a;
+        const int X = ri.lo + p;
+        const T* yr = y + line * olstride;
+        T acc = T(0);
+        for (int i = X & (S - 1); i < len; i += S) {
+            int c = ((X - i) >> log2i(S)) - ro.lo;
+            if (ro.full)
+                c &= nom;
+            else if ((unsigned)c >= (unsigned)ro.cnt)
+                continue;
+            acc = fma(f[i], yr[c * ostride], acc);
+        }
+        out[line * lstride + p * stride] = acc;
+    }
+}
+
+// Scatters the stencil window of one column band from the row's dL/dTheta into a zeroed
+// coefficient array (transpose of write_win).
+template <typename T>
+__device__ __forceinline__ void read_win(const OpDev<T>& op, const T* __restrict__ Gr, T* Zb, int pz, Range r0,
+                                         Range r1, int nj, int f0, int W0, int f1, int W1, int64_t src, int tid,
+                                         int gt)
+{
+    const int tot = W0 * W1;
+    if (tot <= 0) return;
+    const T* g = Gr + src;
+    Stepper st;
+    st.init(tid, gt, W1);
+    if (!r0.full && !r1.full && op.gap >= 0) {
+        T* z = Zb + (f0 - r0.lo) * pz + (f1 - r1.lo);
+        for (int idx = tid; idx < tot; idx += gt, st.next()) z[st.a * pz + st.b] = g[idx];
+    } else {
+        for (int idx = tid; idx < tot; idx += gt, st.next()) {
+            const int p0 = pmod(f0 + st.a - r0.lo, nj), p1 = pmod(f1 + st.b - r1.lo, nj);
+            if ((r0.full || p0 < r0.cnt) && (r1.full || p1 < r1.cnt)) Zb[p0 * pz + p1] = g[idx];
+        }
+    }
+}
+
+// Fills Z = [LL | (0,1) | (1,0) | (1,1)] of level jj from the row's dL/dTheta: detail bands
+// always, LL (the approximation band) when jj == L; other LL entries are left as they are.
+template <typename T>
+__device__ __forceinline__ void read_level(const OpDev<T>& op, const Row2& R, const int* meta, const T* Gth, T* Z,
+                                           Range q0r, Range q1r, int jj, int tid, int gt)
+{
+    const int n = op.n, L = op.L, dense = op.gap < 0;
+    const int zq = q0r.cnt * q1r.cnt, nj = n >> jj;
+    const int tmax = (jj == L) ? 4 : 3;
+    for (int t = 0; t < tmax; ++t) {
+        const int e0 = (t == 3) ? 0 : (t >= 1 ? 1 : 0), e1 = (t == 3) ? 0 : (t == 1 ? 0 : 1);
+        const int b2 = (t == 3) ? 0 : band_of_level(2, L, jj, t);
+        int f0, W0, f1, W1;
+        stencil(R.j, R.Bo.e0, R.l0, jj, e0, op.r, op.Lf, n, dense, &f0, &W0);
+        stencil(R.j, R.Bo.e1, R.l1, jj, e1, op.r, op.Lf, n, dense, &f1, &W1);
+        read_win(op, Gth, Z + ((t == 3) ? 0 : (1 + t) * zq), q1r.cnt, q0r, q1r, nj, f0, W0, f1, W1,
+                 R.row_base + meta[b2], tid, gt);
+    }
+}
+
+// Phase 1.  Same plan (groups, arenas) as k_assemble2d.  Sout: dL/ds of every row.
+template <typename T, int LF>
+__global__ void __launch_bounds__(256, 2) k_backward2d(const __grid_constant__ OpDev<T> op, const AsmCfg cfg,
+                                                       const T* __restrict__ Gth, T* __restrict__ Sout,
+                                                       const int64_t Sband)
+{
+    constexpr int CH = 4;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int gt = cfg.gt;
+    const int gid = threadIdx.x / gt, tid = threadIdx.x - gid * gt;
+    const int n = op.n, L = op.L, Lf = op.Lf;
+
+    T* fS = reinterpret_cast<T*>(smem_raw);
+    int* meta = reinterpret_cast<int*>(smem_raw + sizeof(T) * cfg.filt) + gid * META_INTS;
+    T* arena = reinterpret_cast<T*>(smem_raw + sizeof(T) * cfg.filt + sizeof(int) * cfg.rpc * META_INTS) +
+               (int64_t)gid * cfg.arena;
+    T* const arena_end = arena + cfg.arena;
+    const int A = cfg.arena;
+
+    const Band Bo = band_info(2, n, L, cfg.b);
+    const int dense = op.gap < 0;
+    const int jlo = dense ? 1 : max(1, Bo.j - op.gap);
+    const int k0 = jlo - 1;
+    const int lenk = (k0 > 0) ? wav_len(k0, Lf) : 0;
+    for (int i = threadIdx.x; i < LF; i += blockDim.x) {
+        fS[i] = (i < Lf) ? op.taps[i] : T(0);
+        fS[LF + i] = (i >= LF - Lf) ? op.taps[Lf + i - (LF - Lf)] : T(0);
+    }
+    for (int i = threadIdx.x; i < lenk; i += blockDim.x) fS[2 * LF + i] = op.wav[op.wofs[k0] + i];
+    __syncthreads();
+
+    const int rloc = blockIdx.x * cfg.rpc + gid;
+    if (rloc >= cfg.rows) return;
+    const int rl = cfg.row0 + rloc;
+    const Row2 R = row2_setup(op, cfg.b, rl);
+    if (!row2_meta(op, R, cfg.b, meta, tid, gt, gid)) return;
+
+    T hr[LF], gr[LF];
+#pragma unroll
+    for (int i = 0; i < LF; ++i) {
+        hr[i] = fS[i];
+        gr[i] = fS[LF + i];
+    }
+    const T* phiS = fS + 2 * LF;
+    const Range A0 = R.A0, A1 = R.A1;
+    const int RR = A0.cnt * A1.cnt;
+    const int B = max(1, min(cfg.batch, A0.cnt));
+    const int lv0 = (k0 == 0) ? 1 : k0;
+
+    // forward ranges per level (inputs p*, outputs q*): recomputed from the region
+    Range P0[MAXL + 2], P1[MAXL + 2];  // P*[jj] = output range of level jj
+    {
+        Range p0 = A0, p1 = A1;
+        for (int jj = lv0; jj <= R.jhi; ++jj) {
+            const bool lo_only = (jj == lv0) && k0 > 0;
+            const int nj = n >> jj, S = lo_only ? (1 << k0) : 2;
+            P0[jj] = lo_only ? range_filter(A0, S, 0, lenk, nj) : range_cascade(p0, Lf, nj);
+            P1[jj] = lo_only ? range_filter(A1, S, 0, lenk, nj) : range_cascade(p1, Lf, nj);
+            p0 = P0[jj];
+            p1 = P1[jj];
+        }
+    }
+    // coarse to fine: Z (level jj) -> Y -> X (LL of level jj-1, which is Z's LL next)
+    for (int jj = R.jhi; jj >= lv0; --jj) {
+        const bool first = (jj == lv0);
+        const bool lo_only = first && k0 > 0;
+        const int nj = n >> jj;
+        const int S = lo_only ? (1 << k0) : 2;
+        const Range q0r = P0[jj], q1r = P1[jj];
+        const Range p0 = first ? A0 : P0[jj - 1], p1 = first ? A1 : P1[jj - 1];
+        const int n_in = first ? n : (n >> (jj - 1));
+        const int zq = q0r.cnt * q1r.cnt;
+        const int zsz = (lo_only ? 1 : 4) * zq;
+        const int ysz = (lo_only ? 1 : 2) * p0.cnt * q1r.cnt;
+        const int xsz = first ? B * A1.cnt : p0.cnt * p1.cnt;
+        if (zsz + ysz > A || xsz + ysz > A) {
+            flag_error(op.err, ERR_ARENA);
+            return;
+        }
+        if (!lo_only) {
+            // LL: zero at the top level (it only feeds coarser levels, which are not kept)
+            const int zstart = (jj == R.jhi) ? 0 : zq;
+            for (int e = tid; e < 4 * zq - zstart; e += gt) arena[zstart + e] = T(0);
+            group_sync(gt, gid);
+            read_level(op, R, meta, Gth, arena, q0r, q1r, jj, tid, gt);
+            group_sync(gt, gid);
+        }
+        T* Yl = arena_end - ysz;
+        T* Yh = Yl + p0.cnt * q1r.cnt;
+        // transpose of axis 0 (lines: columns of Y)
+        if (lo_only)
+            pass_lo_adj<T>(arena, 1, q1r.cnt, q0r, nj, Yl, 1, q1r.cnt, A0, q1r.cnt, phiS, lenk, S, tid, gt);
+        else {
+#pragma unroll 1
+            for (int h2 = 0; h2 < 2; ++h2)
+                pass_hg_adj<T, LF, CH>(arena + (h2 ? zq : 0), arena + (h2 ? 3 * zq : 2 * zq), 1, q1r.cnt, q0r, nj,
+                                       h2 ? Yh : Yl, 1, q1r.cnt, p0, q1r.cnt, hr, gr, tid, gt);
+        }
+        group_sync(gt, gid);
+        // transpose of axis 1 (lines: rows of Y)
+        if (!first) {
+            pass_hg_adj<T, LF, CH>(Yl, Yh, q1r.cnt, 1, q1r, nj, arena, p1.cnt, 1, p1, p0.cnt, hr, gr, tid, gt);
+            group_sync(gt, gid);
+        } else {
+            // dL/ds rows in batches, then copied to the scratch
+            T* Srow = Sout + Sband + (int64_t)rl * RR;
+            for (int r0 = 0; r0 < A0.cnt; r0 += B) {
+                const int nr = min(B, A0.cnt - r0);
+                if (lo_only)
+                    pass_lo_adj<T>(Yl + r0 * q1r.cnt, q1r.cnt, 1, q1r, nj, arena, A1.cnt, 1, A1, nr, phiS, lenk, S,
+                                   tid, gt);
+                else
+                    pass_hg_adj<T, LF, CH>(Yl + r0 * q1r.cnt, Yh + r0 * q1r.cnt, q1r.cnt, 1, q1r, nj, arena, A1.cnt,
+                                           1, A1, nr, hr, gr, tid, gt);
+                group_sync(gt, gid);
+                for (int e = tid; e < nr * A1.cnt; e += gt) Srow[r0 * A1.cnt + e] = arena[e];
+                group_sync(gt, gid);
+            }
+            (void)n_in;
+        }
+    }
+}
+
+// Per-band geometry for phases 2 and 3.
+struct BwdBand {
+    int j, nj, P0, P1, R0, R1;  // region start offsets (off - r) and folded sizes
+    int64_t Soff, Foff;
+};
+struct BwdDev {
+    int n, m, nb;
+    int64_t N;
+    BwdBand band[MAXB];
+};
+
+// Phase 2.  One thread per pixel (16 x 16 tiles), KC terms per pass over the scratch.
+template <typename T, int KC>
+__global__ void __launch_bounds__(256) k_bwd_dv(const __grid_constant__ BwdDev bd, const T* __restrict__ F,
+                                                const T* __restrict__ S, T* __restrict__ dv, int kbase)
+{
+    const int n = bd.n;
+    const int x0 = blockIdx.y * 16 + threadIdx.y, x1 = blockIdx.x * 16 + threadIdx.x;
+    if (x0 >= n || x1 >= n) return;
+    T acc[KC];
+#pragma unroll
+    for (int k = 0; k < KC; ++k) acc[k] = T(0);
+    const int kn = min(KC, bd.m - kbase);
+    for (int b = 0; b < bd.nb; ++b) {
+        const BwdBand& B = bd.band[b];
+        const int lg = B.j;
+        // unwrapped translates whose region [2^j l + P, + R) contains x (mod n)
+        const int a0 = x0 - B.P0, a1 = x1 - B.P1;
+        const int l0lo = -((-(a0 - B.R0 + 1)) >> lg), l0hi = a0 >> lg;
+        const int l1lo = -((-(a1 - B.R1 + 1)) >> lg), l1hi = a1 >> lg;
+        const int RR = B.R0 * B.R1;
+        const T* Fb = F + B.Foff + (int64_t)kbase * RR;
+        for (int l0 = l0lo; l0 <= l0hi; ++l0) {
+            const int q0 = a0 - (l0 << lg);
+            const int64_t rb = (int64_t)(l0 & (B.nj - 1)) * B.nj;
+            for (int l1 = l1lo; l1 <= l1hi; ++l1) {
+                const int q1 = a1 - (l1 << lg);
+                const int q = q0 * B.R1 + q1;
+                const T s = __ldg(S + B.Soff + (rb + (l1 & (B.nj - 1))) * RR + q);
+#pragma unroll
+                for (int k = 0; k < KC; ++k)
+                    if (k < kn) acc[k] = fma(__ldg(Fb + (int64_t)k * RR + q), s, acc[k]);
+            }
+        }
+    }
+    const int64_t pix = (int64_t)x0 * n + x1;
+#pragma unroll
+    for (int k = 0; k < KC; ++k)
+        if (k < kn) dv[(int64_t)(kbase + k) * bd.N + pix] = acc[k];
+}
+
+// Phase 3.  Block (band, 128 region positions, chunk of rows); KC terms per pass.
+template <typename T, int KC>
+__global__ void __launch_bounds__(128) k_bwd_dF(const __grid_constant__ BwdDev bd, const T* __restrict__ v,
+                                                const T* __restrict__ S, T* __restrict__ dF, int b, int chunk,
+                                                int kbase)
+{
+    const BwdBand& B = bd.band[b];
+    const int RR = B.R0 * B.R1;
+    const int q = blockIdx.x * 128 + threadIdx.x;
+    if (q >= RR) return;
+    const int n = bd.n, lg = B.j;
+    const int q0 = q / B.R1, q1 = q - q0 * B.R1;
+    const int rows = B.nj * B.nj;
+    const int rbeg = blockIdx.y * chunk, rend = min(rows, rbeg + chunk);
+    const int kn = min(KC, bd.m - kbase);
+    T acc[KC];
+#pragma unroll
+    for (int k = 0; k < KC; ++k) acc[k] = T(0);
+    for (int rl = rbeg; rl < rend; ++rl) {
+        const int l0 = rl >> log2i(B.nj), l1 = rl & (B.nj - 1);
+        const int gy = ((l0 << lg) + B.P0 + q0) & (n - 1), gx = ((l1 << lg) + B.P1 + q1) & (n - 1);
+        const int64_t pix = (int64_t)gy * n + gx;
+        const T s = __ldg(S + B.Soff + (int64_t)rl * RR + q);
+#pragma unroll
+        for (int k = 0; k < KC; ++k)
+            if (k < kn) acc[k] = fma(__ldg(v + (int64_t)(kbase + k) * bd.N + pix), s, acc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < KC; ++k)
+        if (k < kn) atomicAdd(dF + B.Foff + (int64_t)(kbase + k) * RR + q, acc[k]);
+}
+
+}  // namespace pcw

@@ -1015,6 +1015,80 @@ __global__ void __launch_bounds__(256) k_apply(const __grid_constant__ OpDev<TA>
     }
 }
 
+// y = S x for row-stored S (paper order), one warp per stored row.  The warp's lanes are
+// (entry slot, group of 4 right-hand sides): LPE = NR/4 lanes read one entry's NR values of x
+// as float4s (contiguous), 32/LPE entries per step; partial sums are reduced across entry
+// slots with warp shuffles and the LPE lanes of slot 0 write y.  Requires x, y 16-byte
+// aligned with ldx, ldy multiples of 4 (else k_apply is used).
+template <typename TV, int NR>
+__global__ void __launch_bounds__(256) k_apply_vec(const __grid_constant__ OpDev<float> op, const TV* __restrict__ vals,
+                                                   const float* __restrict__ x, int ldx, float* __restrict__ y,
+                                                   int ldy, int c0)
+{
+    static_assert(NR % 4 == 0 && NR <= 32, "NR");
+    constexpr int LPE = NR / 4;        // lanes per entry
+    constexpr int EPS = 32 / LPE;      // entries per step
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int slot = lane / LPE, quad = lane - slot * LPE;
+    const int64_t s = warp;
+    if (s >= op.N) return;
+    const int d = op.d, n = op.n, L = op.L;
+    int b = 0;
+    Band Bo = band_info(d, n, L, 0);
+    for (int bb = op.nb - 1; bb >= 0; --bb) {
+        const Band t = band_info(d, n, L, bb);
+        const int64_t sz = (d == 2) ? (int64_t)t.nj * t.nj : t.nj;
+        if (s >= t.off && s < t.off + sz) {
+            b = bb;
+            Bo = t;
+            break;
+        }
+    }
+    const int rl = (int)(s - Bo.off);
+    const int lg = log2i(Bo.nj);
+    const int l0 = (d == 2) ? (rl >> lg) : 0, l1 = (d == 2) ? (rl & (Bo.nj - 1)) : rl;
+    const int dense = op.gap < 0;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    int64_t pos = op.row_ptr[s];
+    const float* xq = x + c0 + 4 * quad;
+    for (int b2 = 0; b2 < op.nb; ++b2) {
+        if (!block_kept(d, n, L, op.gap, b, b2)) continue;
+        const Band B2 = band_info(d, n, L, b2);
+        int f0 = 0, W0 = 1, f1, W1;
+        stencil(Bo.j, Bo.e1, l1, B2.j, B2.e1, op.r, op.Lf, n, dense, &f1, &W1);
+        if (d == 2) stencil(Bo.j, Bo.e0, l0, B2.j, B2.e0, op.r, op.Lf, n, dense, &f0, &W0);
+        const int nj = B2.nj, njm = nj - 1, tot = W0 * W1;
+        const int64_t rowstride = (d == 2) ? nj : 0;
+        int a = slot / W1, bb = slot - (slot / W1) * W1;
+        const int da = EPS / W1, db = EPS - da * W1;
+        for (int idx = slot; idx < tot; idx += EPS) {
+            const int64_t col = B2.off + (int64_t)((f0 + a) & njm) * rowstride + ((f1 + bb) & njm);
+            const float v = to_acc<float, TV>(vals[pos + idx]);
+            const float4 xv = *reinterpret_cast<const float4*>(xq + col * ldx);
+            acc.x = fmaf(v, xv.x, acc.x);
+            acc.y = fmaf(v, xv.y, acc.y);
+            acc.z = fmaf(v, xv.z, acc.z);
+            acc.w = fmaf(v, xv.w, acc.w);
+            a += da;
+            bb += db;
+            if (bb >= W1) {
+                bb -= W1;
+                ++a;
+            }
+        }
+        pos += tot;
+    }
+#pragma unroll
+    for (int o = LPE; o < 32; o <<= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+        acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
+        acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
+    }
+    if (slot == 0) *reinterpret_cast<float4*>(y + s * ldy + c0 + 4 * quad) = acc;
+}
+
 template <typename TA>
 __global__ void k_zero_rows(TA* y, int64_t N, int ldy, int c0, int nr)
 {

@@ -11,12 +11,14 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/pcwave.h"
 #include "pcw_geom.cuh"
 #include "pcw_kernels.cuh"
 #include "pcw_asm2d.cuh"
+#include "pcw_bwd2d.cuh"
 #include "pcw_taps.h"
 
 using namespace pcw;
@@ -59,6 +61,9 @@ struct pc_op {
     void* G_d = nullptr;
     void* dF_d = nullptr;  // backward scratch: dL/dF
     void* dG_d = nullptr;  // backward scratch: dL/dG
+    void* S_d = nullptr;   // backward scratch: dL/ds of every row (2-D)
+    int64_t Stotal = 0;
+    BwdDev bd{};
     int64_t* row_ptr_d = nullptr;
     void* theta_d = nullptr;
     __nv_bfloat16* theta16_d = nullptr;
@@ -499,6 +504,34 @@ pc_status apply_t(pc_op* h, const TV* vals, const TA* x, TA* y, int nrhs, int ld
     const int transpose = D.order == PC_ORDER_CONV_THEN_MULT;
     const int64_t warps = h->N;
     const int blocks = (int)((warps * 32 + 255) / 256);
+    // vectorised path: paper order, FP32 accumulation, 16-byte aligned x/y with ldx, ldy % 4 == 0;
+    // right-hand sides in groups of 16, 8 or 4, a remainder below 4 by the scalar kernel
+    if constexpr (std::is_same<TA, float>::value) {
+        const bool vec = !transpose && ((uintptr_t)x % 16 == 0) && ((uintptr_t)y % 16 == 0) && ldx % 4 == 0 &&
+                         ldy % 4 == 0;
+        if (vec) {
+            int c = 0;
+            while (nrhs - c >= 4) {
+                const int rem = nrhs - c;
+                if (rem >= 16) {
+                    k_apply_vec<TV, 16><<<blocks, 256, 0, st>>>(od, vals, x, ldx, y, ldy, c);
+                    c += 16;
+                } else if (rem >= 8) {
+                    k_apply_vec<TV, 8><<<blocks, 256, 0, st>>>(od, vals, x, ldx, y, ldy, c);
+                    c += 8;
+                } else {
+                    k_apply_vec<TV, 4><<<blocks, 256, 0, st>>>(od, vals, x, ldx, y, ldy, c);
+                    c += 4;
+                }
+                count_launch();
+            }
+            PC_CUDA(h, cudaGetLastError());
+            if (c == nrhs) return PC_OK;
+            x += c;
+            y += c;
+            nrhs -= c;
+        }
+    }
     for (int c0 = 0; c0 < nrhs; c0 += 16) {
         const int nr = std::min(16, nrhs - c0);
         if (transpose) {
@@ -532,26 +565,83 @@ pc_status dev_alloc(pc_op* h, T** p, size_t bytes)
 
 // Backward kernels with caller-chosen scratch: dF (Ftotal elements, zeroed here) and dG
 // (Gtotal elements, fully overwritten).
+template <typename T, int LF>
+pc_status launch_bwd2d_lf(pc_op* h, const OpDev<T>& od, const BandPlan& bp, int ctas, int threads, const T* G, T* S,
+                          int64_t Sband, cudaStream_t st)
+{
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_backward2d<T, LF>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
+            cudaSuccess)
+            return fail(h, PC_ERR_CUDA, "cudaFuncSetAttribute failed");
+        attr = true;
+    }
+    k_backward2d<T, LF><<<ctas, threads, bp.smem, st>>>(od, bp.cfg, G, S, Sband);
+    return PC_OK;
+}
+
 template <typename T>
-pc_status backward_core(pc_op* h, const T* G, T* du, T* dv, T* dF, T* dG, cudaStream_t st)
+pc_status launch_bwd2d(pc_op* h, const OpDev<T>& od, const BandPlan& bp, int ctas, int threads, const T* G, T* S,
+                       int64_t Sband, cudaStream_t st)
+{
+    switch (lf_template(h->Lf)) {
+        case 2: return launch_bwd2d_lf<T, 2>(h, od, bp, ctas, threads, G, S, Sband, st);
+        case 4: return launch_bwd2d_lf<T, 4>(h, od, bp, ctas, threads, G, S, Sband, st);
+        case 8: return launch_bwd2d_lf<T, 8>(h, od, bp, ctas, threads, G, S, Sband, st);
+        default: return launch_bwd2d_lf<T, 20>(h, od, bp, ctas, threads, G, S, Sband, st);
+    }
+}
+
+// Backward kernels with caller-chosen scratch: dF (Ftotal elements, zeroed here), dG (Gtotal
+// elements, fully overwritten) and, for 2-D operators, optionally S (Stotal elements, fully
+// overwritten).  With S: the three-phase path (dL/ds per row to S, then dv by a per-pixel
+// gather and dF by per-band reductions).  Without S: dv and dF by atomics from the rows.
+template <typename T>
+pc_status backward_core(pc_op* h, const T* G, T* du, T* dv, T* dF, T* dG, cudaStream_t st, T* S = nullptr)
 {
     const pc_desc& D = h->desc;
     pc_status ps = prepare_t<T>(h, st);  // filtered wavelets recomputed from the current u
     if (ps != PC_OK) return ps;
-    PC_CUDA(h, cudaMemsetAsync(dv, 0, h->esz * D.m * h->N, st));
     PC_CUDA(h, cudaMemsetAsync(dF, 0, h->esz * h->Ftotal, st));
     OpDev<T> od = make_opdev<T>(h);
-    for (const BandPlan& bp : h->plan) {
-        const int ctas = (bp.rows + bp.cfg.rpc - 1) / bp.cfg.rpc;
-        const int threads = bp.cfg.gt * bp.cfg.rpc;
-        if (D.dim == 1) {
-            if (set_smem_attr<T, 1>() != PC_OK) return fail(h, PC_ERR_CUDA, "cudaFuncSetAttribute failed");
-            k_backward<T, 1><<<ctas, threads, bp.smem, st>>>(od, bp.cfg, G, dv, dF);
-        } else {
-            if (set_smem_attr<T, 2>() != PC_OK) return fail(h, PC_ERR_CUDA, "cudaFuncSetAttribute failed");
-            k_backward<T, 2><<<ctas, threads, bp.smem, st>>>(od, bp.cfg, G, dv, dF);
+    if (D.dim == 2 && S) {
+        for (const BandPlan& bp : h->plan) {
+            const int ctas = (bp.rows + bp.cfg.rpc - 1) / bp.cfg.rpc;
+            const int threads = bp.cfg.gt * bp.cfg.rpc;
+            pc_status ls = launch_bwd2d<T>(h, od, bp, ctas, threads, G, S, h->bd.band[bp.b].Soff, st);
+            if (ls != PC_OK) return ls;
+            count_launch();
         }
-        count_launch();
+        constexpr int KC = 16;
+        for (int kb = 0; kb < D.m; kb += KC) {
+            k_bwd_dv<T, KC><<<dim3((D.n + 15) / 16, (D.n + 15) / 16), dim3(16, 16), 0, st>>>(h->bd, (const T*)h->F_d,
+                                                                                          S, dv, kb);
+            count_launch();
+        }
+        for (int b = 0; b < h->nb; ++b) {
+            const BwdBand& B = h->bd.band[b];
+            const int rows = B.nj * B.nj, RR = B.R0 * B.R1;
+            const int chunk = 64;
+            for (int kb = 0; kb < D.m; kb += KC) {
+                k_bwd_dF<T, KC><<<dim3((RR + 127) / 128, (rows + chunk - 1) / chunk), 128, 0, st>>>(
+                    h->bd, (const T*)h->v_d, S, dF, b, chunk, kb);
+                count_launch();
+            }
+        }
+    } else {
+        PC_CUDA(h, cudaMemsetAsync(dv, 0, h->esz * D.m * h->N, st));
+        for (const BandPlan& bp : h->plan) {
+            const int ctas = (bp.rows + bp.cfg.rpc - 1) / bp.cfg.rpc;
+            const int threads = bp.cfg.gt * bp.cfg.rpc;
+            if (D.dim == 1) {
+                if (set_smem_attr<T, 1>() != PC_OK) return fail(h, PC_ERR_CUDA, "cudaFuncSetAttribute failed");
+                k_backward<T, 1><<<ctas, threads, bp.smem, st>>>(od, bp.cfg, G, dv, dF);
+            } else {
+                if (set_smem_attr<T, 2>() != PC_OK) return fail(h, PC_ERR_CUDA, "cudaFuncSetAttribute failed");
+                k_backward<T, 2><<<ctas, threads, bp.smem, st>>>(od, bp.cfg, G, dv, dF);
+            }
+            count_launch();
+        }
     }
     int maxU = 0;
     const int K0 = (D.dim == 2) ? h->K : 1;
@@ -571,8 +661,9 @@ pc_status backward_t(pc_op* h, const T* G, T* du, T* dv, cudaStream_t st)
         pc_status a;
         if ((a = dev_alloc(h, &h->dF_d, h->esz * h->Ftotal)) != PC_OK) return a;
         if ((a = dev_alloc(h, &h->dG_d, h->esz * h->Gtotal)) != PC_OK) return a;
+        if (h->desc.dim == 2 && (a = dev_alloc(h, &h->S_d, h->esz * h->Stotal)) != PC_OK) return a;
     }
-    return backward_core<T>(h, G, du, dv, (T*)h->dF_d, (T*)h->dG_d, st);
+    return backward_core<T>(h, G, du, dv, (T*)h->dF_d, (T*)h->dG_d, st, (T*)h->S_d);
 }
 
 // Scratch of pc_backward_noalloc: one static device array per GPU that loads the library.
@@ -622,7 +713,7 @@ pc_status backward_noalloc_t(pc_op* h, const T* G, T* du, T* dv, cudaStream_t st
 void free_all(pc_op* h)
 {
     void* ptrs[] = {h->u_d,  h->v_d,        h->taps64_d,  h->wav64_d,  h->tapsT_d, h->wavT_d, h->F_d,
-                    h->G_d,  h->dF_d, h->dG_d, h->row_ptr_d,  h->theta_d,   h->theta16_d, h->masks_d, h->err_d};
+                    h->G_d,  h->dF_d, h->dG_d, h->S_d, h->row_ptr_d,  h->theta_d,   h->theta16_d, h->masks_d, h->err_d};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -750,6 +841,29 @@ pc_status pc_create(const pc_desc* desc, const void* u, const void* v, void* str
     }
     h->Ftotal = Fo;
     h->Gtotal = Go;
+    // per-band geometry of the backward phases 2 and 3
+    {
+        BwdDev& bd = h->bd;
+        bd.n = D.n;
+        bd.m = D.m;
+        bd.nb = h->nb;
+        bd.N = h->N;
+        int64_t So = 0;
+        for (int b = 0; b < h->nb; ++b) {
+            Band B = band_info(D.dim, D.n, D.levels, b);
+            BwdBand& bb = bd.band[b];
+            bb.j = B.j;
+            bb.nj = B.nj;
+            bb.P0 = wav_off(B.j, B.e0, h->Lf) - D.radius;
+            bb.P1 = wav_off(B.j, B.e1, h->Lf) - D.radius;
+            bb.R0 = fd.band[b].R0;
+            bb.R1 = fd.band[b].R1;
+            bb.Foff = fd.band[b].Foff;
+            bb.Soff = So;
+            So += band_rows(g, b) * (int64_t)bb.R0 * bb.R1;
+        }
+        h->Stotal = So;
+    }
     // window tiles
     h->mwords = (D.m + 63) / 64;
     if (D.dim == 2) {

@@ -54,3 +54,23 @@ def test_apply_strided(pw):
     got = y[:, :5].double().cpu().numpy()
     assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
     assert torch.all(y[:, 5:] == 7.0)
+
+
+@pytest.mark.parametrize("nrhs,ld", [(8, 8), (12, 12), (21, 24), (5, 8), (16, 20)])
+def test_apply_vector_groups(pw, nrhs, ld):
+    """16-byte aligned x/y with ld % 4 == 0 take the float4 path in groups of 16/8/4 columns,
+    the remainder (< 4) the scalar path; padding columns are left untouched."""
+    import torch
+    op = P.workload("small-2d", n=32, levels=3)
+    g = make_gpu_op(pw, op, bf16=1)
+    g.assemble()
+    T = dense_theta_pattern(op)
+    x = torch.randn(op.N, ld, dtype=torch.float32, device="cuda")
+    y = torch.full((op.N, ld), 3.0, dtype=torch.float32, device="cuda")
+    pw.pc_apply(g.h, x, y, nrhs=nrhs, ldx=ld, ldy=ld)
+    g.sync()
+    ref = T @ x[:, :nrhs].double().cpu().numpy()
+    got = y[:, :nrhs].double().cpu().numpy()
+    rel = np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    assert rel.max() <= 1e-2
+    assert torch.all(y[:, nrhs:] == 3.0)
