@@ -141,7 +141,7 @@ __device__ __forceinline__ void read_level(const OpDev<T>& op, const Row2& R, co
 template <typename T, int LF>
 __global__ void __launch_bounds__(256, 2) k_backward2d(const __grid_constant__ OpDev<T> op, const AsmCfg cfg,
                                                        const T* __restrict__ Gth, T* __restrict__ Sout,
-                                                       const int64_t Sband)
+                                                       const int64_t Sband, unsigned long long* __restrict__ amask_out)
 {
     constexpr int CH = 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -185,6 +185,13 @@ __global__ void __launch_bounds__(256, 2) k_backward2d(const __grid_constant__ O
     const int RR = A0.cnt * A1.cnt;
     const int B = max(1, min(cfg.batch, A0.cnt));
     const int lv0 = (k0 == 0) ? 1 : k0;
+    if (amask_out && tid < op.mwords) {  // active terms of this row as a bit mask (for phase 3)
+        const unsigned char* act = reinterpret_cast<const unsigned char*>(meta + ACT_OFF);
+        unsigned long long w = 0ull;
+        for (int t = 0; t < meta[NACT_OFF]; ++t)
+            if ((act[t] >> 6) == tid) w |= 1ull << (act[t] & 63);
+        amask_out[R.srow * op.mwords + tid] = w;
+    }
 
     // forward ranges per level (inputs p*, outputs q*): recomputed from the region
     Range P0[MAXL + 2], P1[MAXL + 2];  // P*[jj] = output range of level jj
@@ -263,7 +270,7 @@ __global__ void __launch_bounds__(256, 2) k_backward2d(const __grid_constant__ O
 // Per-band geometry for phases 2 and 3.
 struct BwdBand {
     int j, nj, P0, P1, R0, R1;  // region start offsets (off - r) and folded sizes
-    int64_t Soff, Foff;
+    int64_t Soff, Foff, rowoff;  // rowoff: canonical index of the band's first row
 };
 struct BwdDev {
     int n, m, nb;
@@ -271,12 +278,14 @@ struct BwdDev {
     BwdBand band[MAXB];
 };
 
-// Phase 2.  One thread per pixel (16 x 16 tiles), KC terms per pass over the scratch.
+// Phase 2.  One thread per pixel (16 x 16 tiles) and KC terms (blockIdx.z picks the chunk);
+// the translate loop is unrolled by 2 so that loads of consecutive translates overlap.
 template <typename T, int KC>
 __global__ void __launch_bounds__(256) k_bwd_dv(const __grid_constant__ BwdDev bd, const T* __restrict__ F,
-                                                const T* __restrict__ S, T* __restrict__ dv, int kbase)
+                                                const T* __restrict__ S, T* __restrict__ dv)
 {
     const int n = bd.n;
+    const int kbase = blockIdx.z * KC;
     const int x0 = blockIdx.y * 16 + threadIdx.y, x1 = blockIdx.x * 16 + threadIdx.x;
     if (x0 >= n || x1 >= n) return;
     T acc[KC];
@@ -285,23 +294,34 @@ __global__ void __launch_bounds__(256) k_bwd_dv(const __grid_constant__ BwdDev b
     const int kn = min(KC, bd.m - kbase);
     for (int b = 0; b < bd.nb; ++b) {
         const BwdBand& B = bd.band[b];
-        const int lg = B.j;
+        const int lg = B.j, njm = B.nj - 1;
         // unwrapped translates whose region [2^j l + P, + R) contains x (mod n)
         const int a0 = x0 - B.P0, a1 = x1 - B.P1;
         const int l0lo = -((-(a0 - B.R0 + 1)) >> lg), l0hi = a0 >> lg;
         const int l1lo = -((-(a1 - B.R1 + 1)) >> lg), l1hi = a1 >> lg;
         const int RR = B.R0 * B.R1;
         const T* Fb = F + B.Foff + (int64_t)kbase * RR;
+        const T* Sb = S + B.Soff;
         for (int l0 = l0lo; l0 <= l0hi; ++l0) {
             const int q0 = a0 - (l0 << lg);
-            const int64_t rb = (int64_t)(l0 & (B.nj - 1)) * B.nj;
-            for (int l1 = l1lo; l1 <= l1hi; ++l1) {
-                const int q1 = a1 - (l1 << lg);
-                const int q = q0 * B.R1 + q1;
-                const T s = __ldg(S + B.Soff + (rb + (l1 & (B.nj - 1))) * RR + q);
+            const int64_t rb = (int64_t)(l0 & njm) * B.nj;
+            int l1 = l1lo;
+            for (; l1 + 1 <= l1hi; l1 += 2) {
+                const int qa = q0 * B.R1 + (a1 - (l1 << lg)), qb = qa - (1 << lg);
+                const T sa = __ldg(Sb + (rb + (l1 & njm)) * RR + qa);
+                const T sb = __ldg(Sb + (rb + ((l1 + 1) & njm)) * RR + qb);
 #pragma unroll
                 for (int k = 0; k < KC; ++k)
-                    if (k < kn) acc[k] = fma(__ldg(Fb + (int64_t)k * RR + q), s, acc[k]);
+                    if (k < kn)
+                        acc[k] = fma(__ldg(Fb + (int64_t)k * RR + qb), sb,
+                                     fma(__ldg(Fb + (int64_t)k * RR + qa), sa, acc[k]));
+            }
+            if (l1 <= l1hi) {
+                const int qa = q0 * B.R1 + (a1 - (l1 << lg));
+                const T sa = __ldg(Sb + (rb + (l1 & njm)) * RR + qa);
+#pragma unroll
+                for (int k = 0; k < KC; ++k)
+                    if (k < kn) acc[k] = fma(__ldg(Fb + (int64_t)k * RR + qa), sa, acc[k]);
             }
         }
     }
@@ -311,33 +331,38 @@ __global__ void __launch_bounds__(256) k_bwd_dv(const __grid_constant__ BwdDev b
         if (k < kn) dv[(int64_t)(kbase + k) * bd.N + pix] = acc[k];
 }
 
-// Phase 3.  Block (band, 128 region positions, chunk of rows); KC terms per pass.
+// Phase 3.  Block (band, 128 region positions, chunk of rows); KC terms per block (blockIdx.z).
+// Only the terms whose window is nonzero on a row's region (the row's active mask, written by
+// phase 1) are read.
 template <typename T, int KC>
 __global__ void __launch_bounds__(128) k_bwd_dF(const __grid_constant__ BwdDev bd, const T* __restrict__ v,
-                                                const T* __restrict__ S, T* __restrict__ dF, int b, int chunk,
-                                                int kbase)
+                                                const T* __restrict__ S, const unsigned long long* __restrict__ amask,
+                                                int mwords, T* __restrict__ dF, int b, int chunk)
 {
     const BwdBand& B = bd.band[b];
     const int RR = B.R0 * B.R1;
     const int q = blockIdx.x * 128 + threadIdx.x;
     if (q >= RR) return;
+    const int kbase = blockIdx.z * KC;
     const int n = bd.n, lg = B.j;
     const int q0 = q / B.R1, q1 = q - q0 * B.R1;
     const int rows = B.nj * B.nj;
     const int rbeg = blockIdx.y * chunk, rend = min(rows, rbeg + chunk);
-    const int kn = min(KC, bd.m - kbase);
     T acc[KC];
 #pragma unroll
     for (int k = 0; k < KC; ++k) acc[k] = T(0);
+    const int lgn = log2i(B.nj);
     for (int rl = rbeg; rl < rend; ++rl) {
-        const int l0 = rl >> log2i(B.nj), l1 = rl & (B.nj - 1);
+        const int l0 = rl >> lgn, l1 = rl & (B.nj - 1);
         const int gy = ((l0 << lg) + B.P0 + q0) & (n - 1), gx = ((l1 << lg) + B.P1 + q1) & (n - 1);
         const int64_t pix = (int64_t)gy * n + gx;
         const T s = __ldg(S + B.Soff + (int64_t)rl * RR + q);
+        const unsigned long long mk = __ldg(amask + (B.rowoff + rl) * mwords + (kbase >> 6)) >> (kbase & 63);
 #pragma unroll
         for (int k = 0; k < KC; ++k)
-            if (k < kn) acc[k] = fma(__ldg(v + (int64_t)(kbase + k) * bd.N + pix), s, acc[k]);
+            if ((mk >> k) & 1ull) acc[k] = fma(__ldg(v + (int64_t)(kbase + k) * bd.N + pix), s, acc[k]);
     }
+    const int kn = min(KC, bd.m - kbase);
 #pragma unroll
     for (int k = 0; k < KC; ++k)
         if (k < kn) atomicAdd(dF + B.Foff + (int64_t)(kbase + k) * RR + q, acc[k]);

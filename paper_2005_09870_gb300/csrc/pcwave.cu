@@ -62,6 +62,7 @@ struct pc_op {
     void* dF_d = nullptr;  // backward scratch: dL/dF
     void* dG_d = nullptr;  // backward scratch: dL/dG
     void* S_d = nullptr;   // backward scratch: dL/ds of every row (2-D)
+    unsigned long long* amask_d = nullptr;  // backward scratch: active terms per row (2-D)
     int64_t Stotal = 0;
     BwdDev bd{};
     int64_t* row_ptr_d = nullptr;
@@ -567,7 +568,7 @@ pc_status dev_alloc(pc_op* h, T** p, size_t bytes)
 // (Gtotal elements, fully overwritten).
 template <typename T, int LF>
 pc_status launch_bwd2d_lf(pc_op* h, const OpDev<T>& od, const BandPlan& bp, int ctas, int threads, const T* G, T* S,
-                          int64_t Sband, cudaStream_t st)
+                          int64_t Sband, unsigned long long* amask, cudaStream_t st)
 {
     static bool attr = false;
     if (!attr) {
@@ -576,19 +577,19 @@ pc_status launch_bwd2d_lf(pc_op* h, const OpDev<T>& od, const BandPlan& bp, int 
             return fail(h, PC_ERR_CUDA, "cudaFuncSetAttribute failed");
         attr = true;
     }
-    k_backward2d<T, LF><<<ctas, threads, bp.smem, st>>>(od, bp.cfg, G, S, Sband);
+    k_backward2d<T, LF><<<ctas, threads, bp.smem, st>>>(od, bp.cfg, G, S, Sband, amask);
     return PC_OK;
 }
 
 template <typename T>
 pc_status launch_bwd2d(pc_op* h, const OpDev<T>& od, const BandPlan& bp, int ctas, int threads, const T* G, T* S,
-                       int64_t Sband, cudaStream_t st)
+                       int64_t Sband, unsigned long long* amask, cudaStream_t st)
 {
     switch (lf_template(h->Lf)) {
-        case 2: return launch_bwd2d_lf<T, 2>(h, od, bp, ctas, threads, G, S, Sband, st);
-        case 4: return launch_bwd2d_lf<T, 4>(h, od, bp, ctas, threads, G, S, Sband, st);
-        case 8: return launch_bwd2d_lf<T, 8>(h, od, bp, ctas, threads, G, S, Sband, st);
-        default: return launch_bwd2d_lf<T, 20>(h, od, bp, ctas, threads, G, S, Sband, st);
+        case 2: return launch_bwd2d_lf<T, 2>(h, od, bp, ctas, threads, G, S, Sband, amask, st);
+        case 4: return launch_bwd2d_lf<T, 4>(h, od, bp, ctas, threads, G, S, Sband, amask, st);
+        case 8: return launch_bwd2d_lf<T, 8>(h, od, bp, ctas, threads, G, S, Sband, amask, st);
+        default: return launch_bwd2d_lf<T, 20>(h, od, bp, ctas, threads, G, S, Sband, amask, st);
     }
 }
 
@@ -597,7 +598,8 @@ pc_status launch_bwd2d(pc_op* h, const OpDev<T>& od, const BandPlan& bp, int cta
 // overwritten).  With S: the three-phase path (dL/ds per row to S, then dv by a per-pixel
 // gather and dF by per-band reductions).  Without S: dv and dF by atomics from the rows.
 template <typename T>
-pc_status backward_core(pc_op* h, const T* G, T* du, T* dv, T* dF, T* dG, cudaStream_t st, T* S = nullptr)
+pc_status backward_core(pc_op* h, const T* G, T* du, T* dv, T* dF, T* dG, cudaStream_t st, T* S = nullptr,
+                        unsigned long long* amask = nullptr)
 {
     const pc_desc& D = h->desc;
     pc_status ps = prepare_t<T>(h, st);  // filtered wavelets recomputed from the current u
@@ -608,25 +610,21 @@ pc_status backward_core(pc_op* h, const T* G, T* du, T* dv, T* dF, T* dG, cudaSt
         for (const BandPlan& bp : h->plan) {
             const int ctas = (bp.rows + bp.cfg.rpc - 1) / bp.cfg.rpc;
             const int threads = bp.cfg.gt * bp.cfg.rpc;
-            pc_status ls = launch_bwd2d<T>(h, od, bp, ctas, threads, G, S, h->bd.band[bp.b].Soff, st);
+            pc_status ls = launch_bwd2d<T>(h, od, bp, ctas, threads, G, S, h->bd.band[bp.b].Soff, amask, st);
             if (ls != PC_OK) return ls;
             count_launch();
         }
-        constexpr int KC = 16;
-        for (int kb = 0; kb < D.m; kb += KC) {
-            k_bwd_dv<T, KC><<<dim3((D.n + 15) / 16, (D.n + 15) / 16), dim3(16, 16), 0, st>>>(h->bd, (const T*)h->F_d,
-                                                                                          S, dv, kb);
-            count_launch();
-        }
+        constexpr int KC = 8;
+        k_bwd_dv<T, KC><<<dim3((D.n + 15) / 16, (D.n + 15) / 16, (D.m + KC - 1) / KC), dim3(16, 16), 0, st>>>(
+            h->bd, (const T*)h->F_d, S, dv);
+        count_launch();
         for (int b = 0; b < h->nb; ++b) {
             const BwdBand& B = h->bd.band[b];
             const int rows = B.nj * B.nj, RR = B.R0 * B.R1;
-            const int chunk = 64;
-            for (int kb = 0; kb < D.m; kb += KC) {
-                k_bwd_dF<T, KC><<<dim3((RR + 127) / 128, (rows + chunk - 1) / chunk), 128, 0, st>>>(
-                    h->bd, (const T*)h->v_d, S, dF, b, chunk, kb);
-                count_launch();
-            }
+            const int chunk = 32;
+            k_bwd_dF<T, 16><<<dim3((RR + 127) / 128, (rows + chunk - 1) / chunk, (D.m + 15) / 16), 128, 0, st>>>(
+                h->bd, (const T*)h->v_d, S, amask, h->mwords, dF, b, chunk);
+            count_launch();
         }
     } else {
         PC_CUDA(h, cudaMemsetAsync(dv, 0, h->esz * D.m * h->N, st));
@@ -662,8 +660,11 @@ pc_status backward_t(pc_op* h, const T* G, T* du, T* dv, cudaStream_t st)
         if ((a = dev_alloc(h, &h->dF_d, h->esz * h->Ftotal)) != PC_OK) return a;
         if ((a = dev_alloc(h, &h->dG_d, h->esz * h->Gtotal)) != PC_OK) return a;
         if (h->desc.dim == 2 && (a = dev_alloc(h, &h->S_d, h->esz * h->Stotal)) != PC_OK) return a;
+        if (h->desc.dim == 2 &&
+            (a = dev_alloc(h, &h->amask_d, sizeof(unsigned long long) * h->N * h->mwords)) != PC_OK)
+            return a;
     }
-    return backward_core<T>(h, G, du, dv, (T*)h->dF_d, (T*)h->dG_d, st, (T*)h->S_d);
+    return backward_core<T>(h, G, du, dv, (T*)h->dF_d, (T*)h->dG_d, st, (T*)h->S_d, h->amask_d);
 }
 
 // Scratch of pc_backward_noalloc: one static device array per GPU that loads the library.
@@ -713,7 +714,7 @@ pc_status backward_noalloc_t(pc_op* h, const T* G, T* du, T* dv, cudaStream_t st
 void free_all(pc_op* h)
 {
     void* ptrs[] = {h->u_d,  h->v_d,        h->taps64_d,  h->wav64_d,  h->tapsT_d, h->wavT_d, h->F_d,
-                    h->G_d,  h->dF_d, h->dG_d, h->S_d, h->row_ptr_d,  h->theta_d,   h->theta16_d, h->masks_d, h->err_d};
+                    h->G_d,  h->dF_d, h->dG_d, h->S_d, h->amask_d, h->row_ptr_d,  h->theta_d,   h->theta16_d, h->masks_d, h->err_d};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -860,6 +861,7 @@ pc_status pc_create(const pc_desc* desc, const void* u, const void* v, void* str
             bb.R1 = fd.band[b].R1;
             bb.Foff = fd.band[b].Foff;
             bb.Soff = So;
+            bb.rowoff = B.off;
             So += band_rows(g, b) * (int64_t)bb.R0 * bb.R1;
         }
         h->Stotal = So;
