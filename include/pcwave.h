@@ -167,10 +167,39 @@ pc_status pc_backward(pc_handle h, const void* dtheta, void* du, void* dv, void*
 #define PC_NOALLOC_SCRATCH_BYTES (8u << 20)
 pc_status pc_backward_noalloc(pc_handle h, const void* dtheta, void* du, void* dv, void* stream);
 
-/* Assembles `count` operators (any mix of sizes, PC_FP32 only) in one persistent launch
- * that takes (operator, band, row-tile) work items from a global queue, longest first.
- * Equivalent to calling pc_assemble on each. */
+/* ---------------------------------------------------------------------------------------
+ * Batches: many operators (any mix of 1-D / 2-D, sizes, terms, kernel radii, db orders and
+ * levels; PC_FP32 only) assembled by one persistent launch.  The launch takes work items
+ * (operator, row band, run of rows) from a global counter, longest first, each with its own
+ * thread-group shape (the operator's plan, see pc_autotune).  The batch object captures the
+ * whole sequence (every operator's base and filtered wavelets, the queue reset and the
+ * persistent kernel) in a CUDA graph once; pc_batch_run replays it.
+ * --------------------------------------------------------------------------------------- */
+typedef struct pc_batch* pc_batch_handle;
+
+/* Plans and captures a batch over `count` handles, which must stay alive (and keep their
+ * plans) until pc_batch_destroy.  Runs the sequence once eagerly on `stream` (which also
+ * assembles every operator), then captures it on a private stream.  Synchronous. */
+pc_status pc_batch_create(pc_handle* ops, int count, void* stream, pc_batch_handle* out);
+
+/* Replays the captured graph on `stream`: re-assembles every operator of the batch from
+ * its current parameters.  Asynchronous. */
+pc_status pc_batch_run(pc_batch_handle b, void* stream);
+
+/* Work items and graph launches of one run (for counting launches). */
+pc_status pc_batch_info(pc_batch_handle b, int* items, int* kernels_per_run);
+
+void pc_batch_destroy(pc_batch_handle b);
+
+/* Convenience: pc_batch_create, one run, pc_batch_destroy (synchronous). */
 pc_status pc_batch_assemble(pc_handle* ops, int count, void* stream);
+
+/* Autotuner: for every row band of h, times the row-assembly kernel with each thread-group
+ * size (32, 64, 128, 256 threads per row, groups per CTA and s batch following) on the
+ * operator's current parameters and keeps the fastest in the handle's plan, which
+ * pc_assemble, pc_backward and batches then use.  Synchronous; overwrites Theta (which is
+ * left assembled). */
+pc_status pc_autotune(pc_handle h, void* stream);
 
 /* ---------------------------------------------------------------------------------------
  * Inspection.

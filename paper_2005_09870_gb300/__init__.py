@@ -58,6 +58,11 @@ _sig = {
     "pc_launch_counter": ([], ctypes.c_int64),
     "pc_backward_noalloc": ([_H, _P, _P, _P, _P], ctypes.c_int),
     "pc_batch_assemble": ([ctypes.POINTER(_H), ctypes.c_int, _P], ctypes.c_int),
+    "pc_batch_create": ([ctypes.POINTER(_H), ctypes.c_int, _P, ctypes.POINTER(_H)], ctypes.c_int),
+    "pc_batch_run": ([_H, _P], ctypes.c_int),
+    "pc_batch_info": ([_H, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "pc_batch_destroy": ([_H], None),
+    "pc_autotune": ([_H, _P], ctypes.c_int),
     "pc_info": ([_H, _I64P, _I64P], ctypes.c_int),
     "pc_theta": ([_H, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P)], ctypes.c_int),
     "pc_lookup": ([_H, _I64, _I64P, _I64P, _I64P], ctypes.c_int),
@@ -186,6 +191,31 @@ def pc_batch_assemble(handles, stream=None):
     _check(_lib.pc_batch_assemble(arr, len(handles), _stream(stream)), first)
 
 
+def pc_batch_create(handles, stream=None) -> int:
+    arr = (_H * len(handles))(*handles)
+    b = _H()
+    _check(_lib.pc_batch_create(arr, len(handles), _stream(stream), ctypes.byref(b)))
+    return b.value
+
+
+def pc_batch_run(b, stream=None):
+    _check(_lib.pc_batch_run(b, _stream(stream)))
+
+
+def pc_batch_info(b):
+    it, k = ctypes.c_int(), ctypes.c_int()
+    _check(_lib.pc_batch_info(b, ctypes.byref(it), ctypes.byref(k)))
+    return it.value, k.value
+
+
+def pc_batch_destroy(b):
+    _lib.pc_batch_destroy(b)
+
+
+def pc_autotune(h, stream=None):
+    _check(_lib.pc_autotune(h, _stream(stream)), h)
+
+
 def pc_info(h):
     nnz, by = ctypes.c_int64(), ctypes.c_int64()
     _check(_lib.pc_info(h, ctypes.byref(nnz), ctypes.byref(by)), h)
@@ -274,6 +304,29 @@ class PCOperator:
         if self.h:
             pc_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class PCBatch:
+    """A captured batch over PCOperator objects (kept alive by the batch)."""
+
+    def __init__(self, operators, stream=None):
+        self.operators = list(operators)
+        self.b = pc_batch_create([o.h for o in self.operators], stream)
+        self.items, self.kernels_per_run = pc_batch_info(self.b)
+
+    def run(self, stream=None):
+        pc_batch_run(self.b, stream)
+
+    def close(self):
+        if self.b:
+            pc_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:

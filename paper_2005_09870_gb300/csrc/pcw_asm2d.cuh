@@ -13,10 +13,6 @@
 
 namespace pcw {
 
-constexpr int META_INTS = 112;  // per group: block offsets [MAXB+1], active terms [64], count
-constexpr int ACT_OFF = MAXB + 1;
-constexpr int NACT_OFF = ACT_OFF + 64;
-static_assert(NACT_OFF < META_INTS, "meta layout");
 
 template <typename T>
 __device__ __forceinline__ void kahan_add(T& s, T& c, T x)
@@ -338,40 +334,38 @@ __device__ __forceinline__ void write_level(const OpDev<T>& op, const Row2& R, c
     }
 }
 
+// Filter area of a 2-D row kernel for rows of band b: h padded to LF | g right-aligned in LF
+// (tap i at position 2 - LF + i) | phi_{k0} when the band's first produced level is k0 > 0.
 template <typename T, int LF>
-__global__ void __launch_bounds__(256, 2) k_assemble2d(const __grid_constant__ OpDev<T> op, const AsmCfg cfg)
+__device__ __forceinline__ void load_filters2d(const OpDev<T>& op, int b, T* fS)
 {
-    constexpr int CH = 4;
-    constexpr int P = 4;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int gt = cfg.gt;
-    const int gid = threadIdx.x / gt, tid = threadIdx.x - gid * gt;
-    const int n = op.n, L = op.L, Lf = op.Lf;
-
-    T* fS = reinterpret_cast<T*>(smem_raw);  // h padded to LF | g padded to LF | phi_k0
-    int* meta = reinterpret_cast<int*>(smem_raw + sizeof(T) * cfg.filt) + gid * META_INTS;
-    T* arena = reinterpret_cast<T*>(smem_raw + sizeof(T) * cfg.filt + sizeof(int) * cfg.rpc * META_INTS) +
-               (int64_t)gid * cfg.arena;
-    T* const arena_end = arena + cfg.arena;
-    const int A = cfg.arena;
-
-    const Band Bo = band_info(2, n, L, cfg.b);
-    const int dense = op.gap < 0;
-    const int jlo = dense ? 1 : max(1, Bo.j - op.gap);
+    const int Lf = op.Lf;
+    const Band Bo = band_info(2, op.n, op.L, b);
+    const int jlo = (op.gap < 0) ? 1 : max(1, Bo.j - op.gap);
     const int k0 = jlo - 1;
     const int lenk = (k0 > 0) ? wav_len(k0, Lf) : 0;
-    // zero-padded taps: h at [0, Lf) then zeros; g right-aligned so that tap i sits at 2 - LF + i
     for (int i = threadIdx.x; i < LF; i += blockDim.x) {
         fS[i] = (i < Lf) ? op.taps[i] : T(0);
         fS[LF + i] = (i >= LF - Lf) ? op.taps[Lf + i - (LF - Lf)] : T(0);
     }
     for (int i = threadIdx.x; i < lenk; i += blockDim.x) fS[2 * LF + i] = op.wav[op.wofs[k0] + i];
-    __syncthreads();
+}
 
-    const int rloc = blockIdx.x * cfg.rpc + gid;
-    if (rloc >= cfg.rows) return;
-    const Row2 R = row2_setup(op, cfg.b, cfg.row0 + rloc);
+// One stored 2-D row (band cfg.b, translate index rl) by one thread group.
+template <typename T, int LF>
+__device__ __forceinline__ void asm2d_row(const OpDev<T>& op, const AsmCfg& cfg, int rl, const T* fS, int* meta,
+                                          T* arena, int gid, int tid)
+{
+    constexpr int CH = 4;
+    constexpr int P = 4;
+    const int gt = cfg.gt;
+    const int n = op.n, Lf = op.Lf;
+    T* const arena_end = arena + cfg.arena;
+    const int A = cfg.arena;
+    const Row2 R = row2_setup(op, cfg.b, rl);
     if (!row2_meta(op, R, cfg.b, meta, tid, gt, gid)) return;
+    const int k0 = R.k0;
+    const int lenk = (k0 > 0) ? wav_len(k0, Lf) : 0;
 
     T hr[LF], gr[LF];
 #pragma unroll
@@ -441,6 +435,100 @@ __global__ void __launch_bounds__(256, 2) k_assemble2d(const __grid_constant__ O
         p1 = q1r;
         n_in = nj;
         prevZ = zsz;
+    }
+}
+
+template <typename T, int LF>
+__global__ void __launch_bounds__(256, 2) k_assemble2d(const __grid_constant__ OpDev<T> op, const AsmCfg cfg)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int gt = cfg.gt;
+    const int gid = threadIdx.x / gt, tid = threadIdx.x - gid * gt;
+    T* fS = reinterpret_cast<T*>(smem_raw);
+    int* meta = reinterpret_cast<int*>(smem_raw + sizeof(T) * cfg.filt) + gid * META_INTS;
+    T* arena = reinterpret_cast<T*>(smem_raw + sizeof(T) * cfg.filt + sizeof(int) * cfg.rpc * META_INTS) +
+               (int64_t)gid * cfg.arena;
+    load_filters2d<T, LF>(op, cfg.b, fS);
+    __syncthreads();
+    const int rloc = blockIdx.x * cfg.rpc + gid;
+    if (rloc >= cfg.rows) return;
+    asm2d_row<T, LF>(op, cfg, cfg.row0 + rloc, fS, meta, arena, gid, tid);
+}
+
+// ------------------------------------------------------------------------------------------
+// A8: persistent batched assembly.  Work items (operator, row band, run of rows) are taken
+// from a global counter, longest first (the host sorts them).  Each item carries its own
+// thread-group shape; the CTA copies the operator's descriptor to shared memory.  FP32.
+// ------------------------------------------------------------------------------------------
+struct BatchItem {
+    int op;   // operator index
+    int dim;  // 1 or 2
+    int lft;  // 2-D filter template (2, 4, 8 or 20)
+    int pad;
+    AsmCfg cfg;
+};
+
+__global__ void __launch_bounds__(256, 1) k_assemble_batch(const OpDev<float>* __restrict__ ops,
+                                                           const BatchItem* __restrict__ items, int nitems,
+                                                           int* __restrict__ counter)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ OpDev<float> op_s;
+    __shared__ BatchItem it_s;
+    __shared__ int idx_s;
+    for (;;) {
+        if (threadIdx.x == 0) idx_s = atomicAdd(counter, 1);
+        __syncthreads();
+        const int idx = idx_s;
+        if (idx >= nitems) return;
+        if (threadIdx.x == 0) it_s = items[idx];
+        __syncthreads();
+        {
+            const int* src = reinterpret_cast<const int*>(ops + it_s.op);
+            int* dst = reinterpret_cast<int*>(&op_s);
+            for (int i = threadIdx.x; i < (int)(sizeof(OpDev<float>) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+        }
+        __syncthreads();
+        const AsmCfg cfg = it_s.cfg;
+        const int dim = it_s.dim, lft = it_s.lft;
+        float* fS = reinterpret_cast<float*>(smem_raw);
+        if (dim == 1) {
+            for (int i = threadIdx.x; i < 2 * op_s.Lf; i += blockDim.x) fS[i] = op_s.taps[i];
+        } else if (lft == 2) {
+            load_filters2d<float, 2>(op_s, cfg.b, fS);
+        } else if (lft == 4) {
+            load_filters2d<float, 4>(op_s, cfg.b, fS);
+        } else if (lft == 8) {
+            load_filters2d<float, 8>(op_s, cfg.b, fS);
+        } else {
+            load_filters2d<float, 20>(op_s, cfg.b, fS);
+        }
+        __syncthreads();
+        const int gt = cfg.gt;
+        const int gid = threadIdx.x / gt, tid = threadIdx.x - gid * gt;
+        if (gid < cfg.rpc) {
+            int* meta = reinterpret_cast<int*>(smem_raw + sizeof(float) * cfg.filt) + gid * META_INTS;
+            float* arena = reinterpret_cast<float*>(smem_raw + sizeof(float) * cfg.filt +
+                                                    sizeof(int) * cfg.rpc * META_INTS) +
+                           (int64_t)gid * cfg.arena;
+            for (int rb = 0; rb < cfg.rows; rb += cfg.rpc) {
+                const int rloc = rb + gid;
+                if (rloc >= cfg.rows) break;
+                const int rl = cfg.row0 + rloc;
+                if (dim == 1)
+                    asm1d_row<float>(op_s, cfg, rl, fS, fS + op_s.Lf, meta, arena, gid, tid);
+                else if (lft == 2)
+                    asm2d_row<float, 2>(op_s, cfg, rl, fS, meta, arena, gid, tid);
+                else if (lft == 4)
+                    asm2d_row<float, 4>(op_s, cfg, rl, fS, meta, arena, gid, tid);
+                else if (lft == 8)
+                    asm2d_row<float, 8>(op_s, cfg, rl, fS, meta, arena, gid, tid);
+                else
+                    asm2d_row<float, 20>(op_s, cfg, rl, fS, meta, arena, gid, tid);
+                group_sync(gt, gid);  // the group's arena and meta are reused by its next row
+            }
+        }
+        __syncthreads();
     }
 }
 

@@ -319,73 +319,48 @@ __device__ __forceinline__ void write_block(const OpDev<T>& op, const T* Zb, Ran
 }
 
 // ------------------------------------------------------------------------------------------
-// A5: fused window-multiply + localized forward transform, one stored row per thread group.
+// A5 (1-D): fused window-multiply + localized forward transform, one stored row per thread
+// group.  hS, gS: taps in shared memory; boff: the group's block-offset table (nb + 1 ints);
+// arena: the group's cfg.arena elements.
 // ------------------------------------------------------------------------------------------
-template <typename T, int DIM>
-__global__ void __launch_bounds__(256) k_assemble(const __grid_constant__ OpDev<T> op, const AsmCfg cfg)
+template <typename T>
+__device__ __forceinline__ void asm1d_row(const OpDev<T>& op, const AsmCfg& cfg, int rl, const T* hS, const T* gS,
+                                          int* boff, T* arena, int gid, int tid)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int gt = cfg.gt;
-    const int gid = threadIdx.x / gt, tid = threadIdx.x % gt;
     const int n = op.n, L = op.L, Lf = op.Lf, r = op.r;
     const int dense = op.gap < 0;
-    const Band Bo = band_info(DIM, n, L, cfg.b);
+    const Band Bo = band_info(1, n, L, cfg.b);
     const int j = Bo.j;
     const int jlo = dense ? 1 : max(1, j - op.gap);
     const int jhi = dense ? L : min(L, j + op.gap);
-    const int k0 = (DIM == 2) ? jlo - 1 : 0;
-
-    // shared layout: filters | per-group block offsets | per-group arenas
-    T* fS = reinterpret_cast<T*>(smem_raw);
-    T* hS = fS;
-    T* gS = fS + Lf;
-    T* phiS = fS + 2 * Lf;
-    const int lenk = (k0 > 0) ? wav_len(k0, Lf) : 0;
-    int* boffAll = reinterpret_cast<int*>(smem_raw + sizeof(T) * cfg.filt);
-    int* boff = boffAll + gid * (MAXB + 1);
-    T* arena = reinterpret_cast<T*>(smem_raw + sizeof(T) * cfg.filt + sizeof(int) * cfg.rpc * (MAXB + 1));
-    arena += (int64_t)gid * cfg.arena;  // the host keeps cfg.arena a multiple of 16 bytes
     T* const arena_end = arena + cfg.arena;
-
-    for (int i = threadIdx.x; i < 2 * Lf; i += blockDim.x) fS[i] = op.taps[i];
-    for (int i = threadIdx.x; i < lenk; i += blockDim.x) phiS[i] = op.wav[op.wofs[k0] + i];
-    __syncthreads();
-
-    const int rl = cfg.row0 + blockIdx.x * cfg.rpc + gid;
-    if (rl >= cfg.row0 + cfg.rows || blockIdx.x * cfg.rpc + gid >= cfg.rows) return;
-    const int l0 = (DIM == 2) ? rl / Bo.nj : 0;
-    const int l1 = (DIM == 2) ? rl % Bo.nj : rl;
+    const int l1 = rl;
     const Range A1 = region0(j, Bo.e1, l1, r, Lf, n);
-    const Range A0 = (DIM == 2) ? region0(j, Bo.e0, l0, r, Lf, n) : Range{0, 1, 0};
-    const int g0 = (DIM == 2) ? pmod(A0.lo, n) : 0;
     const int g1 = pmod(A1.lo, n);
     const int64_t srow = Bo.off + rl;
     const int64_t row_base = op.row_ptr[srow];
-
     if (tid == 0) {
         int acc = 0;
         for (int b2 = 0; b2 < op.nb; ++b2) {
             boff[b2] = acc;
-            if (block_kept(DIM, n, L, op.gap, cfg.b, b2))
-                acc += (int)block_count(DIM, n, L, Lf, r, op.gap, cfg.b, l0, l1, b2);
+            if (block_kept(1, n, L, op.gap, cfg.b, b2)) acc += (int)block_count(1, n, L, Lf, r, op.gap, cfg.b, 0, l1, b2);
         }
         boff[op.nb] = acc;
         if ((int64_t)acc != op.row_ptr[srow + 1] - row_base) flag_error(op.err, ERR_ROWLEN);
     }
-
     // windows nonzero on the region: OR of the tile masks it covers (every warp reduces alone)
     unsigned long long mw[MAXW];
 #pragma unroll
     for (int w = 0; w < MAXW; ++w) mw[w] = 0ull;
     {
         const int lane = threadIdx.x & 31;
-        const int ts0 = op.ts0, ts1 = op.ts1;
-        const int s0 = g0 / ts0, s1 = g1 / ts1;
-        const int nt0 = (DIM == 2) ? min(op.tpa0, (g0 % ts0 + A0.cnt + ts0 - 1) / ts0) : 1;
+        const int ts1 = op.ts1;
+        const int s1 = g1 / ts1;
         const int nt1 = min(op.tpa1, (g1 % ts1 + A1.cnt + ts1 - 1) / ts1);
-        for (int i = lane; i < nt0 * nt1; i += 32) {
-            const int t0 = (s0 + i / nt1) % op.tpa0, t1 = (s1 + i % nt1) % op.tpa1;
-            const unsigned long long* mp = op.masks + ((int64_t)t0 * op.tpa1 + t1) * op.mwords;
+        for (int i = lane; i < nt1; i += 32) {
+            const int t1 = (s1 + i) % op.tpa1;
+            const unsigned long long* mp = op.masks + (int64_t)t1 * op.mwords;
 #pragma unroll
             for (int w = 0; w < MAXW; ++w)
                 if (w < op.mwords) mw[w] |= mp[w];
@@ -397,18 +372,16 @@ __global__ void __launch_bounds__(256) k_assemble(const __grid_constant__ OpDev<
             mw[w] = ((unsigned long long)hi << 32) | lo;
         }
     }
-    const int64_t N = op.N;
     const T* Fb = op.F + op.Foff[cfg.b];
-    const int RR = A0.cnt * A1.cnt;
-
-    // s(q0, q1) = sum_k v_k(g + q) F_{k,b}(q), compensated over k
-    auto s_value = [&](int q0, int q1) -> T {
-        int gy = g0 + q0;
-        if (gy >= n) gy -= n;
-        int gx = g1 + q1;
-        if (gx >= n) gx -= n;
-        const int64_t pix = (DIM == 2) ? (int64_t)gy * n + gx : gx;
-        const int q = q0 * A1.cnt + q1;
+    const int RR = A1.cnt;
+    T* X = arena;
+    if (A1.cnt > cfg.arena) {
+        flag_error(op.err, ERR_ARENA);
+        return;
+    }
+    // s(q) = sum_k v_k(g + q) F_{k,b}(q), compensated over k
+    for (int q1 = tid; q1 < A1.cnt; q1 += gt) {
+        const int gx = (g1 + q1) & (n - 1);
         KahanAcc<T> acc;
         acc.init();
 #pragma unroll
@@ -417,173 +390,70 @@ __global__ void __launch_bounds__(256) k_assemble(const __grid_constant__ OpDev<
             while (bits) {
                 const int k = w * 64 + __ffsll((long long)bits) - 1;
                 bits &= bits - 1;
-                const T vk = __ldg(op.v + (int64_t)k * N + pix);
-                if (vk != T(0)) acc.add(vk * __ldg(Fb + (int64_t)k * RR + q));
+                const T vk = __ldg(op.v + (int64_t)k * op.N + gx);
+                if (vk != T(0)) acc.add(vk * __ldg(Fb + (int64_t)k * RR + q1));
             }
         }
-        return acc.get();
-    };
-
-    if (DIM == 1) {
-        // s on the whole region, then the cascade with a/d ping-pong between the arena ends
-        T* X = arena;
-        if (A1.cnt > cfg.arena) {
-            flag_error(op.err, ERR_ARENA);
-            return;
-        }
-        for (int q1 = tid; q1 < A1.cnt; q1 += gt) X[q1] = s_value(0, q1);
-        group_sync(gt, gid);
-        if ((int64_t)boff[op.nb] != op.row_ptr[srow + 1] - row_base) return;  // flagged above
-        Range cur = A1;
-        const T* in = X;
-        int n_in = n;
-        bool out_top = true;
-        int prev_out = A1.cnt;
-        for (int jj = 1; jj <= jhi; ++jj) {
-            const Range nx = range_cascade(cur, Lf, n >> jj);
-            if (2 * nx.cnt + prev_out > (int)(arena_end - arena)) {
-                flag_error(op.err, ERR_ARENA);
-                return;
-            }
-            T* out = out_top ? (arena_end - 2 * nx.cnt) : arena;
-            for (int c = tid; c < nx.cnt; c += gt) {
-                out[c] = filt(in, 1, cur, n_in, nx, c, hS, Lf, 2, 0);
-                out[nx.cnt + c] = filt(in, 1, cur, n_in, nx, c, gS, Lf, 2, 2 - Lf);
-            }
-            group_sync(gt, gid);
-            if (jj >= jlo) {
-                const int b2 = band_of_level(1, L, jj, 0);
-                write_block<T, 1>(op, out + nx.cnt, Range{0, 1, 0}, nx, jj, 0, 1, row_base + boff[b2], j, 0,
-                                  Bo.e1, 0, l1, tid, gt);
-                if (jj == L)
-                    write_block<T, 1>(op, out, Range{0, 1, 0}, nx, jj, 0, 0, row_base + boff[0], j, 0, Bo.e1, 0,
-                                      l1, tid, gt);
-            }
-            in = out;
-            cur = nx;
-            n_in = n >> jj;
-            out_top = !out_top;
-            prev_out = 2 * nx.cnt;
-        }
-        return;
-    }
-
-    // ---------------- 2-D ----------------
-    const int A = (int)(arena_end - arena);
-    Range c0, c1;
-    int S1, n1;
-    if (k0 == 0) {
-        n1 = n >> 1;
-        S1 = 2;
-        c0 = range_cascade(A0, Lf, n1);
-        c1 = range_cascade(A1, Lf, n1);
-    } else {
-        n1 = n >> k0;
-        S1 = 1 << k0;
-        c0 = range_filter(A0, S1, 0, lenk, n1);
-        c1 = range_filter(A1, S1, 0, lenk, n1);
-    }
-    const int nY = (k0 == 0) ? 2 : 1;
-    const int Ysz = nY * A0.cnt * c1.cnt;
-    const int Zsz = ((k0 == 0) ? 4 : 1) * c0.cnt * c1.cnt;
-    const int B = max(1, min(cfg.batch, A0.cnt));
-    if (B * A1.cnt + Ysz > A || Zsz + Ysz > A) {
-        flag_error(op.err, ERR_ARENA);
-        return;
-    }
-    T* X = arena;
-    T* YL = arena_end - Ysz;
-    T* YH = YL + A0.cnt * c1.cnt;
-    // stage 1a: rows of s, filtered along axis 1
-    for (int q0b = 0; q0b < A0.cnt; q0b += B) {
-        const int nbr = min(B, A0.cnt - q0b);
-        for (int e = tid; e < nbr * A1.cnt; e += gt) {
-            const int bq = e / A1.cnt, q1 = e - bq * A1.cnt;
-            X[e] = s_value(q0b + bq, q1);
-        }
-        group_sync(gt, gid);
-        if ((int64_t)boff[op.nb] != op.row_ptr[srow + 1] - row_base) return;  // flagged above
-        for (int e = tid; e < nbr * c1.cnt; e += gt) {
-            const int bq = e / c1.cnt, c = e - bq * c1.cnt;
-            const T* xr = X + bq * A1.cnt;
-            const int yo = (q0b + bq) * c1.cnt + c;
-            if (k0 == 0) {
-                YL[yo] = filt(xr, 1, A1, n, c1, c, hS, Lf, 2, 0);
-                YH[yo] = filt(xr, 1, A1, n, c1, c, gS, Lf, 2, 2 - Lf);
-            } else {
-                YL[yo] = filt(xr, 1, A1, n, c1, c, phiS, lenk, S1, 0);
-            }
-        }
-        group_sync(gt, gid);
-    }
-    // stage 1b: along axis 0
-    T* Z = arena;
-    const int zb = c0.cnt * c1.cnt;
-    for (int e = tid; e < zb; e += gt) {
-        const int a = e / c1.cnt, c = e - a * c1.cnt;
-        if (k0 == 0) {
-            Z[e] = filt(YL + c, c1.cnt, A0, n, c0, a, hS, Lf, 2, 0);                // (0,0)
-            Z[2 * zb + e] = filt(YL + c, c1.cnt, A0, n, c0, a, gS, Lf, 2, 2 - Lf);  // (1,0)
-            Z[zb + e] = filt(YH + c, c1.cnt, A0, n, c0, a, hS, Lf, 2, 0);           // (0,1)
-            Z[3 * zb + e] = filt(YH + c, c1.cnt, A0, n, c0, a, gS, Lf, 2, 2 - Lf);  // (1,1)
-        } else {
-            Z[e] = filt(YL + c, c1.cnt, A0, n, c0, a, phiS, lenk, S1, 0);
-        }
+        X[q1] = acc.get();
     }
     group_sync(gt, gid);
-    int jj0;
-    if (k0 == 0) {
-        // level 1 bands (0,1), (1,0), (1,1) are Z[zb..4zb)
-        for (int t = 0; t < 3; ++t) {
-            const int b2 = band_of_level(2, L, 1, t);
-            write_block<T, 2>(op, Z + (1 + t) * zb, c0, c1, 1, t >= 1 ? 1 : 0, t == 1 ? 0 : 1, row_base + boff[b2], j,
-                              Bo.e0, Bo.e1, l0, l1, tid, gt);
-        }
-        if (L == 1) write_block<T, 2>(op, Z, c0, c1, 1, 0, 0, row_base + boff[0], j, Bo.e0, Bo.e1, l0, l1, tid, gt);
-        jj0 = 2;
-    } else {
-        jj0 = k0 + 1;
-    }
-    // cascade on the LL band for the remaining output levels
-    Range p0 = c0, p1 = c1;
-    int prevZ = Zsz;
-    for (int jj = jj0; jj <= jhi; ++jj) {
-        const int nj = n >> jj;
-        const Range q0r = range_cascade(p0, Lf, nj), q1r = range_cascade(p1, Lf, nj);
-        const int ysz = 2 * p0.cnt * q1r.cnt, zsz = 4 * q0r.cnt * q1r.cnt;
-        if (prevZ + ysz > A || zsz + ysz > A) {
+    if ((int64_t)boff[op.nb] != op.row_ptr[srow + 1] - row_base) return;  // flagged above
+    // cascade with (a|d) outputs alternating between the arena ends
+    Range cur = A1;
+    const T* in = X;
+    int n_in = n;
+    bool out_top = true;
+    int prev_out = A1.cnt;
+    for (int jj = 1; jj <= jhi; ++jj) {
+        const Range nx = range_cascade(cur, Lf, n >> jj);
+        if (2 * nx.cnt + prev_out > (int)(arena_end - arena)) {
             flag_error(op.err, ERR_ARENA);
             return;
         }
-        const T* Xl = Z;  // LL of level jj-1 (p0.cnt x p1.cnt)
-        T* Yl = arena_end - ysz;
-        T* Yh = Yl + p0.cnt * q1r.cnt;
-        for (int e = tid; e < p0.cnt * q1r.cnt; e += gt) {
-            const int a = e / q1r.cnt, c = e - a * q1r.cnt;
-            Yl[e] = filt(Xl + a * p1.cnt, 1, p1, nj * 2, q1r, c, hS, Lf, 2, 0);
-            Yh[e] = filt(Xl + a * p1.cnt, 1, p1, nj * 2, q1r, c, gS, Lf, 2, 2 - Lf);
+        T* out = out_top ? (arena_end - 2 * nx.cnt) : arena;
+        for (int c = tid; c < nx.cnt; c += gt) {
+            out[c] = filt(in, 1, cur, n_in, nx, c, hS, Lf, 2, 0);
+            out[nx.cnt + c] = filt(in, 1, cur, n_in, nx, c, gS, Lf, 2, 2 - Lf);
         }
         group_sync(gt, gid);
-        const int zq = q0r.cnt * q1r.cnt;
-        for (int e = tid; e < zq; e += gt) {
-            const int a = e / q1r.cnt, c = e - a * q1r.cnt;
-            Z[e] = filt(Yl + c, q1r.cnt, p0, nj * 2, q0r, a, hS, Lf, 2, 0);
-            Z[2 * zq + e] = filt(Yl + c, q1r.cnt, p0, nj * 2, q0r, a, gS, Lf, 2, 2 - Lf);
-            Z[zq + e] = filt(Yh + c, q1r.cnt, p0, nj * 2, q0r, a, hS, Lf, 2, 0);
-            Z[3 * zq + e] = filt(Yh + c, q1r.cnt, p0, nj * 2, q0r, a, gS, Lf, 2, 2 - Lf);
+        if (jj >= jlo) {
+            const int b2 = band_of_level(1, L, jj, 0);
+            write_block<T, 1>(op, out + nx.cnt, Range{0, 1, 0}, nx, jj, 0, 1, row_base + boff[b2], j, 0, Bo.e1, 0, l1,
+                              tid, gt);
+            if (jj == L)
+                write_block<T, 1>(op, out, Range{0, 1, 0}, nx, jj, 0, 0, row_base + boff[0], j, 0, Bo.e1, 0, l1, tid,
+                                  gt);
         }
-        group_sync(gt, gid);
-        for (int t = 0; t < 3; ++t) {
-            const int b2 = band_of_level(2, L, jj, t);
-            write_block<T, 2>(op, Z + (1 + t) * zq, q0r, q1r, jj, t >= 1 ? 1 : 0, t == 1 ? 0 : 1,
-                              row_base + boff[b2], j, Bo.e0, Bo.e1, l0, l1, tid, gt);
-        }
-        if (jj == L)
-            write_block<T, 2>(op, Z, q0r, q1r, jj, 0, 0, row_base + boff[0], j, Bo.e0, Bo.e1, l0, l1, tid, gt);
-        p0 = q0r;
-        p1 = q1r;
-        prevZ = zsz;
+        in = out;
+        cur = nx;
+        n_in = n >> jj;
+        out_top = !out_top;
+        prev_out = 2 * nx.cnt;
     }
+}
+
+// Shared-memory layout of the row kernels: filters (cfg.filt elements of T) | per group a meta
+// area of META_INTS ints | per group an arena of cfg.arena elements of T.
+constexpr int META_INTS = 112;  // block offsets [MAXB+1], active terms (bytes) [64 ints], count
+constexpr int ACT_OFF = MAXB + 1;
+constexpr int NACT_OFF = ACT_OFF + 64;
+static_assert(NACT_OFF < META_INTS, "meta layout");
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_assemble1d(const __grid_constant__ OpDev<T> op, const AsmCfg cfg)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int gt = cfg.gt;
+    const int gid = threadIdx.x / gt, tid = threadIdx.x % gt;
+    T* fS = reinterpret_cast<T*>(smem_raw);
+    int* meta = reinterpret_cast<int*>(smem_raw + sizeof(T) * cfg.filt) + gid * META_INTS;
+    T* arena = reinterpret_cast<T*>(smem_raw + sizeof(T) * cfg.filt + sizeof(int) * cfg.rpc * META_INTS) +
+               (int64_t)gid * cfg.arena;
+    for (int i = threadIdx.x; i < 2 * op.Lf; i += blockDim.x) fS[i] = op.taps[i];
+    __syncthreads();
+    const int rloc = blockIdx.x * cfg.rpc + gid;
+    if (rloc >= cfg.rows) return;
+    asm1d_row<T>(op, cfg, cfg.row0 + rloc, fS, fS + op.Lf, meta, arena, gid, tid);
 }
 
 // ------------------------------------------------------------------------------------------

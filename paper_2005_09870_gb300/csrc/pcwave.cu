@@ -76,6 +76,20 @@ struct pc_op {
     std::string err = "no error";
 };
 
+struct pc_batch {
+    std::vector<pc_op*> ops;
+    OpDev<float>* ops_d = nullptr;
+    BatchItem* items_d = nullptr;
+    int* counter_d = nullptr;
+    int nitems = 0;
+    int grid = 0;
+    size_t smem = 0;
+    int kernels_per_run = 0;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
 namespace {
 
 pc_status fail(pc_op* h, pc_status st, const char* fmt, ...)
@@ -276,79 +290,88 @@ bool stencils_inside(const Geo& g, int b, int k0, int jhi)
     return true;
 }
 
+// Plan of one row band: thread-group size gt (0 = heuristic from the region area), groups per
+// CTA, stage-1 batch of s rows, per-group arena (the maximum over translate phases of what
+// every stage holds at once) and the dynamic shared memory of a CTA.
+pc_status plan_band(pc_op* h, const Geo& g, int b, int gt_req, BandPlan* out)
+{
+    const size_t es = h->esz;
+    Band B = band_info(g.d, g.n, g.L, b);
+    BandPlan bp{};
+    bp.b = b;
+    bp.rows = (int)band_rows(g, b);
+    const int dense = g.gap < 0;
+    bp.jlo = dense ? 1 : std::max(1, B.j - g.gap);
+    bp.jhi = dense ? g.L : std::min(g.L, B.j + g.gap);
+    bp.k0 = (g.d == 2) ? bp.jlo - 1 : 0;
+    int64_t need = 0;
+    int gt, batch = 1;
+    AxisMax M1 = axis_max(g, B.j, B.e1, B.nj, bp.k0, bp.jhi);
+    if (g.d == 1) {
+        // X then alternating (a|d) outputs at the two arena ends
+        int64_t prev = M1.A;
+        for (int jj = 1; jj <= bp.jhi; ++jj) {
+            int64_t cur = 2 * (int64_t)M1.lev[jj];
+            need = std::max(need, prev + cur);
+            prev = cur;
+        }
+        gt = gt_req ? gt_req : ((M1.A > 256) ? 64 : 32);
+    } else {
+        AxisMax M0 = axis_max(g, B.j, B.e0, B.nj, bp.k0, bp.jhi);
+        const int64_t area = (int64_t)M0.A * M1.A;
+        gt = gt_req ? gt_req : (area <= 768 ? 32 : area <= 2048 ? 64 : area <= 6144 ? 128 : 256);
+        const int nY = (bp.k0 == 0) ? 2 : 1;
+        const int64_t Y = (int64_t)nY * M0.A * M1.c;
+        const int64_t Z = (int64_t)((bp.k0 == 0) ? 4 : 1) * M0.c * M1.c;
+        // s rows per stage-1 step: the whole region when it fits a ~96 KB-per-CTA budget,
+        // else as many rows as the budget allows (at least 8 pixels per thread)
+        const int64_t budget = (96 * 1024 / (int64_t)es) / std::max(1, 256 / gt);
+        const int64_t room = std::max<int64_t>(budget - Y, (int64_t)8 * gt);
+        batch = (int)std::max<int64_t>(1, std::min<int64_t>(M0.A, room / M1.A));
+        need = std::max<int64_t>((int64_t)batch * M1.A + Y, Z + Y);
+        int64_t prevZ = Z;
+        int lvl0 = (bp.k0 == 0) ? 1 : bp.k0;
+        for (int jj = lvl0 + 1; jj <= bp.jhi; ++jj) {
+            int64_t ysz = 2 * (int64_t)M0.lev[jj - 1] * M1.lev[jj];
+            int64_t zsz = 4 * (int64_t)M0.lev[jj] * M1.lev[jj];
+            need = std::max(need, std::max(prevZ + ysz, zsz + ysz));
+            prevZ = zsz;
+        }
+    }
+    if (!stencils_inside(g, b, bp.k0, bp.jhi))
+        return fail(h, PC_ERR_UNSUPPORTED, "internal: stencil of band %d outside its transform range", b);
+    need = round_up(need, (int64_t)(16 / es));
+    const int lft = (g.d == 2) ? lf_template(g.Lf) : g.Lf;
+    int filt = 2 * lft + ((bp.k0 > 0) ? wav_len(bp.k0, g.Lf) : 0);
+    filt = (int)round_up(filt, (int64_t)(16 / es));
+    int rpc = std::max(1, 256 / gt);
+    auto smem_of = [&](int rpcv) {
+        return (size_t)filt * es + round_up((int64_t)rpcv * META_INTS * 4, 16) + (size_t)rpcv * need * es;
+    };
+    while (rpc > 1 && smem_of(rpc) > 110 * 1024) rpc /= 2;
+    if (smem_of(rpc) > 227 * 1024)
+        return fail(h, PC_ERR_UNSUPPORTED, "band %d needs %zu bytes of shared memory per row", b, smem_of(rpc));
+    bp.cfg.b = b;
+    bp.cfg.row0 = 0;
+    bp.cfg.rows = bp.rows;
+    bp.cfg.gt = gt;
+    bp.cfg.rpc = rpc;
+    bp.cfg.batch = batch;
+    bp.cfg.arena = (int)need;
+    bp.cfg.filt = filt;
+    bp.smem = smem_of(rpc);
+    *out = bp;
+    return PC_OK;
+}
+
 pc_status plan_bands(pc_op* h)
 {
-    const pc_desc& D = h->desc;
-    Geo g = geo_of(&D);
+    Geo g = geo_of(&h->desc);
     h->plan.clear();
-    const size_t es = h->esz;
     for (int b = 0; b < g.nb; ++b) {
-        Band B = band_info(g.d, g.n, g.L, b);
-        BandPlan bp{};
-        bp.b = b;
-        bp.rows = (int)band_rows(g, b);
-        const int dense = g.gap < 0;
-        bp.jlo = dense ? 1 : std::max(1, B.j - g.gap);
-        bp.jhi = dense ? g.L : std::min(g.L, B.j + g.gap);
-        bp.k0 = (g.d == 2) ? bp.jlo - 1 : 0;
-        int64_t need = 0;
-        int gt, batch = 1;
-        AxisMax M1 = axis_max(g, B.j, B.e1, B.nj, bp.k0, bp.jhi);
-        if (g.d == 1) {
-            // X then alternating (a|d) outputs at the two arena ends
-            int64_t prev = M1.A;
-            for (int jj = 1; jj <= bp.jhi; ++jj) {
-                int64_t cur = 2 * (int64_t)M1.lev[jj];
-                need = std::max(need, prev + cur);
-                prev = cur;
-            }
-            gt = (M1.A > 256) ? 64 : 32;
-        } else {
-            AxisMax M0 = axis_max(g, B.j, B.e0, B.nj, bp.k0, bp.jhi);
-            const int64_t area = (int64_t)M0.A * M1.A;
-            gt = area <= 768 ? 32 : area <= 2048 ? 64 : area <= 6144 ? 128 : 256;
-            const int nY = (bp.k0 == 0) ? 2 : 1;
-            const int64_t Y = (int64_t)nY * M0.A * M1.c;
-            const int64_t Z = (int64_t)((bp.k0 == 0) ? 4 : 1) * M0.c * M1.c;
-            // s rows per stage-1 step: the whole region when it fits a ~96 KB-per-CTA budget,
-            // else as many rows as the budget allows (at least 8 pixels per thread)
-            const int64_t budget = (96 * 1024 / (int64_t)es) / std::max(1, 256 / gt);
-            const int64_t room = std::max<int64_t>(budget - Y, (int64_t)8 * gt);
-            batch = (int)std::max<int64_t>(1, std::min<int64_t>(M0.A, room / M1.A));
-            need = std::max<int64_t>((int64_t)batch * M1.A + Y, Z + Y);
-            int64_t prevZ = Z;
-            int lvl0 = (bp.k0 == 0) ? 1 : bp.k0;
-            for (int jj = lvl0 + 1; jj <= bp.jhi; ++jj) {
-                int64_t ysz = 2 * (int64_t)M0.lev[jj - 1] * M1.lev[jj];
-                int64_t zsz = 4 * (int64_t)M0.lev[jj] * M1.lev[jj];
-                need = std::max(need, std::max(prevZ + ysz, zsz + ysz));
-                prevZ = zsz;
-            }
-        }
-        if (!stencils_inside(g, b, bp.k0, bp.jhi))
-            return fail(h, PC_ERR_UNSUPPORTED, "internal: stencil of band %d outside its transform range", b);
-        need = round_up(need, (int64_t)(16 / es));
-        const int lft = (g.d == 2) ? lf_template(g.Lf) : g.Lf;
-        int filt = 2 * lft + ((bp.k0 > 0) ? wav_len(bp.k0, g.Lf) : 0);
-        filt = (int)round_up(filt, (int64_t)(16 / es));
-        const int meta_ints = (g.d == 2) ? META_INTS : (MAXB + 1);
-        int rpc = std::max(1, 256 / gt);
-        auto smem_of = [&](int rpcv) {
-            return (size_t)filt * es + round_up((int64_t)rpcv * meta_ints * 4, 16) + (size_t)rpcv * need * es;
-        };
-        while (rpc > 1 && smem_of(rpc) > 110 * 1024) rpc /= 2;
-        if (smem_of(rpc) > 227 * 1024)
-            return fail(h, PC_ERR_UNSUPPORTED, "band %d needs %zu bytes of shared memory per row", b, smem_of(rpc));
-        bp.cfg.b = b;
-        bp.cfg.row0 = 0;
-        bp.cfg.rows = bp.rows;
-        bp.cfg.gt = gt;
-        bp.cfg.rpc = rpc;
-        bp.cfg.batch = batch;
-        bp.cfg.arena = (int)need;
-        bp.cfg.filt = filt;
-        bp.smem = smem_of(rpc);
-        // the kernel places the per-group int tables before the arenas: keep 16-byte alignment
+        BandPlan bp;
+        pc_status st = plan_band(h, g, b, 0, &bp);
+        if (st != PC_OK) return st;
         h->plan.push_back(bp);
     }
     return PC_OK;
@@ -394,8 +417,9 @@ pc_status set_smem_attr()
 {
     static bool done = false;
     if (!done) {
-        if (cudaFuncSetAttribute(k_assemble<T, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
-                cudaSuccess ||
+        if ((DIM == 1 &&
+             cudaFuncSetAttribute(k_assemble1d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
+                 cudaSuccess) ||
             cudaFuncSetAttribute(k_backward<T, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
                 cudaSuccess)
             return PC_ERR_CUDA;
@@ -476,7 +500,7 @@ pc_status assemble_t(pc_op* h, cudaStream_t st, int stage_mask)
         const int threads = bp.cfg.gt * bp.cfg.rpc;
         if (D.dim == 1) {
             if (set_smem_attr<T, 1>() != PC_OK) return fail(h, PC_ERR_CUDA, "cudaFuncSetAttribute failed");
-            k_assemble<T, 1><<<ctas, threads, bp.smem, st>>>(od, bp.cfg);
+            k_assemble1d<T><<<ctas, threads, bp.smem, st>>>(od, bp.cfg);
         } else {
             pc_status ls = launch_asm2d<T>(h, od, bp, ctas, threads, st);
             if (ls != PC_OK) return ls;
@@ -717,6 +741,186 @@ void free_all(pc_op* h)
                     h->G_d,  h->dF_d, h->dG_d, h->S_d, h->amask_d, h->row_ptr_d,  h->theta_d,   h->theta16_d, h->masks_d, h->err_d};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+}
+
+// Enqueues one run of a batch on st: every operator's stage 0, the queue reset, the
+// persistent kernel.
+pc_status batch_enqueue(pc_batch* B, cudaStream_t st)
+{
+    for (pc_op* h : B->ops) {
+        pc_status ps = prepare_t<float>(h, st);
+        if (ps != PC_OK) return ps;
+    }
+    if (cudaMemsetAsync(B->counter_d, 0, sizeof(int), st) != cudaSuccess) return PC_ERR_CUDA;
+    k_assemble_batch<<<B->grid, 256, B->smem, st>>>(B->ops_d, B->items_d, B->nitems, B->counter_d);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) return PC_ERR_CUDA;
+    for (pc_op* h : B->ops) {
+        h->prepared = true;
+        h->assembled = true;
+    }
+    return PC_OK;
+}
+
+void batch_free(pc_batch* B)
+{
+    if (!B) return;
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->graph) cudaGraphDestroy(B->graph);
+    if (B->cap) cudaStreamDestroy(B->cap);
+    if (B->ops_d) cudaFree(B->ops_d);
+    if (B->items_d) cudaFree(B->items_d);
+    if (B->counter_d) cudaFree(B->counter_d);
+    delete B;
+}
+
+pc_status batch_build(pc_handle* ops, int count, cudaStream_t st, bool capture, pc_batch** out)
+{
+    *out = nullptr;
+    if (!ops || count < 1) return fail(nullptr, PC_ERR_INVALID_ARG, "batch needs at least one operator");
+    pc_batch* B = new (std::nothrow) pc_batch();
+    if (!B) return fail(nullptr, PC_ERR_OOM, "host allocation failed");
+    std::vector<OpDev<float>> od;
+    struct Cand {
+        double cost;
+        BatchItem it;
+    };
+    std::vector<Cand> cands;
+    for (int i = 0; i < count; ++i) {
+        pc_op* h = ops[i];
+        if (!h) {
+            batch_free(B);
+            return fail(nullptr, PC_ERR_INVALID_ARG, "operator %d is NULL", i);
+        }
+        if (h->desc.precision != PC_FP32) {
+            batch_free(B);
+            return fail(nullptr, PC_ERR_UNSUPPORTED, "batches are FP32 only (operator %d is FP64)", i);
+        }
+        B->ops.push_back(h);
+        od.push_back(make_opdev<float>(h));
+        for (const BandPlan& bp : h->plan) {
+            // cost of a row: its region and its stored entries
+            const double entries = (double)(h->row_ptr_h[band_info(h->desc.dim, h->desc.n, h->desc.levels, bp.b).off +
+                                                         bp.rows] -
+                                            h->row_ptr_h[band_info(h->desc.dim, h->desc.n, h->desc.levels, bp.b).off]) /
+                                   bp.rows;
+            const double area = (double)bp.cfg.arena;
+            const double row_cost = area + entries;
+            int per = (int)std::max(1.0, std::floor(60000.0 / row_cost));
+            per = std::max(bp.cfg.rpc, (per / bp.cfg.rpc) * bp.cfg.rpc);
+            for (int r0 = 0; r0 < bp.rows; r0 += per) {
+                Cand c;
+                c.it.op = i;
+                c.it.dim = h->desc.dim;
+                c.it.lft = (h->desc.dim == 2) ? lf_template(h->Lf) : h->Lf;
+                c.it.pad = 0;
+                c.it.cfg = bp.cfg;
+                c.it.cfg.row0 = r0;
+                c.it.cfg.rows = std::min(per, bp.rows - r0);
+                c.cost = row_cost * c.it.cfg.rows;
+                cands.push_back(c);
+                B->smem = std::max(B->smem, bp.smem);
+            }
+        }
+    }
+    std::stable_sort(cands.begin(), cands.end(), [](const Cand& a, const Cand& b) { return a.cost > b.cost; });
+    std::vector<BatchItem> items;
+    for (const Cand& c : cands) items.push_back(c.it);
+    B->nitems = (int)items.size();
+    cudaError_t e;
+    if ((e = cudaMalloc(&B->ops_d, sizeof(OpDev<float>) * od.size())) ||
+        (e = cudaMalloc(&B->items_d, sizeof(BatchItem) * items.size())) || (e = cudaMalloc(&B->counter_d, sizeof(int))) ||
+        (e = cudaMemcpyAsync(B->ops_d, od.data(), sizeof(OpDev<float>) * od.size(), cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(B->items_d, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice,
+                             st)) ||
+        (e = cudaFuncSetAttribute(k_assemble_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024))) {
+        batch_free(B);
+        return fail(nullptr, e == cudaErrorMemoryAllocation ? PC_ERR_OOM : PC_ERR_CUDA, "batch setup: %s",
+                    cudaGetErrorString(e));
+    }
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_assemble_batch, 256, B->smem);
+    B->grid = std::max(1, sms * std::max(1, per_sm));
+    B->kernels_per_run = 6 * count + 1;
+    // one eager run (sets up every kernel), then capture the same sequence
+    pc_status ps = batch_enqueue(B, st);
+    if (ps != PC_OK || (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+        batch_free(B);
+        return fail(nullptr, PC_ERR_CUDA, "batch run failed");
+    }
+    if (capture) {
+        if ((e = cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking)) ||
+            (e = cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal))) {
+            batch_free(B);
+            return fail(nullptr, PC_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+        }
+        ps = batch_enqueue(B, B->cap);
+        e = cudaStreamEndCapture(B->cap, &B->graph);
+        if (ps != PC_OK || e != cudaSuccess || (e = cudaGraphInstantiate(&B->exec, B->graph, 0)) != cudaSuccess) {
+            batch_free(B);
+            return fail(nullptr, PC_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+        }
+    }
+    *out = B;
+    return PC_OK;
+}
+
+// Times one band's row-assembly launch (3 launches after a warm-up; minimum).
+template <typename T>
+float time_band(pc_op* h, const BandPlan& bp, cudaStream_t st)
+{
+    OpDev<T> od = make_opdev<T>(h);
+    const int ctas = (bp.rows + bp.cfg.rpc - 1) / bp.cfg.rpc;
+    const int threads = bp.cfg.gt * bp.cfg.rpc;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float best = 1e30f;
+    for (int it = 0; it < 4; ++it) {
+        cudaEventRecord(a, st);
+        if (h->desc.dim == 1)
+            k_assemble1d<T><<<ctas, threads, bp.smem, st>>>(od, bp.cfg);
+        else
+            launch_asm2d<T>(h, od, bp, ctas, threads, st);
+        cudaEventRecord(b, st);
+        cudaEventSynchronize(b);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        if (it > 0) best = std::min(best, ms);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return best;
+}
+
+template <typename T>
+pc_status autotune_t(pc_op* h, cudaStream_t st)
+{
+    pc_status ps = prepare_t<T>(h, st);
+    if (ps != PC_OK) return ps;
+    h->prepared = true;
+    if (h->desc.dim == 1 && set_smem_attr<T, 1>() != PC_OK) return fail(h, PC_ERR_CUDA, "cudaFuncSetAttribute failed");
+    Geo g = geo_of(&h->desc);
+    for (BandPlan& cur : h->plan) {
+        BandPlan best = cur;
+        float tbest = time_band<T>(h, cur, st);
+        for (int gt : {32, 64, 128, 256}) {
+            if (gt == cur.cfg.gt) continue;
+            BandPlan cand;
+            if (plan_band(h, g, cur.b, gt, &cand) != PC_OK) continue;
+            const float t = time_band<T>(h, cand, st);
+            if (t < tbest) {
+                tbest = t;
+                best = cand;
+            }
+        }
+        cur = best;
+    }
+    PC_CUDA(h, cudaGetLastError());
+    // leave Theta assembled with the tuned plan
+    return assemble_t<T>(h, st, 2);
 }
 
 }  // namespace
@@ -976,14 +1180,55 @@ pc_status pc_backward_noalloc(pc_handle h, const void* dtheta, void* du, void* d
     return backward_noalloc_t<float>(h, (const float*)dtheta, (float*)du, (float*)dv, s);
 }
 
-pc_status pc_batch_assemble(pc_handle* ops, int count, void* stream)
+pc_status pc_batch_create(pc_handle* ops, int count, void* stream, pc_batch_handle* out)
 {
-    if (!ops || count < 0) return fail(nullptr, PC_ERR_INVALID_ARG, "bad ops/count");
-    for (int i = 0; i < count; ++i) {
-        pc_status st = pc_assemble(ops[i], stream);
-        if (st != PC_OK) return st;
+    if (!out) return fail(nullptr, PC_ERR_INVALID_ARG, "out is NULL");
+    return batch_build(ops, count, (cudaStream_t)stream, true, out);
+}
+
+pc_status pc_batch_run(pc_batch_handle b, void* stream)
+{
+    if (!b || !b->exec) return fail(nullptr, PC_ERR_INVALID_ARG, "batch is NULL or not captured");
+    cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(nullptr, PC_ERR_CUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
+    count_launch(b->kernels_per_run);
+    for (pc_op* h : b->ops) {
+        h->prepared = true;
+        h->assembled = true;
     }
     return PC_OK;
+}
+
+pc_status pc_batch_info(pc_batch_handle b, int* items, int* kernels_per_run)
+{
+    if (!b) return fail(nullptr, PC_ERR_INVALID_ARG, "batch is NULL");
+    if (items) *items = b->nitems;
+    if (kernels_per_run) *kernels_per_run = b->kernels_per_run;
+    return PC_OK;
+}
+
+void pc_batch_destroy(pc_batch_handle b)
+{
+    if (!b) return;
+    cudaDeviceSynchronize();
+    batch_free(b);
+}
+
+pc_status pc_batch_assemble(pc_handle* ops, int count, void* stream)
+{
+    pc_batch* B = nullptr;
+    pc_status st = batch_build(ops, count, (cudaStream_t)stream, false, &B);
+    if (st != PC_OK) return st;
+    batch_free(B);  // the eager run in batch_build assembled every operator (synchronised)
+    return PC_OK;
+}
+
+pc_status pc_autotune(pc_handle h, void* stream)
+{
+    if (!h) return fail(nullptr, PC_ERR_INVALID_ARG, "handle is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->desc.precision == PC_FP64) return autotune_t<double>(h, s);
+    return autotune_t<float>(h, s);
 }
 
 pc_status pc_info(pc_handle h, int64_t* nnz, int64_t* device_bytes)
