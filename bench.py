@@ -276,6 +276,53 @@ def run_ours(args, rank, world, local_rank):
         acc = {"fp32_max_rel_err": e32 / ref, "fp64_max_rel_err": e64 / ref, "columns_checked": 8}
     g64.close()
 
+    # ---------------- A8: batched FP32 vs plain FP64 on 64 uneven operators ----------------
+    batch_info = None
+    if not args.no_batch:
+        bops = P.batch_workload(64, seed_offset=rank)
+        bg = [pw.PCOperator(pw.desc_of(o, pw.PC_FP32, 0), torch.tensor(o.u, dtype=torch.float32, device=dev),
+                            torch.tensor(o.v, dtype=torch.float32, device=dev)) for o in bops]
+        bnnz = sum(x.nnz for x in bg)
+        batch = pw.PCBatch(bg)                 # plans the queue, runs once, captures the graph
+        for _ in range(2):
+            batch.run()
+        bt = []
+        for _ in range(3):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            batch.run()
+            b.record(stream)
+            torch.cuda.synchronize()
+            bt.append(a.elapsed_time(b))
+        for x in bg:
+            x.sync()
+        batch_ms = float(np.median(bt))
+        items = batch.items
+        batch.close()
+        for x in bg:
+            x.close()
+        del bg
+        # plain FP64: one operator per assembly call, the same kernels instantiated in FP64
+        f64 = 0.0
+        for o in bops:
+            x = pw.PCOperator(pw.desc_of(o, pw.PC_FP64, 0), torch.tensor(o.u, dtype=torch.float64, device=dev),
+                              torch.tensor(o.v, dtype=torch.float64, device=dev))
+            x.assemble()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            x.assemble()
+            b.record(stream)
+            torch.cuda.synchronize()
+            f64 += a.elapsed_time(b)
+            x.close()
+        batch_info = {"workload": "64 operators: 32 1-D (n=2^10..2^16) + 32 2-D (64^2..512^2), m 4..25, "
+                                  "kernel widths 5..31, db2/db4, L 3..6; one persistent launch, CUDA graph",
+                      "nnz": bnnz, "work_items": items, "fp32_batched_ms": batch_ms,
+                      "fp32_batched_entries_per_s": bnnz / (batch_ms * 1e-3),
+                      "fp64_plain_ms": f64, "fp64_plain_entries_per_s": bnnz / (f64 * 1e-3),
+                      "fp32_batched_vs_fp64_plain_factor": f64 / batch_ms}
+
     # ---------------- roofline of the dominant kernel (fused row assembly) ----------------
     peak, peak_kind = _peaks()
     alg_bytes = nnz * (4 + 2) + op.m * op.N * 4     # Theta FP32 + BF16 written once, windows read once
@@ -310,6 +357,7 @@ def run_ours(args, rank, world, local_rank):
                          "fp64_ms": fp64_asm_ms, "fp64_entries_per_s": nnz / (fp64_asm_ms * 1e-3),
                          "fp32_vs_fp64_factor": fp64_asm_ms / fp32_asm_ms, **acc},
             "bwd_ms": bwd_ms,
+            "batch": batch_info,
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -332,6 +380,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -833,7 +833,7 @@ pc_status batch_build(pc_handle* ops, int count, cudaStream_t st, bool capture, 
         (e = cudaMemcpyAsync(B->ops_d, od.data(), sizeof(OpDev<float>) * od.size(), cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemcpyAsync(B->items_d, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice,
                              st)) ||
-        (e = cudaFuncSetAttribute(k_assemble_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024))) {
+        (e = cudaFuncSetAttribute(k_assemble_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->smem))) {
         batch_free(B);
         return fail(nullptr, e == cudaErrorMemoryAllocation ? PC_ERR_OOM : PC_ERR_CUDA, "batch setup: %s",
                     cudaGetErrorString(e));
