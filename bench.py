@@ -98,7 +98,7 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_rate(op, seconds, seed=5, max_cols=4096):
+def cpu_oracle_rate(op, seconds, seed=5, max_cols=65536):
     """Algorithm 2 (FP64 oracle, OpenMP over columns) on uniformly drawn columns until about
     `seconds` of oracle time: returns (entries/s counted on the pattern, columns, threads, wall)."""
     import oracle
