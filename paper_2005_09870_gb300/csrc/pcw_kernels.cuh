@@ -959,6 +959,163 @@ __global__ void __launch_bounds__(256) k_apply_vec(const __grid_constant__ OpDev
     if (slot == 0) *reinterpret_cast<float4*>(y + s * ldy + c0 + 4 * quad) = acc;
 }
 
+// ------------------------------------------------------------------------------------------
+// A6 on tensor cores: y = S x for 16 right-hand sides, BF16 S, FP32 accumulation.
+// A CTA (4 warps) owns a tile of 16 stored rows of one band with the same l0 and consecutive
+// l1.  For each kept column band b2 and each stencil row a (warps take a's in turn), the 16
+// rows' entries form a banded 16 x K block A (row i holds its W1(i) values at column offset
+// o_i) and the matching K x 16 slab of x (row f0 + a of band b2, columns u .. u + K - 1 mod
+// nj2) is B; mma.sync m16n8k16 (BF16 inputs, FP32 accumulate) adds A B to the warp's 16 x 16
+// accumulator.  x is split into hi + lo BF16 parts (two products) so that the only rounding
+// beyond FP32 is the BF16 storage of S.  Warps' partial sums are reduced in shared memory.
+// ------------------------------------------------------------------------------------------
+struct TcApply {
+    int d, n, L, Lf, r, gap, nb;
+    int64_t N;
+    const int64_t* row_ptr;
+    int tile_off[MAXB + 1];  // first tile of band b (tiles: l0 x ceil(nj / 16))
+};
+
+__device__ __forceinline__ unsigned pack_bf16(float lo, float hi)
+{
+    const __nv_bfloat16 a = __float2bfloat16_rn(lo), b = __float2bfloat16_rn(hi);
+    return (unsigned)__bfloat16_as_ushort(a) | ((unsigned)__bfloat16_as_ushort(b) << 16);
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float (&c)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                               unsigned b0, unsigned b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(128) k_apply_tc(const __grid_constant__ TcApply tp,
+                                                  const __nv_bfloat16* __restrict__ vals, const float* __restrict__ x,
+                                                  int ldx, float* __restrict__ y, int ldy, int c0)
+{
+    __shared__ int64_t rbase[16];          // row_ptr of the tile's rows
+    __shared__ int boff[16][MAXB];         // block offsets within each row
+    __shared__ int f1s[16][MAXB], w1s[16][MAXB];
+    __shared__ int f0s[MAXB], w0s[MAXB];
+    __shared__ float red[4][16][17];
+    const int d = tp.d, n = tp.n, L = tp.L;
+    const int tile = blockIdx.x;
+    int b = 0;
+    while (b + 1 < tp.nb && tile >= tp.tile_off[b + 1]) ++b;
+    const Band Bo = band_info(d, n, L, b);
+    const int nt1 = (Bo.nj + 15) >> 4;
+    const int tl = tile - tp.tile_off[b];
+    const int l0 = (d == 2) ? tl / nt1 : 0;
+    const int l1base = (tl - l0 * nt1) * 16;
+    const int nvalid = min(16, Bo.nj - l1base);
+    const int dense = tp.gap < 0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // per-row stencils and block offsets (thread i: row i, all blocks)
+    if (threadIdx.x < 16) {
+        const int i = threadIdx.x;
+        const int l1 = l1base + min(i, nvalid - 1);
+        const int64_t s = Bo.off + (int64_t)l0 * ((d == 2) ? Bo.nj : 0) + l1;
+        rbase[i] = tp.row_ptr[s];
+        int acc = 0;
+        for (int b2 = 0; b2 < tp.nb; ++b2) {
+            boff[i][b2] = acc;
+            if (!block_kept(d, n, L, tp.gap, b, b2)) {
+                w1s[i][b2] = 0;
+                continue;
+            }
+            const Band B2 = band_info(d, n, L, b2);
+            int f0 = 0, W0 = 1, f1, W1;
+            stencil(Bo.j, Bo.e1, l1, B2.j, B2.e1, tp.r, tp.Lf, n, dense, &f1, &W1);
+            if (d == 2) stencil(Bo.j, Bo.e0, l0, B2.j, B2.e0, tp.r, tp.Lf, n, dense, &f0, &W0);
+            f1s[i][b2] = f1;
+            w1s[i][b2] = W1;
+            if (i == 0) {
+                f0s[b2] = f0;
+                w0s[b2] = W0;
+            }
+            acc += W0 * W1;
+        }
+    }
+    __syncthreads();
+    const int g = lane >> 2, q = lane & 3;
+    float acc0[4] = {0.f, 0.f, 0.f, 0.f}, acc1[4] = {0.f, 0.f, 0.f, 0.f};  // n-tiles 0 (rhs 0..7), 1 (8..15)
+    const bool vg = g < nvalid, vg8 = g + 8 < nvalid;
+    for (int b2 = 0; b2 < tp.nb; ++b2) {
+        if (w1s[0][b2] == 0) continue;
+        const Band B2 = band_info(d, n, L, b2);
+        const int nj2 = B2.nj, m2 = nj2 - 1;
+        const int W0 = w0s[b2], f0 = f0s[b2];
+        // union of the rows' windows on axis 1 (first rows start first: stencils are monotone)
+        const int u = f1s[0][b2];
+        int K = 0;
+        for (int i = 0; i < nvalid; ++i) K = max(K, f1s[i][b2] + w1s[i][b2] - u);
+        const int Wg = w1s[g][b2], Wg8 = w1s[g + 8][b2];
+        const int og = f1s[g][b2] - u, og8 = f1s[g + 8][b2] - u;
+        const __nv_bfloat16* rg = vals + rbase[g] + boff[g][b2];
+        const __nv_bfloat16* rg8 = vals + rbase[g + 8] + boff[g + 8][b2];
+        for (int a = warp; a < W0; a += 4) {
+            const int64_t xrow = B2.off + (int64_t)((f0 + a) & m2) * ((d == 2) ? nj2 : 0);
+            const __nv_bfloat16* ag = rg + a * Wg - og;
+            const __nv_bfloat16* ag8 = rg8 + a * Wg8 - og8;
+            for (int kc = 0; kc < K; kc += 16) {
+                unsigned A[4];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {        // columns 2q + 8h, 2q + 8h + 1
+                    const int k0 = kc + 2 * q + 8 * h, k1 = k0 + 1;
+                    const bool g0ok = vg && k0 >= og && k0 < og + Wg, g1ok = vg && k1 >= og && k1 < og + Wg;
+                    const bool h0ok = vg8 && k0 >= og8 && k0 < og8 + Wg8, h1ok = vg8 && k1 >= og8 && k1 < og8 + Wg8;
+                    unsigned short x0 = 0, x1 = 0, z0 = 0, z1 = 0;
+                    if (g0ok) x0 = __bfloat16_as_ushort(ag[k0]);
+                    if (g1ok) x1 = __bfloat16_as_ushort(ag[k1]);
+                    if (h0ok) z0 = __bfloat16_as_ushort(ag8[k0]);
+                    if (h1ok) z1 = __bfloat16_as_ushort(ag8[k1]);
+                    A[2 * h] = (unsigned)x0 | ((unsigned)x1 << 16);
+                    A[2 * h + 1] = (unsigned)z0 | ((unsigned)z1 << 16);
+                }
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt) {
+                    float xv[4];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int kk = kc + 2 * q + (t & 1) + 8 * (t >> 1);
+                        xv[t] = (kk < K) ? __ldg(x + (xrow + ((u + kk) & m2)) * ldx + c0 + nt * 8 + g) : 0.f;
+                    }
+                    const unsigned bh0 = pack_bf16(xv[0], xv[1]), bh1 = pack_bf16(xv[2], xv[3]);
+                    float rl[4];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                        rl[t] = xv[t] - __bfloat162float(__float2bfloat16_rn(xv[t]));
+                    const unsigned bl0 = pack_bf16(rl[0], rl[1]), bl1 = pack_bf16(rl[2], rl[3]);
+                    float(&acc)[4] = nt ? acc1 : acc0;
+                    mma_bf16_16816(acc, A[0], A[1], A[2], A[3], bh0, bh1);
+                    mma_bf16_16816(acc, A[0], A[1], A[2], A[3], bl0, bl1);
+                }
+            }
+        }
+    }
+    // C fragments: (row g, cols 2q, 2q+1), (row g + 8, cols 2q, 2q+1) per n-tile
+    red[warp][g][2 * q] = acc0[0];
+    red[warp][g][2 * q + 1] = acc0[1];
+    red[warp][g + 8][2 * q] = acc0[2];
+    red[warp][g + 8][2 * q + 1] = acc0[3];
+    red[warp][g][8 + 2 * q] = acc1[0];
+    red[warp][g][8 + 2 * q + 1] = acc1[1];
+    red[warp][g + 8][8 + 2 * q] = acc1[2];
+    red[warp][g + 8][8 + 2 * q + 1] = acc1[3];
+    __syncthreads();
+    for (int e = threadIdx.x; e < 16 * 16; e += blockDim.x) {
+        const int i = e >> 4, c = e & 15;
+        if (i < nvalid) {
+            const float v = red[0][i][c] + red[1][i][c] + red[2][i][c] + red[3][i][c];
+            const int64_t s = Bo.off + (int64_t)l0 * ((d == 2) ? Bo.nj : 0) + l1base + i;
+            y[s * ldy + c0 + c] = v;
+        }
+    }
+}
+
 template <typename TA>
 __global__ void k_zero_rows(TA* y, int64_t N, int ldy, int c0, int nr)
 {

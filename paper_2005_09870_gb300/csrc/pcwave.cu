@@ -529,6 +529,38 @@ pc_status apply_t(pc_op* h, const TV* vals, const TA* x, TA* y, int nrhs, int ld
     const int transpose = D.order == PC_ORDER_CONV_THEN_MULT;
     const int64_t warps = h->N;
     const int blocks = (int)((warps * 32 + 255) / 256);
+    // tensor-core path: BF16 values, paper order, groups of 16 right-hand sides
+    if constexpr (std::is_same<TV, __nv_bfloat16>::value && std::is_same<TA, float>::value) {
+        if (!transpose && nrhs >= 16) {
+            TcApply tp{};
+            tp.d = D.dim;
+            tp.n = D.n;
+            tp.L = D.levels;
+            tp.Lf = h->Lf;
+            tp.r = D.radius;
+            tp.gap = D.gap;
+            tp.nb = h->nb;
+            tp.N = h->N;
+            tp.row_ptr = h->row_ptr_d;
+            int tiles = 0;
+            for (int b = 0; b < h->nb; ++b) {
+                tp.tile_off[b] = tiles;
+                const Band B = band_info(D.dim, D.n, D.levels, b);
+                tiles += ((D.dim == 2) ? B.nj : 1) * ((B.nj + 15) / 16);
+            }
+            tp.tile_off[h->nb] = tiles;
+            int c = 0;
+            for (; nrhs - c >= 16; c += 16) {
+                k_apply_tc<<<tiles, 128, 0, st>>>(tp, vals, x, ldx, y, ldy, c);
+                count_launch();
+            }
+            PC_CUDA(h, cudaGetLastError());
+            if (c == nrhs) return PC_OK;
+            x += c;
+            y += c;
+            nrhs -= c;
+        }
+    }
     // vectorised path: paper order, FP32 accumulation, 16-byte aligned x/y with ldx, ldy % 4 == 0;
     // right-hand sides in groups of 16, 8 or 4, a remainder below 4 by the scalar kernel
     if constexpr (std::is_same<TA, float>::value) {
