@@ -271,12 +271,70 @@ __global__ void __launch_bounds__(256, 2) k_backward2d(const __grid_constant__ O
 struct BwdBand {
     int j, nj, P0, P1, R0, R1;  // region start offsets (off - r) and folded sizes
     int64_t Soff, Foff, rowoff;  // rowoff: canonical index of the band's first row
+    int64_t FToff;               // band offset in the term-contiguous copy of F
 };
 struct BwdDev {
-    int n, m, nb;
+    int n, m, nb, mp;  // mp: m rounded up to a multiple of 4 (stride of the copy of F)
     int64_t N;
     BwdBand band[MAXB];
 };
+
+// Term-contiguous copy of F for the gathers: FT[band][q][k] (k padded to mp with zeros).
+__global__ void k_transpose_F(const __grid_constant__ BwdDev bd, const float* __restrict__ F, float* __restrict__ FT)
+{
+    const int b = blockIdx.y;
+    const BwdBand& B = bd.band[b];
+    const int RR = B.R0 * B.R1;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= RR) return;
+    float* o = FT + B.FToff + (int64_t)q * bd.mp;
+    for (int k = 0; k < bd.mp; ++k) o[k] = (k < bd.m) ? F[B.Foff + (int64_t)k * RR + q] : 0.f;
+}
+
+// Phase 2 on the term-contiguous copy: 8 terms per thread read as two float4 per translate.
+__global__ void __launch_bounds__(256) k_bwd_dv4(const __grid_constant__ BwdDev bd, const float* __restrict__ FT,
+                                                 const float* __restrict__ S, float* __restrict__ dv)
+{
+    const int n = bd.n;
+    const int kbase = blockIdx.z * 8;
+    const int x0 = blockIdx.y * 16 + threadIdx.y, x1 = blockIdx.x * 16 + threadIdx.x;
+    if (x0 >= n || x1 >= n) return;
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), c = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int b = 0; b < bd.nb; ++b) {
+        const BwdBand& B = bd.band[b];
+        const int lg = B.j, njm = B.nj - 1;
+        const int a0 = x0 - B.P0, a1 = x1 - B.P1;
+        const int l0lo = -((-(a0 - B.R0 + 1)) >> lg), l0hi = a0 >> lg;
+        const int l1lo = -((-(a1 - B.R1 + 1)) >> lg), l1hi = a1 >> lg;
+        const int RR = B.R0 * B.R1;
+        const float* Fb = FT + B.FToff + kbase;
+        const float* Sb = S + B.Soff;
+        for (int l0 = l0lo; l0 <= l0hi; ++l0) {
+            const int q0 = a0 - (l0 << lg);
+            const int64_t rb = (int64_t)(l0 & njm) * B.nj;
+#pragma unroll 2
+            for (int l1 = l1lo; l1 <= l1hi; ++l1) {
+                const int q = q0 * B.R1 + (a1 - (l1 << lg));
+                const float s = __ldg(Sb + (rb + (l1 & njm)) * RR + q);
+                const float4 f0 = __ldg(reinterpret_cast<const float4*>(Fb + (int64_t)q * bd.mp));
+                const float4 f1 = __ldg(reinterpret_cast<const float4*>(Fb + (int64_t)q * bd.mp + 4));
+                a.x = fmaf(f0.x, s, a.x);
+                a.y = fmaf(f0.y, s, a.y);
+                a.z = fmaf(f0.z, s, a.z);
+                a.w = fmaf(f0.w, s, a.w);
+                c.x = fmaf(f1.x, s, c.x);
+                c.y = fmaf(f1.y, s, c.y);
+                c.z = fmaf(f1.z, s, c.z);
+                c.w = fmaf(f1.w, s, c.w);
+            }
+        }
+    }
+    const int64_t pix = (int64_t)x0 * n + x1;
+    const float r[8] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        if (kbase + k < bd.m) dv[(int64_t)(kbase + k) * bd.N + pix] = r[k];
+}
 
 // Phase 2.  One thread per pixel (16 x 16 tiles) and KC terms (blockIdx.z picks the chunk);
 // the translate loop is unrolled by 2 so that loads of consecutive translates overlap.

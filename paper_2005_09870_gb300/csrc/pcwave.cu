@@ -64,6 +64,7 @@ struct pc_op {
     void* S_d = nullptr;   // backward scratch: dL/ds of every row (2-D)
     unsigned long long* amask_d = nullptr;  // backward scratch: active terms per row (2-D)
     int64_t Stotal = 0;
+    int64_t FTtotal = 0;  // term-contiguous copy of F (FP32 backward), after dG in its scratch
     BwdDev bd{};
     int64_t* row_ptr_d = nullptr;
     void* theta_d = nullptr;
@@ -671,9 +672,19 @@ pc_status backward_core(pc_op* h, const T* G, T* du, T* dv, T* dF, T* dG, cudaSt
             count_launch();
         }
         constexpr int KC = 8;
-        k_bwd_dv<T, KC><<<dim3((D.n + 15) / 16, (D.n + 15) / 16, (D.m + KC - 1) / KC), dim3(16, 16), 0, st>>>(
-            h->bd, (const T*)h->F_d, S, dv);
-        count_launch();
+        if constexpr (std::is_same<T, float>::value) {
+            // term-contiguous copy of F (in the tail of the dL/dG scratch), then float4 gathers
+            float* FT = (float*)h->dG_d + (h->Gtotal + 3) / 4 * 4;  // 16-byte aligned
+            int maxRR = 0;
+            for (int b = 0; b < h->nb; ++b) maxRR = std::max(maxRR, h->bd.band[b].R0 * h->bd.band[b].R1);
+            k_transpose_F<<<dim3((maxRR + 255) / 256, h->nb), 256, 0, st>>>(h->bd, (const float*)h->F_d, FT);
+            k_bwd_dv4<<<dim3((D.n + 15) / 16, (D.n + 15) / 16, (D.m + 7) / 8), dim3(16, 16), 0, st>>>(h->bd, FT, S, dv);
+            count_launch(2);
+        } else {
+            k_bwd_dv<T, KC><<<dim3((D.n + 15) / 16, (D.n + 15) / 16, (D.m + KC - 1) / KC), dim3(16, 16), 0, st>>>(
+                h->bd, (const T*)h->F_d, S, dv);
+            count_launch();
+        }
         for (int b = 0; b < h->nb; ++b) {
             const BwdBand& B = h->bd.band[b];
             const int rows = B.nj * B.nj, RR = B.R0 * B.R1;
@@ -714,7 +725,7 @@ pc_status backward_t(pc_op* h, const T* G, T* du, T* dv, cudaStream_t st)
     if (!h->dF_d) {
         pc_status a;
         if ((a = dev_alloc(h, &h->dF_d, h->esz * h->Ftotal)) != PC_OK) return a;
-        if ((a = dev_alloc(h, &h->dG_d, h->esz * h->Gtotal)) != PC_OK) return a;
+        if ((a = dev_alloc(h, &h->dG_d, h->esz * ((h->Gtotal + 3) / 4 * 4 + h->FTtotal))) != PC_OK) return a;
         if (h->desc.dim == 2 && (a = dev_alloc(h, &h->S_d, h->esz * h->Stotal)) != PC_OK) return a;
         if (h->desc.dim == 2 &&
             (a = dev_alloc(h, &h->amask_d, sizeof(unsigned long long) * h->N * h->mwords)) != PC_OK)
@@ -1101,6 +1112,13 @@ pc_status pc_create(const pc_desc* desc, const void* u, const void* v, void* str
             So += band_rows(g, b) * (int64_t)bb.R0 * bb.R1;
         }
         h->Stotal = So;
+        bd.mp = (D.m + 3) / 4 * 4 + 4;  // the last float4 of a k-group may read 4 past m
+        int64_t FTo = 0;
+        for (int b = 0; b < h->nb; ++b) {
+            bd.band[b].FToff = FTo;
+            FTo += (int64_t)bd.band[b].R0 * bd.band[b].R1 * bd.mp;
+        }
+        h->FTtotal = (D.dim == 2 && D.precision == PC_FP32) ? FTo : 0;
     }
     // window tiles
     h->mwords = (D.m + 63) / 64;
