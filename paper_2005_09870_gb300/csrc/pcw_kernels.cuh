@@ -1013,7 +1013,27 @@ __global__ void __launch_bounds__(128) k_apply_tc(const __grid_constant__ TcAppl
     const int nvalid = min(16, Bo.nj - l1base);
     const int dense = tp.gap < 0;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // per-row stencils and block offsets (thread i: row i, all blocks)
+    // per-row stencils (all threads over (row, block) pairs), then block offsets (thread i: row i)
+    for (int e = threadIdx.x; e < 16 * tp.nb; e += blockDim.x) {
+        const int i = e / tp.nb, b2 = e - i * tp.nb;
+        const int l1 = l1base + min(i, nvalid - 1);
+        if (!block_kept(d, n, L, tp.gap, b, b2)) {
+            w1s[i][b2] = 0;
+            if (i == 0) w0s[b2] = 0;
+            continue;
+        }
+        const Band B2 = band_info(d, n, L, b2);
+        int f0 = 0, W0 = 1, f1, W1;
+        stencil(Bo.j, Bo.e1, l1, B2.j, B2.e1, tp.r, tp.Lf, n, dense, &f1, &W1);
+        if (d == 2 && i == 0) stencil(Bo.j, Bo.e0, l0, B2.j, B2.e0, tp.r, tp.Lf, n, dense, &f0, &W0);
+        f1s[i][b2] = f1;
+        w1s[i][b2] = W1;
+        if (i == 0) {
+            f0s[b2] = f0;
+            w0s[b2] = W0;
+        }
+    }
+    __syncthreads();
     if (threadIdx.x < 16) {
         const int i = threadIdx.x;
         const int l1 = l1base + min(i, nvalid - 1);
@@ -1022,21 +1042,7 @@ __global__ void __launch_bounds__(128) k_apply_tc(const __grid_constant__ TcAppl
         int acc = 0;
         for (int b2 = 0; b2 < tp.nb; ++b2) {
             boff[i][b2] = acc;
-            if (!block_kept(d, n, L, tp.gap, b, b2)) {
-                w1s[i][b2] = 0;
-                continue;
-            }
-            const Band B2 = band_info(d, n, L, b2);
-            int f0 = 0, W0 = 1, f1, W1;
-            stencil(Bo.j, Bo.e1, l1, B2.j, B2.e1, tp.r, tp.Lf, n, dense, &f1, &W1);
-            if (d == 2) stencil(Bo.j, Bo.e0, l0, B2.j, B2.e0, tp.r, tp.Lf, n, dense, &f0, &W0);
-            f1s[i][b2] = f1;
-            w1s[i][b2] = W1;
-            if (i == 0) {
-                f0s[b2] = f0;
-                w0s[b2] = W0;
-            }
-            acc += W0 * W1;
+            acc += w0s[b2] * w1s[i][b2];
         }
     }
     __syncthreads();
@@ -1060,6 +1066,7 @@ __global__ void __launch_bounds__(128) k_apply_tc(const __grid_constant__ TcAppl
             const int64_t xrow = B2.off + (int64_t)((f0 + a) & m2) * ((d == 2) ? nj2 : 0);
             const __nv_bfloat16* ag = rg + a * Wg - og;
             const __nv_bfloat16* ag8 = rg8 + a * Wg8 - og8;
+#pragma unroll 2
             for (int kc = 0; kc < K; kc += 16) {
                 unsigned A[4];
 #pragma unroll
