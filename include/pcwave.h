@@ -104,8 +104,10 @@ pc_status pc_plan_row(const pc_desc* desc, int64_t row, int64_t* cols, int64_t* 
 pc_status pc_create(const pc_desc* desc, const void* u, const void* v, void* stream,
                     pc_handle* out);
 
-/* Replaces the kernels and windows (same shapes and type as pc_create).  Theta is stale
- * until the next pc_assemble. */
+/* Replaces the kernels and windows (same shapes and type as pc_create); either may be NULL
+ * to keep the current one.  Theta is stale until the next pc_assemble.  When v is given the
+ * call rebuilds the per-pixel lists of nonzero windows and synchronises `stream` (it reads
+ * back the largest number of nonzero windows at one pixel). */
 pc_status pc_set_params(pc_handle h, const void* u, const void* v, void* stream);
 
 /* Frees everything the handle owns.  Synchronises the device first. */

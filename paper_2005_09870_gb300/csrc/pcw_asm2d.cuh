@@ -96,6 +96,52 @@ __device__ __forceinline__ void s_stage(const OpDev<T>& op, const T* __restrict_
     }
 }
 
+// s over pixel rows [q0b, q0b + nrows) of the region from the per-pixel window lists: each
+// pixel's nonzero windows in increasing k, compensated sum.
+template <typename T, int P>
+__device__ __forceinline__ void s_stage_wl(const OpDev<T>& op, const T* __restrict__ Fb, int RR, int R1, int q0b,
+                                           int nrows, int g0, int g1, T* X, int tid, int gt)
+{
+    const int tot = nrows * R1;
+    const int n = op.n, nm = n - 1;
+    const int64_t N = op.N;
+    const WSlot<T>* wl = reinterpret_cast<const WSlot<T>*>(op.wl);
+    const int S = op.wl_slots;
+    Stepper st;
+    st.init(tid, gt, R1);
+    const T* F0 = Fb + q0b * R1;
+    for (int e0 = tid; e0 < tot; e0 += gt * P) {
+        int pix[P], xo[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const bool ok = e0 + p * gt < tot;
+            const int bq = ok ? st.a : 0, q1 = ok ? st.b : 0;
+            const int gy = (g0 + q0b + bq) & nm, gx = (g1 + q1) & nm;
+            pix[p] = gy * n + gx;
+            xo[p] = bq * R1 + q1;
+            st.next();
+        }
+        T s[P], c[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) s[p] = c[p] = T(0);
+#pragma unroll 2
+        for (int sl = 0; sl < S; ++sl) {
+            WSlot<T> w[P];
+#pragma unroll
+            for (int p = 0; p < P; ++p) w[p] = load_slot(wl + (int64_t)sl * N + pix[p]);
+            T f[P];
+#pragma unroll
+            for (int p = 0; p < P; ++p) f[p] = (w[p].v != T(0)) ? __ldg(F0 + (int64_t)w[p].k * RR + xo[p]) : T(0);
+#pragma unroll
+            for (int p = 0; p < P; ++p)
+                if (w[p].v != T(0)) kahan_add(s[p], c[p], w[p].v * f[p]);
+        }
+#pragma unroll
+        for (int p = 0; p < P; ++p)
+            if (e0 + p * gt < tot) X[xo[p]] = s[p];
+    }
+}
+
 // Low/high-pass pass along one axis.  nlines lines; line l of the input starts at
 // in + l*lstride with samples `stride` apart; outputs at line*olstride + c*ostride.
 // Output c (unwrapped ro.lo + c) reads inputs 2(ro.lo + c) + [2 - LF, LF - 1].
@@ -410,7 +456,10 @@ __device__ __forceinline__ void asm2d_row(const OpDev<T>& op, const AsmCfg& cfg,
             const int r0 = bi * B;
             const int nr = first ? min(B, A0.cnt - r0) : p0.cnt;
             if (first) {
-                s_stage<T, P>(op, Fb, RR, A1.cnt, r0, nr, R.g0, R.g1, act, nact, arena, tid, gt);
+                if (op.wl)
+                    s_stage_wl<T, P>(op, Fb, RR, A1.cnt, r0, nr, R.g0, R.g1, arena, tid, gt);
+                else
+                    s_stage<T, P>(op, Fb, RR, A1.cnt, r0, nr, R.g0, R.g1, act, nact, arena, tid, gt);
                 group_sync(gt, gid);
             }
             if (lo_only)

@@ -410,6 +410,7 @@ __global__ void __launch_bounds__(128) k_bwd_dF(const __grid_constant__ BwdDev b
 #pragma unroll
     for (int k = 0; k < KC; ++k) acc[k] = T(0);
     const int lgn = log2i(B.nj);
+#pragma unroll 4
     for (int rl = rbeg; rl < rend; ++rl) {
         const int l0 = rl >> lgn, l1 = rl & (B.nj - 1);
         const int gy = ((l0 << lg) + B.P0 + q0) & (n - 1), gx = ((l1 << lg) + B.P1 + q1) & (n - 1);

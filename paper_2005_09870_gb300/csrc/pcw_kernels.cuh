@@ -45,7 +45,77 @@ struct OpDev {
     const unsigned long long* masks;  // [tile][mwords]
     int mwords, ts0, ts1, tpa0, tpa1;
     int* err;
+    const void* wl;  // per-pixel window list: slot s of pixel x at wl[s * N + x] (WSlot<T>)
+    int wl_slots;    // slots per pixel (the most nonzero windows at any pixel)
 };
+
+// One nonzero window at a pixel: term index and value (8 bytes for FP32, 16 for FP64).
+template <typename T>
+struct WSlot;
+template <>
+struct __align__(8) WSlot<float> {
+    int k;
+    float v;
+};
+template <>
+struct __align__(16) WSlot<double> {
+    long long k;
+    double v;
+};
+
+__device__ __forceinline__ WSlot<float> load_slot(const WSlot<float>* p)
+{
+    const int2 r = __ldg(reinterpret_cast<const int2*>(p));
+    WSlot<float> w;
+    w.k = r.x;
+    w.v = __int_as_float(r.y);
+    return w;
+}
+__device__ __forceinline__ WSlot<double> load_slot(const WSlot<double>* p)
+{
+    const longlong2 r = __ldg(reinterpret_cast<const longlong2*>(p));
+    WSlot<double> w;
+    w.k = r.x;
+    w.v = __longlong_as_double(r.y);
+    return w;
+}
+
+// Slots needed: the largest number of nonzero windows at one pixel (atomicMax into *out).
+template <typename T>
+__global__ void k_window_count(const T* __restrict__ v, int m, int64_t N, int* __restrict__ out)
+{
+    const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int c = 0;
+    if (x < N)
+        for (int k = 0; k < m; ++k) c += (v[(int64_t)k * N + x] != T(0));
+    c = __reduce_max_sync(0xffffffffu, (unsigned)c);
+    if ((threadIdx.x & 31) == 0) atomicMax(out, c);
+}
+
+// Per-pixel list of the nonzero windows in increasing k; unused slots hold (0, 0).
+template <typename T>
+__global__ void k_window_list(const T* __restrict__ v, int m, int64_t N, int slots, WSlot<T>* __restrict__ wl)
+{
+    const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (x >= N) return;
+    int c = 0;
+    for (int k = 0; k < m; ++k) {
+        const T val = v[(int64_t)k * N + x];
+        if (val != T(0) && c < slots) {
+            WSlot<T> w;
+            w.k = k;
+            w.v = val;
+            wl[(int64_t)c * N + x] = w;
+            ++c;
+        }
+    }
+    for (; c < slots; ++c) {
+        WSlot<T> w;
+        w.k = 0;
+        w.v = T(0);
+        wl[(int64_t)c * N + x] = w;
+    }
+}
 
 // Per-band launch parameters of k_assemble (one launch per row band, or one queue item).
 struct AsmCfg {

@@ -70,6 +70,9 @@ struct pc_op {
     void* theta_d = nullptr;
     __nv_bfloat16* theta16_d = nullptr;
     unsigned long long* masks_d = nullptr;
+    void* wl_d = nullptr;   // per-pixel window list (slots x N)
+    int wl_slots = 0;       // slots allocated and in use
+    int* cnt_d = nullptr;   // scratch int for the slot count
     int* err_d = nullptr;
     int64_t dev_bytes = 0;
     bool assembled = false;
@@ -79,6 +82,7 @@ struct pc_op {
 
 struct pc_batch {
     std::vector<pc_op*> ops;
+    std::vector<OpDev<float>> od;  // host copy of the operators' descriptors (refreshed per run)
     OpDev<float>* ops_d = nullptr;
     BatchItem* items_d = nullptr;
     int* counter_d = nullptr;
@@ -410,6 +414,8 @@ OpDev<T> make_opdev(pc_op* h)
     o.tpa0 = h->tpa0;
     o.tpa1 = h->tpa1;
     o.err = h->err_d;
+    o.wl = h->wl_d;
+    o.wl_slots = h->wl_slots;
     return o;
 }
 
@@ -778,10 +784,51 @@ pc_status backward_noalloc_t(pc_op* h, const T* G, T* du, T* dv, cudaStream_t st
     return backward_core<T>(h, G, du, dv, dF, dG, st);
 }
 
+// Window lists (rebuilt whenever the windows change): count the most nonzero windows at a
+// pixel (synchronous read of one int), grow the list if needed, fill it.
+template <typename T>
+pc_status build_window_list_t(pc_op* h, cudaStream_t st)
+{
+    const pc_desc& D = h->desc;
+    if (!h->cnt_d) {
+        pc_status a = dev_alloc(h, &h->cnt_d, sizeof(int));
+        if (a != PC_OK) return a;
+    }
+    const int blocks = (int)((h->N + 255) / 256);
+    PC_CUDA(h, cudaMemsetAsync(h->cnt_d, 0, sizeof(int), st));
+    k_window_count<T><<<blocks, 256, 0, st>>>((const T*)h->v_d, D.m, h->N, h->cnt_d);
+    count_launch();
+    int slots = 0;
+    PC_CUDA(h, cudaMemcpyAsync(&slots, h->cnt_d, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PC_CUDA(h, cudaStreamSynchronize(st));
+    slots = std::max(slots, 1);
+    if (slots > h->wl_slots || !h->wl_d) {
+        if (h->wl_d) {
+            cudaDeviceSynchronize();  // a batch on another stream may still read the old list
+            cudaFree(h->wl_d);
+            h->dev_bytes -= (int64_t)sizeof(WSlot<T>) * h->wl_slots * h->N;
+            h->wl_d = nullptr;
+        }
+        pc_status a = dev_alloc(h, &h->wl_d, sizeof(WSlot<T>) * (size_t)slots * h->N);
+        if (a != PC_OK) return a;
+    }
+    h->wl_slots = slots;
+    k_window_list<T><<<blocks, 256, 0, st>>>((const T*)h->v_d, D.m, h->N, slots, (WSlot<T>*)h->wl_d);
+    count_launch();
+    PC_CUDA(h, cudaGetLastError());
+    return PC_OK;
+}
+
+pc_status build_window_list(pc_op* h, cudaStream_t st)
+{
+    if (h->desc.dim != 2) return PC_OK;  // the 1-D rows sum over the active terms of their region
+    return h->desc.precision == PC_FP64 ? build_window_list_t<double>(h, st) : build_window_list_t<float>(h, st);
+}
+
 void free_all(pc_op* h)
 {
     void* ptrs[] = {h->u_d,  h->v_d,        h->taps64_d,  h->wav64_d,  h->tapsT_d, h->wavT_d, h->F_d,
-                    h->G_d,  h->dF_d, h->dG_d, h->S_d, h->amask_d, h->row_ptr_d,  h->theta_d,   h->theta16_d, h->masks_d, h->err_d};
+                    h->G_d,  h->dF_d, h->dG_d, h->S_d, h->amask_d, h->wl_d, h->cnt_d, h->row_ptr_d,  h->theta_d,   h->theta16_d, h->masks_d, h->err_d};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -823,7 +870,7 @@ pc_status batch_build(pc_handle* ops, int count, cudaStream_t st, bool capture, 
     if (!ops || count < 1) return fail(nullptr, PC_ERR_INVALID_ARG, "batch needs at least one operator");
     pc_batch* B = new (std::nothrow) pc_batch();
     if (!B) return fail(nullptr, PC_ERR_OOM, "host allocation failed");
-    std::vector<OpDev<float>> od;
+    std::vector<OpDev<float>>& od = B->od;
     struct Cand {
         double cost;
         BatchItem it;
@@ -1154,6 +1201,7 @@ pc_status pc_create(const pc_desc* desc, const void* u, const void* v, void* str
         fail(h, PC_ERR_CUDA, "upload failed: %s", cudaGetErrorString(e));
         return bail(PC_ERR_CUDA);
     }
+    if ((st = build_window_list(h, s)) != PC_OK) return bail(st);
     *out = h;
     return PC_OK;
 }
@@ -1167,6 +1215,7 @@ pc_status pc_set_params(pc_handle h, const void* u, const void* v, void* stream)
     if (v) PC_CUDA(h, cudaMemcpyAsync(h->v_d, v, h->esz * D.m * h->N, cudaMemcpyDefault, s));
     h->assembled = false;
     h->prepared = false;
+    if (v) return build_window_list(h, s);
     return PC_OK;
 }
 
@@ -1239,7 +1288,11 @@ pc_status pc_batch_create(pc_handle* ops, int count, void* stream, pc_batch_hand
 pc_status pc_batch_run(pc_batch_handle b, void* stream)
 {
     if (!b || !b->exec) return fail(nullptr, PC_ERR_INVALID_ARG, "batch is NULL or not captured");
-    cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
+    // descriptors may have changed (window lists are rebuilt by pc_set_params): refresh them
+    for (size_t i = 0; i < b->ops.size(); ++i) b->od[i] = make_opdev<float>(b->ops[i]);
+    cudaError_t e = cudaMemcpyAsync(b->ops_d, b->od.data(), sizeof(OpDev<float>) * b->od.size(),
+                                    cudaMemcpyHostToDevice, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
     if (e != cudaSuccess) return fail(nullptr, PC_ERR_CUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
     count_launch(b->kernels_per_run);
     for (pc_op* h : b->ops) {
