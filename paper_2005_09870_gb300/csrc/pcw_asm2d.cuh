@@ -456,7 +456,9 @@ __device__ __forceinline__ void asm2d_row(const OpDev<T>& op, const AsmCfg& cfg,
             const int r0 = bi * B;
             const int nr = first ? min(B, A0.cnt - r0) : p0.cnt;
             if (first) {
-                if (op.wl)
+                // per-pixel lists pay off when the region's active set is much larger than the
+                // number of windows nonzero at one pixel (coarse rows spanning many windows)
+                if (op.wl && nact >= 2 * op.wl_slots)
                     s_stage_wl<T, P>(op, Fb, RR, A1.cnt, r0, nr, R.g0, R.g1, arena, tid, gt);
                 else
                     s_stage<T, P>(op, Fb, RR, A1.cnt, r0, nr, R.g0, R.g1, act, nact, arena, tid, gt);
