@@ -519,7 +519,7 @@ struct BatchItem {
     AsmCfg cfg;
 };
 
-__global__ void __launch_bounds__(256, 1) k_assemble_batch(const OpDev<float>* __restrict__ ops,
+__global__ void __launch_bounds__(256, 2) k_assemble_batch(const OpDev<float>* __restrict__ ops,
                                                            const BatchItem* __restrict__ items, int nitems,
                                                            int* __restrict__ counter)
 {

@@ -77,6 +77,12 @@ struct pc_op {
     int64_t dev_bytes = 0;
     bool assembled = false;
     bool prepared = false;  // stage 0 ran for the current parameters
+    // FP32 row assembly through the persistent work queue (one launch over all bands)
+    BatchItem* q_items_d = nullptr;
+    OpDev<float>* q_op_d = nullptr;
+    int* q_counter_d = nullptr;
+    int q_nitems = 0, q_grid = 0;
+    size_t q_smem = 0;
     std::string err = "no error";
 };
 
@@ -500,6 +506,19 @@ pc_status assemble_t(pc_op* h, cudaStream_t st, int stage_mask)
     }
     if (!(stage_mask & 2)) return PC_OK;
     if (!h->prepared) return fail(h, PC_ERR_INVALID_ARG, "assembly stage 1 before stage 0");
+    if constexpr (std::is_same<T, float>::value) {
+        if (h->q_items_d && h->q_smem <= 110 * 1024) {
+            // one persistent launch over all row bands, longest work items first
+            const OpDev<float> od = make_opdev<float>(h);
+            PC_CUDA(h, cudaMemcpyAsync(h->q_op_d, &od, sizeof(od), cudaMemcpyHostToDevice, st));
+            PC_CUDA(h, cudaMemsetAsync(h->q_counter_d, 0, sizeof(int), st));
+            k_assemble_batch<<<h->q_grid, 256, h->q_smem, st>>>(h->q_op_d, h->q_items_d, h->q_nitems, h->q_counter_d);
+            count_launch();
+            PC_CUDA(h, cudaGetLastError());
+            h->assembled = true;
+            return PC_OK;
+        }
+    }
     // A5: one launch per row band
     OpDev<T> od = make_opdev<T>(h);
     for (const BandPlan& bp : h->plan) {
@@ -828,9 +847,70 @@ pc_status build_window_list(pc_op* h, cudaStream_t st)
 void free_all(pc_op* h)
 {
     void* ptrs[] = {h->u_d,  h->v_d,        h->taps64_d,  h->wav64_d,  h->tapsT_d, h->wavT_d, h->F_d,
-                    h->G_d,  h->dF_d, h->dG_d, h->S_d, h->amask_d, h->wl_d, h->cnt_d, h->row_ptr_d,  h->theta_d,   h->theta16_d, h->masks_d, h->err_d};
+                    h->G_d,  h->dF_d, h->dG_d, h->S_d, h->amask_d, h->wl_d, h->cnt_d, h->q_items_d, h->q_op_d, h->q_counter_d, h->row_ptr_d,  h->theta_d,   h->theta16_d, h->masks_d, h->err_d};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+}
+
+// Work items of one operator: every row band split into runs of rows of similar cost
+// (region arena + stored entries per row), with the band's plan.
+struct ItemCand {
+    double cost;
+    BatchItem it;
+};
+
+void make_items(pc_op* h, int op_index, std::vector<ItemCand>* out, size_t* smem)
+{
+    for (const BandPlan& bp : h->plan) {
+        const Band B = band_info(h->desc.dim, h->desc.n, h->desc.levels, bp.b);
+        const double entries = (double)(h->row_ptr_h[B.off + bp.rows] - h->row_ptr_h[B.off]) / bp.rows;
+        const double row_cost = (double)bp.cfg.arena + entries;
+        int per = (int)std::max(1.0, std::floor(60000.0 / row_cost));
+        per = std::max(bp.cfg.rpc, (per / bp.cfg.rpc) * bp.cfg.rpc);
+        for (int r0 = 0; r0 < bp.rows; r0 += per) {
+            ItemCand c;
+            c.it.op = op_index;
+            c.it.dim = h->desc.dim;
+            c.it.lft = (h->desc.dim == 2) ? lf_template(h->Lf) : h->Lf;
+            c.it.pad = 0;
+            c.it.cfg = bp.cfg;
+            c.it.cfg.row0 = r0;
+            c.it.cfg.rows = std::min(per, bp.rows - r0);
+            c.cost = row_cost * c.it.cfg.rows;
+            out->push_back(c);
+            *smem = std::max(*smem, bp.smem);
+        }
+    }
+}
+
+// (Re)builds the single-operator queue from the current plan.
+pc_status build_queue(pc_op* h)
+{
+    if (h->desc.precision != PC_FP32) return PC_OK;
+    std::vector<ItemCand> cands;
+    size_t smem = 0;
+    make_items(h, 0, &cands, &smem);
+    std::stable_sort(cands.begin(), cands.end(), [](const ItemCand& a, const ItemCand& b) { return a.cost > b.cost; });
+    std::vector<BatchItem> items;
+    for (const ItemCand& c : cands) items.push_back(c.it);
+    if (h->q_items_d) {
+        cudaFree(h->q_items_d);
+        h->q_items_d = nullptr;
+    }
+    pc_status a;
+    if ((a = dev_alloc(h, &h->q_items_d, sizeof(BatchItem) * items.size())) != PC_OK) return a;
+    if (!h->q_op_d && (a = dev_alloc(h, &h->q_op_d, sizeof(OpDev<float>))) != PC_OK) return a;
+    if (!h->q_counter_d && (a = dev_alloc(h, &h->q_counter_d, sizeof(int))) != PC_OK) return a;
+    PC_CUDA(h, cudaMemcpy(h->q_items_d, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice));
+    PC_CUDA(h, cudaFuncSetAttribute(k_assemble_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024));
+    h->q_nitems = (int)items.size();
+    h->q_smem = smem;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_assemble_batch, 256, smem);
+    h->q_grid = std::max(1, sms * std::max(1, per_sm));
+    return PC_OK;
 }
 
 // Enqueues one run of a batch on st: every operator's stage 0, the queue reset, the
@@ -871,11 +951,7 @@ pc_status batch_build(pc_handle* ops, int count, cudaStream_t st, bool capture, 
     pc_batch* B = new (std::nothrow) pc_batch();
     if (!B) return fail(nullptr, PC_ERR_OOM, "host allocation failed");
     std::vector<OpDev<float>>& od = B->od;
-    struct Cand {
-        double cost;
-        BatchItem it;
-    };
-    std::vector<Cand> cands;
+    std::vector<ItemCand> cands;
     for (int i = 0; i < count; ++i) {
         pc_op* h = ops[i];
         if (!h) {
@@ -888,34 +964,12 @@ pc_status batch_build(pc_handle* ops, int count, cudaStream_t st, bool capture, 
         }
         B->ops.push_back(h);
         od.push_back(make_opdev<float>(h));
-        for (const BandPlan& bp : h->plan) {
-            // cost of a row: its region and its stored entries
-            const double entries = (double)(h->row_ptr_h[band_info(h->desc.dim, h->desc.n, h->desc.levels, bp.b).off +
-                                                         bp.rows] -
-                                            h->row_ptr_h[band_info(h->desc.dim, h->desc.n, h->desc.levels, bp.b).off]) /
-                                   bp.rows;
-            const double area = (double)bp.cfg.arena;
-            const double row_cost = area + entries;
-            int per = (int)std::max(1.0, std::floor(60000.0 / row_cost));
-            per = std::max(bp.cfg.rpc, (per / bp.cfg.rpc) * bp.cfg.rpc);
-            for (int r0 = 0; r0 < bp.rows; r0 += per) {
-                Cand c;
-                c.it.op = i;
-                c.it.dim = h->desc.dim;
-                c.it.lft = (h->desc.dim == 2) ? lf_template(h->Lf) : h->Lf;
-                c.it.pad = 0;
-                c.it.cfg = bp.cfg;
-                c.it.cfg.row0 = r0;
-                c.it.cfg.rows = std::min(per, bp.rows - r0);
-                c.cost = row_cost * c.it.cfg.rows;
-                cands.push_back(c);
-                B->smem = std::max(B->smem, bp.smem);
-            }
-        }
+        make_items(h, i, &cands, &B->smem);
     }
-    std::stable_sort(cands.begin(), cands.end(), [](const Cand& a, const Cand& b) { return a.cost > b.cost; });
+    std::stable_sort(cands.begin(), cands.end(),
+                     [](const ItemCand& a, const ItemCand& b) { return a.cost > b.cost; });
     std::vector<BatchItem> items;
-    for (const Cand& c : cands) items.push_back(c.it);
+    for (const ItemCand& c : cands) items.push_back(c.it);
     B->nitems = (int)items.size();
     cudaError_t e;
     if ((e = cudaMalloc(&B->ops_d, sizeof(OpDev<float>) * od.size())) ||
@@ -1009,6 +1063,8 @@ pc_status autotune_t(pc_op* h, cudaStream_t st)
         cur = best;
     }
     PC_CUDA(h, cudaGetLastError());
+    pc_status qs = build_queue(h);
+    if (qs != PC_OK) return qs;
     // leave Theta assembled with the tuned plan
     return assemble_t<T>(h, st, 2);
 }
@@ -1202,6 +1258,7 @@ pc_status pc_create(const pc_desc* desc, const void* u, const void* v, void* str
         return bail(PC_ERR_CUDA);
     }
     if ((st = build_window_list(h, s)) != PC_OK) return bail(st);
+    if ((st = build_queue(h)) != PC_OK) return bail(st);
     *out = h;
     return PC_OK;
 }
