@@ -137,42 +137,25 @@ __device__ __forceinline__ void read_level(const OpDev<T>& op, const Row2& R, co
     }
 }
 
-// Phase 1.  Same plan (groups, arenas) as k_assemble2d.  Sout: dL/ds of every row.
+// Phase 1, one stored 2-D row by one thread group (same plan, arenas and filter area as the
+// forward).  Writes dL/ds of the row to Sout + Sband + rl * RR and its active-term mask.
 template <typename T, int LF>
-__global__ void __launch_bounds__(256, 2) k_backward2d(const __grid_constant__ OpDev<T> op, const AsmCfg cfg,
-                                                       const T* __restrict__ Gth, T* __restrict__ Sout,
-                                                       const int64_t Sband, unsigned long long* __restrict__ amask_out)
+__device__ __forceinline__ void bwd2d_row(const OpDev<T>& op, const AsmCfg& cfg, int rl, const T* fS, int* meta,
+                                          T* arena, int gid, int tid, const T* __restrict__ Gth,
+                                          T* __restrict__ Sout, int64_t Sband,
+                                          unsigned long long* __restrict__ amask_out)
 {
     constexpr int CH = 4;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int gt = cfg.gt;
-    const int gid = threadIdx.x / gt, tid = threadIdx.x - gid * gt;
-    const int n = op.n, L = op.L, Lf = op.Lf;
-
-    T* fS = reinterpret_cast<T*>(smem_raw);
-    int* meta = reinterpret_cast<int*>(smem_raw + sizeof(T) * cfg.filt) + gid * META_INTS;
-    T* arena = reinterpret_cast<T*>(smem_raw + sizeof(T) * cfg.filt + sizeof(int) * cfg.rpc * META_INTS) +
-               (int64_t)gid * cfg.arena;
+    const int n = op.n, Lf = op.Lf;
     T* const arena_end = arena + cfg.arena;
     const int A = cfg.arena;
-
-    const Band Bo = band_info(2, n, L, cfg.b);
-    const int dense = op.gap < 0;
-    const int jlo = dense ? 1 : max(1, Bo.j - op.gap);
-    const int k0 = jlo - 1;
-    const int lenk = (k0 > 0) ? wav_len(k0, Lf) : 0;
-    for (int i = threadIdx.x; i < LF; i += blockDim.x) {
-        fS[i] = (i < Lf) ? op.taps[i] : T(0);
-        fS[LF + i] = (i >= LF - Lf) ? op.taps[Lf + i - (LF - Lf)] : T(0);
-    }
-    for (int i = threadIdx.x; i < lenk; i += blockDim.x) fS[2 * LF + i] = op.wav[op.wofs[k0] + i];
-    __syncthreads();
-
-    const int rloc = blockIdx.x * cfg.rpc + gid;
-    if (rloc >= cfg.rows) return;
-    const int rl = cfg.row0 + rloc;
+    const int k0_band = (op.gap < 0) ? 0 : max(1, band_info(2, n, op.L, cfg.b).j - op.gap) - 1;
+    const int lenk = (k0_band > 0) ? wav_len(k0_band, Lf) : 0;
     const Row2 R = row2_setup(op, cfg.b, rl);
     if (!row2_meta(op, R, cfg.b, meta, tid, gt, gid)) return;
+    const int k0 = R.k0;
+    (void)k0_band;
 
     T hr[LF], gr[LF];
 #pragma unroll
@@ -264,6 +247,93 @@ __global__ void __launch_bounds__(256, 2) k_backward2d(const __grid_constant__ O
             }
             (void)n_in;
         }
+    }
+}
+
+// Phase 1 as one launch per row band.
+template <typename T, int LF>
+__global__ void __launch_bounds__(256, 2) k_backward2d(const __grid_constant__ OpDev<T> op, const AsmCfg cfg,
+                                                       const T* __restrict__ Gth, T* __restrict__ Sout,
+                                                       const int64_t Sband, unsigned long long* __restrict__ amask_out)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int gt = cfg.gt;
+    const int gid = threadIdx.x / gt, tid = threadIdx.x - gid * gt;
+    T* fS = reinterpret_cast<T*>(smem_raw);
+    int* meta = reinterpret_cast<int*>(smem_raw + sizeof(T) * cfg.filt) + gid * META_INTS;
+    T* arena = reinterpret_cast<T*>(smem_raw + sizeof(T) * cfg.filt + sizeof(int) * cfg.rpc * META_INTS) +
+               (int64_t)gid * cfg.arena;
+    load_filters2d<T, LF>(op, cfg.b, fS);
+    __syncthreads();
+    const int rloc = blockIdx.x * cfg.rpc + gid;
+    if (rloc >= cfg.rows) return;
+    bwd2d_row<T, LF>(op, cfg, cfg.row0 + rloc, fS, meta, arena, gid, tid, Gth, Sout, Sband, amask_out);
+}
+
+// Phase 1 through the persistent work queue of the forward (FP32): one launch over all bands.
+struct BwdQueue {
+    const float* G;
+    float* S;
+    unsigned long long* amask;
+    int64_t Soff[MAXB];
+};
+
+__global__ void __launch_bounds__(256, 2) k_backward_queue(const OpDev<float>* __restrict__ opd,
+                                                           const BatchItem* __restrict__ items, int nitems,
+                                                           int* __restrict__ counter, const __grid_constant__ BwdQueue bq)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ OpDev<float> op_s;
+    __shared__ BatchItem it_s;
+    __shared__ int idx_s;
+    {
+        const int* src = reinterpret_cast<const int*>(opd);
+        int* dst = reinterpret_cast<int*>(&op_s);
+        for (int i = threadIdx.x; i < (int)(sizeof(OpDev<float>) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    }
+    for (;;) {
+        if (threadIdx.x == 0) idx_s = atomicAdd(counter, 1);
+        __syncthreads();
+        const int idx = idx_s;
+        if (idx >= nitems) return;
+        if (threadIdx.x == 0) it_s = items[idx];
+        __syncthreads();
+        const AsmCfg cfg = it_s.cfg;
+        const int lft = it_s.lft;
+        float* fS = reinterpret_cast<float*>(smem_raw);
+        if (lft == 2)
+            load_filters2d<float, 2>(op_s, cfg.b, fS);
+        else if (lft == 4)
+            load_filters2d<float, 4>(op_s, cfg.b, fS);
+        else if (lft == 8)
+            load_filters2d<float, 8>(op_s, cfg.b, fS);
+        else
+            load_filters2d<float, 20>(op_s, cfg.b, fS);
+        __syncthreads();
+        const int gt = cfg.gt;
+        const int gid = threadIdx.x / gt, tid = threadIdx.x - gid * gt;
+        if (gid < cfg.rpc) {
+            int* meta = reinterpret_cast<int*>(smem_raw + sizeof(float) * cfg.filt) + gid * META_INTS;
+            float* arena = reinterpret_cast<float*>(smem_raw + sizeof(float) * cfg.filt +
+                                                    sizeof(int) * cfg.rpc * META_INTS) +
+                           (int64_t)gid * cfg.arena;
+            const int64_t Sband = bq.Soff[cfg.b];
+            for (int rb = 0; rb < cfg.rows; rb += cfg.rpc) {
+                const int rloc = rb + gid;
+                if (rloc >= cfg.rows) break;
+                const int rl = cfg.row0 + rloc;
+                if (lft == 2)
+                    bwd2d_row<float, 2>(op_s, cfg, rl, fS, meta, arena, gid, tid, bq.G, bq.S, Sband, bq.amask);
+                else if (lft == 4)
+                    bwd2d_row<float, 4>(op_s, cfg, rl, fS, meta, arena, gid, tid, bq.G, bq.S, Sband, bq.amask);
+                else if (lft == 8)
+                    bwd2d_row<float, 8>(op_s, cfg, rl, fS, meta, arena, gid, tid, bq.G, bq.S, Sband, bq.amask);
+                else
+                    bwd2d_row<float, 20>(op_s, cfg, rl, fS, meta, arena, gid, tid, bq.G, bq.S, Sband, bq.amask);
+                group_sync(gt, gid);
+            }
+        }
+        __syncthreads();
     }
 }
 

@@ -689,13 +689,42 @@ pc_status backward_core(pc_op* h, const T* G, T* du, T* dv, T* dF, T* dG, cudaSt
     PC_CUDA(h, cudaMemsetAsync(dF, 0, h->esz * h->Ftotal, st));
     OpDev<T> od = make_opdev<T>(h);
     if (D.dim == 2 && S) {
-        for (const BandPlan& bp : h->plan) {
-            const int ctas = (bp.rows + bp.cfg.rpc - 1) / bp.cfg.rpc;
-            const int threads = bp.cfg.gt * bp.cfg.rpc;
-            pc_status ls = launch_bwd2d<T>(h, od, bp, ctas, threads, G, S, h->bd.band[bp.b].Soff, amask, st);
-            if (ls != PC_OK) return ls;
-            count_launch();
+        bool queued = false;
+        if constexpr (std::is_same<T, float>::value) {
+            if (h->q_items_d && h->q_smem <= 110 * 1024) {
+                // phase 1 through the operator's work queue: one launch over all row bands
+                static bool attr = false;
+                if (!attr) {
+                    PC_CUDA(h, cudaFuncSetAttribute(k_backward_queue, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    110 * 1024));
+                    attr = true;
+                }
+                const OpDev<float> odq = make_opdev<float>(h);
+                PC_CUDA(h, cudaMemcpyAsync(h->q_op_d, &odq, sizeof(odq), cudaMemcpyHostToDevice, st));
+                PC_CUDA(h, cudaMemsetAsync(h->q_counter_d, 0, sizeof(int), st));
+                BwdQueue bq{};
+                bq.G = G;
+                bq.S = S;
+                bq.amask = amask;
+                for (int b = 0; b < h->nb; ++b) bq.Soff[b] = h->bd.band[b].Soff;
+                int dev = 0, sms = 0, per_sm = 0;
+                cudaGetDevice(&dev);
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward_queue, 256, h->q_smem);
+                k_backward_queue<<<std::max(1, sms * std::max(1, per_sm)), 256, h->q_smem, st>>>(
+                    h->q_op_d, h->q_items_d, h->q_nitems, h->q_counter_d, bq);
+                count_launch();
+                queued = true;
+            }
         }
+        if (!queued)
+            for (const BandPlan& bp : h->plan) {
+                const int ctas = (bp.rows + bp.cfg.rpc - 1) / bp.cfg.rpc;
+                const int threads = bp.cfg.gt * bp.cfg.rpc;
+                pc_status ls = launch_bwd2d<T>(h, od, bp, ctas, threads, G, S, h->bd.band[bp.b].Soff, amask, st);
+                if (ls != PC_OK) return ls;
+                count_launch();
+            }
         constexpr int KC = 8;
         if constexpr (std::is_same<T, float>::value) {
             // term-contiguous copy of F (in the tail of the dL/dG scratch), then float4 gathers
