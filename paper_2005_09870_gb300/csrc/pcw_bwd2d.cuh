@@ -349,7 +349,8 @@ struct BwdDev {
     BwdBand band[MAXB];
 };
 
-// Term-contiguous copy of F for the gathers: FT[band][q][k] (k padded to mp with zeros).
+// Copy of F grouped by 4 terms for the gathers: FT[band][k/4][q][k%4] (terms padded to mp with
+// zeros), so that consecutive region positions read consecutive float4s.
 __global__ void k_transpose_F(const __grid_constant__ BwdDev bd, const float* __restrict__ F, float* __restrict__ FT)
 {
     const int b = blockIdx.y;
@@ -357,8 +358,8 @@ __global__ void k_transpose_F(const __grid_constant__ BwdDev bd, const float* __
     const int RR = B.R0 * B.R1;
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= RR) return;
-    float* o = FT + B.FToff + (int64_t)q * bd.mp;
-    for (int k = 0; k < bd.mp; ++k) o[k] = (k < bd.m) ? F[B.Foff + (int64_t)k * RR + q] : 0.f;
+    for (int k = 0; k < bd.mp; ++k)
+        FT[B.FToff + ((int64_t)(k >> 2) * RR + q) * 4 + (k & 3)] = (k < bd.m) ? F[B.Foff + (int64_t)k * RR + q] : 0.f;
 }
 
 // Phase 2 on the term-contiguous copy: 8 terms per thread read as two float4 per translate.
@@ -377,7 +378,8 @@ __global__ void __launch_bounds__(256) k_bwd_dv4(const __grid_constant__ BwdDev 
         const int l0lo = -((-(a0 - B.R0 + 1)) >> lg), l0hi = a0 >> lg;
         const int l1lo = -((-(a1 - B.R1 + 1)) >> lg), l1hi = a1 >> lg;
         const int RR = B.R0 * B.R1;
-        const float* Fb = FT + B.FToff + kbase;
+        const float4* Fa = reinterpret_cast<const float4*>(FT + B.FToff) + (int64_t)(kbase >> 2) * RR;
+        const float4* Fc = Fa + RR;
         const float* Sb = S + B.Soff;
         for (int l0 = l0lo; l0 <= l0hi; ++l0) {
             const int q0 = a0 - (l0 << lg);
@@ -386,8 +388,8 @@ __global__ void __launch_bounds__(256) k_bwd_dv4(const __grid_constant__ BwdDev 
             for (int l1 = l1lo; l1 <= l1hi; ++l1) {
                 const int q = q0 * B.R1 + (a1 - (l1 << lg));
                 const float s = __ldg(Sb + (rb + (l1 & njm)) * RR + q);
-                const float4 f0 = __ldg(reinterpret_cast<const float4*>(Fb + (int64_t)q * bd.mp));
-                const float4 f1 = __ldg(reinterpret_cast<const float4*>(Fb + (int64_t)q * bd.mp + 4));
+                const float4 f0 = __ldg(Fa + q);
+                const float4 f1 = __ldg(Fc + q);
                 a.x = fmaf(f0.x, s, a.x);
                 a.y = fmaf(f0.y, s, a.y);
                 a.z = fmaf(f0.z, s, a.z);
