@@ -467,17 +467,24 @@ __global__ void __launch_bounds__(256) k_bwd_dv(const __grid_constant__ BwdDev b
 template <typename T, int KC>
 __global__ void __launch_bounds__(128) k_bwd_dF(const __grid_constant__ BwdDev bd, const T* __restrict__ v,
                                                 const T* __restrict__ S, const unsigned long long* __restrict__ amask,
-                                                int mwords, T* __restrict__ dF, int b, int chunk)
+                                                int mwords, T* __restrict__ dF, const int* __restrict__ blk_off,
+                                                int chunk)
 {
+    // blockIdx.x enumerates (band, region block of 128, chunk of rows) over all bands
+    int b = 0;
+    while (b + 1 < bd.nb && (int)blockIdx.x >= blk_off[b + 1]) ++b;
     const BwdBand& B = bd.band[b];
+    const int bl = blockIdx.x - blk_off[b];
+    const int qblocks = (B.R0 * B.R1 + 127) / 128;
+    const int qb = bl % qblocks, cb = bl / qblocks;
     const int RR = B.R0 * B.R1;
-    const int q = blockIdx.x * 128 + threadIdx.x;
+    const int q = qb * 128 + threadIdx.x;
     if (q >= RR) return;
     const int kbase = blockIdx.z * KC;
     const int n = bd.n, lg = B.j;
     const int q0 = q / B.R1, q1 = q - q0 * B.R1;
     const int rows = B.nj * B.nj;
-    const int rbeg = blockIdx.y * chunk, rend = min(rows, rbeg + chunk);
+    const int rbeg = cb * chunk, rend = min(rows, rbeg + chunk);
     T acc[KC];
 #pragma unroll
     for (int k = 0; k < KC; ++k) acc[k] = T(0);

@@ -73,6 +73,7 @@ struct pc_op {
     void* wl_d = nullptr;   // per-pixel window list (slots x N)
     int wl_slots = 0;       // slots allocated and in use
     int* cnt_d = nullptr;   // scratch int for the slot count
+    int* dfoff_d = nullptr; // block offsets of the dL/dF launch per band
     int* err_d = nullptr;
     int64_t dev_bytes = 0;
     bool assembled = false;
@@ -739,12 +740,20 @@ pc_status backward_core(pc_op* h, const T* G, T* du, T* dv, T* dF, T* dG, cudaSt
                 h->bd, (const T*)h->F_d, S, dv);
             count_launch();
         }
-        for (int b = 0; b < h->nb; ++b) {
-            const BwdBand& B = h->bd.band[b];
-            const int rows = B.nj * B.nj, RR = B.R0 * B.R1;
+        {
+            // one launch over all bands: blocks (band, 128 region positions, 32 rows)
             const int chunk = 32;
-            k_bwd_dF<T, 16><<<dim3((RR + 127) / 128, (rows + chunk - 1) / chunk, (D.m + 15) / 16), 128, 0, st>>>(
-                h->bd, (const T*)h->v_d, S, amask, h->mwords, dF, b, chunk);
+            int offs[MAXB + 1];
+            int tot = 0;
+            for (int b = 0; b < h->nb; ++b) {
+                const BwdBand& B = h->bd.band[b];
+                offs[b] = tot;
+                tot += ((B.R0 * B.R1 + 127) / 128) * ((B.nj * B.nj + chunk - 1) / chunk);
+            }
+            offs[h->nb] = tot;
+            PC_CUDA(h, cudaMemcpyAsync(h->dfoff_d, offs, sizeof(int) * (h->nb + 1), cudaMemcpyHostToDevice, st));
+            k_bwd_dF<T, 16><<<dim3(tot, 1, (D.m + 15) / 16), 128, 0, st>>>(h->bd, (const T*)h->v_d, S, amask,
+                                                                          h->mwords, dF, h->dfoff_d, chunk);
             count_launch();
         }
     } else {
@@ -784,6 +793,7 @@ pc_status backward_t(pc_op* h, const T* G, T* du, T* dv, cudaStream_t st)
         if (h->desc.dim == 2 &&
             (a = dev_alloc(h, &h->amask_d, sizeof(unsigned long long) * h->N * h->mwords)) != PC_OK)
             return a;
+        if (h->desc.dim == 2 && (a = dev_alloc(h, &h->dfoff_d, sizeof(int) * (MAXB + 1))) != PC_OK) return a;
     }
     return backward_core<T>(h, G, du, dv, (T*)h->dF_d, (T*)h->dG_d, st, (T*)h->S_d, h->amask_d);
 }
@@ -876,7 +886,7 @@ pc_status build_window_list(pc_op* h, cudaStream_t st)
 void free_all(pc_op* h)
 {
     void* ptrs[] = {h->u_d,  h->v_d,        h->taps64_d,  h->wav64_d,  h->tapsT_d, h->wavT_d, h->F_d,
-                    h->G_d,  h->dF_d, h->dG_d, h->S_d, h->amask_d, h->wl_d, h->cnt_d, h->q_items_d, h->q_op_d, h->q_counter_d, h->row_ptr_d,  h->theta_d,   h->theta16_d, h->masks_d, h->err_d};
+                    h->G_d,  h->dF_d, h->dG_d, h->S_d, h->amask_d, h->wl_d, h->cnt_d, h->dfoff_d, h->q_items_d, h->q_op_d, h->q_counter_d, h->row_ptr_d,  h->theta_d,   h->theta16_d, h->masks_d, h->err_d};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
