@@ -50,11 +50,11 @@ struct Stepper {
     }
 };
 
-// s over pixel rows [q0b, q0b + nrows) of the region into X (row pitch R1)
+// s over pixel rows [q0b, q0b + nrows) of the region (F rows of pitch R1) into X (row pitch XP)
 template <typename T, int P>
 __device__ __forceinline__ void s_stage(const OpDev<T>& op, const T* __restrict__ Fb, int RR, int R1, int q0b,
-                                        int nrows, int g0, int g1, const unsigned char* act, int nact, T* X, int tid,
-                                        int gt)
+                                        int nrows, int g0, int g1, const unsigned char* act, int nact, T* X, int XP,
+                                        int tid, int gt)
 {
     const int tot = nrows * R1;
     const int n = op.n, nm = n - 1;
@@ -62,7 +62,7 @@ __device__ __forceinline__ void s_stage(const OpDev<T>& op, const T* __restrict_
     Stepper st;
     st.init(tid, gt, R1);
     for (int e0 = tid; e0 < tot; e0 += gt * P) {
-        int pix[P], xo[P];
+        int pix[P], xo[P], xs[P];
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             const bool ok = e0 + p * gt < tot;
@@ -70,6 +70,7 @@ __device__ __forceinline__ void s_stage(const OpDev<T>& op, const T* __restrict_
             const int gy = (g0 + q0b + bq) & nm, gx = (g1 + q1) & nm;
             pix[p] = gy * n + gx;
             xo[p] = bq * R1 + q1;
+            xs[p] = bq * XP + q1;
             st.next();
         }
         T s[P], c[P];
@@ -92,7 +93,7 @@ __device__ __forceinline__ void s_stage(const OpDev<T>& op, const T* __restrict_
         }
 #pragma unroll
         for (int p = 0; p < P; ++p)
-            if (e0 + p * gt < tot) X[xo[p]] = s[p];
+            if (e0 + p * gt < tot) X[xs[p]] = s[p];
     }
 }
 
@@ -100,7 +101,7 @@ __device__ __forceinline__ void s_stage(const OpDev<T>& op, const T* __restrict_
 // pixel's nonzero windows in increasing k, compensated sum.
 template <typename T, int P>
 __device__ __forceinline__ void s_stage_wl(const OpDev<T>& op, const T* __restrict__ Fb, int RR, int R1, int q0b,
-                                           int nrows, int g0, int g1, T* X, int tid, int gt)
+                                           int nrows, int g0, int g1, T* X, int XP, int tid, int gt)
 {
     const int tot = nrows * R1;
     const int n = op.n, nm = n - 1;
@@ -111,7 +112,7 @@ __device__ __forceinline__ void s_stage_wl(const OpDev<T>& op, const T* __restri
     st.init(tid, gt, R1);
     const T* F0 = Fb + q0b * R1;
     for (int e0 = tid; e0 < tot; e0 += gt * P) {
-        int pix[P], xo[P];
+        int pix[P], xo[P], xs[P];
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             const bool ok = e0 + p * gt < tot;
@@ -119,6 +120,7 @@ __device__ __forceinline__ void s_stage_wl(const OpDev<T>& op, const T* __restri
             const int gy = (g0 + q0b + bq) & nm, gx = (g1 + q1) & nm;
             pix[p] = gy * n + gx;
             xo[p] = bq * R1 + q1;
+            xs[p] = bq * XP + q1;
             st.next();
         }
         T s[P], c[P];
@@ -138,17 +140,36 @@ __device__ __forceinline__ void s_stage_wl(const OpDev<T>& op, const T* __restri
         }
 #pragma unroll
         for (int p = 0; p < P; ++p)
-            if (e0 + p * gt < tot) X[xo[p]] = s[p];
+            if (e0 + p * gt < tot) X[xs[p]] = s[p];
     }
 }
 
-// Low/high-pass pass along one axis.  nlines lines; line l of the input starts at
-// in + l*lstride with samples `stride` apart; outputs at line*olstride + c*ostride.
-// Output c (unwrapped ro.lo + c) reads inputs 2(ro.lo + c) + [2 - LF, LF - 1].
+// Zeroes the margins of a padded array: [0, lead) and the pitch - len elements after each of
+// its nl lines (line l at lead + l * pitch).  One line's gap (or the lead) per thread, as up to
+// GMAX >= max(lead, pitch - len) unrolled stores.
+template <typename T, int GMAX>
+__device__ __forceinline__ void zero_gaps(T* a, int lead, int nl, int len, int pitch, int tid, int gt)
+{
+    const int g = pitch - len;
+    for (int l = tid; l <= nl; l += gt) {
+        T* p = (l < nl) ? a + lead + l * pitch + len : a;
+        const int cnt = (l < nl) ? g : lead;
+#pragma unroll
+        for (int i = 0; i < GMAX; ++i)
+            if (i < cnt) p[i] = T(0);
+    }
+}
+
+// Low/high-pass pass along one axis over nlines contiguous input lines (line l starts at
+// in + l * lstride).  Low-pass output c of line l goes to outL[l + c * osL], high-pass output to
+// outH[l + c * osH]: the result is stored transposed, so the next pass again reads contiguous
+// lines.  Output c (unwrapped ro.lo + c) reads inputs 2(ro.lo + c) + [2 - LF, LF - 1].  Unless
+// the output range wraps, the input is a padded array (zero margins, see pass_margin) and the
+// window loads carry no bounds checks.
 template <typename T, int LF, int CH>
-__device__ __forceinline__ void pass_hg(const T* in, int lstride, int stride, Range ri, int n_in, T* outL, T* outH,
-                                        int olstride, int ostride, Range ro, int nlines, const T (&hr)[LF],
-                                        const T (&gr)[LF], int tid, int gt)
+__device__ __forceinline__ void pass_hg(const T* in, int lstride, Range ri, int n_in, T* outL, int osL, T* outH,
+                                        int osH, Range ro, int nlines, const T (&hr)[LF], const T (&gr)[LF], int tid,
+                                        int gt)
 {
     constexpr int WN = 2 * CH + 2 * LF - 4;
     const int nch = (ro.cnt + CH - 1) / CH;
@@ -156,29 +177,24 @@ __device__ __forceinline__ void pass_hg(const T* in, int lstride, int stride, Ra
     Stepper st;  // a = chunk, b = line: consecutive lanes walk lines
     st.init(tid, gt, nlines);
     const int nim = n_in - 1;
+    const int base0 = 2 * ro.lo + (2 - LF) - ri.lo;
     for (int it = tid; it < items; it += gt, st.next()) {
         const int line = st.b, c0 = st.a * CH;
-        const int base = 2 * (ro.lo + c0) + (2 - LF) - ri.lo;
+        const int base = base0 + 2 * c0;
         const T* src = in + line * lstride;
         T w[WN];
         if (!ro.full) {
-            if (base >= 0 && base + WN <= ri.cnt) {
 #pragma unroll
-                for (int i = 0; i < WN; ++i) w[i] = src[(base + i) * stride];
-            } else {
-#pragma unroll
-                for (int i = 0; i < WN; ++i) {
-                    const int p = base + i;
-                    w[i] = ((unsigned)p < (unsigned)ri.cnt) ? src[p * stride] : T(0);
-                }
-            }
+            for (int i = 0; i < WN; ++i) w[i] = src[base + i];
         } else {
 #pragma unroll
             for (int i = 0; i < WN; ++i) {
                 const int p = (base + i) & nim;
-                w[i] = (p < ri.cnt) ? src[p * stride] : T(0);
+                w[i] = (p < ri.cnt) ? src[p] : T(0);
             }
         }
+        T* oL = outL + line + c0 * osL;
+        T* oH = outH + line + c0 * osH;
 #pragma unroll
         for (int o = 0; o < CH; ++o) {
             T a = T(0), d = T(0);
@@ -188,8 +204,8 @@ __device__ __forceinline__ void pass_hg(const T* in, int lstride, int stride, Ra
                 d = fma(gr[i], w[2 * o + i], d);
             }
             if (c0 + o < ro.cnt) {
-                outL[line * olstride + (c0 + o) * ostride] = a;
-                outH[line * olstride + (c0 + o) * ostride] = d;
+                oL[o * osL] = a;
+                oH[o * osH] = d;
             }
         }
     }
@@ -230,7 +246,7 @@ __device__ __forceinline__ void pass_lo(const T* in, int lstride, int stride, Ra
 }
 
 // Copies the stencil window of one column band from its coefficient array (pitch pz) to the
-// row's storage (and the BF16 copy).
+// row's storage (and the BF16 copy), which holds the window row-major.
 template <typename T>
 __device__ __forceinline__ void write_win(const OpDev<T>& op, const T* Zb, int pz, Range r0, Range r1, int nj, int f0,
                                           int W0, int f1, int W1, int64_t dst, int tid, int gt)
@@ -359,23 +375,22 @@ __device__ __forceinline__ bool row2_meta(const OpDev<T>& op, const Row2& R, int
     return (int64_t)meta[op.nb] == op.row_ptr[R.srow + 1] - R.row_base;
 }
 
-// Writes the three detail bands of level jj (and the approximation band when jj == L) from
-// Z = [LL | (0,1) | (1,0) | (1,1)], each q0r.cnt x q1r.cnt.
+// Writes the three detail bands of level jj (and the approximation band when jj == L):
+// D = [(0,1) | (1,0) | (1,1)], each q0r.cnt x q1r.cnt at pitch q1r.cnt; LL at pitch LP.
 template <typename T>
-__device__ __forceinline__ void write_level(const OpDev<T>& op, const Row2& R, const int* meta, const T* Z, Range q0r,
-                                            Range q1r, int jj, int tid, int gt)
+__device__ __forceinline__ void write_level(const OpDev<T>& op, const Row2& R, const int* meta, const T* LL, int LP,
+                                            const T* D, Range q0r, Range q1r, int jj, int tid, int gt)
 {
     const int n = op.n, L = op.L, dense = op.gap < 0;
-    const int zq = q0r.cnt * q1r.cnt, nj = n >> jj;
+    const int dq = q0r.cnt * q1r.cnt, nj = n >> jj;
     const int tmax = (jj == L) ? 4 : 3;
     for (int t = 0; t < tmax; ++t) {
-        // t < 3: detail band t at Z + (1 + t) * zq; t == 3: approximation band at Z
-        const int e0 = (t == 3) ? 0 : (t >= 1 ? 1 : 0), e1 = (t == 3) ? 0 : (t == 1 ? 0 : 1);
         const int b2 = (t == 3) ? 0 : band_of_level(2, L, jj, t);
+        const int e0 = (t == 3) ? 0 : (t >= 1 ? 1 : 0), e1 = (t == 3) ? 0 : (t == 1 ? 0 : 1);
         int f0, W0, f1, W1;
         stencil(R.j, R.Bo.e0, R.l0, jj, e0, op.r, op.Lf, n, dense, &f0, &W0);
         stencil(R.j, R.Bo.e1, R.l1, jj, e1, op.r, op.Lf, n, dense, &f1, &W1);
-        write_win(op, Z + ((t == 3) ? 0 : (1 + t) * zq), q1r.cnt, q0r, q1r, nj, f0, W0, f1, W1,
+        write_win(op, (t == 3) ? LL : D + t * dq, (t == 3) ? LP : q1r.cnt, q0r, q1r, nj, f0, W0, f1, W1,
                   R.row_base + meta[b2], tid, gt);
     }
 }
@@ -402,7 +417,7 @@ template <typename T, int LF>
 __device__ __forceinline__ void asm2d_row(const OpDev<T>& op, const AsmCfg& cfg, int rl, const T* fS, int* meta,
                                           T* arena, int gid, int tid)
 {
-    constexpr int CH = 4;
+    constexpr int CH = PASS_CH;
     constexpr int P = 4;
     const int gt = cfg.gt;
     const int n = op.n, Lf = op.Lf;
@@ -429,8 +444,17 @@ __device__ __forceinline__ void asm2d_row(const OpDev<T>& op, const AsmCfg& cfg,
 
     // Level loop.  The first produced level is 1 (cascade step on s), or k0 when the row's
     // finest kept level is k0 + 1 > 1 (LL of level k0 directly by phi_k0 at stride 2^k0).
+    // Arena: the level's input lines (s rows, or LL of the previous level) and its outputs
+    // (LL, then the detail bands) at the start, the axis-1 results Y at the end.  Every array a
+    // low/high-pass pass reads is padded (pass_margin): s rows at pitch XP, Y transposed (one
+    // line per axis-1 coefficient), LL at pitch LP.
+    const int mg = pass_margin(Lf, LF);
+    const int XP = (k0 > 0) ? (A1.cnt | 1) : odd_pitch(A1.cnt, mg);  // the scaling-filter pass checks bounds
     const int lv0 = (k0 == 0) ? 1 : k0;
     Range p0 = A0, p1 = A1;
+    T* const xs0 = (k0 > 0) ? arena : arena + mg;  // s rows
+    const T* xin = xs0;
+    int xpitch = XP;
     int n_in = n;
     int prevZ = 0;
     for (int jj = lv0; jj <= R.jhi; ++jj) {
@@ -440,50 +464,63 @@ __device__ __forceinline__ void asm2d_row(const OpDev<T>& op, const AsmCfg& cfg,
         const int S = lo_only ? (1 << k0) : 2;
         const Range q0r = lo_only ? range_filter(A0, S, 0, lenk, nj) : range_cascade(p0, Lf, nj);
         const Range q1r = lo_only ? range_filter(A1, S, 0, lenk, nj) : range_cascade(p1, Lf, nj);
-        const int ysz = (lo_only ? 1 : 2) * p0.cnt * q1r.cnt;
-        const int zq = q0r.cnt * q1r.cnt;
-        const int zsz = (lo_only ? 1 : 4) * zq;
-        const int xsz = first ? B * A1.cnt : prevZ;
+        const int YP = odd_pitch(p0.cnt, mg);
+        const int y1 = lo_only ? p0.cnt * q1r.cnt : padded_size(q1r.cnt, p0.cnt, mg);
+        const int ysz = (lo_only ? 1 : 2) * y1;
+        const int LP = odd_pitch(q1r.cnt, mg);
+        const int llsz = padded_size(q0r.cnt, q1r.cnt, mg);
+        const int dq = q0r.cnt * q1r.cnt;
+        const int zsz = llsz + (lo_only ? 0 : 3 * dq);
+        const int xsz = first ? (lo_only ? B * XP : padded_size(B, A1.cnt, mg)) : prevZ;
         if (xsz + ysz > A || zsz + ysz > A) {
             flag_error(op.err, ERR_ARENA);
             return;
         }
         T* Yl = arena_end - ysz;
-        T* Yh = Yl + p0.cnt * q1r.cnt;
+        T* Yh = Yl + y1;
         // axis 1 (batched over pixel rows of s on the first level)
         const int nbatch = first ? (A0.cnt + B - 1) / B : 1;
         for (int bi = 0; bi < nbatch; ++bi) {
             const int r0 = bi * B;
             const int nr = first ? min(B, A0.cnt - r0) : p0.cnt;
             if (first) {
-                // per-pixel lists pay off when the region's active set is much larger than the
-                // number of windows nonzero at one pixel (coarse rows spanning many windows)
-                if (op.wl && nact >= 2 * op.wl_slots)
-                    s_stage_wl<T, P>(op, Fb, RR, A1.cnt, r0, nr, R.g0, R.g1, arena, tid, gt);
+                if (bi == 0 && !lo_only) zero_gaps<T, 2 * LF - 2>(arena, mg, B, A1.cnt, XP, tid, gt);
+                // per-pixel window lists: a fixed number of slots per pixel, each a dependent
+                // pair of loads, instead of every window active somewhere in the region
+                if (op.wl)
+                    s_stage_wl<T, P>(op, Fb, RR, A1.cnt, r0, nr, R.g0, R.g1, xs0, XP, tid, gt);
                 else
-                    s_stage<T, P>(op, Fb, RR, A1.cnt, r0, nr, R.g0, R.g1, act, nact, arena, tid, gt);
+                    s_stage<T, P>(op, Fb, RR, A1.cnt, r0, nr, R.g0, R.g1, act, nact, xs0, XP, tid, gt);
                 group_sync(gt, gid);
             }
-            if (lo_only)
-                pass_lo<T>(arena, A1.cnt, 1, A1, n, Yl + r0 * q1r.cnt, q1r.cnt, 1, q1r, nr, phiS, lenk, S, tid, gt);
-            else
-                pass_hg<T, LF, CH>(arena, p1.cnt, 1, p1, n_in, Yl + r0 * q1r.cnt, Yh + r0 * q1r.cnt, q1r.cnt, 1, q1r,
-                                   nr, hr, gr, tid, gt);
+            if (lo_only) {
+                pass_lo<T>(xs0, XP, 1, A1, n, Yl + r0 * q1r.cnt, q1r.cnt, 1, q1r, nr, phiS, lenk, S, tid, gt);
+            } else {
+                if (bi == 0) {
+                    zero_gaps<T, 2 * LF - 2>(Yl, mg, q1r.cnt, p0.cnt, YP, tid, gt);
+                    zero_gaps<T, 2 * LF - 2>(Yh, mg, q1r.cnt, p0.cnt, YP, tid, gt);
+                }
+                pass_hg<T, LF, CH>(xin, xpitch, p1, n_in, Yl + mg + r0, YP, Yh + mg + r0, YP, q1r, nr, hr, gr, tid,
+                                   gt);
+            }
             group_sync(gt, gid);
         }
-        // axis 0: lines are the columns of Y
+        // axis 0: lines are the axis-1 coefficients (rows of Y^T)
+        T* LL = arena + mg;
+        T* D = arena + llsz;
+        zero_gaps<T, 2 * LF - 2>(arena, mg, q0r.cnt, q1r.cnt, LP, tid, gt);
         if (lo_only) {
-            pass_lo<T>(Yl, 1, q1r.cnt, A0, n, arena, 1, q1r.cnt, q0r, q1r.cnt, phiS, lenk, S, tid, gt);
+            pass_lo<T>(Yl, 1, q1r.cnt, A0, n, LL, 1, LP, q0r, q1r.cnt, phiS, lenk, S, tid, gt);
         } else {
-#pragma unroll 1
-            for (int h2 = 0; h2 < 2; ++h2)
-                pass_hg<T, LF, CH>(h2 ? Yh : Yl, 1, q1r.cnt, p0, n_in, arena + (h2 ? zq : 0),
-                                   arena + (h2 ? 3 * zq : 2 * zq), 1, q1r.cnt, q0r, q1r.cnt, hr, gr, tid, gt);
+            pass_hg<T, LF, CH>(Yl + mg, YP, p0, n_in, LL, LP, D + dq, q1r.cnt, q0r, q1r.cnt, hr, gr, tid, gt);
+            pass_hg<T, LF, CH>(Yh + mg, YP, p0, n_in, D, q1r.cnt, D + 2 * dq, q1r.cnt, q0r, q1r.cnt, hr, gr, tid, gt);
         }
         group_sync(gt, gid);
-        if (!lo_only) write_level(op, R, meta, arena, q0r, q1r, jj, tid, gt);
+        if (!lo_only) write_level(op, R, meta, LL, LP, D, q0r, q1r, jj, tid, gt);
         p0 = q0r;
         p1 = q1r;
+        xin = LL;
+        xpitch = LP;
         n_in = nj;
         prevZ = zsz;
     }
@@ -519,6 +556,11 @@ struct BatchItem {
     AsmCfg cfg;
 };
 
+// KIND selects the row kernel compiled into one instantiation: 1 = 1-D rows, else the 2-D
+// filter template LF (2, 4, 8 or 20).  Items of other kinds are not taken: the host queues
+// each kind's items in a range of their own with its own counter, so that every instantiation
+// holds one row path and keeps its registers.
+template <int KIND>
 __global__ void __launch_bounds__(256, 2) k_assemble_batch(const OpDev<float>* __restrict__ ops,
                                                            const BatchItem* __restrict__ items, int nitems,
                                                            int* __restrict__ counter)
@@ -541,18 +583,11 @@ __global__ void __launch_bounds__(256, 2) k_assemble_batch(const OpDev<float>* _
         }
         __syncthreads();
         const AsmCfg cfg = it_s.cfg;
-        const int dim = it_s.dim, lft = it_s.lft;
         float* fS = reinterpret_cast<float*>(smem_raw);
-        if (dim == 1) {
+        if constexpr (KIND == 1) {
             for (int i = threadIdx.x; i < 2 * op_s.Lf; i += blockDim.x) fS[i] = op_s.taps[i];
-        } else if (lft == 2) {
-            load_filters2d<float, 2>(op_s, cfg.b, fS);
-        } else if (lft == 4) {
-            load_filters2d<float, 4>(op_s, cfg.b, fS);
-        } else if (lft == 8) {
-            load_filters2d<float, 8>(op_s, cfg.b, fS);
         } else {
-            load_filters2d<float, 20>(op_s, cfg.b, fS);
+            load_filters2d<float, KIND>(op_s, cfg.b, fS);
         }
         __syncthreads();
         const int gt = cfg.gt;
@@ -566,16 +601,10 @@ __global__ void __launch_bounds__(256, 2) k_assemble_batch(const OpDev<float>* _
                 const int rloc = rb + gid;
                 if (rloc >= cfg.rows) break;
                 const int rl = cfg.row0 + rloc;
-                if (dim == 1)
+                if constexpr (KIND == 1)
                     asm1d_row<float>(op_s, cfg, rl, fS, fS + op_s.Lf, meta, arena, gid, tid);
-                else if (lft == 2)
-                    asm2d_row<float, 2>(op_s, cfg, rl, fS, meta, arena, gid, tid);
-                else if (lft == 4)
-                    asm2d_row<float, 4>(op_s, cfg, rl, fS, meta, arena, gid, tid);
-                else if (lft == 8)
-                    asm2d_row<float, 8>(op_s, cfg, rl, fS, meta, arena, gid, tid);
                 else
-                    asm2d_row<float, 20>(op_s, cfg, rl, fS, meta, arena, gid, tid);
+                    asm2d_row<float, KIND>(op_s, cfg, rl, fS, meta, arena, gid, tid);
                 group_sync(gt, gid);  // the group's arena and meta are reused by its next row
             }
         }

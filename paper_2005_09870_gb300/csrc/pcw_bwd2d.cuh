@@ -127,8 +127,8 @@ __device__ __forceinline__ void read_level(const OpDev<T>& op, const Row2& R, co
     const int zq = q0r.cnt * q1r.cnt, nj = n >> jj;
     const int tmax = (jj == L) ? 4 : 3;
     for (int t = 0; t < tmax; ++t) {
-        const int e0 = (t == 3) ? 0 : (t >= 1 ? 1 : 0), e1 = (t == 3) ? 0 : (t == 1 ? 0 : 1);
         const int b2 = (t == 3) ? 0 : band_of_level(2, L, jj, t);
+        const int e0 = (t == 3) ? 0 : (t >= 1 ? 1 : 0), e1 = (t == 3) ? 0 : (t == 1 ? 0 : 1);
         int f0, W0, f1, W1;
         stencil(R.j, R.Bo.e0, R.l0, jj, e0, op.r, op.Lf, n, dense, &f0, &W0);
         stencil(R.j, R.Bo.e1, R.l1, jj, e1, op.r, op.Lf, n, dense, &f1, &W1);
@@ -278,6 +278,7 @@ struct BwdQueue {
     int64_t Soff[MAXB];
 };
 
+template <int LF>
 __global__ void __launch_bounds__(256, 2) k_backward_queue(const OpDev<float>* __restrict__ opd,
                                                            const BatchItem* __restrict__ items, int nitems,
                                                            int* __restrict__ counter, const __grid_constant__ BwdQueue bq)
@@ -299,16 +300,8 @@ __global__ void __launch_bounds__(256, 2) k_backward_queue(const OpDev<float>* _
         if (threadIdx.x == 0) it_s = items[idx];
         __syncthreads();
         const AsmCfg cfg = it_s.cfg;
-        const int lft = it_s.lft;
         float* fS = reinterpret_cast<float*>(smem_raw);
-        if (lft == 2)
-            load_filters2d<float, 2>(op_s, cfg.b, fS);
-        else if (lft == 4)
-            load_filters2d<float, 4>(op_s, cfg.b, fS);
-        else if (lft == 8)
-            load_filters2d<float, 8>(op_s, cfg.b, fS);
-        else
-            load_filters2d<float, 20>(op_s, cfg.b, fS);
+        load_filters2d<float, LF>(op_s, cfg.b, fS);
         __syncthreads();
         const int gt = cfg.gt;
         const int gid = threadIdx.x / gt, tid = threadIdx.x - gid * gt;
@@ -322,14 +315,7 @@ __global__ void __launch_bounds__(256, 2) k_backward_queue(const OpDev<float>* _
                 const int rloc = rb + gid;
                 if (rloc >= cfg.rows) break;
                 const int rl = cfg.row0 + rloc;
-                if (lft == 2)
-                    bwd2d_row<float, 2>(op_s, cfg, rl, fS, meta, arena, gid, tid, bq.G, bq.S, Sband, bq.amask);
-                else if (lft == 4)
-                    bwd2d_row<float, 4>(op_s, cfg, rl, fS, meta, arena, gid, tid, bq.G, bq.S, Sband, bq.amask);
-                else if (lft == 8)
-                    bwd2d_row<float, 8>(op_s, cfg, rl, fS, meta, arena, gid, tid, bq.G, bq.S, Sband, bq.amask);
-                else
-                    bwd2d_row<float, 20>(op_s, cfg, rl, fS, meta, arena, gid, tid, bq.G, bq.S, Sband, bq.amask);
+                bwd2d_row<float, LF>(op_s, cfg, rl, fS, meta, arena, gid, tid, bq.G, bq.S, Sband, bq.amask);
                 group_sync(gt, gid);
             }
         }

@@ -187,4 +187,18 @@ PCW_HD int64_t block_count(int d, int n, int L, int Lf, int r, int gap, int b, i
     return (int64_t)c0 * c1;
 }
 
+// Padded line arrays in shared memory.  The 2-D low/high-pass passes read each output's
+// window 2c + [2 - LF, LF - 1] (LF = filter template length >= Lf) without bounds checks; the
+// union output range of an input line spans ceil((lo - Lf + 1) / 2) .. floor((hi + Lf - 2) / 2),
+// so those windows reach at most Lf + LF - 3 elements past either end of the line.  An array
+// of nl lines of len elements therefore keeps that many zeros before its first line and
+// between lines (line l starts at margin + l * pitch, pitch >= len + margin, odd so that
+// lanes walking lines hit distinct banks), and PASS_SLACK elements after the last line for
+// the discarded outputs of a line's last chunk of PASS_CH outputs.
+constexpr int PASS_CH = 4;
+constexpr int PASS_SLACK = 2 * (PASS_CH - 1);
+PCW_HD int pass_margin(int Lf, int LF) { return Lf + LF - 3; }
+PCW_HD int odd_pitch(int len, int mg) { return (len + mg) | 1; }
+PCW_HD int padded_size(int nl, int len, int mg) { return mg + nl * odd_pitch(len, mg) + PASS_SLACK; }
+
 }  // namespace pcw

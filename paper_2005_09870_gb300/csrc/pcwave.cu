@@ -31,8 +31,10 @@ inline void count_launch(long long k = 1) { g_launches.fetch_add(k, std::memory_
 
 struct BandPlan {
     int b, rows, jlo, jhi, k0;
-    AsmCfg cfg;
+    AsmCfg cfg;    // forward rows
     size_t smem;
+    AsmCfg cfg_b;  // adjoint rows (same groups, their own arena)
+    size_t smem_b;
 };
 
 }  // namespace
@@ -80,11 +82,17 @@ struct pc_op {
     bool prepared = false;  // stage 0 ran for the current parameters
     // FP32 row assembly through the persistent work queue (one launch over all bands)
     BatchItem* q_items_d = nullptr;
+    BatchItem* q_items_b_d = nullptr;  // the same items with the adjoint rows' plan
     OpDev<float>* q_op_d = nullptr;
     int* q_counter_d = nullptr;
-    int q_nitems = 0, q_grid = 0;
-    size_t q_smem = 0;
+    int q_nitems = 0, q_grid = 0, q_kind = 0;
+    size_t q_smem = 0, q_smem_b = 0;
     std::string err = "no error";
+};
+
+// Work items of one kernel kind (see k_assemble_batch) in a contiguous range of the queue.
+struct QGroup {
+    int kind, start, count, grid;
 };
 
 struct pc_batch {
@@ -92,9 +100,9 @@ struct pc_batch {
     std::vector<OpDev<float>> od;  // host copy of the operators' descriptors (refreshed per run)
     OpDev<float>* ops_d = nullptr;
     BatchItem* items_d = nullptr;
-    int* counter_d = nullptr;
+    int* counter_d = nullptr;  // one counter per group
     int nitems = 0;
-    int grid = 0;
+    std::vector<QGroup> groups;
     size_t smem = 0;
     int kernels_per_run = 0;
     cudaStream_t cap = nullptr;
@@ -227,10 +235,48 @@ pc_status plan_nnz(const Geo& g, std::vector<int64_t>* row_ptr, int64_t* nnz)
     return PC_OK;
 }
 
+// Persistent queue kernels, one instantiation per kind: 1 = 1-D rows, else the 2-D filter
+// template length.
+int item_kind(int dim, int lft) { return dim == 1 ? 1 : lft; }
+
+using QueueKernel = decltype(&k_assemble_batch<8>);
+QueueKernel queue_kernel(int kind)
+{
+    switch (kind) {
+    case 1: return k_assemble_batch<1>;
+    case 2: return k_assemble_batch<2>;
+    case 4: return k_assemble_batch<4>;
+    case 8: return k_assemble_batch<8>;
+    default: return k_assemble_batch<20>;
+    }
+}
+
+using BwdQueueKernel = decltype(&k_backward_queue<8>);
+BwdQueueKernel bwd_queue_kernel(int lft)
+{
+    switch (lft) {
+    case 2: return k_backward_queue<2>;
+    case 4: return k_backward_queue<4>;
+    case 8: return k_backward_queue<8>;
+    default: return k_backward_queue<20>;
+    }
+}
+
+// Resident CTAs of a 256-thread kernel over the device (the grid of a persistent launch).
+template <typename K>
+int persistent_grid(K fn, size_t smem)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem);
+    return std::max(1, sms * std::max(1, per_sm));
+}
+
 // per-axis maxima of the ranges a row group meets, over the translate phases of a band
 struct AxisMax {
-    int A;           // region count
-    int c;           // stage-1 output count
+    int A;              // region count
+    int c;              // stage-1 output count
     int lev[MAXL + 2];  // cascade counts per level
 };
 
@@ -316,7 +362,7 @@ pc_status plan_band(pc_op* h, const Geo& g, int b, int gt_req, BandPlan* out)
     bp.jlo = dense ? 1 : std::max(1, B.j - g.gap);
     bp.jhi = dense ? g.L : std::min(g.L, B.j + g.gap);
     bp.k0 = (g.d == 2) ? bp.jlo - 1 : 0;
-    int64_t need = 0;
+    int64_t need = 0, bneed = -1;  // forward / adjoint arena (bneed < 0: the same)
     int gt, batch = 1;
     AxisMax M1 = axis_max(g, B.j, B.e1, B.nj, bp.k0, bp.jhi);
     if (g.d == 1) {
@@ -332,37 +378,54 @@ pc_status plan_band(pc_op* h, const Geo& g, int b, int gt_req, BandPlan* out)
         AxisMax M0 = axis_max(g, B.j, B.e0, B.nj, bp.k0, bp.jhi);
         const int64_t area = (int64_t)M0.A * M1.A;
         gt = gt_req ? gt_req : (area <= 768 ? 32 : area <= 2048 ? 64 : area <= 6144 ? 128 : 256);
-        const int nY = (bp.k0 == 0) ? 2 : 1;
-        const int64_t Y = (int64_t)nY * M0.A * M1.c;
-        const int64_t Z = (int64_t)((bp.k0 == 0) ? 4 : 1) * M0.c * M1.c;
+        const int lo1 = bp.k0 > 0;
+        // forward row (asm2d_row): padded line arrays; every size below is monotone in the
+        // counts, so the per-axis maxima bound every translate phase
+        const int mg = pass_margin(g.Lf, lf_template(g.Lf));
+        const int64_t XP = lo1 ? (M1.A | 1) : odd_pitch(M1.A, mg);  // s rows (padded unless the first pass is phi_k0)
+        const int lvl0 = lo1 ? bp.k0 : 1;
+        const int64_t Yf = lo1 ? (int64_t)M0.A * M1.c : 2 * (int64_t)padded_size(M1.c, M0.A, mg);
+        const int64_t Zf = padded_size(M0.c, M1.c, mg) + (lo1 ? 0 : 3 * (int64_t)M0.c * M1.c);
         // s rows per stage-1 step: the whole region when it fits a ~96 KB-per-CTA budget,
         // else as many rows as the budget allows (at least 8 pixels per thread)
         const int64_t budget = (96 * 1024 / (int64_t)es) / std::max(1, 256 / gt);
-        const int64_t room = std::max<int64_t>(budget - Y, (int64_t)8 * gt);
-        batch = (int)std::max<int64_t>(1, std::min<int64_t>(M0.A, room / M1.A));
-        need = std::max<int64_t>((int64_t)batch * M1.A + Y, Z + Y);
-        int64_t prevZ = Z;
-        int lvl0 = (bp.k0 == 0) ? 1 : bp.k0;
+        const int64_t room = std::max<int64_t>(budget - Yf, (int64_t)8 * gt);
+        batch = (int)std::max<int64_t>(1, std::min<int64_t>(M0.A, room / XP));
+        need = std::max<int64_t>((lo1 ? (int64_t)batch * XP : padded_size(batch, M1.A, mg)) + Yf, Zf + Yf);
+        int64_t prevZ = Zf;
         for (int jj = lvl0 + 1; jj <= bp.jhi; ++jj) {
-            int64_t ysz = 2 * (int64_t)M0.lev[jj - 1] * M1.lev[jj];
-            int64_t zsz = 4 * (int64_t)M0.lev[jj] * M1.lev[jj];
+            const int64_t ysz = 2 * (int64_t)padded_size(M1.lev[jj], M0.lev[jj - 1], mg);
+            const int64_t zsz = padded_size(M0.lev[jj], M1.lev[jj], mg) + 3 * (int64_t)M0.lev[jj] * M1.lev[jj];
             need = std::max(need, std::max(prevZ + ysz, zsz + ysz));
+            prevZ = zsz;
+        }
+        // adjoint row (bwd2d_row, and the atomic adjoint k_backward): compact arrays
+        const int64_t Yb = (int64_t)(lo1 ? 1 : 2) * M0.A * M1.c;
+        const int64_t Zb = (int64_t)(lo1 ? 1 : 4) * M0.c * M1.c;
+        bneed = std::max<int64_t>((int64_t)batch * M1.A + Yb, Zb + Yb);
+        prevZ = Zb;
+        for (int jj = lvl0 + 1; jj <= bp.jhi; ++jj) {
+            const int64_t ysz = 2 * (int64_t)M0.lev[jj - 1] * M1.lev[jj];
+            const int64_t zsz = 4 * (int64_t)M0.lev[jj] * M1.lev[jj];
+            bneed = std::max(bneed, std::max(prevZ + ysz, zsz + ysz));
             prevZ = zsz;
         }
     }
     if (!stencils_inside(g, b, bp.k0, bp.jhi))
         return fail(h, PC_ERR_UNSUPPORTED, "internal: stencil of band %d outside its transform range", b);
     need = round_up(need, (int64_t)(16 / es));
+    bneed = (bneed < 0) ? need : round_up(bneed, (int64_t)(16 / es));
     const int lft = (g.d == 2) ? lf_template(g.Lf) : g.Lf;
     int filt = 2 * lft + ((bp.k0 > 0) ? wav_len(bp.k0, g.Lf) : 0);
     filt = (int)round_up(filt, (int64_t)(16 / es));
     int rpc = std::max(1, 256 / gt);
-    auto smem_of = [&](int rpcv) {
-        return (size_t)filt * es + round_up((int64_t)rpcv * META_INTS * 4, 16) + (size_t)rpcv * need * es;
+    auto smem_of = [&](int rpcv, int64_t ar) {
+        return (size_t)filt * es + round_up((int64_t)rpcv * META_INTS * 4, 16) + (size_t)rpcv * ar * es;
     };
-    while (rpc > 1 && smem_of(rpc) > 110 * 1024) rpc /= 2;
-    if (smem_of(rpc) > 227 * 1024)
-        return fail(h, PC_ERR_UNSUPPORTED, "band %d needs %zu bytes of shared memory per row", b, smem_of(rpc));
+    const int64_t amax = std::max(need, bneed);
+    while (rpc > 1 && smem_of(rpc, amax) > 110 * 1024) rpc /= 2;
+    if (smem_of(rpc, amax) > 227 * 1024)
+        return fail(h, PC_ERR_UNSUPPORTED, "band %d needs %zu bytes of shared memory per row", b, smem_of(rpc, amax));
     bp.cfg.b = b;
     bp.cfg.row0 = 0;
     bp.cfg.rows = bp.rows;
@@ -371,7 +434,10 @@ pc_status plan_band(pc_op* h, const Geo& g, int b, int gt_req, BandPlan* out)
     bp.cfg.batch = batch;
     bp.cfg.arena = (int)need;
     bp.cfg.filt = filt;
-    bp.smem = smem_of(rpc);
+    bp.smem = smem_of(rpc, need);
+    bp.cfg_b = bp.cfg;
+    bp.cfg_b.arena = (int)bneed;
+    bp.smem_b = smem_of(rpc, bneed);
     *out = bp;
     return PC_OK;
 }
@@ -513,7 +579,8 @@ pc_status assemble_t(pc_op* h, cudaStream_t st, int stage_mask)
             const OpDev<float> od = make_opdev<float>(h);
             PC_CUDA(h, cudaMemcpyAsync(h->q_op_d, &od, sizeof(od), cudaMemcpyHostToDevice, st));
             PC_CUDA(h, cudaMemsetAsync(h->q_counter_d, 0, sizeof(int), st));
-            k_assemble_batch<<<h->q_grid, 256, h->q_smem, st>>>(h->q_op_d, h->q_items_d, h->q_nitems, h->q_counter_d);
+            queue_kernel(h->q_kind)<<<h->q_grid, 256, h->q_smem, st>>>(h->q_op_d, h->q_items_d, h->q_nitems,
+                                                                       h->q_counter_d);
             count_launch();
             PC_CUDA(h, cudaGetLastError());
             h->assembled = true;
@@ -660,7 +727,7 @@ pc_status launch_bwd2d_lf(pc_op* h, const OpDev<T>& od, const BandPlan& bp, int 
             return fail(h, PC_ERR_CUDA, "cudaFuncSetAttribute failed");
         attr = true;
     }
-    k_backward2d<T, LF><<<ctas, threads, bp.smem, st>>>(od, bp.cfg, G, S, Sband, amask);
+    k_backward2d<T, LF><<<ctas, threads, bp.smem_b, st>>>(od, bp.cfg_b, G, S, Sband, amask);
     return PC_OK;
 }
 
@@ -692,14 +759,10 @@ pc_status backward_core(pc_op* h, const T* G, T* du, T* dv, T* dF, T* dG, cudaSt
     if (D.dim == 2 && S) {
         bool queued = false;
         if constexpr (std::is_same<T, float>::value) {
-            if (h->q_items_d && h->q_smem <= 110 * 1024) {
+            if (h->q_items_b_d && h->q_smem_b <= 110 * 1024) {
                 // phase 1 through the operator's work queue: one launch over all row bands
-                static bool attr = false;
-                if (!attr) {
-                    PC_CUDA(h, cudaFuncSetAttribute(k_backward_queue, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                    110 * 1024));
-                    attr = true;
-                }
+                const BwdQueueKernel kq = bwd_queue_kernel(h->q_kind);
+                PC_CUDA(h, cudaFuncSetAttribute(kq, cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024));
                 const OpDev<float> odq = make_opdev<float>(h);
                 PC_CUDA(h, cudaMemcpyAsync(h->q_op_d, &odq, sizeof(odq), cudaMemcpyHostToDevice, st));
                 PC_CUDA(h, cudaMemsetAsync(h->q_counter_d, 0, sizeof(int), st));
@@ -708,12 +771,8 @@ pc_status backward_core(pc_op* h, const T* G, T* du, T* dv, T* dF, T* dG, cudaSt
                 bq.S = S;
                 bq.amask = amask;
                 for (int b = 0; b < h->nb; ++b) bq.Soff[b] = h->bd.band[b].Soff;
-                int dev = 0, sms = 0, per_sm = 0;
-                cudaGetDevice(&dev);
-                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward_queue, 256, h->q_smem);
-                k_backward_queue<<<std::max(1, sms * std::max(1, per_sm)), 256, h->q_smem, st>>>(
-                    h->q_op_d, h->q_items_d, h->q_nitems, h->q_counter_d, bq);
+                kq<<<persistent_grid(kq, h->q_smem_b), 256, h->q_smem_b, st>>>(h->q_op_d, h->q_items_b_d,
+                                                                               h->q_nitems, h->q_counter_d, bq);
                 count_launch();
                 queued = true;
             }
@@ -763,10 +822,10 @@ pc_status backward_core(pc_op* h, const T* G, T* du, T* dv, T* dF, T* dG, cudaSt
             const int threads = bp.cfg.gt * bp.cfg.rpc;
             if (D.dim == 1) {
                 if (set_smem_attr<T, 1>() != PC_OK) return fail(h, PC_ERR_CUDA, "cudaFuncSetAttribute failed");
-                k_backward<T, 1><<<ctas, threads, bp.smem, st>>>(od, bp.cfg, G, dv, dF);
+                k_backward<T, 1><<<ctas, threads, bp.smem_b, st>>>(od, bp.cfg_b, G, dv, dF);
             } else {
                 if (set_smem_attr<T, 2>() != PC_OK) return fail(h, PC_ERR_CUDA, "cudaFuncSetAttribute failed");
-                k_backward<T, 2><<<ctas, threads, bp.smem, st>>>(od, bp.cfg, G, dv, dF);
+                k_backward<T, 2><<<ctas, threads, bp.smem_b, st>>>(od, bp.cfg_b, G, dv, dF);
             }
             count_launch();
         }
@@ -886,7 +945,7 @@ pc_status build_window_list(pc_op* h, cudaStream_t st)
 void free_all(pc_op* h)
 {
     void* ptrs[] = {h->u_d,  h->v_d,        h->taps64_d,  h->wav64_d,  h->tapsT_d, h->wavT_d, h->F_d,
-                    h->G_d,  h->dF_d, h->dG_d, h->S_d, h->amask_d, h->wl_d, h->cnt_d, h->dfoff_d, h->q_items_d, h->q_op_d, h->q_counter_d, h->row_ptr_d,  h->theta_d,   h->theta16_d, h->masks_d, h->err_d};
+                    h->G_d,  h->dF_d, h->dG_d, h->S_d, h->amask_d, h->wl_d, h->cnt_d, h->dfoff_d, h->q_items_d, h->q_items_b_d, h->q_op_d, h->q_counter_d, h->row_ptr_d,  h->theta_d,   h->theta16_d, h->masks_d, h->err_d};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -898,7 +957,7 @@ struct ItemCand {
     BatchItem it;
 };
 
-void make_items(pc_op* h, int op_index, std::vector<ItemCand>* out, size_t* smem)
+void make_items(pc_op* h, int op_index, std::vector<ItemCand>* out, size_t* smem, bool adjoint = false)
 {
     for (const BandPlan& bp : h->plan) {
         const Band B = band_info(h->desc.dim, h->desc.n, h->desc.levels, bp.b);
@@ -912,12 +971,12 @@ void make_items(pc_op* h, int op_index, std::vector<ItemCand>* out, size_t* smem
             c.it.dim = h->desc.dim;
             c.it.lft = (h->desc.dim == 2) ? lf_template(h->Lf) : h->Lf;
             c.it.pad = 0;
-            c.it.cfg = bp.cfg;
+            c.it.cfg = adjoint ? bp.cfg_b : bp.cfg;
             c.it.cfg.row0 = r0;
             c.it.cfg.rows = std::min(per, bp.rows - r0);
             c.cost = row_cost * c.it.cfg.rows;
             out->push_back(c);
-            *smem = std::max(*smem, bp.smem);
+            *smem = std::max(*smem, adjoint ? bp.smem_b : bp.smem);
         }
     }
 }
@@ -926,29 +985,32 @@ void make_items(pc_op* h, int op_index, std::vector<ItemCand>* out, size_t* smem
 pc_status build_queue(pc_op* h)
 {
     if (h->desc.precision != PC_FP32) return PC_OK;
-    std::vector<ItemCand> cands;
-    size_t smem = 0;
-    make_items(h, 0, &cands, &smem);
-    std::stable_sort(cands.begin(), cands.end(), [](const ItemCand& a, const ItemCand& b) { return a.cost > b.cost; });
-    std::vector<BatchItem> items;
-    for (const ItemCand& c : cands) items.push_back(c.it);
-    if (h->q_items_d) {
-        cudaFree(h->q_items_d);
-        h->q_items_d = nullptr;
-    }
     pc_status a;
-    if ((a = dev_alloc(h, &h->q_items_d, sizeof(BatchItem) * items.size())) != PC_OK) return a;
+    for (int adj = 0; adj < 2; ++adj) {
+        // forward and adjoint items in the same order (sorted by the forward cost)
+        std::vector<ItemCand> cands;
+        size_t smem = 0;
+        make_items(h, 0, &cands, &smem, adj == 1);
+        std::stable_sort(cands.begin(), cands.end(),
+                         [](const ItemCand& x, const ItemCand& y) { return x.cost > y.cost; });
+        std::vector<BatchItem> items;
+        for (const ItemCand& c : cands) items.push_back(c.it);
+        if (items.empty()) return PC_OK;
+        BatchItem*& dst = adj ? h->q_items_b_d : h->q_items_d;
+        if (dst) {
+            cudaFree(dst);
+            dst = nullptr;
+        }
+        if ((a = dev_alloc(h, &dst, sizeof(BatchItem) * items.size())) != PC_OK) return a;
+        PC_CUDA(h, cudaMemcpy(dst, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice));
+        h->q_nitems = (int)items.size();
+        h->q_kind = item_kind(h->desc.dim, items.front().lft);
+        (adj ? h->q_smem_b : h->q_smem) = smem;
+    }
     if (!h->q_op_d && (a = dev_alloc(h, &h->q_op_d, sizeof(OpDev<float>))) != PC_OK) return a;
     if (!h->q_counter_d && (a = dev_alloc(h, &h->q_counter_d, sizeof(int))) != PC_OK) return a;
-    PC_CUDA(h, cudaMemcpy(h->q_items_d, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice));
-    PC_CUDA(h, cudaFuncSetAttribute(k_assemble_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024));
-    h->q_nitems = (int)items.size();
-    h->q_smem = smem;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_assemble_batch, 256, smem);
-    h->q_grid = std::max(1, sms * std::max(1, per_sm));
+    PC_CUDA(h, cudaFuncSetAttribute(queue_kernel(h->q_kind), cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024));
+    h->q_grid = persistent_grid(queue_kernel(h->q_kind), h->q_smem);
     return PC_OK;
 }
 
@@ -960,9 +1022,13 @@ pc_status batch_enqueue(pc_batch* B, cudaStream_t st)
         pc_status ps = prepare_t<float>(h, st);
         if (ps != PC_OK) return ps;
     }
-    if (cudaMemsetAsync(B->counter_d, 0, sizeof(int), st) != cudaSuccess) return PC_ERR_CUDA;
-    k_assemble_batch<<<B->grid, 256, B->smem, st>>>(B->ops_d, B->items_d, B->nitems, B->counter_d);
-    count_launch();
+    if (cudaMemsetAsync(B->counter_d, 0, sizeof(int) * B->groups.size(), st) != cudaSuccess) return PC_ERR_CUDA;
+    for (size_t gi = 0; gi < B->groups.size(); ++gi) {
+        const QGroup& q = B->groups[gi];
+        queue_kernel(q.kind)<<<q.grid, 256, B->smem, st>>>(B->ops_d, B->items_d + q.start, q.count,
+                                                           B->counter_d + gi);
+        count_launch();
+    }
     if (cudaGetLastError() != cudaSuccess) return PC_ERR_CUDA;
     for (pc_op* h : B->ops) {
         h->prepared = true;
@@ -1005,28 +1071,40 @@ pc_status batch_build(pc_handle* ops, int count, cudaStream_t st, bool capture, 
         od.push_back(make_opdev<float>(h));
         make_items(h, i, &cands, &B->smem);
     }
-    std::stable_sort(cands.begin(), cands.end(),
-                     [](const ItemCand& a, const ItemCand& b) { return a.cost > b.cost; });
+    // one range per kernel kind, longest items first within each
+    std::stable_sort(cands.begin(), cands.end(), [](const ItemCand& a, const ItemCand& b) {
+        const int ka = item_kind(a.it.dim, a.it.lft), kb = item_kind(b.it.dim, b.it.lft);
+        return ka != kb ? ka < kb : a.cost > b.cost;
+    });
     std::vector<BatchItem> items;
-    for (const ItemCand& c : cands) items.push_back(c.it);
+    for (const ItemCand& c : cands) {
+        const int kind = item_kind(c.it.dim, c.it.lft);
+        if (B->groups.empty() || B->groups.back().kind != kind)
+            B->groups.push_back(QGroup{kind, (int)items.size(), 0, 0});
+        B->groups.back().count++;
+        items.push_back(c.it);
+    }
     B->nitems = (int)items.size();
     cudaError_t e;
     if ((e = cudaMalloc(&B->ops_d, sizeof(OpDev<float>) * od.size())) ||
-        (e = cudaMalloc(&B->items_d, sizeof(BatchItem) * items.size())) || (e = cudaMalloc(&B->counter_d, sizeof(int))) ||
+        (e = cudaMalloc(&B->items_d, sizeof(BatchItem) * items.size())) ||
+        (e = cudaMalloc(&B->counter_d, sizeof(int) * B->groups.size())) ||
         (e = cudaMemcpyAsync(B->ops_d, od.data(), sizeof(OpDev<float>) * od.size(), cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemcpyAsync(B->items_d, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice,
-                             st)) ||
-        (e = cudaFuncSetAttribute(k_assemble_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->smem))) {
+                             st))) {
         batch_free(B);
         return fail(nullptr, e == cudaErrorMemoryAllocation ? PC_ERR_OOM : PC_ERR_CUDA, "batch setup: %s",
                     cudaGetErrorString(e));
     }
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_assemble_batch, 256, B->smem);
-    B->grid = std::max(1, sms * std::max(1, per_sm));
-    B->kernels_per_run = 6 * count + 1;
+    for (QGroup& q : B->groups) {
+        if ((e = cudaFuncSetAttribute(queue_kernel(q.kind), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)B->smem)) != cudaSuccess) {
+            batch_free(B);
+            return fail(nullptr, PC_ERR_CUDA, "batch setup: %s", cudaGetErrorString(e));
+        }
+        q.grid = persistent_grid(queue_kernel(q.kind), B->smem);
+    }
+    B->kernels_per_run = 6 * count + (int)B->groups.size();
     // one eager run (sets up every kernel), then capture the same sequence
     pc_status ps = batch_enqueue(B, st);
     if (ps != PC_OK || (e = cudaStreamSynchronize(st)) != cudaSuccess) {
@@ -1193,8 +1271,11 @@ pc_status pc_create(const pc_desc* desc, const void* u, const void* v, void* str
     if ((st = plan_bands(h)) != PC_OK) return bail(st);
     if (getenv("PCW_DEBUG"))
         for (const BandPlan& bp : h->plan)
-            fprintf(stderr, "band %2d rows %7d j[%d..%d] k0 %d gt %3d rpc %2d batch %3d arena %7d smem %7zu\n", bp.b,
-                    bp.rows, bp.jlo, bp.jhi, bp.k0, bp.cfg.gt, bp.cfg.rpc, bp.cfg.batch, bp.cfg.arena, bp.smem);
+            fprintf(stderr,
+                    "band %2d rows %7d j[%d..%d] k0 %d gt %3d rpc %2d batch %3d arena %7d smem %7zu arena_b %7d "
+                    "smem_b %7zu\n",
+                    bp.b, bp.rows, bp.jlo, bp.jhi, bp.k0, bp.cfg.gt, bp.cfg.rpc, bp.cfg.batch, bp.cfg.arena, bp.smem,
+                    bp.cfg_b.arena, bp.smem_b);
     // geometry of the base wavelets and filtered wavelets
     int acc = 0;
     for (int j = 1; j <= D.levels; ++j) {
