@@ -348,15 +348,19 @@ __global__ void k_transpose_F(const __grid_constant__ BwdDev bd, const float* __
         FT[B.FToff + ((int64_t)(k >> 2) * RR + q) * 4 + (k & 3)] = (k < bd.m) ? F[B.Foff + (int64_t)k * RR + q] : 0.f;
 }
 
-// Phase 2 on the term-contiguous copy: 8 terms per thread read as two float4 per translate.
+// Phase 2 on the term-contiguous copy: 4 * NQ terms per thread, read as NQ float4 per translate.
+template <int NQ>
 __global__ void __launch_bounds__(256) k_bwd_dv4(const __grid_constant__ BwdDev bd, const float* __restrict__ FT,
                                                  const float* __restrict__ S, float* __restrict__ dv)
 {
     const int n = bd.n;
-    const int kbase = blockIdx.z * 8;
+    const int kbase = blockIdx.z * 4 * NQ;
     const int x0 = blockIdx.y * 16 + threadIdx.y, x1 = blockIdx.x * 16 + threadIdx.x;
     if (x0 >= n || x1 >= n) return;
-    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), c = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 acc[NQ];
+#pragma unroll
+    for (int g = 0; g < NQ; ++g) acc[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int ng = min(NQ, (bd.mp - kbase) >> 2);  // float4 groups present in the copy
     for (int b = 0; b < bd.nb; ++b) {
         const BwdBand& B = bd.band[b];
         const int lg = B.j, njm = B.nj - 1;
@@ -365,7 +369,6 @@ __global__ void __launch_bounds__(256) k_bwd_dv4(const __grid_constant__ BwdDev 
         const int l1lo = -((-(a1 - B.R1 + 1)) >> lg), l1hi = a1 >> lg;
         const int RR = B.R0 * B.R1;
         const float4* Fa = reinterpret_cast<const float4*>(FT + B.FToff) + (int64_t)(kbase >> 2) * RR;
-        const float4* Fc = Fa + RR;
         const float* Sb = S + B.Soff;
         for (int l0 = l0lo; l0 <= l0hi; ++l0) {
             const int q0 = a0 - (l0 << lg);
@@ -374,24 +377,27 @@ __global__ void __launch_bounds__(256) k_bwd_dv4(const __grid_constant__ BwdDev 
             for (int l1 = l1lo; l1 <= l1hi; ++l1) {
                 const int q = q0 * B.R1 + (a1 - (l1 << lg));
                 const float s = __ldg(Sb + (rb + (l1 & njm)) * RR + q);
-                const float4 f0 = __ldg(Fa + q);
-                const float4 f1 = __ldg(Fc + q);
-                a.x = fmaf(f0.x, s, a.x);
-                a.y = fmaf(f0.y, s, a.y);
-                a.z = fmaf(f0.z, s, a.z);
-                a.w = fmaf(f0.w, s, a.w);
-                c.x = fmaf(f1.x, s, c.x);
-                c.y = fmaf(f1.y, s, c.y);
-                c.z = fmaf(f1.z, s, c.z);
-                c.w = fmaf(f1.w, s, c.w);
+#pragma unroll
+                for (int g = 0; g < NQ; ++g) {
+                    if (g < ng) {
+                        const float4 f = __ldg(Fa + (int64_t)g * RR + q);
+                        acc[g].x = fmaf(f.x, s, acc[g].x);
+                        acc[g].y = fmaf(f.y, s, acc[g].y);
+                        acc[g].z = fmaf(f.z, s, acc[g].z);
+                        acc[g].w = fmaf(f.w, s, acc[g].w);
+                    }
+                }
             }
         }
     }
     const int64_t pix = (int64_t)x0 * n + x1;
-    const float r[8] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
-        if (kbase + k < bd.m) dv[(int64_t)(kbase + k) * bd.N + pix] = r[k];
+    for (int g = 0; g < NQ; ++g) {
+        const float r[4] = {acc[g].x, acc[g].y, acc[g].z, acc[g].w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (kbase + 4 * g + k < bd.m) dv[(int64_t)(kbase + 4 * g + k) * bd.N + pix] = r[k];
+    }
 }
 
 // Phase 2.  One thread per pixel (16 x 16 tiles) and KC terms (blockIdx.z picks the chunk);
