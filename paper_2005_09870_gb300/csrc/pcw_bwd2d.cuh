@@ -17,10 +17,15 @@ namespace pcw {
 //   in_bar[p] = sum_i h[i] yl_bar(C) [2C + i = X]  +  sum_i g[i] yh_bar(C) [2C + 2 - LF + i = X]
 // with C - ro.lo in [0, ro.cnt) (or modulo the output length when the output is full).
 // Work items are chunks of 2*CH inputs starting at an even unwrapped position.
+// exact (the filter fills the template, Lf == LF): the outputs ro of a non-wrapping input
+// range ri are exactly the C that the kept positions read, so the window loads need no bounds
+// checks; the positions of a line's last chunk past ri read up to ADJ_SLACK elements (lines)
+// beyond its end, which must lie inside the arena, and are discarded.
+constexpr int ADJ_SLACK = 2 * PASS_CH;
 template <typename T, int LF, int CH>
 __device__ __forceinline__ void pass_hg_adj(const T* yl, const T* yh, int olstride, int ostride, Range ro, int n_out,
                                             T* out, int lstride, int stride, Range ri, int nlines,
-                                            const T (&hr)[LF], const T (&gr)[LF], int tid, int gt)
+                                            const T (&hr)[LF], const T (&gr)[LF], int tid, int gt, bool exact)
 {
     constexpr int WL = CH + LF / 2 - 1;
     const int xs = ri.lo & ~1;               // first chunk start (even, unwrapped)
@@ -37,17 +42,27 @@ __device__ __forceinline__ void pass_hg_adj(const T* yl, const T* yh, int olstri
         const T* ylr = yl + line * olstride;
         const T* yhr = yh + line * olstride;
         T wl[WL], wh[WL];
+        if (exact && !ro.full) {
+            const T* pl = ylr + h0 * ostride;
+            const T* ph = yhr + g0 * ostride;
 #pragma unroll
-        for (int t = 0; t < WL; ++t) {
-            int cl = h0 + t, ch = g0 + t;
-            if (ro.full) {
-                cl &= nom;
-                ch &= nom;
-                wl[t] = ylr[cl * ostride];
-                wh[t] = yhr[ch * ostride];
-            } else {
-                wl[t] = ((unsigned)cl < (unsigned)ro.cnt) ? ylr[cl * ostride] : T(0);
-                wh[t] = ((unsigned)ch < (unsigned)ro.cnt) ? yhr[ch * ostride] : T(0);
+            for (int t = 0; t < WL; ++t) {
+                wl[t] = pl[t * ostride];
+                wh[t] = ph[t * ostride];
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < WL; ++t) {
+                int cl = h0 + t, ch = g0 + t;
+                if (ro.full) {
+                    cl &= nom;
+                    ch &= nom;
+                    wl[t] = ylr[cl * ostride];
+                    wh[t] = yhr[ch * ostride];
+                } else {
+                    wl[t] = ((unsigned)cl < (unsigned)ro.cnt) ? ylr[cl * ostride] : T(0);
+                    wh[t] = ((unsigned)ch < (unsigned)ro.cnt) ? yhr[ch * ostride] : T(0);
+                }
             }
         }
 #pragma unroll
@@ -202,7 +217,9 @@ __device__ __forceinline__ void bwd2d_row(const OpDev<T>& op, const AsmCfg& cfg,
         const int zsz = (lo_only ? 1 : 4) * zq;
         const int ysz = (lo_only ? 1 : 2) * p0.cnt * q1r.cnt;
         const int xsz = first ? B * A1.cnt : p0.cnt * p1.cnt;
-        if (zsz + ysz > A || xsz + ysz > A) {
+        // Y sits ADJ_SLACK below the arena end; the column reads of Z run up to ADJ_SLACK rows
+        // past it (see pass_hg_adj)
+        if (zsz + ysz + ADJ_SLACK > A || xsz + ysz + ADJ_SLACK > A || zsz + ADJ_SLACK * q1r.cnt > A) {
             flag_error(op.err, ERR_ARENA);
             return;
         }
@@ -214,8 +231,9 @@ __device__ __forceinline__ void bwd2d_row(const OpDev<T>& op, const AsmCfg& cfg,
             read_level(op, R, meta, Gth, arena, q0r, q1r, jj, tid, gt);
             group_sync(gt, gid);
         }
-        T* Yl = arena_end - ysz;
+        T* Yl = arena_end - ADJ_SLACK - ysz;
         T* Yh = Yl + p0.cnt * q1r.cnt;
+        const bool exact = (Lf == LF);
         // transpose of axis 0 (lines: columns of Y)
         if (lo_only)
             pass_lo_adj<T>(arena, 1, q1r.cnt, q0r, nj, Yl, 1, q1r.cnt, A0, q1r.cnt, phiS, lenk, S, tid, gt);
@@ -223,12 +241,12 @@ __device__ __forceinline__ void bwd2d_row(const OpDev<T>& op, const AsmCfg& cfg,
 #pragma unroll 1
             for (int h2 = 0; h2 < 2; ++h2)
                 pass_hg_adj<T, LF, CH>(arena + (h2 ? zq : 0), arena + (h2 ? 3 * zq : 2 * zq), 1, q1r.cnt, q0r, nj,
-                                       h2 ? Yh : Yl, 1, q1r.cnt, p0, q1r.cnt, hr, gr, tid, gt);
+                                       h2 ? Yh : Yl, 1, q1r.cnt, p0, q1r.cnt, hr, gr, tid, gt, exact);
         }
         group_sync(gt, gid);
         // transpose of axis 1 (lines: rows of Y)
         if (!first) {
-            pass_hg_adj<T, LF, CH>(Yl, Yh, q1r.cnt, 1, q1r, nj, arena, p1.cnt, 1, p1, p0.cnt, hr, gr, tid, gt);
+            pass_hg_adj<T, LF, CH>(Yl, Yh, q1r.cnt, 1, q1r, nj, arena, p1.cnt, 1, p1, p0.cnt, hr, gr, tid, gt, exact);
             group_sync(gt, gid);
         } else {
             // dL/ds rows in batches, then copied to the scratch
@@ -240,7 +258,7 @@ __device__ __forceinline__ void bwd2d_row(const OpDev<T>& op, const AsmCfg& cfg,
                                    tid, gt);
                 else
                     pass_hg_adj<T, LF, CH>(Yl + r0 * q1r.cnt, Yh + r0 * q1r.cnt, q1r.cnt, 1, q1r, nj, arena, A1.cnt,
-                                           1, A1, nr, hr, gr, tid, gt);
+                                           1, A1, nr, hr, gr, tid, gt, exact);
                 group_sync(gt, gid);
                 for (int e = tid; e < nr * A1.cnt; e += gt) Srow[r0 * A1.cnt + e] = arena[e];
                 group_sync(gt, gid);
