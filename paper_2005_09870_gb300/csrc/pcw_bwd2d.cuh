@@ -123,7 +123,22 @@ __device__ __forceinline__ void read_win(const OpDev<T>& op, const T* __restrict
     st.init(tid, gt, W1);
     if (!r0.full && !r1.full && op.gap >= 0) {
         T* z = Zb + (f0 - r0.lo) * pz + (f1 - r1.lo);
-        for (int idx = tid; idx < tot; idx += gt, st.next()) z[st.a * pz + st.b] = g[idx];
+        // RD loads in flight per thread before their stores
+        constexpr int RD = 4;
+        for (int i0 = tid; i0 < tot; i0 += RD * gt) {
+            T val[RD];
+            int zi[RD];
+#pragma unroll
+            for (int u = 0; u < RD; ++u) {
+                const bool ok = i0 + u * gt < tot;
+                zi[u] = st.a * pz + st.b;
+                val[u] = ok ? __ldg(g + i0 + u * gt) : T(0);
+                st.next();
+            }
+#pragma unroll
+            for (int u = 0; u < RD; ++u)
+                if (i0 + u * gt < tot) z[zi[u]] = val[u];
+        }
     } else {
         for (int idx = tid; idx < tot; idx += gt, st.next()) {
             const int p0 = pmod(f0 + st.a - r0.lo, nj), p1 = pmod(f1 + st.b - r1.lo, nj);
@@ -514,6 +529,49 @@ __global__ void __launch_bounds__(128) k_bwd_dF(const __grid_constant__ BwdDev b
 #pragma unroll
     for (int k = 0; k < KC; ++k)
         if (k < kn) atomicAdd(dF + B.Foff + (int64_t)(kbase + k) * RR + q, acc[k]);
+}
+
+// Phase 3 with the per-pixel window lists: the same blocks as k_bwd_dF, but a region position
+// visits only the (at most `slots`) windows nonzero at its pixel; each thread keeps the m
+// partial sums of its position in its own column of shared memory ([m][128]).
+template <typename T>
+__global__ void __launch_bounds__(128) k_bwd_dF_wl(const __grid_constant__ BwdDev bd, const WSlot<T>* __restrict__ wl,
+                                                   int slots, const T* __restrict__ S, T* __restrict__ dF,
+                                                   const int* __restrict__ blk_off, int chunk)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* acc = reinterpret_cast<T*>(smem_raw) + threadIdx.x;  // acc[k * 128]
+    int b = 0;
+    while (b + 1 < bd.nb && (int)blockIdx.x >= blk_off[b + 1]) ++b;
+    const BwdBand& B = bd.band[b];
+    const int bl = blockIdx.x - blk_off[b];
+    const int qblocks = (B.R0 * B.R1 + 127) / 128;
+    const int qb = bl % qblocks, cb = bl / qblocks;
+    const int RR = B.R0 * B.R1;
+    const int q = qb * 128 + threadIdx.x;
+    if (q >= RR) return;
+    const int n = bd.n, lg = B.j, m = bd.m;
+    const int64_t N = bd.N;
+    for (int k = 0; k < m; ++k) acc[k * 128] = T(0);
+    const int q0 = q / B.R1, q1 = q - q0 * B.R1;
+    const int rows = B.nj * B.nj;
+    const int rbeg = cb * chunk, rend = min(rows, rbeg + chunk);
+    const int lgn = log2i(B.nj);
+#pragma unroll 2
+    for (int rl = rbeg; rl < rend; ++rl) {
+        const int l0 = rl >> lgn, l1 = rl & (B.nj - 1);
+        const int gy = ((l0 << lg) + B.P0 + q0) & (n - 1), gx = ((l1 << lg) + B.P1 + q1) & (n - 1);
+        const int64_t pix = (int64_t)gy * n + gx;
+        const T sv = __ldg(S + B.Soff + (int64_t)rl * RR + q);
+        for (int sl = 0; sl < slots; ++sl) {
+            const WSlot<T> w = load_slot(wl + (int64_t)sl * N + pix);
+            if (w.v != T(0)) acc[w.k * 128] += w.v * sv;
+        }
+    }
+    for (int k = 0; k < m; ++k) {
+        const T a = acc[k * 128];
+        if (a != T(0)) atomicAdd(dF + B.Foff + (int64_t)k * RR + q, a);
+    }
 }
 
 }  // namespace pcw

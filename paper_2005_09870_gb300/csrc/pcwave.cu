@@ -815,8 +815,13 @@ pc_status backward_core(pc_op* h, const T* G, T* du, T* dv, T* dF, T* dG, cudaSt
             }
             offs[h->nb] = tot;
             PC_CUDA(h, cudaMemcpyAsync(h->dfoff_d, offs, sizeof(int) * (h->nb + 1), cudaMemcpyHostToDevice, st));
-            k_bwd_dF<T, 16><<<dim3(tot, 1, (D.m + 15) / 16), 128, 0, st>>>(h->bd, (const T*)h->v_d, S, amask,
-                                                                          h->mwords, dF, h->dfoff_d, chunk);
+            const size_t acc_bytes = (size_t)D.m * 128 * h->esz;
+            if (h->wl_d && acc_bytes <= 48 * 1024)
+                k_bwd_dF_wl<T><<<tot, 128, acc_bytes, st>>>(h->bd, (const WSlot<T>*)h->wl_d, h->wl_slots, S, dF,
+                                                           h->dfoff_d, chunk);
+            else
+                k_bwd_dF<T, 16><<<dim3(tot, 1, (D.m + 15) / 16), 128, 0, st>>>(h->bd, (const T*)h->v_d, S, amask,
+                                                                              h->mwords, dF, h->dfoff_d, chunk);
             count_launch();
         }
     } else {
