@@ -214,7 +214,7 @@ __device__ __forceinline__ void bwd2d_row(const OpDev<T>& op, const AsmCfg& cfg,
             const bool lo_only = (jj == lv0) && k0 > 0;
             const int nj = n >> jj, S = lo_only ? (1 << k0) : 2;
             P0[jj] = lo_only ? range_filter(A0, S, 0, lenk, nj) : range_cascade(p0, Lf, nj);
-            P1[jj] = lo_only ? range_filter(A1, S, 0, lenk, nj) : range_cascade(p1, Lf, nj);
+            P1[jj] = pad_odd(lo_only ? range_filter(A1, S, 0, lenk, nj) : range_cascade(p1, Lf, nj), nj);
             p0 = P0[jj];
             p1 = P1[jj];
         }

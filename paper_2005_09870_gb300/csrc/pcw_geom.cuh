@@ -187,6 +187,16 @@ PCW_HD int64_t block_count(int d, int n, int L, int Lf, int r, int gap, int b, i
     return (int64_t)c0 * c1;
 }
 
+// Arrays of one level are stored row-major with the axis-1 range as pitch, and thread groups
+// walk rows with consecutive lanes; an odd pitch keeps those accesses free of shared-memory bank
+// conflicts.  A non-wrapping range is extended by one coefficient to an odd count: the extra
+// cascade output lies past every filter tap of the input range, so it is exactly zero.
+PCW_HD Range pad_odd(Range q, int n_out)
+{
+    if (!q.full && !(q.cnt & 1) && q.cnt + 1 < n_out) q.cnt += 1;
+    return q;
+}
+
 // Padded line arrays in shared memory.  The 2-D low/high-pass passes read each output's
 // window 2c + [2 - LF, LF - 1] (LF = filter template length >= Lf) without bounds checks; the
 // union output range of an input line spans ceil((lo - Lf + 1) / 2) .. floor((hi + Lf - 2) / 2),

@@ -401,15 +401,18 @@ pc_status plan_band(pc_op* h, const Geo& g, int b, int gt_req, BandPlan* out)
         }
         // adjoint row (bwd2d_row, and the atomic adjoint k_backward): compact arrays
         // (bwd2d_row keeps ADJ_SLACK elements below the arena end and ADJ_SLACK rows after Z)
-        const int64_t Yb = (int64_t)(lo1 ? 1 : 2) * M0.A * M1.c + ADJ_SLACK;
-        const int64_t Zb = (int64_t)(lo1 ? 1 : 4) * M0.c * M1.c;
-        bneed = std::max<int64_t>((int64_t)batch * M1.A + Yb, std::max(Zb + Yb, Zb + ADJ_SLACK * (int64_t)M1.c));
+        // (axis-1 ranges one longer: bwd2d_row pads them to odd counts)
+        const int64_t c1 = M1.c + 1;
+        const int64_t Yb = (int64_t)(lo1 ? 1 : 2) * M0.A * c1 + ADJ_SLACK;
+        const int64_t Zb = (int64_t)(lo1 ? 1 : 4) * M0.c * c1;
+        bneed = std::max<int64_t>((int64_t)batch * M1.A + Yb, std::max(Zb + Yb, Zb + ADJ_SLACK * c1));
         prevZ = Zb;
         for (int jj = lvl0 + 1; jj <= bp.jhi; ++jj) {
-            const int64_t ysz = 2 * (int64_t)M0.lev[jj - 1] * M1.lev[jj] + ADJ_SLACK;
-            const int64_t zsz = 4 * (int64_t)M0.lev[jj] * M1.lev[jj];
+            const int64_t l1 = M1.lev[jj] + 1;
+            const int64_t ysz = 2 * (int64_t)M0.lev[jj - 1] * l1 + ADJ_SLACK;
+            const int64_t zsz = 4 * (int64_t)M0.lev[jj] * l1;
             bneed = std::max(bneed, std::max(prevZ + ysz, zsz + ysz));
-            bneed = std::max(bneed, zsz + ADJ_SLACK * (int64_t)M1.lev[jj]);
+            bneed = std::max(bneed, zsz + ADJ_SLACK * l1);
             prevZ = zsz;
         }
     }
