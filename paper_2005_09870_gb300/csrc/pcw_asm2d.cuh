@@ -311,18 +311,18 @@ __device__ __forceinline__ Row2 row2_setup(const OpDev<T>& op, int b, int rl)
 // returns false (uniformly) when the row length disagrees with row_ptr.
 template <typename T>
 __device__ __forceinline__ bool row2_meta(const OpDev<T>& op, const Row2& R, int b, int* meta, int tid, int gt,
-                                          int gid)
+                                          int gid, bool terms)
 {
     const int n = op.n, L = op.L;
     const int lane = threadIdx.x & 31;
     if (tid < 32) {
-        // OR of the tile masks over the region
+        // OR of the tile masks over the region (only when the active-term list is wanted)
         unsigned long long mw[MAXW];
 #pragma unroll
         for (int w = 0; w < MAXW; ++w) mw[w] = 0ull;
         const int ts0 = op.ts0, ts1 = op.ts1;
         const int s0 = R.g0 / ts0, s1 = R.g1 / ts1;
-        const int nt0 = min(op.tpa0, (R.g0 % ts0 + R.A0.cnt + ts0 - 1) / ts0);
+        const int nt0 = terms ? min(op.tpa0, (R.g0 % ts0 + R.A0.cnt + ts0 - 1) / ts0) : 0;
         const int nt1 = min(op.tpa1, (R.g1 % ts1 + R.A1.cnt + ts1 - 1) / ts1);
         for (int i = lane; i < nt0 * nt1; i += 32) {
             const int i0 = i / nt1;
@@ -353,7 +353,7 @@ __device__ __forceinline__ bool row2_meta(const OpDev<T>& op, const Row2& R, int
         int na = 0;
 #pragma unroll
         for (int w = 0; w < MAXW; ++w) {
-            if (w >= op.mwords) break;
+            if (w >= op.mwords || !terms) break;
             const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)mw[w]);
             const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(mw[w] >> 32));
 #pragma unroll
@@ -424,7 +424,7 @@ __device__ __forceinline__ void asm2d_row(const OpDev<T>& op, const AsmCfg& cfg,
     T* const arena_end = arena + cfg.arena;
     const int A = cfg.arena;
     const Row2 R = row2_setup(op, cfg.b, rl);
-    if (!row2_meta(op, R, cfg.b, meta, tid, gt, gid)) return;
+    if (!row2_meta(op, R, cfg.b, meta, tid, gt, gid, op.wl == nullptr)) return;  // window lists: no term list
     const int k0 = R.k0;
     const int lenk = (k0 > 0) ? wav_len(k0, Lf) : 0;
 

@@ -183,7 +183,7 @@ __device__ __forceinline__ void bwd2d_row(const OpDev<T>& op, const AsmCfg& cfg,
     const int k0_band = (op.gap < 0) ? 0 : max(1, band_info(2, n, op.L, cfg.b).j - op.gap) - 1;
     const int lenk = (k0_band > 0) ? wav_len(k0_band, Lf) : 0;
     const Row2 R = row2_setup(op, cfg.b, rl);
-    if (!row2_meta(op, R, cfg.b, meta, tid, gt, gid)) return;
+    if (!row2_meta(op, R, cfg.b, meta, tid, gt, gid, amask_out != nullptr)) return;
     const int k0 = R.k0;
     (void)k0_band;
 

@@ -762,6 +762,9 @@ pc_status backward_core(pc_op* h, const T* G, T* du, T* dv, T* dF, T* dG, cudaSt
     PC_CUDA(h, cudaMemsetAsync(dF, 0, h->esz * h->Ftotal, st));
     OpDev<T> od = make_opdev<T>(h);
     if (D.dim == 2 && S) {
+        // phase 3 sums over the window lists when they exist: no active-term masks needed then
+        const bool dF_wl = h->wl_d && (size_t)D.m * 128 * h->esz <= 48 * 1024;
+        if (dF_wl) amask = nullptr;
         bool queued = false;
         if constexpr (std::is_same<T, float>::value) {
             if (h->q_items_b_d && h->q_smem_b <= 110 * 1024) {
@@ -819,7 +822,7 @@ pc_status backward_core(pc_op* h, const T* G, T* du, T* dv, T* dF, T* dG, cudaSt
             offs[h->nb] = tot;
             PC_CUDA(h, cudaMemcpyAsync(h->dfoff_d, offs, sizeof(int) * (h->nb + 1), cudaMemcpyHostToDevice, st));
             const size_t acc_bytes = (size_t)D.m * 128 * h->esz;
-            if (h->wl_d && acc_bytes <= 48 * 1024)
+            if (dF_wl)
                 k_bwd_dF_wl<T><<<tot, 128, acc_bytes, st>>>(h->bd, (const WSlot<T>*)h->wl_d, h->wl_slots, S, dF,
                                                            h->dfoff_d, chunk);
             else
