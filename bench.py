@@ -117,6 +117,28 @@ def cpu_oracle_rate(op, seconds, seed=5, max_cols=65536):
     return entries / wall, done, threads, wall
 
 
+# ---------------- multi-rank plumbing (one process per GPU, replicas of the workload) ----------------
+def rank_workload(name, rank):
+    """The rank's replica: the same workload shape with rank-dependent seeds (independent data)."""
+    import pc_inputs as P
+    return P.workload(name, seed_offset=rank)
+
+
+def max_over_ranks(x, device, world):
+    """Max of a per-rank float over the process group (the slowest rank times the job)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, units_per_rank, ms):
+    """Weak scaling: every rank processes its own replica; units of all ranks / the max time."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 def run_reference(args, rank, world):
     """The oracle arm: FP64 CPU Algorithm 2 on the host cores, rank 0 only."""
     if rank != 0:
@@ -160,7 +182,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream()
-    op = P.workload(args.workload, seed_offset=rank)
+    op = rank_workload(args.workload, rank)
     u = torch.tensor(op.u, dtype=torch.float32, device=dev)
     v = torch.tensor(op.v, dtype=torch.float32, device=dev)
     g = pw.PCOperator(pw.desc_of(op, pw.PC_FP32, 1), u, v)
@@ -208,13 +230,9 @@ def run_ours(args, rank, world, local_rank):
     g.sync()
     ph = np.array([[ev[i][k].elapsed_time(ev[i][k + 1]) for k in range(4)] for i in range(args.steps)])
     step_ms = ph.sum(axis=1)
-    ms = float(step_ms.mean())
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(float(step_ms.mean()), dev, world)
     prep_ms, rows_ms, apply_ms, bwd_ms = (float(a) for a in ph.mean(axis=0))
-    value = world * nnz / (ms * 1e-3)
+    value = job_value(world, nnz, ms)
 
     # ---------------- end to end through the C-ABI with host buffers ----------------
     u_h = torch.tensor(op.u, dtype=torch.float32).pin_memory()
@@ -239,8 +257,8 @@ def run_ours(args, rank, world, local_rank):
         dv_h.copy_(dv, non_blocking=True)
         if e: e[1].record(stream)
     torch.cuda.synchronize()
-    e2e_ms = float(np.mean([a.elapsed_time(b) for a, b in e2e_ev]))
-    e2e_value = world * nnz / (e2e_ms * 1e-3)
+    e2e_ms = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in e2e_ev])), dev, world)
+    e2e_value = job_value(world, nnz, e2e_ms)
 
     # ---------------- plain FP64 single-operator baseline (same kernels in FP64) ----------------
     u64 = torch.tensor(op.u, dtype=torch.float64, device=dev)
