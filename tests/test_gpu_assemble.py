@@ -23,6 +23,9 @@ CASES = [
     ("small-2d", {"delta": 2, "levels": 4}),
     ("small-2d", {"n": 32, "levels": 4, "r": 4}),        # supports wrap the torus
     ("small-2d", {"n": 128, "levels": 5, "r": 5}),       # LL-only first levels for coarse rows
+    ("small-2d", {"delta": 3}),                          # db3: 6 taps in the 8-tap template (zero-padded)
+    ("small-2d", {"delta": 1, "levels": 4}),             # Haar: 2-tap template
+    ("small-2d", {"delta": 5, "n": 128, "levels": 3}),   # db5: 10 taps in the 20-tap template
     ("c1", {}),                                          # dense 256 x 256
 ]
 

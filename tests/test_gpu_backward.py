@@ -38,6 +38,8 @@ def _random_G(op, g, seed):
                                      ("small-1d", {"n": 64, "levels": 5, "r": 7}),
                                      ("small-2d", {"n": 32, "levels": 3}), ("small-2d", {"n": 32, "levels": 3, "order": 1}),
                                      ("small-2d", {"n": 32, "levels": 4, "r": 4}), ("small-2d", {"n": 64, "levels": 4, "gap": 1}),
+                                     ("small-2d", {"n": 32, "levels": 3, "delta": 3}),
+                                     ("small-2d", {"n": 32, "levels": 3, "delta": 1}),
                                      ("c1", {})])
 @pytest.mark.parametrize("precision", [0, 1], ids=["fp32", "fp64"])
 def test_backward_matches_oracle(pw, name, kw, precision):
