@@ -337,7 +337,8 @@ def run_ours(args, rank, world, local_rank):
             f64 += a.elapsed_time(b)
             x.close()
         batch_info = {"workload": "64 operators: 32 1-D (n=2^10..2^16) + 32 2-D (64^2..512^2), m 4..25, "
-                                  "kernel widths 5..31, db2/db4, L 3..6; one persistent launch, CUDA graph",
+                                  "kernel widths 5..31, db2/db4, L 3..6; one persistent launch per kernel kind (1-D, "
+                                  "db2, db4 templates), side by side, in one CUDA graph",
                       "nnz": bnnz, "work_items": items, "fp32_batched_ms": batch_ms,
                       "fp32_batched_entries_per_s": bnnz / (batch_ms * 1e-3),
                       "fp64_plain_ms": f64, "fp64_plain_entries_per_s": bnnz / (f64 * 1e-3),

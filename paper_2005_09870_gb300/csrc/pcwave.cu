@@ -108,6 +108,10 @@ struct pc_batch {
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    // the kinds' persistent launches run side by side: group g > 0 on side[g - 1], forked
+    // from and joined back into the run's stream by events
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> fork, join;
 };
 
 namespace {
@@ -1038,11 +1042,18 @@ pc_status batch_enqueue(pc_batch* B, cudaStream_t st)
         if (ps != PC_OK) return ps;
     }
     if (cudaMemsetAsync(B->counter_d, 0, sizeof(int) * B->groups.size(), st) != cudaSuccess) return PC_ERR_CUDA;
-    for (size_t gi = 0; gi < B->groups.size(); ++gi) {
+    const size_t ng = B->groups.size();
+    if (ng > 1 && cudaEventRecord(B->fork[0], st) != cudaSuccess) return PC_ERR_CUDA;
+    for (size_t gi = 0; gi < ng; ++gi) {
         const QGroup& q = B->groups[gi];
-        queue_kernel(q.kind)<<<q.grid, 256, B->smem, st>>>(B->ops_d, B->items_d + q.start, q.count,
+        cudaStream_t sg = gi ? B->side[gi - 1] : st;
+        if (gi && cudaStreamWaitEvent(sg, B->fork[0], 0) != cudaSuccess) return PC_ERR_CUDA;
+        queue_kernel(q.kind)<<<q.grid, 256, B->smem, sg>>>(B->ops_d, B->items_d + q.start, q.count,
                                                            B->counter_d + gi);
         count_launch();
+        if (gi && (cudaEventRecord(B->join[gi - 1], sg) != cudaSuccess ||
+                   cudaStreamWaitEvent(st, B->join[gi - 1], 0) != cudaSuccess))
+            return PC_ERR_CUDA;
     }
     if (cudaGetLastError() != cudaSuccess) return PC_ERR_CUDA;
     for (pc_op* h : B->ops) {
@@ -1058,6 +1069,9 @@ void batch_free(pc_batch* B)
     if (B->exec) cudaGraphExecDestroy(B->exec);
     if (B->graph) cudaGraphDestroy(B->graph);
     if (B->cap) cudaStreamDestroy(B->cap);
+    for (cudaStream_t s : B->side) cudaStreamDestroy(s);
+    for (cudaEvent_t e : B->fork) cudaEventDestroy(e);
+    for (cudaEvent_t e : B->join) cudaEventDestroy(e);
     if (B->ops_d) cudaFree(B->ops_d);
     if (B->items_d) cudaFree(B->items_d);
     if (B->counter_d) cudaFree(B->counter_d);
@@ -1120,6 +1134,27 @@ pc_status batch_build(pc_handle* ops, int count, cudaStream_t st, bool capture, 
         q.grid = persistent_grid(queue_kernel(q.kind), B->smem);
     }
     B->kernels_per_run = 6 * count + (int)B->groups.size();
+    {
+        cudaEvent_t ev;
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) {
+            batch_free(B);
+            return fail(nullptr, PC_ERR_CUDA, "batch setup: %s", cudaGetErrorString(e));
+        }
+        B->fork.push_back(ev);
+        for (size_t gi = 1; gi < B->groups.size(); ++gi) {
+            cudaStream_t s2;
+            if ((e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking)) != cudaSuccess) {
+                batch_free(B);
+                return fail(nullptr, PC_ERR_CUDA, "batch setup: %s", cudaGetErrorString(e));
+            }
+            B->side.push_back(s2);
+            if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) {
+                batch_free(B);
+                return fail(nullptr, PC_ERR_CUDA, "batch setup: %s", cudaGetErrorString(e));
+            }
+            B->join.push_back(ev);
+        }
+    }
     // one eager run (sets up every kernel), then capture the same sequence
     pc_status ps = batch_enqueue(B, st);
     if (ps != PC_OK || (e = cudaStreamSynchronize(st)) != cudaSuccess) {
