@@ -356,7 +356,8 @@ def run_ours(args, rank, world, local_rank):
         except Exception:
             traffic = None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel": "k_assemble_batch (row assembly: one persistent launch over all row bands)",
+            "traffic": traffic, "kernel": "stage 1 of the assembly: k_s_rows (s of every row) + k_assemble_batch "
+                                   "(localized transforms, one persistent launch over all row bands)",
             "peak_kind": peak_kind}
 
     cpu = None

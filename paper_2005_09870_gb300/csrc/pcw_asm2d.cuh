@@ -275,6 +275,55 @@ __device__ __forceinline__ void write_win(const OpDev<T>& op, const T* Zb, int p
     }
 }
 
+// Stage 1 of every stored 2-D row in one launch: s(q) = sum over the window list of pixel
+// g + q of v_k * F_{k,b}(q), compensated, in the slot order of s_stage_wl (the same values),
+// written to op.sf + Soff[b] + rl * RR + q.  One CTA per stored row (blockIdx.x = canonical
+// row index); its threads walk the region positions.
+template <typename T>
+__global__ void __launch_bounds__(256) k_s_rows(const OpDev<T>* __restrict__ opd)
+{
+    __shared__ const T* F0s;
+    __shared__ T* outs;
+    __shared__ int g0s, g1s, c1s, RRs;
+    const OpDev<T>& op = *opd;  // device copy (refreshed before each run, also inside graphs)
+    const int n = op.n, nm = n - 1;
+    if (threadIdx.x == 0) {
+        const int64_t srow = blockIdx.x;
+        int b = op.nb - 1;
+        while (b > 0 && band_info(2, n, op.L, b).off > srow) --b;
+        const Band Bo = band_info(2, n, op.L, b);
+        const int rl = (int)(srow - Bo.off);
+        const int lg = log2i(Bo.nj);
+        const Range R0 = region0(Bo.j, Bo.e0, rl >> lg, op.r, op.Lf, n);
+        const Range R1 = region0(Bo.j, Bo.e1, rl & (Bo.nj - 1), op.r, op.Lf, n);
+        g0s = pmod(R0.lo, n);
+        g1s = pmod(R1.lo, n);
+        c1s = R1.cnt;
+        RRs = R0.cnt * R1.cnt;
+        F0s = op.F + op.Foff[b];
+        outs = op.sf + op.Soff[b] + (int64_t)rl * RRs;
+    }
+    __syncthreads();
+    const int g0 = g0s, g1 = g1s, c1 = c1s, RR = RRs;
+    const T* F0 = F0s;
+    T* out = outs;
+    const WSlot<T>* wl = reinterpret_cast<const WSlot<T>*>(op.wl);
+    const int S = op.wl_slots;
+    const int64_t N = op.N;
+    Stepper st;  // a = q0, b = q1
+    st.init(threadIdx.x, blockDim.x, c1);
+    for (int q = threadIdx.x; q < RR; q += blockDim.x, st.next()) {
+        const int64_t pix = (int64_t)((g0 + st.a) & nm) * n + ((g1 + st.b) & nm);
+        T s = T(0), c = T(0);
+#pragma unroll 2
+        for (int sl = 0; sl < S; ++sl) {
+            const WSlot<T> w = load_slot(wl + (int64_t)sl * N + pix);
+            if (w.v != T(0)) kahan_add(s, c, w.v * __ldg(F0 + (int64_t)w.k * RR + q));
+        }
+        out[q] = s;
+    }
+}
+
 // Per-row constants of a 2-D row.
 struct Row2 {
     Band Bo;
@@ -487,10 +536,32 @@ __device__ __forceinline__ void asm2d_row(const OpDev<T>& op, const AsmCfg& cfg,
                 if (bi == 0 && !lo_only) zero_gaps<T, 2 * LF - 2>(arena, mg, B, A1.cnt, XP, tid, gt);
                 // per-pixel window lists: a fixed number of slots per pixel, each a dependent
                 // pair of loads, instead of every window active somewhere in the region
-                if (op.wl)
+                if (op.sf) {
+                    // s rows computed for all rows beforehand (k_s_rows): RD loads in flight
+                    constexpr int RD = 4;
+                    const T* sr = op.sf + op.Soff[cfg.b] + (int64_t)rl * RR + r0 * A1.cnt;
+                    const int tot = nr * A1.cnt;
+                    Stepper sq;  // a = row, b = column
+                    sq.init(tid, gt, A1.cnt);
+                    for (int i0 = tid; i0 < tot; i0 += RD * gt) {
+                        T val[RD];
+                        int xi[RD];
+#pragma unroll
+                        for (int u = 0; u < RD; ++u) {
+                            const int e = i0 + u * gt;
+                            xi[u] = sq.a * XP + sq.b;
+                            val[u] = (e < tot) ? __ldg(sr + e) : T(0);
+                            sq.next();
+                        }
+#pragma unroll
+                        for (int u = 0; u < RD; ++u)
+                            if (i0 + u * gt < tot) xs0[xi[u]] = val[u];
+                    }
+                } else if (op.wl) {
                     s_stage_wl<T, P>(op, Fb, RR, A1.cnt, r0, nr, R.g0, R.g1, xs0, XP, tid, gt);
-                else
+                } else {
                     s_stage<T, P>(op, Fb, RR, A1.cnt, r0, nr, R.g0, R.g1, act, nact, xs0, XP, tid, gt);
+                }
                 group_sync(gt, gid);
             }
             if (lo_only) {

@@ -47,6 +47,8 @@ struct OpDev {
     int* err;
     const void* wl;  // per-pixel window list: slot s of pixel x at wl[s * N + x] (WSlot<T>)
     int wl_slots;    // slots per pixel (the most nonzero windows at any pixel)
+    T* sf;           // 2-D: stage-1 values s of every row (band b at Soff[b], row rl at + rl * RR), or null
+    int64_t Soff[MAXB];
 };
 
 // One nonzero window at a pixel: term index and value (8 bytes for FP32, 16 for FP64).

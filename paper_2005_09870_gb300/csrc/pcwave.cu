@@ -63,7 +63,10 @@ struct pc_op {
     void* G_d = nullptr;
     void* dF_d = nullptr;  // backward scratch: dL/dF
     void* dG_d = nullptr;  // backward scratch: dL/dG
-    void* S_d = nullptr;   // backward scratch: dL/ds of every row (2-D)
+    void* S_d = nullptr;   // 2-D: stage-1 values s of every row (assembly), then dL/ds (backward)
+    int* sblk_d = nullptr;  // first k_s_rows block of each band
+    int sblk_total = 0;
+    void* od_d = nullptr;   // device copy of the operator descriptor for k_s_rows
     unsigned long long* amask_d = nullptr;  // backward scratch: active terms per row (2-D)
     int64_t Stotal = 0;
     int64_t FTtotal = 0;  // term-contiguous copy of F (FP32 backward), after dG in its scratch
@@ -497,6 +500,8 @@ OpDev<T> make_opdev(pc_op* h)
     o.tpa1 = h->tpa1;
     o.err = h->err_d;
     o.wl = h->wl_d;
+    o.sf = (h->desc.dim == 2) ? (T*)h->S_d : nullptr;
+    for (int b = 0; b < h->nb; ++b) o.Soff[b] = h->bd.band[b].Soff;
     o.wl_slots = h->wl_slots;
     return o;
 }
@@ -571,6 +576,21 @@ pc_status prepare_t(pc_op* h, cudaStream_t st)
     return PC_OK;
 }
 
+// Stage 1 of every 2-D row (k_s_rows) into the s scratch, before the row kernels.
+template <typename T>
+pc_status s_rows_t(pc_op* h, const OpDev<T>& od, cudaStream_t st, const OpDev<T>* od_dev = nullptr)
+{
+    if (h->desc.dim != 2 || !h->S_d) return PC_OK;
+    if (!od_dev) {
+        PC_CUDA(h, cudaMemcpyAsync(h->od_d, &od, sizeof(od), cudaMemcpyHostToDevice, st));
+        od_dev = (const OpDev<T>*)h->od_d;
+    }
+    k_s_rows<T><<<(int)h->N, 256, 0, st>>>(od_dev);
+    count_launch();
+    PC_CUDA(h, cudaGetLastError());
+    return PC_OK;
+}
+
 template <typename T>
 pc_status assemble_t(pc_op* h, cudaStream_t st, int stage_mask)
 {
@@ -587,6 +607,8 @@ pc_status assemble_t(pc_op* h, cudaStream_t st, int stage_mask)
             // one persistent launch over all row bands, longest work items first
             const OpDev<float> od = make_opdev<float>(h);
             PC_CUDA(h, cudaMemcpyAsync(h->q_op_d, &od, sizeof(od), cudaMemcpyHostToDevice, st));
+            pc_status sp = s_rows_t<float>(h, od, st, h->q_op_d);
+            if (sp != PC_OK) return sp;
             PC_CUDA(h, cudaMemsetAsync(h->q_counter_d, 0, sizeof(int), st));
             queue_kernel(h->q_kind)<<<h->q_grid, 256, h->q_smem, st>>>(h->q_op_d, h->q_items_d, h->q_nitems,
                                                                        h->q_counter_d);
@@ -598,6 +620,10 @@ pc_status assemble_t(pc_op* h, cudaStream_t st, int stage_mask)
     }
     // A5: one launch per row band
     OpDev<T> od = make_opdev<T>(h);
+    {
+        pc_status sp = s_rows_t<T>(h, od, st);
+        if (sp != PC_OK) return sp;
+    }
     for (const BandPlan& bp : h->plan) {
         const int ctas = (bp.rows + bp.cfg.rpc - 1) / bp.cfg.rpc;
         const int threads = bp.cfg.gt * bp.cfg.rpc;
@@ -867,7 +893,7 @@ pc_status backward_t(pc_op* h, const T* G, T* du, T* dv, cudaStream_t st)
         pc_status a;
         if ((a = dev_alloc(h, &h->dF_d, h->esz * h->Ftotal)) != PC_OK) return a;
         if ((a = dev_alloc(h, &h->dG_d, h->esz * ((h->Gtotal + 3) / 4 * 4 + h->FTtotal))) != PC_OK) return a;
-        if (h->desc.dim == 2 && (a = dev_alloc(h, &h->S_d, h->esz * h->Stotal)) != PC_OK) return a;
+        if (h->desc.dim == 2 && !h->S_d && (a = dev_alloc(h, &h->S_d, h->esz * h->Stotal)) != PC_OK) return a;
         if (h->desc.dim == 2 &&
             (a = dev_alloc(h, &h->amask_d, sizeof(unsigned long long) * h->N * h->mwords)) != PC_OK)
             return a;
@@ -964,7 +990,7 @@ pc_status build_window_list(pc_op* h, cudaStream_t st)
 void free_all(pc_op* h)
 {
     void* ptrs[] = {h->u_d,  h->v_d,        h->taps64_d,  h->wav64_d,  h->tapsT_d, h->wavT_d, h->F_d,
-                    h->G_d,  h->dF_d, h->dG_d, h->S_d, h->amask_d, h->wl_d, h->cnt_d, h->dfoff_d, h->q_items_d, h->q_items_b_d, h->q_op_d, h->q_counter_d, h->row_ptr_d,  h->theta_d,   h->theta16_d, h->masks_d, h->err_d};
+                    h->G_d,  h->dF_d, h->dG_d, h->S_d, h->amask_d, h->wl_d, h->cnt_d, h->dfoff_d, h->q_items_d, h->q_items_b_d, h->q_op_d, h->q_counter_d, h->row_ptr_d,  h->theta_d,   h->theta16_d, h->sblk_d, h->od_d, h->masks_d, h->err_d};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -1037,8 +1063,10 @@ pc_status build_queue(pc_op* h)
 // persistent kernel.
 pc_status batch_enqueue(pc_batch* B, cudaStream_t st)
 {
-    for (pc_op* h : B->ops) {
+    for (size_t i = 0; i < B->ops.size(); ++i) {
+        pc_op* h = B->ops[i];
         pc_status ps = prepare_t<float>(h, st);
+        if (ps == PC_OK) ps = s_rows_t<float>(h, B->od[i], st, B->ops_d + i);
         if (ps != PC_OK) return ps;
     }
     if (cudaMemsetAsync(B->counter_d, 0, sizeof(int) * B->groups.size(), st) != cudaSuccess) return PC_ERR_CUDA;
@@ -1134,6 +1162,7 @@ pc_status batch_build(pc_handle* ops, int count, cudaStream_t st, bool capture, 
         q.grid = persistent_grid(queue_kernel(q.kind), B->smem);
     }
     B->kernels_per_run = 6 * count + (int)B->groups.size();
+    for (pc_op* h : B->ops) B->kernels_per_run += (h->desc.dim == 2 && h->S_d) ? 1 : 0;  // k_s_rows
     {
         cudaEvent_t ev;
         if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) {
@@ -1417,6 +1446,23 @@ pc_status pc_create(const pc_desc* desc, const void* u, const void* v, void* str
         (st = dev_alloc(h, &h->err_d, sizeof(int))))
         return bail(st);
     if (D.store_bf16 && (st = dev_alloc(h, &h->theta16_d, sizeof(__nv_bfloat16) * h->nnz))) return bail(st);
+    if (D.dim == 2) {
+        // s scratch (stage 1 of the assembly, dL/ds of the backward) and the k_s_rows grid
+        std::vector<int> sblk(h->nb + 1, 0);
+        int64_t tot = 0;
+        for (int b = 0; b < h->nb; ++b) {
+            sblk[b] = (int)tot;
+            const int64_t RR = (int64_t)h->bd.band[b].R0 * h->bd.band[b].R1;
+            tot += band_rows(g, b) * ((RR + 255) / 256);
+        }
+        sblk[h->nb] = (int)tot;
+        h->sblk_total = (int)tot;
+        if ((st = dev_alloc(h, &h->S_d, h->esz * h->Stotal)) || (st = dev_alloc(h, &h->sblk_d, sizeof(int) * (h->nb + 1))) ||
+            (st = dev_alloc(h, &h->od_d, std::max(sizeof(OpDev<double>), sizeof(OpDev<float>)))))
+            return bail(st);
+        if (cudaMemcpy(h->sblk_d, sblk.data(), sizeof(int) * (h->nb + 1), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(fail(h, PC_ERR_CUDA, "upload failed"));
+    }
     cudaError_t e;
     if ((e = cudaMemcpyAsync(h->taps64_d, h->h, sizeof(double) * h->Lf, cudaMemcpyHostToDevice, s)) ||
         (e = cudaMemcpyAsync(h->row_ptr_d, h->row_ptr_h.data(), sizeof(int64_t) * (h->N + 1), cudaMemcpyHostToDevice,
