@@ -1,7 +1,8 @@
 // 2-D row assembly (A5) and its adjoint (A7), register-blocked.
 //
-// One stored row per thread group (gt threads; several groups per CTA).  Per row:
-//   s(q) = sum_{k active} v_k(g + q) F_{k,b}(q)            compensated over k (FP32)
+// Stage 1 (k_s_rows, one launch over all rows): s(q) = sum_k v_k(g + q) F_{k,b}(q) over the
+// windows nonzero at each pixel, compensated over k (FP32), into the s scratch.
+// Stage 2, one stored row per thread group (gt threads; several groups per CTA): the row's s,
 //   level 1 (or LL of level k0 by the scaling filter phi_{k0} at stride 2^k0 for rows whose
 //   finest kept level is k0 + 1), then the cascade on LL up to the coarsest kept level; the
 //   coefficients inside the row's stencil windows are written to its storage segment.
@@ -49,100 +50,6 @@ struct Stepper {
         }
     }
 };
-
-// s over pixel rows [q0b, q0b + nrows) of the region (F rows of pitch R1) into X (row pitch XP)
-template <typename T, int P>
-__device__ __forceinline__ void s_stage(const OpDev<T>& op, const T* __restrict__ Fb, int RR, int R1, int q0b,
-                                        int nrows, int g0, int g1, const unsigned char* act, int nact, T* X, int XP,
-                                        int tid, int gt)
-{
-    const int tot = nrows * R1;
-    const int n = op.n, nm = n - 1;
-    const int64_t N = op.N;
-    Stepper st;
-    st.init(tid, gt, R1);
-    for (int e0 = tid; e0 < tot; e0 += gt * P) {
-        int pix[P], xo[P], xs[P];
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-            const bool ok = e0 + p * gt < tot;
-            const int bq = ok ? st.a : 0, q1 = ok ? st.b : 0;
-            const int gy = (g0 + q0b + bq) & nm, gx = (g1 + q1) & nm;
-            pix[p] = gy * n + gx;
-            xo[p] = bq * R1 + q1;
-            xs[p] = bq * XP + q1;
-            st.next();
-        }
-        T s[P], c[P];
-#pragma unroll
-        for (int p = 0; p < P; ++p) s[p] = c[p] = T(0);
-        const T* F0 = Fb + q0b * R1;
-#pragma unroll 2
-        for (int t = 0; t < nact; ++t) {
-            const int k = act[t];
-            const T* vk = op.v + (int64_t)k * N;
-            const T* Fk = F0 + (int64_t)k * RR;
-            T vv[P], ff[P];
-#pragma unroll
-            for (int p = 0; p < P; ++p) {
-                vv[p] = __ldg(vk + pix[p]);
-                ff[p] = __ldg(Fk + xo[p]);
-            }
-#pragma unroll
-            for (int p = 0; p < P; ++p) kahan_add(s[p], c[p], vv[p] * ff[p]);
-        }
-#pragma unroll
-        for (int p = 0; p < P; ++p)
-            if (e0 + p * gt < tot) X[xs[p]] = s[p];
-    }
-}
-
-// s over pixel rows [q0b, q0b + nrows) of the region from the per-pixel window lists: each
-// pixel's nonzero windows in increasing k, compensated sum.
-template <typename T, int P>
-__device__ __forceinline__ void s_stage_wl(const OpDev<T>& op, const T* __restrict__ Fb, int RR, int R1, int q0b,
-                                           int nrows, int g0, int g1, T* X, int XP, int tid, int gt)
-{
-    const int tot = nrows * R1;
-    const int n = op.n, nm = n - 1;
-    const int64_t N = op.N;
-    const WSlot<T>* wl = reinterpret_cast<const WSlot<T>*>(op.wl);
-    const int S = op.wl_slots;
-    Stepper st;
-    st.init(tid, gt, R1);
-    const T* F0 = Fb + q0b * R1;
-    for (int e0 = tid; e0 < tot; e0 += gt * P) {
-        int pix[P], xo[P], xs[P];
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-            const bool ok = e0 + p * gt < tot;
-            const int bq = ok ? st.a : 0, q1 = ok ? st.b : 0;
-            const int gy = (g0 + q0b + bq) & nm, gx = (g1 + q1) & nm;
-            pix[p] = gy * n + gx;
-            xo[p] = bq * R1 + q1;
-            xs[p] = bq * XP + q1;
-            st.next();
-        }
-        T s[P], c[P];
-#pragma unroll
-        for (int p = 0; p < P; ++p) s[p] = c[p] = T(0);
-#pragma unroll 2
-        for (int sl = 0; sl < S; ++sl) {
-            WSlot<T> w[P];
-#pragma unroll
-            for (int p = 0; p < P; ++p) w[p] = load_slot(wl + (int64_t)sl * N + pix[p]);
-            T f[P];
-#pragma unroll
-            for (int p = 0; p < P; ++p) f[p] = (w[p].v != T(0)) ? __ldg(F0 + (int64_t)w[p].k * RR + xo[p]) : T(0);
-#pragma unroll
-            for (int p = 0; p < P; ++p)
-                if (w[p].v != T(0)) kahan_add(s[p], c[p], w[p].v * f[p]);
-        }
-#pragma unroll
-        for (int p = 0; p < P; ++p)
-            if (e0 + p * gt < tot) X[xs[p]] = s[p];
-    }
-}
 
 // Zeroes the margins of a padded array: [0, lead) and the pitch - len elements after each of
 // its nl lines (line l at lead + l * pitch).  One line's gap (or the lead) per thread, as up to
@@ -276,7 +183,7 @@ __device__ __forceinline__ void write_win(const OpDev<T>& op, const T* Zb, int p
 }
 
 // Stage 1 of every stored 2-D row in one launch: s(q) = sum over the window list of pixel
-// g + q of v_k * F_{k,b}(q), compensated, in the slot order of s_stage_wl (the same values),
+// g + q of v_k * F_{k,b}(q) (the windows nonzero there, in increasing k), compensated,
 // written to op.sf + Soff[b] + rl * RR + q.  One CTA per stored row (blockIdx.x = canonical
 // row index); its threads walk the region positions.
 template <typename T>
@@ -473,7 +380,7 @@ __device__ __forceinline__ void asm2d_row(const OpDev<T>& op, const AsmCfg& cfg,
     T* const arena_end = arena + cfg.arena;
     const int A = cfg.arena;
     const Row2 R = row2_setup(op, cfg.b, rl);
-    if (!row2_meta(op, R, cfg.b, meta, tid, gt, gid, op.wl == nullptr)) return;  // window lists: no term list
+    if (!row2_meta(op, R, cfg.b, meta, tid, gt, gid, false)) return;  // s comes from k_s_rows: no term list
     const int k0 = R.k0;
     const int lenk = (k0 > 0) ? wav_len(k0, Lf) : 0;
 
@@ -484,9 +391,6 @@ __device__ __forceinline__ void asm2d_row(const OpDev<T>& op, const AsmCfg& cfg,
         gr[i] = fS[LF + i];
     }
     const T* phiS = fS + 2 * LF;
-    const unsigned char* act = reinterpret_cast<const unsigned char*>(meta + ACT_OFF);
-    const int nact = meta[NACT_OFF];
-    const T* Fb = op.F + op.Foff[cfg.b];
     const Range A0 = R.A0, A1 = R.A1;
     const int RR = A0.cnt * A1.cnt;
     const int B = max(1, min(cfg.batch, A0.cnt));
@@ -534,33 +438,25 @@ __device__ __forceinline__ void asm2d_row(const OpDev<T>& op, const AsmCfg& cfg,
             const int nr = first ? min(B, A0.cnt - r0) : p0.cnt;
             if (first) {
                 if (bi == 0 && !lo_only) zero_gaps<T, 2 * LF - 2>(arena, mg, B, A1.cnt, XP, tid, gt);
-                // per-pixel window lists: a fixed number of slots per pixel, each a dependent
-                // pair of loads, instead of every window active somewhere in the region
-                if (op.sf) {
-                    // s rows computed for all rows beforehand (k_s_rows): RD loads in flight
-                    constexpr int RD = 4;
-                    const T* sr = op.sf + op.Soff[cfg.b] + (int64_t)rl * RR + r0 * A1.cnt;
-                    const int tot = nr * A1.cnt;
-                    Stepper sq;  // a = row, b = column
-                    sq.init(tid, gt, A1.cnt);
-                    for (int i0 = tid; i0 < tot; i0 += RD * gt) {
-                        T val[RD];
-                        int xi[RD];
+                // s rows computed for all rows beforehand (k_s_rows): RD loads in flight
+                constexpr int RD = 4;
+                const T* sr = op.sf + op.Soff[cfg.b] + (int64_t)rl * RR + r0 * A1.cnt;
+                const int tot = nr * A1.cnt;
+                Stepper sq;  // a = row, b = column
+                sq.init(tid, gt, A1.cnt);
+                for (int i0 = tid; i0 < tot; i0 += RD * gt) {
+                    T val[RD];
+                    int xi[RD];
 #pragma unroll
-                        for (int u = 0; u < RD; ++u) {
-                            const int e = i0 + u * gt;
-                            xi[u] = sq.a * XP + sq.b;
-                            val[u] = (e < tot) ? __ldg(sr + e) : T(0);
-                            sq.next();
-                        }
-#pragma unroll
-                        for (int u = 0; u < RD; ++u)
-                            if (i0 + u * gt < tot) xs0[xi[u]] = val[u];
+                    for (int u = 0; u < RD; ++u) {
+                        const int e = i0 + u * gt;
+                        xi[u] = sq.a * XP + sq.b;
+                        val[u] = (e < tot) ? __ldg(sr + e) : T(0);
+                        sq.next();
                     }
-                } else if (op.wl) {
-                    s_stage_wl<T, P>(op, Fb, RR, A1.cnt, r0, nr, R.g0, R.g1, xs0, XP, tid, gt);
-                } else {
-                    s_stage<T, P>(op, Fb, RR, A1.cnt, r0, nr, R.g0, R.g1, act, nact, xs0, XP, tid, gt);
+#pragma unroll
+                    for (int u = 0; u < RD; ++u)
+                        if (i0 + u * gt < tot) xs0[xi[u]] = val[u];
                 }
                 group_sync(gt, gid);
             }
