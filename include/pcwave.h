@@ -99,8 +99,9 @@ pc_status pc_plan_row(const pc_desc* desc, int64_t row, int64_t* cols, int64_t* 
 /* Creates an operator.  u: m x (2r+1)^dim kernels, v: m x n^dim windows, both of the
  * precision's type (float for PC_FP32, double for PC_FP64), host or device memory (detected);
  * both are copied.  Computes the FP64 filter taps, plans the pattern (row offsets) and
- * allocates Theta.  Synchronous with respect to the host for planning and allocation; the
- * copies of u and v are ordered on `stream`. */
+ * allocates Theta and, for 2-D operators, the s scratch (one value per region pixel of every
+ * stored row: step 3 below writes it, pc_backward reuses it).  Synchronous with respect to the
+ * host for planning and allocation; the copies of u and v are ordered on `stream`. */
 pc_status pc_create(const pc_desc* desc, const void* u, const void* v, void* stream,
                     pc_handle* out);
 
@@ -138,8 +139,9 @@ pc_status pc_apply(pc_handle h, const void* x, void* y, int nrhs, int ldx, int l
 
 /* The two stages of pc_assemble, for callers that time or overlap them separately:
  * stage 0 = base wavelets, filtered wavelets and window tile masks (steps 1-2 above);
- * stage 1 = the per-row fused window-multiply + localized transform (step 3), which needs a
- * stage 0 for the current parameters before it.  pc_assemble(h, s) equals stage 0 then 1. */
+ * stage 1 = step 3 (for 2-D operators the window-weighted sums of all rows in one launch into
+ * the s scratch, then the per-row localized transforms), which needs a stage 0 for the current
+ * parameters before it.  pc_assemble(h, s) equals stage 0 then 1. */
 pc_status pc_assemble_stage(pc_handle h, int stage, void* stream);
 
 /* Gradient of a loss of Theta.  dtheta: dL/dTheta on the stored entries, same layout and
