@@ -19,7 +19,7 @@ def pw():
 
 @pytest.mark.parametrize("name,kw", [("small-1d", {}), ("small-2d", {"n": 32, "levels": 3}),
                                      ("small-2d", {"n": 32, "levels": 3, "order": 1}), ("c1", {})])
-@pytest.mark.parametrize("nrhs", [1, 3, 16, 21])
+@pytest.mark.parametrize("nrhs", [1, 3, 16, 21, 64])
 @pytest.mark.parametrize("mode", ["fp32", "bf16", "fp64"])
 def test_apply_matches_oracle(pw, name, kw, nrhs, mode):
     import torch
@@ -74,3 +74,21 @@ def test_apply_vector_groups(pw, nrhs, ld):
     rel = np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0)
     assert rel.max() <= 1e-2
     assert torch.all(y[:, nrhs:] == 3.0)
+
+
+def test_apply_errors(pw):
+    """pc_apply before the first assembly, and right-hand-side counts outside 1..64."""
+    import torch
+    op = P.workload("small-2d", n=32, levels=3)
+    g = make_gpu_op(pw, op, bf16=1)
+    x = torch.zeros((op.N, 4), dtype=torch.float32, device="cuda")
+    y = torch.zeros_like(x)
+    with pytest.raises(pw.PCError) as e:
+        pw.pc_apply(g.h, x, y, nrhs=4)
+    assert e.value.status == pw.PC_ERR_NOT_ASSEMBLED
+    g.assemble()
+    for bad in (0, 65):
+        with pytest.raises(pw.PCError) as e:
+            pw.pc_apply(g.h, x, y, nrhs=bad, ldx=max(bad, 1), ldy=max(bad, 1))
+        assert e.value.status == pw.PC_ERR_INVALID_ARG
+    g.sync()

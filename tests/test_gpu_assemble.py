@@ -26,6 +26,11 @@ CASES = [
     ("small-2d", {"delta": 3}),                          # db3: 6 taps in the 8-tap template (zero-padded)
     ("small-2d", {"delta": 1, "levels": 4}),             # Haar: 2-tap template
     ("small-2d", {"delta": 5, "n": 128, "levels": 3}),   # db5: 10 taps in the 20-tap template
+    ("small-2d", {"r": 0}),                              # point kernels (no widening of the supports)
+    ("small-2d", {"gap": 0}),                            # same-level blocks only
+    ("small-2d", {"n": 16, "levels": 2, "r": 1}),        # smallest grid: every range wraps
+    ("small-2d", {"levels": 1}),                         # one level: approximation + one detail level
+    ("small-1d", {"levels": 1}),
     ("c1", {}),                                          # dense 256 x 256
 ]
 
