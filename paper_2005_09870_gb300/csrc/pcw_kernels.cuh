@@ -1038,8 +1038,9 @@ __global__ void __launch_bounds__(256) k_apply_vec(const __grid_constant__ OpDev
 // rows' entries form a banded 16 x K block A (row i holds its W1(i) values at column offset
 // o_i) and the matching K x 16 slab of x (row f0 + a of band b2, columns u .. u + K - 1 mod
 // nj2) is B; mma.sync m16n8k16 (BF16 inputs, FP32 accumulate) adds A B to the warp's 16 x 16
-// accumulator.  x is split into hi + lo BF16 parts (two products) so that the only rounding
-// beyond FP32 is the BF16 storage of S.  Warps' partial sums are reduced in shared memory.
+// accumulator.  x is split once per call into hi + lo BF16 parts (k_split_x; two products) so
+// that the only rounding beyond FP32 is the BF16 storage of S.  Warps' partial sums are reduced
+// in shared memory.
 // ------------------------------------------------------------------------------------------
 struct TcApply {
     int d, n, L, Lf, r, gap, nb;
@@ -1064,9 +1065,22 @@ __device__ __forceinline__ void mma_bf16_16816(float (&c)[4], unsigned a0, unsig
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
+// x (16 right-hand sides from column c0) split once per call into BF16 parts hi + lo (x to
+// ~2^-16 relative), packed per element as hi | lo << 16: xs[i * 16 + c].
+__global__ void k_split_x(const float* __restrict__ x, int ldx, int c0, int64_t N, unsigned* __restrict__ xs)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N * 16) return;
+    const float v = x[(i >> 4) * ldx + c0 + (i & 15)];
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+    xs[i] = (unsigned)__bfloat16_as_ushort(h) | ((unsigned)__bfloat16_as_ushort(l) << 16);
+}
+
 __global__ void __launch_bounds__(128) k_apply_tc(const __grid_constant__ TcApply tp,
-                                                  const __nv_bfloat16* __restrict__ vals, const float* __restrict__ x,
-                                                  int ldx, float* __restrict__ y, int ldy, int c0)
+                                                  const __nv_bfloat16* __restrict__ vals,
+                                                  const unsigned* __restrict__ xs, float* __restrict__ y, int ldy,
+                                                  int c0)
 {
     __shared__ int64_t rbase[16];          // row_ptr of the tile's rows
     __shared__ int boff[16][MAXB];         // block offsets within each row
@@ -1156,18 +1170,14 @@ __global__ void __launch_bounds__(128) k_apply_tc(const __grid_constant__ TcAppl
                 }
 #pragma unroll
                 for (int nt = 0; nt < 2; ++nt) {
-                    float xv[4];
+                    unsigned xp[4];  // (hi, lo) of x at chunk columns 2q, 2q+1, 2q+8, 2q+9
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
                         const int kk = kc + 2 * q + (t & 1) + 8 * (t >> 1);
-                        xv[t] = (kk < K) ? __ldg(x + (xrow + ((u + kk) & m2)) * ldx + c0 + nt * 8 + g) : 0.f;
+                        xp[t] = (kk < K) ? __ldg(xs + (xrow + ((u + kk) & m2)) * 16 + nt * 8 + g) : 0u;
                     }
-                    const unsigned bh0 = pack_bf16(xv[0], xv[1]), bh1 = pack_bf16(xv[2], xv[3]);
-                    float rl[4];
-#pragma unroll
-                    for (int t = 0; t < 4; ++t)
-                        rl[t] = xv[t] - __bfloat162float(__float2bfloat16_rn(xv[t]));
-                    const unsigned bl0 = pack_bf16(rl[0], rl[1]), bl1 = pack_bf16(rl[2], rl[3]);
+                    const unsigned bh0 = __byte_perm(xp[0], xp[1], 0x5410), bh1 = __byte_perm(xp[2], xp[3], 0x5410);
+                    const unsigned bl0 = __byte_perm(xp[0], xp[1], 0x7632), bl1 = __byte_perm(xp[2], xp[3], 0x7632);
                     float(&acc)[4] = nt ? acc1 : acc0;
                     mma_bf16_16816(acc, A[0], A[1], A[2], A[3], bh0, bh1);
                     mma_bf16_16816(acc, A[0], A[1], A[2], A[3], bl0, bl1);

@@ -74,6 +74,7 @@ struct pc_op {
     int64_t* row_ptr_d = nullptr;
     void* theta_d = nullptr;
     __nv_bfloat16* theta16_d = nullptr;
+    unsigned* xsplit_d = nullptr;  // 16 right-hand sides split into packed BF16 hi / lo (tensor-core apply)
     unsigned long long* masks_d = nullptr;
     void* wl_d = nullptr;   // per-pixel window list (slots x N)
     int wl_slots = 0;       // slots allocated and in use
@@ -660,7 +661,7 @@ pc_status apply_t(pc_op* h, const TV* vals, const TA* x, TA* y, int nrhs, int ld
     const int blocks = (int)((warps * 32 + 255) / 256);
     // tensor-core path: BF16 values, paper order, groups of 16 right-hand sides
     if constexpr (std::is_same<TV, __nv_bfloat16>::value && std::is_same<TA, float>::value) {
-        if (!transpose && nrhs >= 16) {
+        if (!transpose && nrhs >= 16 && h->xsplit_d) {
             TcApply tp{};
             tp.d = D.dim;
             tp.n = D.n;
@@ -680,8 +681,9 @@ pc_status apply_t(pc_op* h, const TV* vals, const TA* x, TA* y, int nrhs, int ld
             tp.tile_off[h->nb] = tiles;
             int c = 0;
             for (; nrhs - c >= 16; c += 16) {
-                k_apply_tc<<<tiles, 128, 0, st>>>(tp, vals, x, ldx, y, ldy, c);
-                count_launch();
+                k_split_x<<<(int)((h->N * 16 + 255) / 256), 256, 0, st>>>(x, ldx, c, h->N, h->xsplit_d);
+                k_apply_tc<<<tiles, 128, 0, st>>>(tp, vals, h->xsplit_d, y, ldy, c);
+                count_launch(2);
             }
             PC_CUDA(h, cudaGetLastError());
             if (c == nrhs) return PC_OK;
@@ -990,7 +992,7 @@ pc_status build_window_list(pc_op* h, cudaStream_t st)
 void free_all(pc_op* h)
 {
     void* ptrs[] = {h->u_d,  h->v_d,        h->taps64_d,  h->wav64_d,  h->tapsT_d, h->wavT_d, h->F_d,
-                    h->G_d,  h->dF_d, h->dG_d, h->S_d, h->amask_d, h->wl_d, h->cnt_d, h->dfoff_d, h->q_items_d, h->q_items_b_d, h->q_op_d, h->q_counter_d, h->row_ptr_d,  h->theta_d,   h->theta16_d, h->sblk_d, h->od_d, h->masks_d, h->err_d};
+                    h->G_d,  h->dF_d, h->dG_d, h->S_d, h->amask_d, h->wl_d, h->cnt_d, h->dfoff_d, h->q_items_d, h->q_items_b_d, h->q_op_d, h->q_counter_d, h->row_ptr_d,  h->theta_d,   h->theta16_d, h->xsplit_d, h->sblk_d, h->od_d, h->masks_d, h->err_d};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -1446,6 +1448,7 @@ pc_status pc_create(const pc_desc* desc, const void* u, const void* v, void* str
         (st = dev_alloc(h, &h->err_d, sizeof(int))))
         return bail(st);
     if (D.store_bf16 && (st = dev_alloc(h, &h->theta16_d, sizeof(__nv_bfloat16) * h->nnz))) return bail(st);
+    if (D.store_bf16 && (st = dev_alloc(h, &h->xsplit_d, sizeof(unsigned) * 16 * h->N))) return bail(st);
     if (D.dim == 2) {
         // s scratch (stage 1 of the assembly, dL/ds of the backward) and the k_s_rows grid
         std::vector<int> sblk(h->nb + 1, 0);
