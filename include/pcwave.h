@@ -173,11 +173,12 @@ pc_status pc_backward_noalloc(pc_handle h, const void* dtheta, void* du, void* d
 
 /* ---------------------------------------------------------------------------------------
  * Batches: many operators (any mix of 1-D / 2-D, sizes, terms, kernel radii, db orders and
- * levels; PC_FP32 only) assembled by one persistent launch.  The launch takes work items
- * (operator, row band, run of rows) from a global counter, longest first, each with its own
- * thread-group shape (the operator's plan, see pc_autotune).  The batch object captures the
- * whole sequence (every operator's base and filtered wavelets, the queue reset and the
- * persistent kernel) in a CUDA graph once; pc_batch_run replays it.
+ * levels; PC_FP32 only) assembled by one persistent launch per kernel kind (1-D rows, and
+ * each 2-D filter template), the kinds running side by side.  A launch takes work items
+ * (operator, row band, run of rows) from its own global counter, longest first, each with its
+ * own thread-group shape (the operator's plan, see pc_autotune).  The batch object captures
+ * the whole sequence (every operator's base and filtered wavelets and stage-1 sums, the queue
+ * resets and the persistent kernels) in a CUDA graph once; pc_batch_run replays it.
  * --------------------------------------------------------------------------------------- */
 typedef struct pc_batch* pc_batch_handle;
 

@@ -1,12 +1,13 @@
 // 2-D backward (A7): adjoint of the row assembly, in three phases.
 //
-//   phase 1 (k_backward2d): per stored row s, dL/ds on the row's region by the transposed
-//           localized transform of the row's dL/dTheta entries, written to the scratch S
-//           (band b at Soff[b], row rl at + rl * RR_b, region row-major);
-//   phase 2 (k_bwd_dv):     dL/dv_k(x) = sum_b sum_{rows l covering x} F_{k,b}(x - t_l) S_{b,l}(x - t_l),
-//           one thread per pixel, no atomics;
-//   phase 3 (k_bwd_dF):     dL/dF_{k,b}(q) = sum_l v_k(t_l + q) S_{b,l}(q), chunks of rows per CTA,
-//           one atomic per (k, q, chunk).
+//   phase 1 (k_backward_queue, persistent; k_backward2d per band for FP64): per stored row s,
+//           dL/ds on the row's region by the transposed localized transform of the row's
+//           dL/dTheta entries, written to the scratch S (band b at Soff[b], row rl at
+//           + rl * RR_b, region row-major);
+//   phase 2 (k_bwd_dv4, k_bwd_dv for FP64): dL/dv_k(x) = sum_b sum_{rows l covering x}
+//           F_{k,b}(x - t_l) S_{b,l}(x - t_l), one thread per pixel, no atomics;
+//   phase 3 (k_bwd_dF_wl, k_bwd_dF without window lists): dL/dF_{k,b}(q) =
+//           sum_l v_k(t_l + q) S_{b,l}(q), chunks of rows per CTA, one atomic per (k, q, chunk).
 // The adjoint of F = kappa_k * rho_b (dL/dkappa_k) then runs in k_dfilt_pass2 / pass1.
 #pragma once
 #include "pcw_asm2d.cuh"
