@@ -44,6 +44,76 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+# ---------------- algorithmic FP32 work of stage 1 (the second roofline: the FP32 pipe) ----------------
+# FP32 peak derived from the unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def _cdiv(a, b):
+    return -((-a) // b)
+
+
+def _wlen(j, Lf):
+    return ((1 << j) - 1) * (Lf - 1) + 1
+
+
+def _woff(j, e, Lf):
+    return (1 << (j - 1)) * (2 - Lf) if e else 0
+
+
+def _rng_cascade(lo, cnt, full, Lf, nout):
+    # union of the low- and high-pass output ranges of one cascade step (taps [0, Lf-1], [2-Lf, 1])
+    nlo = _cdiv(lo - Lf + 1, 2)
+    c = (lo + cnt - 1 + Lf - 2) // 2 - nlo + 1
+    return (nlo, nout, 1) if (full or c >= nout) else (nlo, c, 0)
+
+
+def _rng_filter(lo, cnt, full, S, ln, nout):
+    nlo = _cdiv(lo - ln + 1, S)
+    c = (lo + cnt - 1) // S - nlo + 1
+    return (nlo, nout, 1) if (full or c >= nout) else (nlo, c, 0)
+
+
+def assembly_flops(op, phases=8):
+    """Algorithmic FP32 operations of one 2-D assembly (no compensation terms counted): the
+    window-weighted sums (a multiply and an add per nonzero window of each region pixel) and the
+    localized transforms (per output position of a level, both filters: 4 Lf flops per line of
+    the union output range), averaged over `phases` translates per axis of every band."""
+    n, L, Lf, r, gap = op.n, op.levels, 2 * op.delta, op.r, op.gap
+    nzw = float(np.mean((np.asarray(op.v) != 0).sum(axis=0)))   # nonzero windows per pixel
+    bands = [(L, 0, 0)] + [(j, e0, e1) for j in range(L, 0, -1) for (e0, e1) in ((0, 1), (1, 0), (1, 1))]
+    total = 0.0
+    for (j, e0, e1) in bands:
+        nj = n >> j
+        jlo = 1 if gap < 0 else max(1, j - gap)
+        jhi = L if gap < 0 else min(L, j + gap)
+        k0 = jlo - 1
+        lenk = _wlen(k0, Lf) if k0 > 0 else 0
+        acc, cnt = 0.0, 0
+        for l in range(min(nj, phases)):
+            def region(e):
+                lo, c = (l << j) + _woff(j, e, Lf) - r, _wlen(j, Lf) + 2 * r
+                return (lo, n, 1) if c >= n else (lo, c, 0)
+            A0, A1 = region(e0), region(e1)
+            f = 2.0 * nzw * A0[1] * A1[1]
+            p0, p1 = A0, A1
+            for jj in range(1 if k0 == 0 else k0, jhi + 1):
+                njj = n >> jj
+                if jj == k0:   # LL of level k0 by the sampled scaling function at stride 2^k0
+                    q0 = _rng_filter(*A0, 1 << k0, lenk, njj)
+                    q1 = _rng_filter(*A1, 1 << k0, lenk, njj)
+                    f += 2.0 * lenk * (A0[1] * q1[1] + q1[1] * q0[1])
+                else:
+                    q0 = _rng_cascade(*p0, Lf, njj)
+                    q1 = _rng_cascade(*p1, Lf, njj)
+                    f += 4.0 * Lf * (p0[1] * q1[1] + 2 * q1[1] * q0[1])
+                p0, p1 = q0, q1
+            acc += f
+            cnt += 1
+        total += acc / cnt * nj * nj
+    return total
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
@@ -359,6 +429,15 @@ def run_ours(args, rank, world, local_rank):
             "traffic": traffic, "kernel": "stage 1 of the assembly: k_s_rows (s of every row) + k_assemble_batch "
                                    "(localized transforms, one persistent launch over all row bands)",
             "peak_kind": peak_kind}
+    flops = assembly_flops(op) if op.d == 2 else None
+    roof_fp32 = None
+    if flops:
+        tf = flops / (rows_ms * 1e-3) / 1e12
+        roof_fp32 = {"bound": "alu", "achieved": tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": tf / FP32_PEAK_TFLOPS, "flops": flops,
+                     "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                     "note": "algorithmic FP32 work of stage 1 (window sums + localized transforms, "
+                             "compensation terms not counted)"}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -381,6 +460,7 @@ def run_ours(args, rank, world, local_rank):
             "bwd_ms": bwd_ms,
             "batch": batch_info,
             "roofline": roof,
+            "roofline_fp32": roof_fp32,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": e2e_ms},
