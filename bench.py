@@ -168,19 +168,20 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_rate(op, seconds, seed=5, max_cols=65536):
-    """Algorithm 2 (FP64 oracle, OpenMP over columns) on uniformly drawn columns until about
-    `seconds` of oracle time: returns (entries/s counted on the pattern, columns, threads, wall)."""
+def cpu_oracle_rate(op, seconds, seed=5, max_cols=65536, nthreads=0):
+    """Algorithm 2 (FP64 oracle, OpenMP over columns; nthreads 0 = all cores) on uniformly drawn
+    columns until about `seconds` of oracle time: returns (entries/s counted on the pattern,
+    columns, threads, wall)."""
     import oracle
     rng = np.random.default_rng(seed)
-    threads = oracle.max_threads()
-    batch = max(threads, 8)
+    threads = nthreads if nthreads > 0 else oracle.max_threads()
+    batch = max(threads, 8) if nthreads != 1 else 2
     done = entries = 0
     wall = 0.0
     while wall < seconds and done < max_cols:
         cols = rng.integers(0, op.N, size=batch)
         t0 = time.perf_counter()
-        oracle.theta_columns(op, cols)
+        oracle.theta_columns(op, cols, nthreads=threads)
         wall += time.perf_counter() - t0
         entries += sum(int(oracle.pattern_column(op, c).sum()) for c in cols)   # untimed
         done += batch
@@ -442,8 +443,12 @@ def run_ours(args, rank, world, local_rank):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         rate, cols, threads, wall = cpu_oracle_rate(op, args.cpu_seconds)
+        rate1, cols1, _, wall1 = cpu_oracle_rate(op, min(4.0, args.cpu_seconds / 3), seed=6, nthreads=1)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"{cols} uniformly drawn columns of the workload, Algorithm 2 in FP64, {wall:.1f} s"}
+               "sample": f"{cols} uniformly drawn columns of the workload, Algorithm 2 in FP64, {wall:.1f} s",
+               "single_thread": {"value": rate1, "unit": UNIT,
+                                 "sample": f"{cols1} columns on one core, {wall1:.1f} s"},
+               "full_theta_s_extrapolated": nnz / rate}
 
     clocks = clk.summary()
     if rank == 0:
