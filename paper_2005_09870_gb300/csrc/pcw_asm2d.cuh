@@ -374,7 +374,6 @@ __device__ __forceinline__ void asm2d_row(const OpDev<T>& op, const AsmCfg& cfg,
                                           T* arena, int gid, int tid)
 {
     constexpr int CH = PASS_CH;
-    constexpr int P = 4;
     const int gt = cfg.gt;
     const int n = op.n, Lf = op.Lf;
     T* const arena_end = arena + cfg.arena;
