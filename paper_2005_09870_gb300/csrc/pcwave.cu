@@ -1241,6 +1241,7 @@ template <typename T>
 pc_status autotune_t(pc_op* h, cudaStream_t st)
 {
     pc_status ps = prepare_t<T>(h, st);
+    if (ps == PC_OK) ps = s_rows_t<T>(h, make_opdev<T>(h), st);  // the row kernels time on current s rows
     if (ps != PC_OK) return ps;
     h->prepared = true;
     if (h->desc.dim == 1 && set_smem_attr<T, 1>() != PC_OK) return fail(h, PC_ERR_CUDA, "cudaFuncSetAttribute failed");
