@@ -48,6 +48,9 @@ def _load():
         lib.or_pattern_mask.argtypes = [I, I, I, I, I, I, D, _u8p]
         lib.or_theta_grad.argtypes = [I, I, I, I, I, I, I, _dp, _dp, D, _i64p, _dp, _dp, _dp, I]
         lib.or_max_threads.argtypes = []
+        lib.or_jacobi.argtypes = [D, _dp, _dp]
+        lib.or_power_norm.argtypes = [D, _dp, _dp, I, _dp]
+        lib.or_fista.argtypes = [D, _dp, _dp, _dp, _dp, I, ctypes.c_double, _dp]
         _lib = lib
     return _lib
 
@@ -140,3 +143,38 @@ def theta_grad(op, cols, G, u=None, v=None, nthreads: int = 0):
                                du.ctypes.data_as(_dp), dv.ctypes.data_as(_dp), nthreads)
     _check(rc, "theta_grad")
     return du, dv
+
+
+def _opt(a):
+    if a is None:
+        return None, None
+    return _d(np.asarray(a).reshape(-1))
+
+
+def jacobi(T):
+    """diag(Theta^T Theta) of a dense Theta (N, N): the FISTA-WP preconditioner."""
+    T, Tp = _d(T)
+    out = np.zeros(T.shape[0])
+    _check(_load().or_jacobi(T.shape[0], Tp, out.ctypes.data_as(_dp)), "jacobi")
+    return out
+
+
+def power_norm(T, iters, sigma=None):
+    """Power-iteration estimate of the largest eigenvalue of S^(1/2) Theta^T Theta S^(1/2)."""
+    T, Tp = _d(T)
+    _, sp = _opt(sigma)
+    out = ctypes.c_double(0.0)
+    _check(_load().or_power_norm(T.shape[0], Tp, sp, int(iters), ctypes.byref(out)), "power_norm")
+    return out.value
+
+
+def fista(T, z0, w, iters, tau, z_init=None, sigma=None):
+    """FISTA-W (sigma None) / FISTA-WP iterates on the dense Theta; returns z^(iters)."""
+    T, Tp = _d(T)
+    N = T.shape[0]
+    z0, z0p = _d(np.asarray(z0).reshape(-1))
+    w, wp = _d(np.asarray(w).reshape(-1))
+    _, sp = _opt(sigma)
+    z = np.zeros(N) if z_init is None else np.array(z_init, dtype=np.float64).reshape(-1)
+    _check(_load().or_fista(N, Tp, z0p, wp, sp, int(iters), float(tau), z.ctypes.data_as(_dp)), "fista")
+    return z

@@ -465,6 +465,100 @@ int or_theta_grad(int d, int n, int L, int delta, int m, int r, int order,
     return bad ? -1 : 0;
 }
 
+/* ------------------------------------------------------------------------------------
+ * Deblurring in the wavelet domain (Section 4.3, problem min_z 1/2 ||Theta z - z0||^2 +
+ * ||z||_{1,w}, and the FISTA iteration of the appendix on deblurring algorithms).
+ * Theta is a dense row-major N x N array here: Theta[mu * N + lambda].
+ * ------------------------------------------------------------------------------------ */
+
+/* y = Theta x */
+static void dense_mv(int64_t N, const double *T, const double *x, double *y)
+{
+    for (int64_t mu = 0; mu < N; ++mu) {
+        double acc = 0.0;
+        for (int64_t la = 0; la < N; ++la) acc += T[mu * N + la] * x[la];
+        y[mu] = acc;
+    }
+}
+
+/* y = Theta^T x */
+static void dense_mtv(int64_t N, const double *T, const double *x, double *y)
+{
+    for (int64_t la = 0; la < N; ++la) y[la] = 0.0;
+    for (int64_t mu = 0; mu < N; ++mu)
+        for (int64_t la = 0; la < N; ++la) y[la] += T[mu * N + la] * x[mu];
+}
+
+/* Jacobi diagonal diag(Theta^T Theta): out[lambda] = sum_mu Theta[mu, lambda]^2 (the
+ * preconditioner of FISTA-WP). */
+int or_jacobi(int64_t N, const double *T, double *out)
+{
+    for (int64_t la = 0; la < N; ++la) {
+        double acc = 0.0;
+        for (int64_t mu = 0; mu < N; ++mu) acc += T[mu * N + la] * T[mu * N + la];
+        out[la] = acc;
+    }
+    return 0;
+}
+
+/* Power iteration for the largest eigenvalue of M = S^(1/2) Theta^T Theta S^(1/2), with
+ * S = diag(sigma) (identity when sigma is NULL); its inverse bounds the FISTA step.
+ * Start u = (1, ..., 1) / sqrt(N); each iteration g = M u, estimate = ||g||, u = g / ||g||.
+ * Writes the last estimate to *out. */
+int or_power_norm(int64_t N, const double *T, const double *sigma, int iters, double *out)
+{
+    double *u = malloc(sizeof(double) * N), *r = malloc(sizeof(double) * N), *g = malloc(sizeof(double) * N);
+    if (!u || !r || !g) { free(u); free(r); free(g); return -1; }
+    for (int64_t i = 0; i < N; ++i) u[i] = 1.0 / sqrt((double)N);
+    double est = 0.0;
+    for (int it = 0; it < iters; ++it) {
+        if (sigma)
+            for (int64_t i = 0; i < N; ++i) u[i] *= sqrt(sigma[i]);
+        dense_mv(N, T, u, r);
+        dense_mtv(N, T, r, g);
+        if (sigma)
+            for (int64_t i = 0; i < N; ++i) g[i] *= sqrt(sigma[i]);
+        double s = 0.0;
+        for (int64_t i = 0; i < N; ++i) s += g[i] * g[i];
+        est = sqrt(s);
+        for (int64_t i = 0; i < N; ++i) u[i] = (s > 0.0) ? g[i] / est : 0.0;
+    }
+    *out = est;
+    free(u); free(r); free(g);
+    return 0;
+}
+
+/* FISTA in the wavelet domain: z holds z^(0) = y^(1) on entry and z^(iters) on return.
+ * For i = 1..iters:
+ *   z^(i)   = Prox^S (y^(i) - tau S Theta^T (Theta y^(i) - z0)),
+ *   y^(i+1) = z^(i) + (i - 1) / (i + 2) (z^(i) - z^(i-1)),
+ * with S = diag(sigma) (identity when sigma is NULL: FISTA-W; else FISTA-WP) and the prox of
+ * tau ||.||_{1,w} in the metric S^-1: soft thresholding of entry lambda at tau sigma[lambda]
+ * w[lambda]. */
+int or_fista(int64_t N, const double *T, const double *z0, const double *w, const double *sigma,
+             int iters, double tau, double *z)
+{
+    double *y = malloc(sizeof(double) * N), *r = malloc(sizeof(double) * N), *g = malloc(sizeof(double) * N);
+    if (!y || !r || !g) { free(y); free(r); free(g); return -1; }
+    for (int64_t i = 0; i < N; ++i) y[i] = z[i];
+    for (int it = 1; it <= iters; ++it) {
+        dense_mv(N, T, y, r);
+        for (int64_t mu = 0; mu < N; ++mu) r[mu] -= z0[mu];
+        dense_mtv(N, T, r, g);
+        const double beta = (double)(it - 1) / (double)(it + 2);
+        for (int64_t la = 0; la < N; ++la) {
+            const double s = sigma ? sigma[la] : 1.0;
+            const double a = y[la] - tau * s * g[la];
+            const double t = tau * s * w[la];
+            const double zn = (a > t) ? a - t : (a < -t) ? a + t : 0.0;
+            y[la] = zn + beta * (zn - z[la]);
+            z[la] = zn;
+        }
+    }
+    free(y); free(r); free(g);
+    return 0;
+}
+
 int or_max_threads(void)
 {
 #ifdef _OPENMP
