@@ -367,7 +367,7 @@ def run_ours(args, rank, world, local_rank):
         acc = {"fp32_max_rel_err": e32 / ref, "fp64_max_rel_err": e64 / ref, "columns_checked": 8}
     g64.close()
 
-    # ---------------- A8: batched FP32 vs plain FP64 on 64 uneven operators ----------------
+    # ---------------- batched FP32 vs plain FP64 on 64 uneven operators ----------------
     batch_info = None
     if not args.no_batch:
         bops = P.batch_workload(64, seed_offset=rank)

@@ -137,6 +137,40 @@ pc_status pc_assemble(pc_handle h, void* stream);
 pc_status pc_apply(pc_handle h, const void* x, void* y, int nrhs, int ldx, int ldy,
                    void* stream);
 
+/* y = Theta^T x: the adjoint product, same arguments, layout, value copy and errors as
+ * pc_apply.  The product that is not the stored direction scatters with atomic adds, so its
+ * FP32 rounding order (not its value) varies between runs. */
+pc_status pc_apply_adjoint(pc_handle h, const void* x, void* y, int nrhs, int ldx, int ldy,
+                           void* stream);
+
+/* Wavelet-domain deblurring (Section 4.3, min_z 1/2 ||Theta z - z0||^2 + ||z||_{1,w}; the
+ * FISTA-W and FISTA-WP iterations of the appendix on deblurring algorithms).  These three
+ * calls use the FP32 (or FP64) stored values, never the BF16 copy; vectors are N elements of
+ * the handle's type, device, in the canonical coefficient order.  They share handle-owned
+ * scratch of 3 N elements (allocated on first use), so a handle runs one of them at a time.
+ *
+ * pc_jacobi: diag[lambda] = sum_mu Theta[mu, lambda]^2, the diagonal of Theta^T Theta (the
+ * Jacobi preconditioner of FISTA-WP).  diag is overwritten.  Asynchronous.
+ *
+ * pc_power_norm: *norm2 = estimate of the largest eigenvalue of S^(1/2) Theta^T Theta S^(1/2),
+ * S = diag(sigma) (sigma NULL: S = I, so *norm2 estimates ||Theta||_2^2), by `iters` >= 1
+ * power iterations from u = (1, ..., 1)/sqrt(N): g = M u, estimate ||g||, u = g/||g||.  The
+ * estimate never exceeds the eigenvalue; a FISTA step tau <= 1 / *norm2 needs a margin.
+ * Synchronises `stream` (it returns a host value).
+ *
+ * pc_fista: `iters` >= 0 iterations of
+ *     z^(i)   = soft(y^(i) - tau S Theta^T (Theta y^(i) - z0), tau S w),
+ *     y^(i+1) = z^(i) + (i - 1)/(i + 2) (z^(i) - z^(i-1)),
+ * with soft() entrywise soft thresholding and S = diag(sigma) (NULL: FISTA-W; a Jacobi
+ * sigma = 1/pc_jacobi(): FISTA-WP).  z holds z^(0) = y^(1) on entry and z^(iters) on return;
+ * z0 (the observed image's wavelet coefficients) and the weights w (>= 0) are inputs.
+ * tau > 0 (convergence needs tau <= 1 / pc_power_norm(sigma)).  Asynchronous; five kernel
+ * launches per iteration.  PC_ERR_INVALID_ARG for NULL z0/w/z, iters < 0 or tau <= 0. */
+pc_status pc_jacobi(pc_handle h, void* diag, void* stream);
+pc_status pc_power_norm(pc_handle h, const void* sigma, int iters, double* norm2, void* stream);
+pc_status pc_fista(pc_handle h, const void* z0, const void* w, const void* sigma, void* z, int iters,
+                   double tau, void* stream);
+
 /* The two stages of pc_assemble, for callers that time or overlap them separately:
  * stage 0 = base wavelets, filtered wavelets and window tile masks (steps 1-2 above);
  * stage 1 = step 3 (for 2-D operators the window-weighted sums of all rows in one launch into

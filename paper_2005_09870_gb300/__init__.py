@@ -68,6 +68,10 @@ _sig = {
     "pc_lookup": ([_H, _I64, _I64P, _I64P, _I64P], ctypes.c_int),
     "pc_sync": ([_H, _P], ctypes.c_int),
     "pc_last_error": ([_H], ctypes.c_char_p),
+    "pc_apply_adjoint": ([_H, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P], ctypes.c_int),
+    "pc_jacobi": ([_H, _P, _P], ctypes.c_int),
+    "pc_power_norm": ([_H, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
+    "pc_fista": ([_H, _P, _P, _P, _P, ctypes.c_int, ctypes.c_double, _P], ctypes.c_int),
 }
 for _name, (_args, _ret) in _sig.items():
     _f = getattr(_lib, _name)
@@ -174,6 +178,28 @@ def pc_apply(h, x, y, nrhs=None, ldx=None, ldy=None, stream=None):
     ldx = nrhs if ldx is None else ldx
     ldy = nrhs if ldy is None else ldy
     _check(_lib.pc_apply(h, _ptr(x), _ptr(y), nrhs, ldx, ldy, _stream(stream)), h)
+
+
+def pc_apply_adjoint(h, x, y, nrhs=None, ldx=None, ldy=None, stream=None):
+    if nrhs is None:
+        nrhs = 1 if x.dim() == 1 else x.shape[1]
+    ldx = nrhs if ldx is None else ldx
+    ldy = nrhs if ldy is None else ldy
+    _check(_lib.pc_apply_adjoint(h, _ptr(x), _ptr(y), nrhs, ldx, ldy, _stream(stream)), h)
+
+
+def pc_jacobi(h, diag, stream=None):
+    _check(_lib.pc_jacobi(h, _ptr(diag), _stream(stream)), h)
+
+
+def pc_power_norm(h, sigma=None, iters=50, stream=None) -> float:
+    out = ctypes.c_double(0.0)
+    _check(_lib.pc_power_norm(h, _ptr(sigma), int(iters), ctypes.byref(out), _stream(stream)), h)
+    return out.value
+
+
+def pc_fista(h, z0, w, sigma, z, iters, tau, stream=None):
+    _check(_lib.pc_fista(h, _ptr(z0), _ptr(w), _ptr(sigma), _ptr(z), int(iters), float(tau), _stream(stream)), h)
 
 
 def pc_backward(h, dtheta, du, dv, stream=None):
@@ -285,6 +311,30 @@ class PCOperator:
         y = t.empty_like(x)
         pc_apply(self.h, x, y, stream=stream)
         return y
+
+    def apply_adjoint(self, x, stream=None):
+        t = _torch()
+        y = t.empty_like(x)
+        pc_apply_adjoint(self.h, x, y, stream=stream)
+        return y
+
+    def jacobi(self, stream=None):
+        t = _torch()
+        d = t.empty(self.N, dtype=self.dtype, device="cuda")
+        pc_jacobi(self.h, d, stream)
+        return d
+
+    def power_norm(self, sigma=None, iters=50, stream=None) -> float:
+        return pc_power_norm(self.h, sigma, iters, stream)
+
+    def fista(self, z0, w, iters, tau, z=None, sigma=None, stream=None):
+        """FISTA-W (sigma None) or FISTA-WP iterates from z (zeros when None); returns z."""
+        t = _torch()
+        z = t.zeros_like(z0) if z is None else z
+        if not t.is_tensor(w):
+            w = t.full_like(z0, float(w))
+        pc_fista(self.h, z0, w, sigma, z, iters, tau, stream)
+        return z
 
     def backward(self, dtheta, stream=None):
         t = _torch()

@@ -1,4 +1,4 @@
-// 2-D row assembly (A5) and its adjoint (A7), register-blocked.
+// 2-D row assembly and its adjoint, register-blocked.
 //
 // Stage 1 (k_s_rows, one launch over all rows): s(q) = sum_k v_k(g + q) F_{k,b}(q) over the
 // windows nonzero at each pixel, compensated over k (FP32), into the s scratch.
@@ -510,7 +510,7 @@ __global__ void __launch_bounds__(256, 2) k_assemble2d(const __grid_constant__ O
 }
 
 // ------------------------------------------------------------------------------------------
-// A8: persistent batched assembly.  Work items (operator, row band, run of rows) are taken
+// Persistent batched assembly.  Work items (operator, row band, run of rows) are taken
 // from a global counter, longest first (the host sorts them).  Each item carries its own
 // thread-group shape; the CTA copies the operator's descriptor to shared memory.  FP32.
 // ------------------------------------------------------------------------------------------

@@ -1,4 +1,4 @@
-// 2-D backward (A7): adjoint of the row assembly, in three phases.
+// 2-D backward: adjoint of the row assembly, in three phases.
 //
 //   phase 1 (k_backward_queue, persistent; k_backward2d per band for FP64): per stored row s,
 //           dL/ds on the row's region by the transposed localized transform of the row's

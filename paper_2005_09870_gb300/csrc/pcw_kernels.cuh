@@ -170,7 +170,7 @@ __device__ __forceinline__ void flag_error(int* err, int bits)
 }
 
 // ------------------------------------------------------------------------------------------
-// A2: base wavelets by the FP64 cascade (Section 2.1):
+// Base wavelets by the FP64 cascade (Section 2.1):
 //   phi_{1,0} = h,  psi_{1,0}(x) = g(x);
 //   phi_{j,0}(x) = sum_n h[n] phi_{j-1,0}(x - 2^(j-1) n),  psi_{j,0}(x) = sum_n g[n] phi_{j-1,0}(x - 2^(j-1) n)
 // stored unwrapped: phi_j[i] at x = i, psi_j[i] at x = off(j,1) + i.  One CTA.
@@ -232,7 +232,7 @@ __global__ void k_taps(const double* __restrict__ h, int Lf, T* __restrict__ out
 }
 
 // ------------------------------------------------------------------------------------------
-// A3: filtered base wavelets.  For band b (level j, factors e0, e1) and term k the region is
+// Filtered base wavelets.  For band b (level j, factors e0, e1) and term k the region is
 // supp rho widened by r: unfolded extents U = len_j + 2r per axis, local coordinate q <-> pixel
 // x = off(j,e) - r + q.  kappa_k(t) = u_k(-t) in the paper's order (adjoint of the
 // convolution), u_k(t) otherwise.
@@ -391,7 +391,7 @@ __device__ __forceinline__ void write_block(const OpDev<T>& op, const T* Zb, Ran
 }
 
 // ------------------------------------------------------------------------------------------
-// A5 (1-D): fused window-multiply + localized forward transform, one stored row per thread
+// 1-D assembly: fused window-multiply + localized forward transform, one stored row per thread
 // group.  hS, gS: taps in shared memory; boff: the group's block-offset table (nb + 1 ints);
 // arena: the group's cfg.arena elements.
 // ------------------------------------------------------------------------------------------
@@ -529,7 +529,7 @@ __global__ void __launch_bounds__(256) k_assemble1d(const __grid_constant__ OpDe
 }
 
 // ------------------------------------------------------------------------------------------
-// A7: adjoint (backward).  The transpose of filt(): for an input position p,
+// Adjoint (backward).  The transpose of filt(): for an input position p,
 //   in_bar[p] = sum over (c, i) with S*(ro.lo + c) + off + i = ri.lo + p (mod n_in when the
 //   output is full) of f[i] * out_bar[c].
 // ------------------------------------------------------------------------------------------
@@ -821,7 +821,7 @@ __global__ void __launch_bounds__(256) k_backward(const __grid_constant__ OpDev<
     }
 }
 
-// Adjoint of A3.  pass 2^T: dG[t0][q1] = sum_{q0 < U0} dF[q0 mod n][q1 mod n] rho^{e0}_j(q0 - r - t0)
+// Adjoint of the filtered base wavelets.  pass 2^T: dG[t0][q1] = sum_{q0 < U0} dF[q0 mod n][q1 mod n] rho^{e0}_j(q0 - r - t0)
 template <typename T>
 __global__ void k_dfilt_pass2(const __grid_constant__ FiltDev fd, const T* __restrict__ wav,
                               const T* __restrict__ dF, T* __restrict__ dG)
@@ -872,16 +872,18 @@ __global__ void k_dfilt_pass1(const __grid_constant__ FiltDev fd, const T* __res
 }
 
 // ------------------------------------------------------------------------------------------
-// A6: y = S x (stored rows are outputs) or y = S^T x (convolution-first order, stored rows are
-// inputs; scatter with atomics into a zeroed y).  One warp per stored row, NR right-hand
-// sides per pass, warp-shuffle reduction of the row sums.
+// y = S x (gather over a stored row) or y = S^T x (scatter with atomics into a zeroed y), S
+// the stored matrix: Theta in the paper's order, Theta^T in the convolution-first order, so
+// the adjoint apply takes the other direction.  One warp per stored row, NR right-hand
+// sides per pass, warp-shuffle reduction of the row sums.  SQ squares the stored values:
+// (Theta o Theta)^T 1 = diag(Theta^T Theta).
 // ------------------------------------------------------------------------------------------
 template <typename TA, typename TV>
 __device__ __forceinline__ TA to_acc(TV v) { return (TA)v; }
 template <>
 __device__ __forceinline__ float to_acc<float, __nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
 
-template <typename TV, typename TA, int NR>
+template <typename TV, typename TA, int NR, bool SQ = false>
 __global__ void __launch_bounds__(256) k_apply(const __grid_constant__ OpDev<TA> op, const TV* __restrict__ vals,
                                                const TA* __restrict__ x, int ldx, TA* __restrict__ y, int ldy,
                                                int c0, int nr, int transpose)
@@ -924,7 +926,8 @@ __global__ void __launch_bounds__(256) k_apply(const __grid_constant__ OpDev<TA>
         for (int idx = lane; idx < tot; idx += 32) {
             const int a = idx / W1, bb = idx - a * W1;
             const int64_t col = B2.off + (int64_t)pmod(f0 + a, nj) * ((d == 2) ? nj : 0) + pmod(f1 + bb, nj);
-            const TA v = to_acc<TA, TV>(vals[pos + idx]);
+            TA v = to_acc<TA, TV>(vals[pos + idx]);
+            if (SQ) v *= v;
             if (!transpose) {
                 const TA* xr = x + col * ldx + c0;
 #pragma unroll
@@ -1032,7 +1035,7 @@ __global__ void __launch_bounds__(256) k_apply_vec(const __grid_constant__ OpDev
 }
 
 // ------------------------------------------------------------------------------------------
-// A6 on tensor cores: y = S x for 16 right-hand sides, BF16 S, FP32 accumulation.
+// Apply on tensor cores: y = S x for 16 right-hand sides, BF16 S, FP32 accumulation.
 // A CTA (4 warps) owns a tile of 16 stored rows of one band with the same l0 and consecutive
 // l1.  For each kept column band b2 and each stencil row a (warps take a's in turn), the 16
 // rows' entries form a banded 16 x K block A (row i holds its W1(i) values at column offset
@@ -1210,6 +1213,77 @@ __global__ void k_zero_rows(TA* y, int64_t N, int ldy, int c0, int nr)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < N * nr) y[(i / nr) * ldy + c0 + (i % nr)] = TA(0);
+}
+
+// ------------------------------------------------------------------------------------------
+// Deblurring in the wavelet domain (Section 4.3; FISTA-W / FISTA-WP of the appendix on
+// deblurring algorithms): the vector kernels of one iteration and of the power iteration
+// that bounds the step.  S = diag(sigma) is the preconditioner (identity when sigma is null).
+// ------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_sub_vec(T* __restrict__ r, const T* __restrict__ b, int64_t N)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) r[i] -= b[i];
+}
+
+template <typename T>
+__global__ void k_fill_vec(T* __restrict__ v, int64_t N, T val)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) v[i] = val;
+}
+
+// v[i] *= sqrt(sigma[i])
+template <typename T>
+__global__ void k_scale_sqrt(T* __restrict__ v, const T* __restrict__ sigma, int64_t N)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) v[i] *= sqrt(sigma[i]);
+}
+
+// out[0] += sum_i v[i]^2, FP64 block partial sums (out zeroed by the caller)
+template <typename T>
+__global__ void __launch_bounds__(256) k_norm2(const T* __restrict__ v, int64_t N, double* __restrict__ out)
+{
+    __shared__ double part[8];
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        acc += (double)v[i] * (double)v[i];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+        atomicAdd(out, t);
+    }
+}
+
+// u = g / sqrt(nrm2[0]) (zero when the norm is zero)
+template <typename T>
+__global__ void k_normalize(T* __restrict__ u, const T* __restrict__ g, int64_t N, const double* __restrict__ nrm2)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const double s = nrm2[0];
+    if (i < N) u[i] = (s > 0.0) ? (T)((double)g[i] / sqrt(s)) : T(0);
+}
+
+// One FISTA update from the gradient g = Theta^T (Theta y - z0):
+//   a = y - tau s g,  z' = soft(a, tau s w),  y = z' + beta (z' - z),  z = z'
+// with s = sigma[i] (1 without preconditioner).
+template <typename T>
+__global__ void k_fista_step(T* __restrict__ z, T* __restrict__ y, const T* __restrict__ g, const T* __restrict__ w,
+                             const T* __restrict__ sigma, int64_t N, T tau, T beta)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const T ts = sigma ? tau * sigma[i] : tau;
+    const T a = y[i] - ts * g[i];
+    const T t = ts * w[i];
+    const T zn = (a > t) ? a - t : (a < -t) ? a + t : T(0);
+    y[i] = zn + beta * (zn - z[i]);
+    z[i] = zn;
 }
 
 }  // namespace pcw

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <mutex>
 #include <cstdarg>
@@ -74,6 +75,7 @@ struct pc_op {
     int64_t* row_ptr_d = nullptr;
     void* theta_d = nullptr;
     __nv_bfloat16* theta16_d = nullptr;
+    void* fista_d = nullptr;       // solver scratch: y, r, g (3 N elements), then two doubles
     unsigned* xsplit_d = nullptr;  // 16 right-hand sides split into packed BF16 hi / lo (tensor-core apply)
     unsigned long long* masks_d = nullptr;
     void* wl_d = nullptr;   // per-pixel window list (slots x N)
@@ -552,12 +554,12 @@ template <typename T>
 pc_status prepare_t(pc_op* h, cudaStream_t st)
 {
     const pc_desc& D = h->desc;
-    // A1/A2: taps in T and the FP64 cascade of the base wavelets
+    // taps in T and the FP64 cascade of the base wavelets
     k_taps<T><<<1, 64, 0, st>>>(h->taps64_d, h->Lf, (T*)h->tapsT_d);
     k_base_wavelets<<<1, 256, 0, st>>>(h->taps64_d, h->Lf, D.levels, h->wav64_d);
     k_cast<T><<<std::max(1, std::min(1024, (h->wav_total + 255) / 256)), 256, 0, st>>>(h->wav64_d, (T*)h->wavT_d,
                                                                                       h->wav_total);
-    // A3: filtered base wavelets
+    // filtered base wavelets
     {
         int maxU = 0, maxR = 0;
         const int K0 = (D.dim == 2) ? h->K : 1;
@@ -619,7 +621,7 @@ pc_status assemble_t(pc_op* h, cudaStream_t st, int stage_mask)
             return PC_OK;
         }
     }
-    // A5: one launch per row band
+    // one launch per row band
     OpDev<T> od = make_opdev<T>(h);
     {
         pc_status sp = s_rows_t<T>(h, od, st);
@@ -642,8 +644,10 @@ pc_status assemble_t(pc_op* h, cudaStream_t st, int stage_mask)
     return PC_OK;
 }
 
-template <typename TV, typename TA>
-pc_status apply_t(pc_op* h, const TV* vals, const TA* x, TA* y, int nrhs, int ldx, int ldy, cudaStream_t st)
+// y = Theta x (adjoint = false) or y = Theta^T x; SQ squares the stored values first.
+template <typename TV, typename TA, bool SQ = false>
+pc_status apply_t(pc_op* h, const TV* vals, const TA* x, TA* y, int nrhs, int ldx, int ldy, cudaStream_t st,
+                  bool adjoint = false)
 {
     OpDev<TA> od{};
     const pc_desc& D = h->desc;
@@ -656,12 +660,12 @@ pc_status apply_t(pc_op* h, const TV* vals, const TA* x, TA* y, int nrhs, int ld
     od.nb = h->nb;
     od.N = h->N;
     od.row_ptr = h->row_ptr_d;
-    const int transpose = D.order == PC_ORDER_CONV_THEN_MULT;
+    const int transpose = (D.order == PC_ORDER_CONV_THEN_MULT) != adjoint;
     const int64_t warps = h->N;
     const int blocks = (int)((warps * 32 + 255) / 256);
     // tensor-core path: BF16 values, paper order, groups of 16 right-hand sides
     if constexpr (std::is_same<TV, __nv_bfloat16>::value && std::is_same<TA, float>::value) {
-        if (!transpose && nrhs >= 16 && h->xsplit_d) {
+        if (!SQ && !transpose && nrhs >= 16 && h->xsplit_d) {
             TcApply tp{};
             tp.d = D.dim;
             tp.n = D.n;
@@ -695,7 +699,7 @@ pc_status apply_t(pc_op* h, const TV* vals, const TA* x, TA* y, int nrhs, int ld
     // vectorised path: paper order, FP32 accumulation, 16-byte aligned x/y with ldx, ldy % 4 == 0;
     // right-hand sides in groups of 16, 8 or 4, a remainder below 4 by the scalar kernel
     if constexpr (std::is_same<TA, float>::value) {
-        const bool vec = !transpose && ((uintptr_t)x % 16 == 0) && ((uintptr_t)y % 16 == 0) && ldx % 4 == 0 &&
+        const bool vec = !SQ && !transpose && ((uintptr_t)x % 16 == 0) && ((uintptr_t)y % 16 == 0) && ldx % 4 == 0 &&
                          ldy % 4 == 0;
         if (vec) {
             int c = 0;
@@ -728,11 +732,11 @@ pc_status apply_t(pc_op* h, const TV* vals, const TA* x, TA* y, int nrhs, int ld
         }
         count_launch();
         if (nr == 1)
-            k_apply<TV, TA, 1><<<blocks, 256, 0, st>>>(od, vals, x, ldx, y, ldy, c0, nr, transpose);
+            k_apply<TV, TA, 1, SQ><<<blocks, 256, 0, st>>>(od, vals, x, ldx, y, ldy, c0, nr, transpose);
         else if (nr <= 4)
-            k_apply<TV, TA, 4><<<blocks, 256, 0, st>>>(od, vals, x, ldx, y, ldy, c0, nr, transpose);
+            k_apply<TV, TA, 4, SQ><<<blocks, 256, 0, st>>>(od, vals, x, ldx, y, ldy, c0, nr, transpose);
         else
-            k_apply<TV, TA, 16><<<blocks, 256, 0, st>>>(od, vals, x, ldx, y, ldy, c0, nr, transpose);
+            k_apply<TV, TA, 16, SQ><<<blocks, 256, 0, st>>>(od, vals, x, ldx, y, ldy, c0, nr, transpose);
     }
     PC_CUDA(h, cudaGetLastError());
     return PC_OK;
@@ -992,7 +996,7 @@ pc_status build_window_list(pc_op* h, cudaStream_t st)
 void free_all(pc_op* h)
 {
     void* ptrs[] = {h->u_d,  h->v_d,        h->taps64_d,  h->wav64_d,  h->tapsT_d, h->wavT_d, h->F_d,
-                    h->G_d,  h->dF_d, h->dG_d, h->S_d, h->amask_d, h->wl_d, h->cnt_d, h->dfoff_d, h->q_items_d, h->q_items_b_d, h->q_op_d, h->q_counter_d, h->row_ptr_d,  h->theta_d,   h->theta16_d, h->xsplit_d, h->sblk_d, h->od_d, h->masks_d, h->err_d};
+                    h->G_d,  h->dF_d, h->dG_d, h->S_d, h->amask_d, h->wl_d, h->cnt_d, h->dfoff_d, h->q_items_d, h->q_items_b_d, h->q_op_d, h->q_counter_d, h->row_ptr_d,  h->theta_d,   h->theta16_d, h->xsplit_d, h->sblk_d, h->od_d, h->masks_d, h->err_d, h->fista_d};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -1273,6 +1277,115 @@ pc_status autotune_t(pc_op* h, cudaStream_t st)
 // =========================================================================================
 // C-ABI
 // =========================================================================================
+// ---------------------------------------------------------------------------------------
+// Wavelet-domain deblurring solver (Section 4.3; FISTA-W / FISTA-WP).  All of it runs on
+// the stored Theta in its own precision (FP32 or FP64 values, never the BF16 copy).
+// ---------------------------------------------------------------------------------------
+namespace {
+
+template <typename T>
+pc_status solver_scratch(pc_op* h, T** y, T** r, T** g, double** nrm)
+{
+    const int64_t N = h->N;
+    if (!h->fista_d) {
+        char* p = nullptr;
+        pc_status st = dev_alloc(h, &p, sizeof(T) * 3 * N + 2 * sizeof(double));
+        if (st != PC_OK) return st;
+        h->fista_d = p;
+    }
+    *y = (T*)h->fista_d;
+    *r = *y + N;
+    *g = *r + N;
+    *nrm = (double*)(*g + N);
+    return PC_OK;
+}
+
+inline int vec_blocks(int64_t N) { return (int)((N + 255) / 256); }
+
+// r = Theta u, then g = Theta^T r (minus z0 in between when z0 is given)
+template <typename T>
+pc_status normal_apply(pc_op* h, const T* u, T* r, T* g, const T* z0, cudaStream_t st)
+{
+    const T* vals = (const T*)h->theta_d;
+    pc_status e = apply_t<T, T>(h, vals, u, r, 1, 1, 1, st, false);
+    if (e != PC_OK) return e;
+    if (z0) {
+        k_sub_vec<T><<<vec_blocks(h->N), 256, 0, st>>>(r, z0, h->N);
+        count_launch();
+    }
+    return apply_t<T, T>(h, vals, r, g, 1, 1, 1, st, true);
+}
+
+template <typename T>
+pc_status jacobi_t(pc_op* h, T* diag, cudaStream_t st)
+{
+    T *y, *r, *g;
+    double* nrm;
+    pc_status e = solver_scratch<T>(h, &y, &r, &g, &nrm);
+    if (e != PC_OK) return e;
+    k_fill_vec<T><<<vec_blocks(h->N), 256, 0, st>>>(y, h->N, T(1));
+    count_launch();
+    e = apply_t<T, T, true>(h, (const T*)h->theta_d, y, diag, 1, 1, 1, st, true);
+    if (e != PC_OK) return e;
+    PC_CUDA(h, cudaGetLastError());
+    return PC_OK;
+}
+
+template <typename T>
+pc_status power_norm_t(pc_op* h, const T* sigma, int iters, double* out, cudaStream_t st)
+{
+    T *u, *r, *g;
+    double* nrm;
+    pc_status e = solver_scratch<T>(h, &u, &r, &g, &nrm);
+    if (e != PC_OK) return e;
+    const int64_t N = h->N;
+    const int vb = vec_blocks(N);
+    k_fill_vec<T><<<vb, 256, 0, st>>>(u, N, (T)(1.0 / std::sqrt((double)N)));
+    count_launch();
+    for (int it = 0; it < iters; ++it) {
+        if (sigma) {
+            k_scale_sqrt<T><<<vb, 256, 0, st>>>(u, sigma, N);
+            count_launch();
+        }
+        if ((e = normal_apply<T>(h, u, r, g, nullptr, st)) != PC_OK) return e;
+        if (sigma) {
+            k_scale_sqrt<T><<<vb, 256, 0, st>>>(g, sigma, N);
+            count_launch();
+        }
+        PC_CUDA(h, cudaMemsetAsync(nrm, 0, sizeof(double), st));
+        k_norm2<T><<<std::min(vb, 1024), 256, 0, st>>>(g, N, nrm);
+        k_normalize<T><<<vb, 256, 0, st>>>(u, g, N, nrm);
+        count_launch(2);
+    }
+    double s2 = 0.0;
+    PC_CUDA(h, cudaMemcpyAsync(&s2, nrm, sizeof(double), cudaMemcpyDeviceToHost, st));
+    PC_CUDA(h, cudaStreamSynchronize(st));
+    PC_CUDA(h, cudaGetLastError());
+    *out = std::sqrt(s2);
+    return PC_OK;
+}
+
+template <typename T>
+pc_status fista_t(pc_op* h, const T* z0, const T* w, const T* sigma, T* z, int iters, double tau, cudaStream_t st)
+{
+    T *y, *r, *g;
+    double* nrm;
+    pc_status e = solver_scratch<T>(h, &y, &r, &g, &nrm);
+    if (e != PC_OK) return e;
+    const int64_t N = h->N;
+    PC_CUDA(h, cudaMemcpyAsync(y, z, sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
+    for (int i = 1; i <= iters; ++i) {
+        if ((e = normal_apply<T>(h, y, r, g, z0, st)) != PC_OK) return e;
+        const T beta = (T)((double)(i - 1) / (double)(i + 2));
+        k_fista_step<T><<<vec_blocks(N), 256, 0, st>>>(z, y, g, w, sigma, N, (T)tau, beta);
+        count_launch();
+    }
+    PC_CUDA(h, cudaGetLastError());
+    return PC_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 pc_status pc_plan_check(const pc_desc* desc) { return check_desc(desc, nullptr); }
@@ -1535,6 +1648,55 @@ pc_status pc_apply(pc_handle h, const void* x, void* y, int nrhs, int ldx, int l
         return apply_t<double, double>(h, (const double*)h->theta_d, (const double*)x, (double*)y, nrhs, ldx, ldy, s);
     if (h->theta16_d) return apply_t<__nv_bfloat16, float>(h, h->theta16_d, (const float*)x, (float*)y, nrhs, ldx, ldy, s);
     return apply_t<float, float>(h, (const float*)h->theta_d, (const float*)x, (float*)y, nrhs, ldx, ldy, s);
+}
+
+pc_status pc_apply_adjoint(pc_handle h, const void* x, void* y, int nrhs, int ldx, int ldy, void* stream)
+{
+    if (!h) return fail(nullptr, PC_ERR_INVALID_ARG, "handle is NULL");
+    if (!h->assembled) return fail(h, PC_ERR_NOT_ASSEMBLED, "pc_apply_adjoint before pc_assemble");
+    if (!x || !y || nrhs < 1 || nrhs > 64 || ldx < nrhs || ldy < nrhs)
+        return fail(h, PC_ERR_INVALID_ARG, "bad x/y/nrhs/ldx/ldy (nrhs=%d ldx=%d ldy=%d)", nrhs, ldx, ldy);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->desc.precision == PC_FP64)
+        return apply_t<double, double>(h, (const double*)h->theta_d, (const double*)x, (double*)y, nrhs, ldx, ldy, s,
+                                       true);
+    if (h->theta16_d)
+        return apply_t<__nv_bfloat16, float>(h, h->theta16_d, (const float*)x, (float*)y, nrhs, ldx, ldy, s, true);
+    return apply_t<float, float>(h, (const float*)h->theta_d, (const float*)x, (float*)y, nrhs, ldx, ldy, s, true);
+}
+
+pc_status pc_jacobi(pc_handle h, void* diag, void* stream)
+{
+    if (!h) return fail(nullptr, PC_ERR_INVALID_ARG, "handle is NULL");
+    if (!h->assembled) return fail(h, PC_ERR_NOT_ASSEMBLED, "pc_jacobi before pc_assemble");
+    if (!diag) return fail(h, PC_ERR_INVALID_ARG, "diag must not be NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->desc.precision == PC_FP64) return jacobi_t<double>(h, (double*)diag, s);
+    return jacobi_t<float>(h, (float*)diag, s);
+}
+
+pc_status pc_power_norm(pc_handle h, const void* sigma, int iters, double* norm2, void* stream)
+{
+    if (!h) return fail(nullptr, PC_ERR_INVALID_ARG, "handle is NULL");
+    if (!h->assembled) return fail(h, PC_ERR_NOT_ASSEMBLED, "pc_power_norm before pc_assemble");
+    if (!norm2 || iters < 1) return fail(h, PC_ERR_INVALID_ARG, "norm2 must not be NULL and iters >= 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->desc.precision == PC_FP64) return power_norm_t<double>(h, (const double*)sigma, iters, norm2, s);
+    return power_norm_t<float>(h, (const float*)sigma, iters, norm2, s);
+}
+
+pc_status pc_fista(pc_handle h, const void* z0, const void* w, const void* sigma, void* z, int iters, double tau,
+                   void* stream)
+{
+    if (!h) return fail(nullptr, PC_ERR_INVALID_ARG, "handle is NULL");
+    if (!h->assembled) return fail(h, PC_ERR_NOT_ASSEMBLED, "pc_fista before pc_assemble");
+    if (!z0 || !w || !z || iters < 0 || !(tau > 0.0))
+        return fail(h, PC_ERR_INVALID_ARG, "bad z0/w/z/iters/tau (iters=%d tau=%g)", iters, tau);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->desc.precision == PC_FP64)
+        return fista_t<double>(h, (const double*)z0, (const double*)w, (const double*)sigma, (double*)z, iters, tau,
+                               s);
+    return fista_t<float>(h, (const float*)z0, (const float*)w, (const float*)sigma, (float*)z, iters, tau, s);
 }
 
 pc_status pc_backward(pc_handle h, const void* dtheta, void* du, void* dv, void* stream)
