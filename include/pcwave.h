@@ -164,8 +164,11 @@ pc_status pc_apply_adjoint(pc_handle h, const void* x, void* y, int nrhs, int ld
  * with soft() entrywise soft thresholding and S = diag(sigma) (NULL: FISTA-W; a Jacobi
  * sigma = 1/pc_jacobi(): FISTA-WP).  z holds z^(0) = y^(1) on entry and z^(iters) on return;
  * z0 (the observed image's wavelet coefficients) and the weights w (>= 0) are inputs.
- * tau > 0 (convergence needs tau <= 1 / pc_power_norm(sigma)).  Asynchronous; five kernel
- * launches per iteration.  PC_ERR_INVALID_ARG for NULL z0/w/z, iters < 0 or tau <= 0. */
+ * tau > 0 (convergence needs tau <= 1 / pc_power_norm(sigma)).  Asynchronous; three kernel
+ * launches per iteration in the paper's order (Theta y - z0 with g cleared, the scatter of
+ * Theta^T r into g, the update), five in the convolution-first order.  The first call on a
+ * handle also builds per-row column-block descriptors (8 bytes per row and kept block).
+ * PC_ERR_INVALID_ARG for NULL z0/w/z, iters < 0 or tau <= 0. */
 pc_status pc_jacobi(pc_handle h, void* diag, void* stream);
 pc_status pc_power_norm(pc_handle h, const void* sigma, int iters, double* norm2, void* stream);
 pc_status pc_fista(pc_handle h, const void* z0, const void* w, const void* sigma, void* z, int iters,

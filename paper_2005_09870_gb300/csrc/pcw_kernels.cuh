@@ -960,6 +960,143 @@ __global__ void __launch_bounds__(256) k_apply(const __grid_constant__ OpDev<TA>
     }
 }
 
+// Column-block descriptors of every stored row for the one-right-hand-side products: for
+// row s, slot k < stride (the most kept blocks of any row band) holds the k-th kept column block (band b2, first translates f0, f1 on
+// the torus, extents W0 x W1) packed in 64 bits, 0 after the last one.
+//   2-D: W0 [0,14) W1 [14,28) f0 [28,42) f1 [42,56) b2 [56,62)   (n <= 16384, so nj < 2^14)
+//   1-D: W1 [0,28) f1 [28,56) b2 [56,62)                          (n <= 2^28)
+constexpr int BLK_B2_SHIFT = 56;
+template <typename TA>
+__global__ void __launch_bounds__(256) k_block_desc(const __grid_constant__ OpDev<TA> op,
+                                                    unsigned long long* __restrict__ desc, int stride)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= op.N) return;
+    const int d = op.d, n = op.n, L = op.L;
+    int b = 0;
+    Band Bo = band_info(d, n, L, 0);
+    for (int bb = op.nb - 1; bb >= 0; --bb) {
+        const Band t = band_info(d, n, L, bb);
+        const int64_t sz = (d == 2) ? (int64_t)t.nj * t.nj : t.nj;
+        if (s >= t.off && s < t.off + sz) {
+            b = bb;
+            Bo = t;
+            break;
+        }
+    }
+    const int rl = (int)(s - Bo.off);
+    const int l0 = (d == 2) ? rl / Bo.nj : 0, l1 = (d == 2) ? rl % Bo.nj : rl;
+    const int dense = op.gap < 0;
+    int k = 0;
+    for (int b2 = 0; b2 < op.nb; ++b2) {
+        if (!block_kept(d, n, L, op.gap, b, b2)) continue;
+        const Band B2 = band_info(d, n, L, b2);
+        int f0 = 0, W0 = 1, f1, W1;
+        stencil(Bo.j, Bo.e1, l1, B2.j, B2.e1, op.r, op.Lf, n, dense, &f1, &W1);
+        if (d == 2) stencil(Bo.j, Bo.e0, l0, B2.j, B2.e0, op.r, op.Lf, n, dense, &f0, &W0);
+        const unsigned long long f0p = (unsigned)pmod(f0, B2.nj), f1p = (unsigned)pmod(f1, B2.nj);
+        unsigned long long w;
+        if (d == 2)
+            w = (unsigned long long)W0 | ((unsigned long long)W1 << 14) | (f0p << 28) | (f1p << 42);
+        else
+            w = (unsigned long long)W1 | (f1p << 28);
+        desc[s * stride + k++] = w | ((unsigned long long)b2 << BLK_B2_SHIFT);
+    }
+    for (; k < stride; ++k) desc[s * stride + k] = 0ull;
+}
+
+// One right-hand side (the solver's products): one warp per stored row, lane t of the warp
+// takes entries t, t + 32, ... of each kept column block (a W0 x W1 rectangle of translates,
+// row-major), described by k_block_desc.  The rectangle coordinates advance by the fixed step
+// 32 = qa * W1 + rb without divisions and wrap around the torus with one conditional
+// subtraction (W0, W1 <= nj); column indices are 32-bit (N < 2^31).  Entries are taken four
+// at a time so that four value and four x loads are in flight.
+// TR = 0: y[s] = sum_e v_e x[col_e] - sub[s] (sub optional), and zero[s] = 0 when zero is
+//         given (it clears the output of a following TR = 1 product);
+// TR = 1: y[col_e] += v_e x[s] (atomics into a zeroed y).
+template <typename TV, typename TA, bool SQ, int TR>
+__global__ void __launch_bounds__(256) k_apply1(const __grid_constant__ OpDev<TA> op,
+                                                const unsigned long long* __restrict__ desc,
+                                                const TV* __restrict__ vals, const TA* __restrict__ x,
+                                                TA* __restrict__ y, const TA* __restrict__ sub, TA* __restrict__ zero)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t s = warp;
+    if (s >= op.N) return;
+    const int d = op.d, n = op.n, L = op.L;
+    const TA xs = TR ? x[s] : TA(0);
+    TA acc = TA(0);
+    const TV* vp = vals + op.row_ptr[s];
+    const unsigned long long* dp = desc + s * op.nb;
+    for (int k = 0; k < op.nb; ++k) {
+        const unsigned long long w = dp[k];
+        if (w == 0ull) break;
+        const int b2 = (int)(w >> BLK_B2_SHIFT);
+        int W0, W1, f0p, f1p;
+        if (d == 2) {
+            W0 = (int)(w & 0x3FFF);
+            W1 = (int)((w >> 14) & 0x3FFF);
+            f0p = (int)((w >> 28) & 0x3FFF);
+            f1p = (int)((w >> 42) & 0x3FFF);
+        } else {
+            W0 = 1;
+            W1 = (int)(w & 0xFFFFFFF);
+            f0p = 0;
+            f1p = (int)((w >> 28) & 0xFFFFFFF);
+        }
+        const Band B2 = band_info(d, n, L, b2);
+        const int nj = B2.nj, tot = W0 * W1;
+        const int rowstep = (d == 2) ? nj : 0;
+        const int off = (int)B2.off;
+        const int qa = 32 / W1, rb = 32 - qa * W1;
+        int a = lane / W1, c = lane - a * W1;
+        for (int i0 = lane; i0 < tot; i0 += 128) {
+            int col[4];
+            TA v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                int ra = f0p + a, cb = f1p + c;
+                ra -= (ra >= nj) ? nj : 0;
+                cb -= (cb >= nj) ? nj : 0;
+                col[u] = off + ra * rowstep + cb;
+                c += rb;
+                a += qa;
+                if (c >= W1) {
+                    c -= W1;
+                    ++a;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + 32 * u;
+                v[u] = (i < tot) ? to_acc<TA, TV>(vp[i]) : TA(0);
+                if (SQ) v[u] *= v[u];
+            }
+            if (!TR) {
+                TA xv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) xv[u] = (i0 + 32 * u < tot) ? x[col[u]] : TA(0);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc = fma(v[u], xv[u], acc);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (i0 + 32 * u < tot) atomicAdd(y + col[u], v[u] * xs);
+            }
+        }
+        vp += tot;
+    }
+    if (!TR) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+            y[s] = sub ? acc - sub[s] : acc;
+            if (zero) zero[s] = TA(0);
+        }
+    }
+}
+
 // y = S x for row-stored S (paper order), one warp per stored row.  The warp's lanes are
 // (entry slot, group of 4 right-hand sides): LPE = NR/4 lanes read one entry's NR values of x
 // as float4s (contiguous), 32/LPE entries per step; partial sums are reduced across entry

@@ -76,6 +76,8 @@ struct pc_op {
     void* theta_d = nullptr;
     __nv_bfloat16* theta16_d = nullptr;
     void* fista_d = nullptr;       // solver scratch: y, r, g (3 N elements), then two doubles
+    unsigned long long* bdesc_d = nullptr;  // column-block descriptors for one-column products
+    int bdesc_stride = 0;                   // slots per row (most kept blocks of any row band)
     unsigned* xsplit_d = nullptr;  // 16 right-hand sides split into packed BF16 hi / lo (tensor-core apply)
     unsigned long long* masks_d = nullptr;
     void* wl_d = nullptr;   // per-pixel window list (slots x N)
@@ -644,6 +646,77 @@ pc_status assemble_t(pc_op* h, cudaStream_t st, int stage_mask)
     return PC_OK;
 }
 
+template <typename TA>
+OpDev<TA> apply_od(const pc_op* h)
+{
+    OpDev<TA> od{};
+    const pc_desc& D = h->desc;
+    od.d = D.dim;
+    od.n = D.n;
+    od.L = D.levels;
+    od.Lf = h->Lf;
+    od.r = D.radius;
+    od.gap = D.gap;
+    od.nb = h->nb;
+    od.N = h->N;
+    od.row_ptr = h->row_ptr_d;
+    return od;
+}
+
+template <typename T>
+pc_status dev_alloc(pc_op* h, T** p, size_t bytes);
+
+// Column-block descriptors (built once per handle; they depend on the pattern only).
+template <typename TA>
+pc_status ensure_block_desc(pc_op* h, cudaStream_t st)
+{
+    if (h->bdesc_d) return PC_OK;
+    const pc_desc& D = h->desc;
+    int kmax = 1;
+    for (int b = 0; b < h->nb; ++b) {
+        int k = 0;
+        for (int b2 = 0; b2 < h->nb; ++b2) k += block_kept(D.dim, D.n, D.levels, D.gap, b, b2) ? 1 : 0;
+        kmax = std::max(kmax, k);
+    }
+    pc_status e = dev_alloc(h, &h->bdesc_d, sizeof(unsigned long long) * (size_t)h->N * kmax);
+    if (e != PC_OK) return e;
+    h->bdesc_stride = kmax;
+    OpDev<TA> od = apply_od<TA>(h);
+    od.nb = h->nb;
+    k_block_desc<TA><<<(int)((h->N + 255) / 256), 256, 0, st>>>(od, h->bdesc_d, kmax);
+    count_launch();
+    PC_CUDA(h, cudaGetLastError());
+    return PC_OK;
+}
+
+// One column: y = Theta x - sub (adjoint = false; zero[] cleared on the side) or
+// y = Theta^T x (adjoint = true; y zeroed first unless y_zeroed).  sub and zero may be null.
+template <typename TV, typename TA, bool SQ>
+pc_status apply1_t(pc_op* h, const TV* vals, const TA* x, TA* y, const TA* sub, TA* zero, bool adjoint,
+                   cudaStream_t st, bool y_zeroed = false)
+{
+    pc_status e = ensure_block_desc<TA>(h, st);
+    if (e != PC_OK) return e;
+    OpDev<TA> od = apply_od<TA>(h);
+    od.nb = h->bdesc_stride;
+    const int blocks = (int)((h->N * 32 + 255) / 256);
+    const bool transpose = (h->desc.order == PC_ORDER_CONV_THEN_MULT) != adjoint;
+    if (transpose) {
+        if (sub || zero) return fail(h, PC_ERR_INVALID_ARG, "internal: sub/zero on a scattered product");
+        if (!y_zeroed) {
+            k_zero_rows<TA><<<(int)((h->N + 255) / 256), 256, 0, st>>>(y, h->N, 1, 0, 1);
+            count_launch();
+        }
+        k_apply1<TV, TA, SQ, 1><<<blocks, 256, 0, st>>>(od, h->bdesc_d, vals, x, y, nullptr, nullptr);
+        count_launch();
+    } else {
+        k_apply1<TV, TA, SQ, 0><<<blocks, 256, 0, st>>>(od, h->bdesc_d, vals, x, y, sub, zero);
+        count_launch();
+    }
+    PC_CUDA(h, cudaGetLastError());
+    return PC_OK;
+}
+
 // y = Theta x (adjoint = false) or y = Theta^T x; SQ squares the stored values first.
 template <typename TV, typename TA, bool SQ = false>
 pc_status apply_t(pc_op* h, const TV* vals, const TA* x, TA* y, int nrhs, int ldx, int ldy, cudaStream_t st,
@@ -724,6 +797,7 @@ pc_status apply_t(pc_op* h, const TV* vals, const TA* x, TA* y, int nrhs, int ld
             nrhs -= c;
         }
     }
+    if (nrhs == 1 && ldx == 1 && ldy == 1) return apply1_t<TV, TA, SQ>(h, vals, x, y, nullptr, nullptr, adjoint, st);
     for (int c0 = 0; c0 < nrhs; c0 += 16) {
         const int nr = std::min(16, nrhs - c0);
         if (transpose) {
@@ -996,7 +1070,7 @@ pc_status build_window_list(pc_op* h, cudaStream_t st)
 void free_all(pc_op* h)
 {
     void* ptrs[] = {h->u_d,  h->v_d,        h->taps64_d,  h->wav64_d,  h->tapsT_d, h->wavT_d, h->F_d,
-                    h->G_d,  h->dF_d, h->dG_d, h->S_d, h->amask_d, h->wl_d, h->cnt_d, h->dfoff_d, h->q_items_d, h->q_items_b_d, h->q_op_d, h->q_counter_d, h->row_ptr_d,  h->theta_d,   h->theta16_d, h->xsplit_d, h->sblk_d, h->od_d, h->masks_d, h->err_d, h->fista_d};
+                    h->G_d,  h->dF_d, h->dG_d, h->S_d, h->amask_d, h->wl_d, h->cnt_d, h->dfoff_d, h->q_items_d, h->q_items_b_d, h->q_op_d, h->q_counter_d, h->row_ptr_d,  h->theta_d,   h->theta16_d, h->xsplit_d, h->sblk_d, h->od_d, h->masks_d, h->err_d, h->fista_d, h->bdesc_d};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -1307,13 +1381,18 @@ template <typename T>
 pc_status normal_apply(pc_op* h, const T* u, T* r, T* g, const T* z0, cudaStream_t st)
 {
     const T* vals = (const T*)h->theta_d;
-    pc_status e = apply_t<T, T>(h, vals, u, r, 1, 1, 1, st, false);
-    if (e != PC_OK) return e;
+    pc_status e;
+    if (h->desc.order == PC_ORDER_MULT_THEN_CONV) {
+        // Theta u gathers over stored rows: it subtracts z0 and clears g for the scatter
+        if ((e = apply1_t<T, T, false>(h, vals, u, r, z0, g, false, st)) != PC_OK) return e;
+        return apply1_t<T, T, false>(h, vals, r, g, nullptr, nullptr, true, st, true);
+    }
+    if ((e = apply1_t<T, T, false>(h, vals, u, r, nullptr, nullptr, false, st)) != PC_OK) return e;
     if (z0) {
         k_sub_vec<T><<<vec_blocks(h->N), 256, 0, st>>>(r, z0, h->N);
         count_launch();
     }
-    return apply_t<T, T>(h, vals, r, g, 1, 1, 1, st, true);
+    return apply1_t<T, T, false>(h, vals, r, g, nullptr, nullptr, true, st);
 }
 
 template <typename T>
