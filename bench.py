@@ -248,8 +248,9 @@ def run_reference(args, rank, world):
 def run_fista(pw, g, op, rank, dev, stream, iters):
     """FISTA-W and FISTA-WP iterations (pc_fista) on the FP32 Theta of the bench operator: a
     seeded sparse-plus-noise problem z0, weights 0.02, step 0.95 / (power-iteration norm).  One
-    iteration = Theta y - z0 (gather), Theta^T r (atomic scatter), the update; Theta's FP32
-    values (4 bytes x nnz, larger than L2) stream from HBM twice per iteration."""
+    iteration = Theta y - z0 and Theta^T r (both gathers, the second over the transposed copy),
+    then the update; the FP32 values (4 bytes x nnz, larger than L2) stream from HBM twice per
+    iteration."""
     import torch
     import pc_inputs as P
     N, nnz = op.N, g.nnz
@@ -284,10 +285,10 @@ def run_fista(pw, g, op, rank, dev, stream, iters):
         launches = pw.pc_launch_counter() - l0
         g.sync()
         ms_it = a.elapsed_time(b) / iters
-        # algorithmic bytes: Theta twice (4 B/entry), x gathered once and r once per product (N each),
-        # z0 read, r written, g zeroed and scattered (read + write), update reads z, y, g, w (+ sigma)
-        # and writes z, y
-        vec = N * 4 * (1 + 1 + 1 + 1 + 1 + 2 + 4 + 2 + (1 if sig is not None else 0))
+        # algorithmic bytes: Theta twice (4 B/entry: the stored values, then the transposed copy),
+        # y gathered, z0 read and r written by the first product, r gathered and g written by the
+        # second, the update reads z, y, g, w (+ sigma) and writes z, y
+        vec = N * 4 * (3 + 2 + 6 + (1 if sig is not None else 0))
         alg = 2 * 4 * nnz + vec
         gbs = alg / (ms_it * 1e-3) / 1e9
         out[name] = {"ms_per_iter": ms_it, "iters_per_s": 1e3 / ms_it, "lipschitz": L, "tau": tau,

@@ -968,7 +968,8 @@ __global__ void __launch_bounds__(256) k_apply(const __grid_constant__ OpDev<TA>
 constexpr int BLK_B2_SHIFT = 56;
 template <typename TA>
 __global__ void __launch_bounds__(256) k_block_desc(const __grid_constant__ OpDev<TA> op,
-                                                    unsigned long long* __restrict__ desc, int stride)
+                                                    unsigned long long* __restrict__ desc,
+                                                    unsigned* __restrict__ boff, int stride)
 {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= op.N) return;
@@ -988,12 +989,15 @@ __global__ void __launch_bounds__(256) k_block_desc(const __grid_constant__ OpDe
     const int l0 = (d == 2) ? rl / Bo.nj : 0, l1 = (d == 2) ? rl % Bo.nj : rl;
     const int dense = op.gap < 0;
     int k = 0;
+    unsigned start = 0;
     for (int b2 = 0; b2 < op.nb; ++b2) {
         if (!block_kept(d, n, L, op.gap, b, b2)) continue;
         const Band B2 = band_info(d, n, L, b2);
         int f0 = 0, W0 = 1, f1, W1;
         stencil(Bo.j, Bo.e1, l1, B2.j, B2.e1, op.r, op.Lf, n, dense, &f1, &W1);
         if (d == 2) stencil(Bo.j, Bo.e0, l0, B2.j, B2.e0, op.r, op.Lf, n, dense, &f0, &W0);
+        boff[s * stride + k] = start;
+        start += (unsigned)(W0 * W1);
         const unsigned long long f0p = (unsigned)pmod(f0, B2.nj), f1p = (unsigned)pmod(f1, B2.nj);
         unsigned long long w;
         if (d == 2)
@@ -1002,7 +1006,97 @@ __global__ void __launch_bounds__(256) k_block_desc(const __grid_constant__ OpDe
             w = (unsigned long long)W1 | (f1p << 28);
         desc[s * stride + k++] = w | ((unsigned long long)b2 << BLK_B2_SHIFT);
     }
-    for (; k < stride; ++k) desc[s * stride + k] = 0ull;
+    for (; k < stride; ++k) {
+        desc[s * stride + k] = 0ull;
+        boff[s * stride + k] = start;
+    }
+}
+
+// Transposed copy of the stored matrix in the same pattern (the pattern is symmetric):
+// valsT[row lambda, column mu] = vals[row mu, column lambda], each row in the stored order, so
+// that Theta^T x is a gather with the row pointers and descriptors of Theta.  One warp per
+// stored row mu; for its entry (mu, lambda) the block of row lambda that holds band(mu) is slot
+// kk of lambda's list (the same for every lambda of one band), and mu's place in it follows from
+// that block's first translates.  A place outside the block (a pattern that is not symmetric)
+// flags ERR_INDEX and is skipped.
+template <typename T>
+__global__ void __launch_bounds__(256) k_transpose_theta(const __grid_constant__ OpDev<T> op,
+                                                         const unsigned long long* __restrict__ desc,
+                                                         const unsigned* __restrict__ boff, int nbands,
+                                                         const T* __restrict__ vals, T* __restrict__ valsT)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t s = warp;
+    if (s >= op.N) return;
+    const int d = op.d, n = op.n, L = op.L;
+    int b = 0;
+    Band Bo = band_info(d, n, L, 0);
+    for (int bb = nbands - 1; bb >= 0; --bb) {
+        const Band t = band_info(d, n, L, bb);
+        const int64_t sz = (d == 2) ? (int64_t)t.nj * t.nj : t.nj;
+        if (s >= t.off && s < t.off + sz) {
+            b = bb;
+            Bo = t;
+            break;
+        }
+    }
+    const int rl = (int)(s - Bo.off);
+    const int l0 = (d == 2) ? rl / Bo.nj : 0, l1 = (d == 2) ? rl % Bo.nj : rl;
+    const int njb = Bo.nj;
+    const T* vp = vals + op.row_ptr[s];
+    const unsigned long long* dp = desc + s * op.nb;
+    for (int k = 0; k < op.nb; ++k) {
+        const unsigned long long w = dp[k];
+        if (w == 0ull) break;
+        const int b2 = (int)(w >> BLK_B2_SHIFT);
+        int W0, W1, f0p, f1p;
+        if (d == 2) {
+            W0 = (int)(w & 0x3FFF);
+            W1 = (int)((w >> 14) & 0x3FFF);
+            f0p = (int)((w >> 28) & 0x3FFF);
+            f1p = (int)((w >> 42) & 0x3FFF);
+        } else {
+            W0 = 1;
+            W1 = (int)(w & 0xFFFFFFF);
+            f0p = 0;
+            f1p = (int)((w >> 28) & 0xFFFFFFF);
+        }
+        int kk = 0;
+        for (int b3 = 0; b3 < b; ++b3) kk += block_kept(d, n, L, op.gap, b2, b3) ? 1 : 0;
+        const Band B2 = band_info(d, n, L, b2);
+        const int nj = B2.nj, tot = W0 * W1;
+        const int rowstep = (d == 2) ? nj : 0;
+        for (int i = lane; i < tot; i += 32) {
+            const int a = i / W1, c = i - a * W1;
+            int ra = f0p + a, cb = f1p + c;
+            ra -= (ra >= nj) ? nj : 0;
+            cb -= (cb >= nj) ? nj : 0;
+            const int64_t lam = B2.off + (int64_t)ra * rowstep + cb;
+            const unsigned long long w2 = desc[lam * op.nb + kk];
+            int V0, V1, g0p, g1p;
+            if (d == 2) {
+                V0 = (int)(w2 & 0x3FFF);
+                V1 = (int)((w2 >> 14) & 0x3FFF);
+                g0p = (int)((w2 >> 28) & 0x3FFF);
+                g1p = (int)((w2 >> 42) & 0x3FFF);
+            } else {
+                V0 = 1;
+                V1 = (int)(w2 & 0xFFFFFFF);
+                g0p = 0;
+                g1p = (int)((w2 >> 28) & 0xFFFFFFF);
+            }
+            int a2 = l0 - g0p, c2 = l1 - g1p;
+            a2 += (a2 < 0) ? njb : 0;
+            c2 += (c2 < 0) ? njb : 0;
+            if (w2 == 0ull || (int)(w2 >> BLK_B2_SHIFT) != b || a2 >= V0 || c2 >= V1) {
+                flag_error(op.err, ERR_INDEX);
+                continue;
+            }
+            valsT[op.row_ptr[lam] + boff[lam * op.nb + kk] + (int64_t)a2 * V1 + c2] = vp[i];
+        }
+        vp += tot;
+    }
 }
 
 // One right-hand side (the solver's products): one warp per stored row, lane t of the warp
@@ -1011,14 +1105,13 @@ __global__ void __launch_bounds__(256) k_block_desc(const __grid_constant__ OpDe
 // 32 = qa * W1 + rb without divisions and wrap around the torus with one conditional
 // subtraction (W0, W1 <= nj); column indices are 32-bit (N < 2^31).  Entries are taken four
 // at a time so that four value and four x loads are in flight.
-// TR = 0: y[s] = sum_e v_e x[col_e] - sub[s] (sub optional), and zero[s] = 0 when zero is
-//         given (it clears the output of a following TR = 1 product);
+// TR = 0: y[s] = sum_e v_e x[col_e] - sub[s] (sub optional);
 // TR = 1: y[col_e] += v_e x[s] (atomics into a zeroed y).
 template <typename TV, typename TA, bool SQ, int TR>
 __global__ void __launch_bounds__(256) k_apply1(const __grid_constant__ OpDev<TA> op,
                                                 const unsigned long long* __restrict__ desc,
                                                 const TV* __restrict__ vals, const TA* __restrict__ x,
-                                                TA* __restrict__ y, const TA* __restrict__ sub, TA* __restrict__ zero)
+                                                TA* __restrict__ y, const TA* __restrict__ sub)
 {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -1090,10 +1183,7 @@ __global__ void __launch_bounds__(256) k_apply1(const __grid_constant__ OpDev<TA
     if (!TR) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) {
-            y[s] = sub ? acc - sub[s] : acc;
-            if (zero) zero[s] = TA(0);
-        }
+        if (lane == 0) y[s] = sub ? acc - sub[s] : acc;
     }
 }
 
@@ -1357,13 +1447,6 @@ __global__ void k_zero_rows(TA* y, int64_t N, int ldy, int c0, int nr)
 // deblurring algorithms): the vector kernels of one iteration and of the power iteration
 // that bounds the step.  S = diag(sigma) is the preconditioner (identity when sigma is null).
 // ------------------------------------------------------------------------------------------
-template <typename T>
-__global__ void k_sub_vec(T* __restrict__ r, const T* __restrict__ b, int64_t N)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < N) r[i] -= b[i];
-}
-
 template <typename T>
 __global__ void k_fill_vec(T* __restrict__ v, int64_t N, T val)
 {

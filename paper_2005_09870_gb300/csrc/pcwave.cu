@@ -77,7 +77,10 @@ struct pc_op {
     __nv_bfloat16* theta16_d = nullptr;
     void* fista_d = nullptr;       // solver scratch: y, r, g (3 N elements), then two doubles
     unsigned long long* bdesc_d = nullptr;  // column-block descriptors for one-column products
+    unsigned* boff_d = nullptr;             // offset of each described block within its row
     int bdesc_stride = 0;                   // slots per row (most kept blocks of any row band)
+    void* thetaT_d = nullptr;               // transposed copy of the stored values (same pattern)
+    long long theta_gen = 0, thetaT_gen = -1;  // assemblies so far / the one thetaT_d reflects
     unsigned* xsplit_d = nullptr;  // 16 right-hand sides split into packed BF16 hi / lo (tensor-core apply)
     unsigned long long* masks_d = nullptr;
     void* wl_d = nullptr;   // per-pixel window list (slots x N)
@@ -620,6 +623,7 @@ pc_status assemble_t(pc_op* h, cudaStream_t st, int stage_mask)
             count_launch();
             PC_CUDA(h, cudaGetLastError());
             h->assembled = true;
+            h->theta_gen++;
             return PC_OK;
         }
     }
@@ -643,6 +647,7 @@ pc_status assemble_t(pc_op* h, cudaStream_t st, int stage_mask)
     }
     PC_CUDA(h, cudaGetLastError());
     h->assembled = true;
+    h->theta_gen++;
     return PC_OK;
 }
 
@@ -680,37 +685,68 @@ pc_status ensure_block_desc(pc_op* h, cudaStream_t st)
     }
     pc_status e = dev_alloc(h, &h->bdesc_d, sizeof(unsigned long long) * (size_t)h->N * kmax);
     if (e != PC_OK) return e;
+    if ((e = dev_alloc(h, &h->boff_d, sizeof(unsigned) * (size_t)h->N * kmax)) != PC_OK) return e;
     h->bdesc_stride = kmax;
     OpDev<TA> od = apply_od<TA>(h);
     od.nb = h->nb;
-    k_block_desc<TA><<<(int)((h->N + 255) / 256), 256, 0, st>>>(od, h->bdesc_d, kmax);
+    k_block_desc<TA><<<(int)((h->N + 255) / 256), 256, 0, st>>>(od, h->bdesc_d, h->boff_d, kmax);
     count_launch();
     PC_CUDA(h, cudaGetLastError());
     return PC_OK;
 }
 
-// One column: y = Theta x - sub (adjoint = false; zero[] cleared on the side) or
-// y = Theta^T x (adjoint = true; y zeroed first unless y_zeroed).  sub and zero may be null.
+// Transposed copy of the stored values for the current assembly (built on first use after
+// each assembly; descriptors must exist).
+template <typename T>
+pc_status ensure_thetaT(pc_op* h, cudaStream_t st)
+{
+    if (h->thetaT_d && h->thetaT_gen == h->theta_gen) return PC_OK;
+    if (!h->thetaT_d) {
+        T* p = nullptr;
+        pc_status e = dev_alloc(h, &p, sizeof(T) * (size_t)h->nnz);
+        if (e != PC_OK) return e;
+        h->thetaT_d = p;
+    }
+    OpDev<T> od = apply_od<T>(h);
+    od.nb = h->bdesc_stride;
+    od.err = h->err_d;
+    k_transpose_theta<T><<<(int)((h->N * 32 + 255) / 256), 256, 0, st>>>(od, h->bdesc_d, h->boff_d, h->nb,
+                                                                         (const T*)h->theta_d, (T*)h->thetaT_d);
+    count_launch();
+    PC_CUDA(h, cudaGetLastError());
+    h->thetaT_gen = h->theta_gen;
+    return PC_OK;
+}
+
+// One column: y = Theta x - sub (adjoint = false; sub may be null) or y = Theta^T x
+// (adjoint = true).
+// With use_T (values of the handle's own type only) a product that would scatter over the
+// stored rows gathers over the rows of the transposed copy instead: no atomics, and the same
+// cost as the stored direction.
 template <typename TV, typename TA, bool SQ>
-pc_status apply1_t(pc_op* h, const TV* vals, const TA* x, TA* y, const TA* sub, TA* zero, bool adjoint,
-                   cudaStream_t st, bool y_zeroed = false)
+pc_status apply1_t(pc_op* h, const TV* vals, const TA* x, TA* y, const TA* sub, bool adjoint, cudaStream_t st,
+                   bool use_T = false)
 {
     pc_status e = ensure_block_desc<TA>(h, st);
     if (e != PC_OK) return e;
     OpDev<TA> od = apply_od<TA>(h);
     od.nb = h->bdesc_stride;
     const int blocks = (int)((h->N * 32 + 255) / 256);
-    const bool transpose = (h->desc.order == PC_ORDER_CONV_THEN_MULT) != adjoint;
-    if (transpose) {
-        if (sub || zero) return fail(h, PC_ERR_INVALID_ARG, "internal: sub/zero on a scattered product");
-        if (!y_zeroed) {
-            k_zero_rows<TA><<<(int)((h->N + 255) / 256), 256, 0, st>>>(y, h->N, 1, 0, 1);
-            count_launch();
+    bool transpose = (h->desc.order == PC_ORDER_CONV_THEN_MULT) != adjoint;
+    if constexpr (std::is_same<TV, TA>::value) {
+        if (transpose && use_T) {
+            if ((e = ensure_thetaT<TA>(h, st)) != PC_OK) return e;
+            vals = (const TV*)h->thetaT_d;
+            transpose = false;
         }
-        k_apply1<TV, TA, SQ, 1><<<blocks, 256, 0, st>>>(od, h->bdesc_d, vals, x, y, nullptr, nullptr);
-        count_launch();
+    }
+    if (transpose) {
+        if (sub) return fail(h, PC_ERR_INVALID_ARG, "internal: subtraction on a scattered product");
+        k_zero_rows<TA><<<(int)((h->N + 255) / 256), 256, 0, st>>>(y, h->N, 1, 0, 1);
+        k_apply1<TV, TA, SQ, 1><<<blocks, 256, 0, st>>>(od, h->bdesc_d, vals, x, y, nullptr);
+        count_launch(2);
     } else {
-        k_apply1<TV, TA, SQ, 0><<<blocks, 256, 0, st>>>(od, h->bdesc_d, vals, x, y, sub, zero);
+        k_apply1<TV, TA, SQ, 0><<<blocks, 256, 0, st>>>(od, h->bdesc_d, vals, x, y, sub);
         count_launch();
     }
     PC_CUDA(h, cudaGetLastError());
@@ -797,7 +833,7 @@ pc_status apply_t(pc_op* h, const TV* vals, const TA* x, TA* y, int nrhs, int ld
             nrhs -= c;
         }
     }
-    if (nrhs == 1 && ldx == 1 && ldy == 1) return apply1_t<TV, TA, SQ>(h, vals, x, y, nullptr, nullptr, adjoint, st);
+    if (nrhs == 1 && ldx == 1 && ldy == 1) return apply1_t<TV, TA, SQ>(h, vals, x, y, nullptr, adjoint, st);
     for (int c0 = 0; c0 < nrhs; c0 += 16) {
         const int nr = std::min(16, nrhs - c0);
         if (transpose) {
@@ -1070,7 +1106,7 @@ pc_status build_window_list(pc_op* h, cudaStream_t st)
 void free_all(pc_op* h)
 {
     void* ptrs[] = {h->u_d,  h->v_d,        h->taps64_d,  h->wav64_d,  h->tapsT_d, h->wavT_d, h->F_d,
-                    h->G_d,  h->dF_d, h->dG_d, h->S_d, h->amask_d, h->wl_d, h->cnt_d, h->dfoff_d, h->q_items_d, h->q_items_b_d, h->q_op_d, h->q_counter_d, h->row_ptr_d,  h->theta_d,   h->theta16_d, h->xsplit_d, h->sblk_d, h->od_d, h->masks_d, h->err_d, h->fista_d, h->bdesc_d};
+                    h->G_d,  h->dF_d, h->dG_d, h->S_d, h->amask_d, h->wl_d, h->cnt_d, h->dfoff_d, h->q_items_d, h->q_items_b_d, h->q_op_d, h->q_counter_d, h->row_ptr_d,  h->theta_d,   h->theta16_d, h->xsplit_d, h->sblk_d, h->od_d, h->masks_d, h->err_d, h->fista_d, h->bdesc_d, h->boff_d, h->thetaT_d};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -1167,6 +1203,7 @@ pc_status batch_enqueue(pc_batch* B, cudaStream_t st)
     for (pc_op* h : B->ops) {
         h->prepared = true;
         h->assembled = true;
+        h->theta_gen++;
     }
     return PC_OK;
 }
@@ -1380,19 +1417,11 @@ inline int vec_blocks(int64_t N) { return (int)((N + 255) / 256); }
 template <typename T>
 pc_status normal_apply(pc_op* h, const T* u, T* r, T* g, const T* z0, cudaStream_t st)
 {
+    // both products gather (the scattering one over the transposed copy)
     const T* vals = (const T*)h->theta_d;
-    pc_status e;
-    if (h->desc.order == PC_ORDER_MULT_THEN_CONV) {
-        // Theta u gathers over stored rows: it subtracts z0 and clears g for the scatter
-        if ((e = apply1_t<T, T, false>(h, vals, u, r, z0, g, false, st)) != PC_OK) return e;
-        return apply1_t<T, T, false>(h, vals, r, g, nullptr, nullptr, true, st, true);
-    }
-    if ((e = apply1_t<T, T, false>(h, vals, u, r, nullptr, nullptr, false, st)) != PC_OK) return e;
-    if (z0) {
-        k_sub_vec<T><<<vec_blocks(h->N), 256, 0, st>>>(r, z0, h->N);
-        count_launch();
-    }
-    return apply1_t<T, T, false>(h, vals, r, g, nullptr, nullptr, true, st);
+    pc_status e = apply1_t<T, T, false>(h, vals, u, r, z0, false, st, true);
+    if (e != PC_OK) return e;
+    return apply1_t<T, T, false>(h, vals, r, g, nullptr, true, st, true);
 }
 
 template <typename T>
@@ -1404,7 +1433,7 @@ pc_status jacobi_t(pc_op* h, T* diag, cudaStream_t st)
     if (e != PC_OK) return e;
     k_fill_vec<T><<<vec_blocks(h->N), 256, 0, st>>>(y, h->N, T(1));
     count_launch();
-    e = apply_t<T, T, true>(h, (const T*)h->theta_d, y, diag, 1, 1, 1, st, true);
+    e = apply1_t<T, T, true>(h, (const T*)h->theta_d, y, diag, nullptr, true, st, true);
     if (e != PC_OK) return e;
     PC_CUDA(h, cudaGetLastError());
     return PC_OK;
@@ -1816,6 +1845,7 @@ pc_status pc_batch_run(pc_batch_handle b, void* stream)
     for (pc_op* h : b->ops) {
         h->prepared = true;
         h->assembled = true;
+        h->theta_gen++;
     }
     return PC_OK;
 }

@@ -168,3 +168,36 @@ def test_full_size_adjoint_and_first_iteration(pw):
         want = np.sign(a) * max(abs(a) - tau * w[lam], 0.0)
         assert abs(float(z1[lam]) - want) <= 1e-5 * np.sqrt(np.sum(col * col) * op.N) * tau + 1e-6, lam
     g.close()
+
+
+@pytest.mark.parametrize("order", [0, 1])
+def test_solver_follows_reassembly(pw, order):
+    """The solver's transposed copy of Theta is rebuilt after every assembly: parameters
+    alternate between two operators through pc_set_params, assembled by pc_assemble, by the
+    two stages and by the batched path, each followed by FISTA against the oracle."""
+    import dataclasses
+    import torch
+    op1 = P.workload("small-2d", n=32, levels=3, order=order)
+    op2 = dataclasses.replace(op1, u=op1.u[::-1].copy() * 0.8, v=np.roll(op1.v, 5, axis=1))
+    g = make_gpu_op(pw, op1)
+    z0 = torch.tensor(P.normal(P.BASE_SEED + 97, op1.N), dtype=torch.float32, device="cuda")
+    w = torch.full((op1.N,), 0.01, dtype=torch.float32, device="cuda")
+    want = {}
+    for k, o in (("op1", op1), ("op2", op2)):
+        want[k] = oracle.fista(dense_theta_pattern(o), z0.double().cpu().numpy(), w.double().cpu().numpy(), 10, 0.5)
+    for how in ("assemble", "stages", "batch"):
+        for k, o in (("op1", op1), ("op2", op2)):
+            pw.pc_set_params(g.h, torch.tensor(o.u, dtype=torch.float32, device="cuda"),
+                             torch.tensor(o.v, dtype=torch.float32, device="cuda"))
+            if how == "assemble":
+                g.assemble()
+            elif how == "stages":
+                pw.pc_assemble_stage(g.h, 0)
+                pw.pc_assemble_stage(g.h, 1)
+            else:
+                pw.pc_batch_assemble([g.h])
+            z = g.fista(z0, w, 10, 0.5)
+            g.sync()
+            got = z.double().cpu().numpy()
+            assert np.abs(got - want[k]).max() <= 2e-4 * np.abs(want[k]).max(), (how, k)
+    g.close()
