@@ -1099,91 +1099,101 @@ __global__ void __launch_bounds__(256) k_transpose_theta(const __grid_constant__
     }
 }
 
-// One right-hand side (the solver's products): one warp per stored row, lane t of the warp
-// takes entries t, t + 32, ... of each kept column block (a W0 x W1 rectangle of translates,
+// One right-hand side (the solver's products).  LPR lanes per stored row (8, 16 or 32), so
+// that with many rows the per-block set-up is shared by several rows of a warp and a block's
+// last step wastes fewer lanes, while few rows still fill the device.  Lane t of a row takes
+// entries t, t + LPR, ... of each kept column block (a W0 x W1 rectangle of translates,
 // row-major), described by k_block_desc.  The rectangle coordinates advance by the fixed step
-// 32 = qa * W1 + rb without divisions and wrap around the torus with one conditional
-// subtraction (W0, W1 <= nj); column indices are 32-bit (N < 2^31).  Entries are taken four
-// at a time so that four value and four x loads are in flight.
+// LPR = qa * W1 + rb without divisions and wrap around
+// the torus with one conditional subtraction (W0, W1 <= nj); column indices are 32-bit
+// (N < 2^31).  Entries are taken four at a time so that four value and four x loads are in
+// flight.
 // TR = 0: y[s] = sum_e v_e x[col_e] - sub[s] (sub optional);
 // TR = 1: y[col_e] += v_e x[s] (atomics into a zeroed y).
-template <typename TV, typename TA, bool SQ, int TR>
+template <typename TV, typename TA, bool SQ, int TR, int LPR>
 __global__ void __launch_bounds__(256) k_apply1(const __grid_constant__ OpDev<TA> op,
                                                 const unsigned long long* __restrict__ desc,
                                                 const TV* __restrict__ vals, const TA* __restrict__ x,
                                                 TA* __restrict__ y, const TA* __restrict__ sub)
 {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    const int64_t s = warp;
-    if (s >= op.N) return;
+    static_assert(LPR == 8 || LPR == 16 || LPR == 32, "LPR");
+    const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LPR;
+    const int t = threadIdx.x & (LPR - 1);
+    const bool live = s < op.N;
     const int d = op.d, n = op.n, L = op.L;
-    const TA xs = TR ? x[s] : TA(0);
     TA acc = TA(0);
-    const TV* vp = vals + op.row_ptr[s];
-    const unsigned long long* dp = desc + s * op.nb;
-    for (int k = 0; k < op.nb; ++k) {
-        const unsigned long long w = dp[k];
-        if (w == 0ull) break;
-        const int b2 = (int)(w >> BLK_B2_SHIFT);
-        int W0, W1, f0p, f1p;
-        if (d == 2) {
-            W0 = (int)(w & 0x3FFF);
-            W1 = (int)((w >> 14) & 0x3FFF);
-            f0p = (int)((w >> 28) & 0x3FFF);
-            f1p = (int)((w >> 42) & 0x3FFF);
-        } else {
-            W0 = 1;
-            W1 = (int)(w & 0xFFFFFFF);
-            f0p = 0;
-            f1p = (int)((w >> 28) & 0xFFFFFFF);
-        }
-        const Band B2 = band_info(d, n, L, b2);
-        const int nj = B2.nj, tot = W0 * W1;
-        const int rowstep = (d == 2) ? nj : 0;
-        const int off = (int)B2.off;
-        const int qa = 32 / W1, rb = 32 - qa * W1;
-        int a = lane / W1, c = lane - a * W1;
-        for (int i0 = lane; i0 < tot; i0 += 128) {
-            int col[4];
-            TA v[4];
+    if (live) {
+        const TA xs = TR ? x[s] : TA(0);
+        const TV* vp = vals + op.row_ptr[s];
+        const unsigned long long* dp = desc + s * op.nb;
+        for (int k = 0; k < op.nb; ++k) {
+            const unsigned long long w = dp[k];
+            if (w == 0ull) break;
+            const int b2 = (int)(w >> BLK_B2_SHIFT);
+            int W0, W1, f0p, f1p;
+            if (d == 2) {
+                W0 = (int)(w & 0x3FFF);
+                W1 = (int)((w >> 14) & 0x3FFF);
+                f0p = (int)((w >> 28) & 0x3FFF);
+                f1p = (int)((w >> 42) & 0x3FFF);
+            } else {
+                W0 = 1;
+                W1 = (int)(w & 0xFFFFFFF);
+                f0p = 0;
+                f1p = (int)((w >> 28) & 0xFFFFFFF);
+            }
+            const Band B2 = band_info(d, n, L, b2);
+            const int nj = B2.nj, tot = W0 * W1;
+            const int rowstep = (d == 2) ? nj : 0;
+            const int off = (int)B2.off;
+            int qa = 0, rb = LPR, a = 0, c = t;
+            if (W1 < LPR) {
+                qa = LPR / W1;
+                rb = LPR - qa * W1;
+                a = t / W1;
+                c = t - a * W1;
+            }
+            for (int i0 = t; i0 < tot; i0 += 4 * LPR) {
+                int col[4];
+                TA v[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                int ra = f0p + a, cb = f1p + c;
-                ra -= (ra >= nj) ? nj : 0;
-                cb -= (cb >= nj) ? nj : 0;
-                col[u] = off + ra * rowstep + cb;
-                c += rb;
-                a += qa;
-                if (c >= W1) {
-                    c -= W1;
-                    ++a;
+                for (int u = 0; u < 4; ++u) {
+                    int ra = f0p + a, cb = f1p + c;
+                    ra -= (ra >= nj) ? nj : 0;
+                    cb -= (cb >= nj) ? nj : 0;
+                    col[u] = off + ra * rowstep + cb;
+                    c += rb;
+                    a += qa;
+                    if (c >= W1) {
+                        c -= W1;
+                        ++a;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = i0 + LPR * u;
+                    v[u] = (i < tot) ? to_acc<TA, TV>(vp[i]) : TA(0);
+                    if (SQ) v[u] *= v[u];
+                }
+                if (!TR) {
+                    TA xv[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) xv[u] = (i0 + LPR * u < tot) ? x[col[u]] : TA(0);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) acc = fma(v[u], xv[u], acc);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (i0 + LPR * u < tot) atomicAdd(y + col[u], v[u] * xs);
                 }
             }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int i = i0 + 32 * u;
-                v[u] = (i < tot) ? to_acc<TA, TV>(vp[i]) : TA(0);
-                if (SQ) v[u] *= v[u];
-            }
-            if (!TR) {
-                TA xv[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) xv[u] = (i0 + 32 * u < tot) ? x[col[u]] : TA(0);
-#pragma unroll
-                for (int u = 0; u < 4; ++u) acc = fma(v[u], xv[u], acc);
-            } else {
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (i0 + 32 * u < tot) atomicAdd(y + col[u], v[u] * xs);
-            }
+            vp += tot;
         }
-        vp += tot;
     }
     if (!TR) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) y[s] = sub ? acc - sub[s] : acc;
+        for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (live && t == 0) y[s] = sub ? acc - sub[s] : acc;
     }
 }
 

@@ -731,7 +731,6 @@ pc_status apply1_t(pc_op* h, const TV* vals, const TA* x, TA* y, const TA* sub, 
     if (e != PC_OK) return e;
     OpDev<TA> od = apply_od<TA>(h);
     od.nb = h->bdesc_stride;
-    const int blocks = (int)((h->N * 32 + 255) / 256);
     bool transpose = (h->desc.order == PC_ORDER_CONV_THEN_MULT) != adjoint;
     if constexpr (std::is_same<TV, TA>::value) {
         if (transpose && use_T) {
@@ -743,10 +742,23 @@ pc_status apply1_t(pc_op* h, const TV* vals, const TA* x, TA* y, const TA* sub, 
     if (transpose) {
         if (sub) return fail(h, PC_ERR_INVALID_ARG, "internal: subtraction on a scattered product");
         k_zero_rows<TA><<<(int)((h->N + 255) / 256), 256, 0, st>>>(y, h->N, 1, 0, 1);
-        k_apply1<TV, TA, SQ, 1><<<blocks, 256, 0, st>>>(od, h->bdesc_d, vals, x, y, nullptr);
+        k_apply1<TV, TA, SQ, 1, 32><<<(int)((h->N * 32 + 255) / 256), 256, 0, st>>>(od, h->bdesc_d, vals, x, y,
+                                                                                   nullptr);
         count_launch(2);
     } else {
-        k_apply1<TV, TA, SQ, 0><<<blocks, 256, 0, st>>>(od, h->bdesc_d, vals, x, y, sub);
+        // the fewest lanes per row that still give three quarters of a wave of warps (64 per SM)
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int64_t want = (int64_t)std::max(sms, 1) * 64 * 32 * 3 / 4;
+        if (h->N * 8 >= want)
+            k_apply1<TV, TA, SQ, 0, 8><<<(int)((h->N * 8 + 255) / 256), 256, 0, st>>>(od, h->bdesc_d, vals, x, y, sub);
+        else if (h->N * 16 >= want)
+            k_apply1<TV, TA, SQ, 0, 16><<<(int)((h->N * 16 + 255) / 256), 256, 0, st>>>(od, h->bdesc_d, vals, x, y,
+                                                                                        sub);
+        else
+            k_apply1<TV, TA, SQ, 0, 32><<<(int)((h->N * 32 + 255) / 256), 256, 0, st>>>(od, h->bdesc_d, vals, x, y,
+                                                                                        sub);
         count_launch();
     }
     PC_CUDA(h, cudaGetLastError());
