@@ -40,6 +40,7 @@ def _load():
         lib = ctypes.CDLL(build())
         I, D = ctypes.c_int, ctypes.c_int64
         lib.or_daubechies.argtypes = [I, _dp]
+        lib.or_symmlet.argtypes = [I, _dp]
         lib.or_dwt.argtypes = [I, I, I, I, _dp, _dp]
         lib.or_idwt.argtypes = [I, I, I, I, _dp, _dp]
         lib.or_pc_apply.argtypes = [I, I, I, I, I, _dp, _dp, _dp, _dp]
@@ -77,19 +78,36 @@ def daubechies(delta: int) -> np.ndarray:
     return h[:rc].copy()
 
 
-def dwt(d, n, L, delta, f):
+def symmlet(delta: int) -> np.ndarray:
+    """Low-pass taps h[0..2 delta - 1] of the least-asymmetric spectral factor (sum sqrt 2)."""
+    h = np.zeros(64)
+    rc = _load().or_symmlet(delta, h.ctypes.data_as(_dp))
+    _check(rc, "symmlet")
+    return h[:rc].copy()
+
+
+def _wcode(delta, family=0):
+    """The library's filter code: delta + 100 * family (0 Daubechies, 1 Symmlet)."""
+    return int(delta) + 100 * int(family)
+
+
+def _opcode(op):
+    return _wcode(op.delta, getattr(op, "family", 0))
+
+
+def dwt(d, n, L, delta, f, family=0):
     """Forward periodic transform Psi^* of pixels f (n^d, row-major) -> canonical coefficients."""
     f, fp = _d(np.asarray(f).reshape(-1))
     c = np.zeros(f.size)
-    _check(_load().or_dwt(d, n, L, delta, fp, c.ctypes.data_as(_dp)), "dwt")
+    _check(_load().or_dwt(d, n, L, _wcode(delta, family), fp, c.ctypes.data_as(_dp)), "dwt")
     return c
 
 
-def idwt(d, n, L, delta, c):
+def idwt(d, n, L, delta, c, family=0):
     """Inverse periodic transform Psi: canonical coefficients -> pixels."""
     c, cp = _d(np.asarray(c).reshape(-1))
     f = np.zeros(c.size)
-    _check(_load().or_idwt(d, n, L, delta, cp, f.ctypes.data_as(_dp)), "idwt")
+    _check(_load().or_idwt(d, n, L, _wcode(delta, family), cp, f.ctypes.data_as(_dp)), "idwt")
     return f
 
 
@@ -110,7 +128,7 @@ def theta_columns(op, cols, u=None, v=None, nthreads: int = 0):
     v, vp = _d(op.v if v is None else v)
     cols = np.ascontiguousarray(cols, dtype=np.int64)
     out = np.zeros((cols.size, op.N))
-    rc = _load().or_theta_columns(op.d, op.n, op.levels, op.delta, u.shape[0], op.r, op.order,
+    rc = _load().or_theta_columns(op.d, op.n, op.levels, _opcode(op), u.shape[0], op.r, op.order,
                                   up, vp, cols.size, cols.ctypes.data_as(_i64p),
                                   out.ctypes.data_as(_dp), nthreads)
     _check(rc, "theta_columns")
@@ -118,13 +136,13 @@ def theta_columns(op, cols, u=None, v=None, nthreads: int = 0):
 
 
 def in_pattern(op, mu: int, lam: int) -> bool:
-    return bool(_load().or_in_pattern(op.d, op.n, op.levels, op.delta, op.r, op.gap, int(mu), int(lam)))
+    return bool(_load().or_in_pattern(op.d, op.n, op.levels, _opcode(op), op.r, op.gap, int(mu), int(lam)))
 
 
 def pattern_column(op, lam: int) -> np.ndarray:
     """Boolean mask over mu of the pattern entries (mu, lam)."""
     mask = np.zeros(op.N, dtype=np.uint8)
-    _load().or_pattern_mask(op.d, op.n, op.levels, op.delta, op.r, op.gap, int(lam),
+    _load().or_pattern_mask(op.d, op.n, op.levels, _opcode(op), op.r, op.gap, int(lam),
                             mask.ctypes.data_as(_u8p))
     return mask.astype(bool)
 
@@ -138,7 +156,7 @@ def theta_grad(op, cols, G, u=None, v=None, nthreads: int = 0):
     G, Gp = _d(G)
     du = np.zeros(u.shape)
     dv = np.zeros(v.shape)
-    rc = _load().or_theta_grad(op.d, op.n, op.levels, op.delta, u.shape[0], op.r, op.order,
+    rc = _load().or_theta_grad(op.d, op.n, op.levels, _opcode(op), u.shape[0], op.r, op.order,
                                up, vp, cols.size, cols.ctypes.data_as(_i64p), Gp,
                                du.ctypes.data_as(_dp), dv.ctypes.data_as(_dp), nthreads)
     _check(rc, "theta_grad")

@@ -16,7 +16,9 @@
  *
  * Conventions (the paper leaves them open; see the readings in the design notes):
  *   - levels j = 1 (finest) .. L (coarsest); level j has n_j = n / 2^j translates per axis;
- *   - Daubechies low-pass h with Lf = 2*delta taps on [0, Lf-1], minimum phase, sum sqrt(2);
+ *   - Daubechies low-pass h with Lf = 2*delta taps on [0, Lf-1], minimum phase, sum sqrt(2)
+ *     (or the Symmlet of the same order: same support, least-asymmetric phase); functions
+ *     take the filter as a code delta + 100 * family (family 0 Daubechies, 1 Symmlet);
  *     high-pass g[i] = (-1)^(1-i) h[1-i] on [2-Lf, 1]                    (Section 2.1);
  *   - analysis a_j[l] = sum_n h[n-2l] a_{j-1}[n],  d_j[l] = sum_n g[n-2l] a_{j-1}[n],
  *     indices mod n_{j-1} (the recursion of Section 2.1 on the torus);
@@ -108,6 +110,152 @@ int or_daubechies(int delta, double *h)
     return 2 * delta;
 }
 
+/* ------------------------------------------------------------------------------------
+ * Symmlet (least-asymmetric) filter (Section 4.3 uses the Symmlet basis of order 6).  Same
+ * |m0|^2 as Daubechies' filter of the same order (same P), but for every root y_i of P -- each
+ * conjugate pair once, so that the taps stay real -- the factor (z - z_i) takes the root z_i
+ * of z^2 - (2 - 4 y_i) z + 1 = 0 outside or inside the unit circle, whichever makes the phase
+ * of prod_i (e^{-iw} - z_i) closest to linear on [0, pi]: the smallest mean squared residual of
+ * the least-squares line through the unwrapped phase at w_k = (k + 1/2) pi / 512, k < 512.
+ * A choice and its mirror (all roots inverted: the reversed filter) have the same residual;
+ * ties within 1e-9 (relative) go to the smaller energy centre sum_n n h[n]^2.
+ * ------------------------------------------------------------------------------------ */
+#define OR_SYM_K 512
+#define OR_PI 3.14159265358979323846
+
+static double phase_residual(const double complex *z, int nz)
+{
+    double ph[OR_SYM_K];
+    for (int k = 0; k < OR_SYM_K; ++k) ph[k] = 0.0;
+    for (int i = 0; i < nz; ++i) {
+        double prev = 0.0, acc = 0.0;
+        for (int k = 0; k < OR_SYM_K; ++k) {
+            const double w = (k + 0.5) * OR_PI / OR_SYM_K;
+            const double a = carg(cexp(-I * w) - z[i]);
+            if (k == 0) acc = a;
+            else {
+                double dlt = a - prev;
+                while (dlt > OR_PI) dlt -= 2.0 * OR_PI;
+                while (dlt < -OR_PI) dlt += 2.0 * OR_PI;
+                acc += dlt;
+            }
+            prev = a;
+            ph[k] += acc;
+        }
+    }
+    /* least-squares line a + b w */
+    double sw = 0.0, sww = 0.0, sp = 0.0, swp = 0.0;
+    for (int k = 0; k < OR_SYM_K; ++k) {
+        const double w = (k + 0.5) * OR_PI / OR_SYM_K;
+        sw += w; sww += w * w; sp += ph[k]; swp += w * ph[k];
+    }
+    const double n = OR_SYM_K, det = n * sww - sw * sw;
+    const double b = (n * swp - sw * sp) / det, a = (sp - b * sw) / n;
+    double r = 0.0;
+    for (int k = 0; k < OR_SYM_K; ++k) {
+        const double w = (k + 0.5) * OR_PI / OR_SYM_K;
+        const double e = ph[k] - a - b * w;
+        r += e * e;
+    }
+    return r / n;
+}
+
+/* taps of (1 + z)^delta prod_i (z - z_i), normalised to sum sqrt 2; returns the tap count */
+static int taps_from_roots(int delta, const double complex *z, int nz, double *h)
+{
+    double complex poly[OR_MAXTAPS + 1];
+    for (int i = 0; i <= OR_MAXTAPS; ++i) poly[i] = 0.0;
+    poly[0] = 1.0;
+    int deg = 0;
+    for (int k = 0; k < delta; ++k) {
+        for (int i = deg + 1; i >= 1; --i) poly[i] += poly[i - 1];
+        ++deg;
+    }
+    for (int i = 0; i < nz; ++i) {
+        for (int q = deg + 1; q >= 0; --q) {
+            double complex lower = (q >= 1) ? poly[q - 1] : 0.0;
+            poly[q] = lower - z[i] * poly[q];
+        }
+        ++deg;
+    }
+    double sum = 0.0;
+    for (int i = 0; i <= deg; ++i) sum += creal(poly[i]);
+    for (int i = 0; i <= deg; ++i) h[i] = creal(poly[i]) * sqrt(2.0) / sum;
+    return deg + 1;
+}
+
+int or_symmlet(int delta, double *h)
+{
+    if (delta < 1 || 2 * delta > OR_MAXTAPS) return -1;
+    if (delta == 1) return taps_from_roots(1, NULL, 0, h);
+    double c[OR_MAXTAPS];
+    for (int k = 0; k < delta; ++k) c[k] = binom(delta - 1 + k, k);
+    double complex y[OR_MAXTAPS], zout[OR_MAXTAPS];
+    const int ny = delta - 1;
+    poly_roots(c, ny, y);
+    for (int i = 0; i < ny; ++i) {
+        double complex b = 2.0 - 4.0 * y[i];
+        double complex s = csqrt(b * b - 4.0);
+        zout[i] = (b + s) / 2.0;
+        if (cabs(zout[i]) < 1.0) zout[i] = (b - s) / 2.0;
+    }
+    /* groups: a real root alone, a root with positive imaginary part with its conjugate */
+    int g_first[OR_MAXTAPS], g_second[OR_MAXTAPS], ng = 0;
+    for (int i = 0; i < ny; ++i) {
+        const double tol = 1e-9 * (1.0 + cabs(y[i]));
+        if (fabs(cimag(y[i])) <= tol) {
+            g_first[ng] = i; g_second[ng] = -1; ++ng;
+        } else if (cimag(y[i]) > 0.0) {
+            int best = -1;
+            double bd = 1e300;
+            for (int j = 0; j < ny; ++j) {
+                if (j == i || cimag(y[j]) >= 0.0) continue;
+                const double dd = cabs(y[j] - conj(y[i]));
+                if (dd < bd) { bd = dd; best = j; }
+            }
+            if (best < 0) return -1;
+            g_first[ng] = i; g_second[ng] = best; ++ng;
+        }
+    }
+    double best_r = 1e300, best_c = 1e300;
+    double hb[OR_MAXTAPS];
+    int Lf = 2 * delta;
+    for (long mask = 0; mask < (1L << ng); ++mask) {
+        double complex z[OR_MAXTAPS];
+        int nz = 0;
+        for (int g = 0; g < ng; ++g) {
+            const int i = g_first[g];
+            const double complex zi = ((mask >> g) & 1) ? 1.0 / zout[i] : zout[i];
+            z[nz++] = zi;
+            if (g_second[g] >= 0) z[nz++] = conj(zi);
+        }
+        double ht[OR_MAXTAPS];
+        if (taps_from_roots(delta, z, nz, ht) != Lf) return -1;
+        const double r = phase_residual(z, nz);
+        double cen = 0.0;
+        for (int n = 0; n < Lf; ++n) cen += n * ht[n] * ht[n];
+        const int tie = fabs(r - best_r) <= 1e-9 * fmax(best_r, 1e-300);
+        if (r < best_r && !tie) {
+            best_r = r; best_c = cen;
+            memcpy(hb, ht, sizeof(double) * Lf);
+        } else if (tie && cen < best_c) {
+            best_c = cen;
+            memcpy(hb, ht, sizeof(double) * Lf);
+        }
+    }
+    memcpy(h, hb, sizeof(double) * Lf);
+    return Lf;
+}
+
+/* Filter code: delta + 100 * family (family 0 = Daubechies, 1 = Symmlet). */
+static int filter_taps(int code, double *h)
+{
+    const int family = code / 100, delta = code % 100;
+    if (family == 0) return or_daubechies(delta, h);
+    if (family == 1) return or_symmlet(delta, h);
+    return -1;
+}
+
 /* g[i] = (-1)^(1-i) h[1-i] for i in [2-Lf, 1], stored at g_arr[i - (2 - Lf)] */
 static void highpass(const double *h, int Lf, double *g_arr)
 {
@@ -146,10 +294,10 @@ static void synthesis_line(const double *h, const double *g, int Lf, int64_t M,
 }
 
 /* forward transform Psi^*: f (n^d pixels, row-major) -> c (canonical order) */
-int or_dwt(int d, int n, int L, int delta, const double *f, double *c)
+int or_dwt(int d, int n, int L, int wcode, const double *f, double *c)
 {
     double h[OR_MAXTAPS], g[OR_MAXTAPS];
-    int Lf = or_daubechies(delta, h);
+    int Lf = filter_taps(wcode, h);
     if (Lf < 0 || (n >> L) < 1 || (d != 1 && d != 2)) return -1;
     highpass(h, Lf, g);
     int64_t N = (d == 1) ? n : (int64_t)n * n;
@@ -186,10 +334,10 @@ int or_dwt(int d, int n, int L, int delta, const double *f, double *c)
 }
 
 /* inverse transform Psi: c (canonical) -> f (pixels) */
-int or_idwt(int d, int n, int L, int delta, const double *c, double *f)
+int or_idwt(int d, int n, int L, int wcode, const double *c, double *f)
 {
     double h[OR_MAXTAPS], g[OR_MAXTAPS];
-    int Lf = or_daubechies(delta, h);
+    int Lf = filter_taps(wcode, h);
     if (Lf < 0 || (n >> L) < 1 || (d != 1 && d != 2)) return -1;
     highpass(h, Lf, g);
     int64_t N = (d == 1) ? n : (int64_t)n * n;
@@ -271,7 +419,7 @@ int or_pc_apply(int d, int n, int m, int r, int order, const double *u, const do
  * w = H psi_lambda, column lambda of Theta = Psi^* w.  out is ncols x N (column-major
  * by requested column: out[c*N + mu] = Theta[mu, cols[c]]).
  * ---------------------------------------------------------------------------------- */
-int or_theta_columns(int d, int n, int L, int delta, int m, int r, int order,
+int or_theta_columns(int d, int n, int L, int wcode, int m, int r, int order,
                      const double *u, const double *v, int64_t ncols, const int64_t *cols,
                      double *out, int nthreads)
 {
@@ -291,10 +439,10 @@ int or_theta_columns(int d, int n, int L, int delta, int m, int r, int order,
             int64_t lam = cols[c];
             if (lam < 0 || lam >= N) { bad = 1; continue; }
             e[lam] = 1.0;
-            or_idwt(d, n, L, delta, e, psi);
+            or_idwt(d, n, L, wcode, e, psi);
             e[lam] = 0.0;
             or_pc_apply(d, n, m, r, order, u, v, psi, w);
-            or_dwt(d, n, L, delta, w, out + c * N);
+            or_dwt(d, n, L, wcode, w, out + c * N);
         }
         free(e);
         free(psi);
@@ -360,8 +508,9 @@ static int near_on_circle(int64_t A0, int64_t A1, int64_t B0, int64_t B1, int r,
 /* (mu, lambda) in P: gap < 0 keeps everything; otherwise | |mu| - |lambda| | <= gap and,
  * on every axis, the supports of psi_mu and psi_lambda are within r of each other on the
  * torus (entries failing this are exactly zero: the kernels have radius r). */
-int or_in_pattern(int d, int n, int L, int delta, int r, int gap, int64_t mu, int64_t lam)
+int or_in_pattern(int d, int n, int L, int wcode, int r, int gap, int64_t mu, int64_t lam)
 {
+    const int delta = wcode % 100;
     if (gap < 0) return 1;
     int Lf = 2 * delta;
     int jm, e0m, e1m, jl, e0l, e1l;
@@ -382,11 +531,11 @@ int or_in_pattern(int d, int n, int L, int delta, int r, int gap, int64_t mu, in
     return 1;
 }
 
-int or_pattern_mask(int d, int n, int L, int delta, int r, int gap, int64_t lam,
+int or_pattern_mask(int d, int n, int L, int wcode, int r, int gap, int64_t lam,
                     unsigned char *mask)
 {
     int64_t N = (d == 1) ? n : (int64_t)n * n;
-    for (int64_t mu = 0; mu < N; ++mu) mask[mu] = (unsigned char)or_in_pattern(d, n, L, delta, r, gap, mu, lam);
+    for (int64_t mu = 0; mu < N; ++mu) mask[mu] = (unsigned char)or_in_pattern(d, n, L, wcode, r, gap, mu, lam);
     return 0;
 }
 
@@ -398,7 +547,7 @@ int or_pattern_mask(int d, int n, int L, int delta, int r, int gap, int64_t lam,
  *   order 1: dL/du_k(t) += sum_y g(y) v_k(y) psi(y - t), dL/dv_k(y) += g(y) (u_k * psi)(y)
  * du (m x K) and dv (m x N) are overwritten.
  * ---------------------------------------------------------------------------------- */
-int or_theta_grad(int d, int n, int L, int delta, int m, int r, int order,
+int or_theta_grad(int d, int n, int L, int wcode, int m, int r, int order,
                   const double *u, const double *v, int64_t ncols, const int64_t *cols,
                   const double *G, double *du, double *dv, int nthreads)
 {
@@ -423,9 +572,9 @@ int or_theta_grad(int d, int n, int L, int delta, int m, int r, int order,
             int64_t lam = cols[ci];
             if (lam < 0 || lam >= N) { bad = 1; continue; }
             e[lam] = 1.0;
-            or_idwt(d, n, L, delta, e, psi);
+            or_idwt(d, n, L, wcode, e, psi);
             e[lam] = 0.0;
-            or_idwt(d, n, L, delta, G + ci * N, g);
+            or_idwt(d, n, L, wcode, G + ci * N, g);
             for (int k = 0; k < m; ++k) {
                 const double *uk = u + k * Ku, *vk = v + k * N;
                 double *duk = du_t + k * Ku, *dvk = dv_t + k * N;

@@ -124,7 +124,8 @@ class Operator:
 
     u: (m, (2r+1)^d) kernels, row-major stencil, centre index = offset 0.
     v: (m, n^d) windows, row-major pixels (axis 0 slow).
-    delta: Daubechies order (number of vanishing moments; 2*delta taps).
+    delta: wavelet order (number of vanishing moments; 2*delta taps).
+    family: 0 = Daubechies (minimum phase), 1 = Symmlet (least asymmetric), same support.
     levels: number of decomposition levels L (level 1 finest, L coarsest).
     gap: keep entries with | |mu| - |lambda| | <= gap; -1 keeps every entry.
     order: 0 = u_k * (v_k . f) (paper), 1 = v_k . (u_k * f).
@@ -140,6 +141,7 @@ class Operator:
     gap: int = 2
     order: int = 0
     extra: dict = field(default_factory=dict)
+    family: int = 0
 
     @property
     def m(self) -> int:

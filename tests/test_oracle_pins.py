@@ -43,9 +43,9 @@ def _cascade_1d(h, n, L):
     return Phi, Psis
 
 
-def dense_psi(d, n, L, delta):
+def dense_psi(d, n, L, delta, family=0):
     """N x N matrix whose column lambda is psi_lambda, canonical order."""
-    h = oracle.daubechies(delta)
+    h = oracle.symmlet(delta) if family else oracle.daubechies(delta)
     Phi, Psis = _cascade_1d(h, n, L)
     if d == 1:
         return np.concatenate([Phi] + [Psis[j - 1] for j in range(L, 0, -1)], 1)
@@ -81,12 +81,12 @@ def dense_H(op, u=None, v=None):
     return H
 
 
-def tiny(d, n, L, delta, r, m, order=0, seed=0, gap=-1):
+def tiny(d, n, L, delta, r, m, order=0, seed=0, gap=-1, family=0):
     N = n ** d
     K = (2 * r + 1) ** d
     u = P.normal(P.BASE_SEED + 100 + seed, m * K).reshape(m, K)
     v = P.uniform(P.BASE_SEED + 200 + seed, m * N).reshape(m, N) + 0.1
-    return P.Operator("tiny", d, n, delta, L, r, u, v, gap=gap, order=order)
+    return P.Operator("tiny", d, n, delta, L, r, u, v, gap=gap, order=order, family=family)
 
 
 # ----------------------------------------------------------------- filter taps
