@@ -62,6 +62,9 @@ typedef enum {
 
 typedef enum { PC_ORDER_MULT_THEN_CONV = 0, PC_ORDER_CONV_THEN_MULT = 1 } pc_order;
 typedef enum { PC_FP32 = 0, PC_FP64 = 1 } pc_precision;
+/* Wavelet family (Section 2.1 filter banks; the experiments of Section 4.3 use Symmlets):
+ * both have 2*delta taps on [0, 2 delta - 1] and delta vanishing moments. */
+typedef enum { PC_DAUBECHIES = 0, PC_SYMMLET = 1 } pc_family;
 
 typedef struct {
     int dim;       /* 1 or 2 */
@@ -75,6 +78,8 @@ typedef struct {
     int precision; /* PC_FP32: FP32 arithmetic, compensated (Kahan) sum over k, FP32 Theta;
                       PC_FP64: FP64 arithmetic and FP64 Theta (the plain baseline) */
     int store_bf16;/* PC_FP32 only: also keep a BF16 copy of Theta, used by pc_apply */
+    int family;    /* pc_family: PC_DAUBECHIES (minimum phase; a zeroed descriptor) or
+                      PC_SYMMLET (least-asymmetric factor of the same |m0|^2) */
 } pc_desc;
 
 /* ---------------------------------------------------------------------------------------
@@ -91,6 +96,16 @@ pc_status pc_plan_nnz(const pc_desc* desc, int64_t* nnz);
  * cols may be NULL to query the count only; otherwise it must hold *count entries
  * (query first).  Host only. */
 pc_status pc_plan_row(const pc_desc* desc, int64_t row, int64_t* cols, int64_t* count);
+
+/* Host only: the low-pass taps h[0 .. 2 delta - 1] (FP64, sum sqrt 2) the library uses for a
+ * family and order.  Daubechies: the minimum-phase spectral factor of |m0(w)|^2 =
+ * cos^(2 delta)(w/2) P(sin^2(w/2)) (Section 2.1).  Symmlet: of the real spectral factors (z_i
+ * or 1/z_i per root of P, conjugate roots alike), the one whose phase of prod (e^{-iw} - z_i)
+ * has the smallest mean squared residual from its least-squares line on w_k = (k + 1/2) pi /
+ * 512, k < 512; a tie with the mirror filter goes to the smaller energy centre sum n h[n]^2.
+ * h: caller-owned, 2 delta doubles.  PC_ERR_INVALID_ARG for NULL h, delta outside 1..10 or an
+ * unknown family. */
+pc_status pc_filter_taps(int family, int delta, double* h);
 
 /* ---------------------------------------------------------------------------------------
  * Operator lifetime.

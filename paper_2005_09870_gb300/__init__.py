@@ -19,6 +19,7 @@ if not os.path.exists(LIB_PATH):
                       "or python paper_2005_09870_gb300/build.py")
 _lib = ctypes.CDLL(LIB_PATH)
 
+PC_DAUBECHIES, PC_SYMMLET = 0, 1
 PC_OK, PC_ERR_INVALID_ARG, PC_ERR_UNSUPPORTED, PC_ERR_OOM, PC_ERR_CUDA, PC_ERR_TIMEOUT, \
     PC_ERR_NOT_ASSEMBLED, PC_ERR_DEVICE = range(8)
 PC_ORDER_MULT_THEN_CONV, PC_ORDER_CONV_THEN_MULT = 0, 1
@@ -29,7 +30,8 @@ _STATUS = ["PC_OK", "PC_ERR_INVALID_ARG", "PC_ERR_UNSUPPORTED", "PC_ERR_OOM", "P
 
 class pc_desc(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int) for f in
-                ("dim", "n", "levels", "delta", "m", "radius", "gap", "order", "precision", "store_bf16")]
+                ("dim", "n", "levels", "delta", "m", "radius", "gap", "order", "precision", "store_bf16",
+                 "family")]
 
 
 class PCError(RuntimeError):
@@ -72,6 +74,7 @@ _sig = {
     "pc_jacobi": ([_H, _P, _P], ctypes.c_int),
     "pc_power_norm": ([_H, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
     "pc_fista": ([_H, _P, _P, _P, _P, ctypes.c_int, ctypes.c_double, _P], ctypes.c_int),
+    "pc_filter_taps": ([ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
 }
 for _name, (_args, _ret) in _sig.items():
     _f = getattr(_lib, _name)
@@ -84,13 +87,24 @@ def _check(st, h=None):
         raise PCError(st, _lib.pc_last_error(h).decode())
 
 
-def make_desc(dim, n, levels, delta, m, radius, gap=2, order=0, precision=PC_FP32, store_bf16=0) -> pc_desc:
-    return pc_desc(dim, n, levels, delta, m, radius, gap, order, precision, int(store_bf16))
+def make_desc(dim, n, levels, delta, m, radius, gap=2, order=0, precision=PC_FP32, store_bf16=0,
+              family=0) -> pc_desc:
+    return pc_desc(dim, n, levels, delta, m, radius, gap, order, precision, int(store_bf16), int(family))
 
 
 def desc_of(op, precision=PC_FP32, store_bf16=0) -> pc_desc:
-    """Descriptor for a pc_inputs.Operator-like object (fields d, n, levels, delta, m, r, gap, order)."""
-    return make_desc(op.d, op.n, op.levels, op.delta, op.m, op.r, op.gap, op.order, precision, store_bf16)
+    """Descriptor for a pc_inputs.Operator-like object (fields d, n, levels, delta, m, r, gap,
+    order and optionally family)."""
+    return make_desc(op.d, op.n, op.levels, op.delta, op.m, op.r, op.gap, op.order, precision, store_bf16,
+                     getattr(op, "family", 0))
+
+
+def pc_filter_taps(family: int, delta: int):
+    """Host-only: the library's low-pass taps for a family (0 Daubechies, 1 Symmlet) and order."""
+    import numpy as np
+    h = np.zeros(2 * int(delta))
+    _check(_lib.pc_filter_taps(int(family), int(delta), h.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return h
 
 
 # ----------------------------------------------------------------- host-only planning

@@ -167,6 +167,8 @@ pc_status check_desc(const pc_desc* d, pc_op* h)
     if (d->order != 0 && d->order != 1) return fail(h, PC_ERR_INVALID_ARG, "order must be 0 or 1");
     if (d->precision != PC_FP32 && d->precision != PC_FP64) return fail(h, PC_ERR_INVALID_ARG, "bad precision");
     if (d->store_bf16 && d->precision != PC_FP32) return fail(h, PC_ERR_INVALID_ARG, "store_bf16 needs PC_FP32");
+    if (d->family != PC_DAUBECHIES && d->family != PC_SYMMLET)
+        return fail(h, PC_ERR_INVALID_ARG, "family must be PC_DAUBECHIES or PC_SYMMLET (got %d)", d->family);
     if (d->gap < 0) {
         int64_t N = (d->dim == 2) ? (int64_t)d->n * d->n : d->n;
         if (N > 16384) return fail(h, PC_ERR_UNSUPPORTED, "dense pattern limited to N <= 16384");
@@ -1569,9 +1571,9 @@ pc_status pc_create(const pc_desc* desc, const void* u, const void* v, void* str
     h->nb = g.nb;
     h->N = (D.dim == 2) ? (int64_t)D.n * D.n : D.n;
     h->esz = (D.precision == PC_FP64) ? 8 : 4;
-    if (daubechies_taps(D.delta, h->h) != h->Lf) {
+    if (filter_taps(D.family, D.delta, h->h) != h->Lf) {
         delete h;
-        return fail(nullptr, PC_ERR_INVALID_ARG, "filter taps failed for delta=%d", D.delta);
+        return fail(nullptr, PC_ERR_INVALID_ARG, "filter taps failed for family=%d delta=%d", D.family, D.delta);
     }
     cudaStream_t s = (cudaStream_t)stream;
     auto bail = [&](pc_status e) {
@@ -1756,6 +1758,17 @@ pc_status pc_assemble_stage(pc_handle h, int stage, void* stream)
 }
 
 int64_t pc_launch_counter(void) { return (int64_t)g_launches.load(); }
+
+pc_status pc_filter_taps(int family, int delta, double* h)
+{
+    if (!h) return fail(nullptr, PC_ERR_INVALID_ARG, "h is NULL");
+    if (delta < 1 || delta > 10) return fail(nullptr, PC_ERR_INVALID_ARG, "delta must be in 1..10");
+    if (family != PC_DAUBECHIES && family != PC_SYMMLET)
+        return fail(nullptr, PC_ERR_INVALID_ARG, "family must be PC_DAUBECHIES or PC_SYMMLET (got %d)", family);
+    if (filter_taps(family, delta, h) != 2 * delta)
+        return fail(nullptr, PC_ERR_INVALID_ARG, "filter taps failed for family=%d delta=%d", family, delta);
+    return PC_OK;
+}
 
 pc_status pc_apply(pc_handle h, const void* x, void* y, int nrhs, int ldx, int ldy, void* stream)
 {

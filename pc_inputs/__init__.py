@@ -91,6 +91,17 @@ def motion_kernel(r: int, length: float, theta: float) -> np.ndarray:
     return k / k.sum()
 
 
+def skewed_gaussian(r: int, s_long: float, s_short: float, theta: float, skew: float) -> np.ndarray:
+    """(2r+1)^2 stencil of an anisotropic Gaussian: standard deviations s_long along the
+    direction theta and s_short across it, skewed along the long axis by the factor
+    (1 + skew * tanh(t / s_long)) (t the coordinate along theta); normalised to sum 1."""
+    y0, y1 = np.mgrid[-r:r + 1, -r:r + 1].astype(np.float64)
+    t = math.cos(theta) * y1 + math.sin(theta) * y0
+    q = -math.sin(theta) * y1 + math.cos(theta) * y0
+    k = np.exp(-0.5 * ((t / s_long) ** 2 + (q / s_short) ** 2)) * (1.0 + skew * np.tanh(t / s_long))
+    return k / k.sum()
+
+
 def _conv2_same(a: np.ndarray, b: np.ndarray) -> np.ndarray:
     """Full 2-D convolution of two centred odd-size kernels, cropped back to a's size."""
     ra, rb = a.shape[0] // 2, b.shape[0] // 2
@@ -168,6 +179,12 @@ def workload(name: str, seed_offset: int = 0, **over) -> Operator:
         target kernels (Gaussians sigma_k = 0.8 + 1.7 k/8).
     c5  2-D 1024^2, db4, L=5, m=64 (8x8 hats), 31x31 kernels = normalised
         Gaussian(sigma ~ U[0.5,4]) * motion(length ~ U{3..15}, angle ~ U[0,pi)).
+    op1  stand-in for the paper's first blur (Section 4.1): isotropic Gaussians whose sigma
+         grows along axis 0 only, sigma_k = 3 (k + 1/2) / 5 px for the m = 5 windows (hats
+         along axis 0, constant along axis 1), 19x19 stencils (r = 9); Symmlet 6, L = 4.
+    op2  stand-in for the second blur: m = 25 (5x5 bilinear hats), 25x25 stencils (r = 12)
+         of rotated, skewed Gaussians whose elongation grows with the distance of the window
+         centre from the field centre and whose long axis points to it; Symmlet 6, L = 4.
     small-1d / small-2d  parity cases that span several tiles with a ragged tail.
     Keyword overrides replace fields (n, levels, ...) before the inputs are drawn.
     """
@@ -182,13 +199,13 @@ def workload(name: str, seed_offset: int = 0, **over) -> Operator:
             u[k, r - rk:r + rk + 1] = gaussian_kernel(1, rk, s)
         v = hat_windows(1, n, 4)
         return Operator("c1", 1, n, over.get("delta", 2), over.get("levels", 5), r, u, v,
-                        gap=over.get("gap", -1), order=over.get("order", 0))
+                        gap=over.get("gap", -1), order=over.get("order", 0), family=over.get("family", 0))
     if name == "c2":
         n, g, r = over.get("n", 256), 4, over.get("r", 7)
         m = g * g
         u = _stack([gaussian_kernel(2, r, 0.5 + 2.5 * k / (m - 1)) for k in range(m)], 2)
         return Operator("c2", 2, n, over.get("delta", 4), over.get("levels", 4), r, u,
-                        hat_windows(2, n, g), gap=over.get("gap", 2), order=over.get("order", 0))
+                        hat_windows(2, n, g), gap=over.get("gap", 2), order=over.get("order", 0), family=over.get("family", 0))
     if name == "c3":
         n, g, r = over.get("n", 128), 3, 5
         m = g * g
@@ -198,7 +215,7 @@ def workload(name: str, seed_offset: int = 0, **over) -> Operator:
         ut = _stack([gaussian_kernel(2, r, 0.8 + 1.7 * k / (m - 1)) for k in range(m)], 2)
         return Operator("c3", 2, n, over.get("delta", 4), over.get("levels", 3), r, u,
                         hat_windows(2, n, g), gap=over.get("gap", 2), order=over.get("order", 0),
-                        extra={"u_target": ut})
+                        extra={"u_target": ut}, family=over.get("family", 0))
     if name == "c5":
         n, g, r = over.get("n", 1024), 8, 15
         m = g * g
@@ -211,7 +228,26 @@ def workload(name: str, seed_offset: int = 0, **over) -> Operator:
             ks.append(_conv2_same(motion_kernel(r, length, theta), gaussian_kernel(2, r, sigma)))
         u = _stack([k / k.sum() for k in ks], 2)
         return Operator("c5", 2, n, over.get("delta", 4), over.get("levels", 5), r, u,
-                        hat_windows(2, n, g), gap=over.get("gap", 2), order=over.get("order", 0))
+                        hat_windows(2, n, g), gap=over.get("gap", 2), order=over.get("order", 0), family=over.get("family", 0))
+    if name == "op1":
+        n, g, r = over.get("n", 256), 5, over.get("r", 9)
+        u = _stack([gaussian_kernel(2, r, 3.0 * (k + 0.5) / g) for k in range(g)], 2)
+        w1 = hat_windows(1, n, g)
+        v = np.repeat(w1, n, axis=1)             # v_k(y0, y1) = hat_k(y0)
+        return Operator("op1", 2, n, over.get("delta", 6), over.get("levels", 4), r, u, v,
+                        gap=over.get("gap", 2), order=over.get("order", 0), family=over.get("family", 1))
+    if name == "op2":
+        n, g, r = over.get("n", 256), 5, over.get("r", 12)
+        ks = []
+        for i in range(g):
+            for j in range(g):
+                c0, c1 = (i + 0.5) / g - 0.5, (j + 0.5) / g - 0.5     # window centre - field centre
+                rho = math.hypot(c0, c1) / math.hypot(0.5, 0.5)
+                ks.append(skewed_gaussian(r, 1.0 + 3.0 * rho, 1.0, math.atan2(c0, c1), 0.4 * rho))
+        u = _stack(ks, 2)
+        return Operator("op2", 2, n, over.get("delta", 6), over.get("levels", 4), r, u,
+                        hat_windows(2, n, g), gap=over.get("gap", 2), order=over.get("order", 0),
+                        family=over.get("family", 1))
     if name in ("small-1d", "small-2d"):
         d = 1 if name == "small-1d" else 2
         n = over.get("n", 512 if d == 1 else 64)
@@ -224,7 +260,7 @@ def workload(name: str, seed_offset: int = 0, **over) -> Operator:
         u = u + 0.05 * normal(seed + 1, u.size).reshape(u.shape) * u.max()
         v = hat_windows(d, n, g) * (1.0 + 0.25 * uniform(seed + 2, m)[:, None])
         return Operator(name, d, n, over.get("delta", 4), over.get("levels", 3), r, u, v,
-                        gap=over.get("gap", 2), order=over.get("order", 0))
+                        gap=over.get("gap", 2), order=over.get("order", 0), family=over.get("family", 0))
     raise KeyError(name)
 
 

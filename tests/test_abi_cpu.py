@@ -41,7 +41,8 @@ def test_plan_check_rejects_bad_descriptors(pw):
            pw.make_desc(2, 64, 3, 0, 9, 3), pw.make_desc(2, 64, 3, 4, 0, 3), pw.make_desc(2, 64, 3, 4, 300, 3),
            pw.make_desc(2, 64, 3, 4, 9, -1), pw.make_desc(2, 64, 3, 4, 9, 3, gap=-2),
            pw.make_desc(2, 64, 3, 4, 9, 3, order=2), pw.make_desc(2, 64, 3, 4, 9, 3, precision=1, store_bf16=1),
-           pw.make_desc(2, 256, 3, 4, 9, 3, gap=-1)]
+           pw.make_desc(2, 256, 3, 4, 9, 3, gap=-1), pw.make_desc(2, 64, 3, 4, 9, 3, family=2),
+           pw.make_desc(2, 64, 3, 4, 9, 3, family=-1)]
     for d in bad:
         with pytest.raises(pw.PCError):
             pw.pc_plan_check(d)
@@ -80,3 +81,28 @@ def test_oracle_pattern_row_counts_sampled(pw):
     for lam in list(rng.integers(0, op.N, 12)) + [0, op.N - 1, 16 * 16, 4096]:
         cols = pw.pc_plan_row(desc, int(lam))
         assert set(cols.tolist()) == set(np.nonzero(oracle.pattern_column(op, int(lam)))[0].tolist())
+
+
+@pytest.mark.parametrize("family", [0, 1])
+def test_host_filter_taps_equal_oracle(pw, family):
+    """The library's host taps (C++, Laguerre roots) against the oracle's (C, Durand-Kerner
+    roots): two implementations of the same spectral factor choice."""
+    for delta in range(1, 11):
+        got = pw.pc_filter_taps(family, delta)
+        want = oracle.symmlet(delta) if family else oracle.daubechies(delta)
+        assert np.abs(got - want).max() < 1e-13, delta
+    with pytest.raises(pw.PCError):
+        pw.pc_filter_taps(2, 4)
+    with pytest.raises(pw.PCError):
+        pw.pc_filter_taps(family, 11)
+
+
+def test_planner_pattern_equals_oracle_symmlet(pw):
+    for name, kw in (("op1", {"n": 32, "levels": 3}), ("small-1d", {"delta": 6, "family": 1})):
+        op = P.workload(name, **kw)
+        desc = pw.desc_of(op)
+        assert desc.family == 1
+        for lam in np.random.default_rng(4).integers(0, op.N, 40):
+            cols = pw.pc_plan_row(desc, int(lam))
+            mask = oracle.pattern_column(op, int(lam))
+            assert np.array_equal(np.sort(cols), np.flatnonzero(mask))

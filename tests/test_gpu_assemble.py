@@ -32,6 +32,11 @@ CASES = [
     ("small-2d", {"levels": 1}),                         # one level: approximation + one detail level
     ("small-1d", {"levels": 1}),
     ("c1", {}),                                          # dense 256 x 256
+    ("small-2d", {"delta": 6, "family": 1, "n": 64, "levels": 3}),   # Symmlet 6: 12 taps, 20-tap template
+    ("small-2d", {"delta": 4, "family": 1}),             # Symmlet 4: 8-tap template
+    ("small-1d", {"delta": 6, "family": 1}),
+    ("op1", {"n": 64}),                                  # stand-ins for the paper's two blurs (Symmlet 6)
+    ("op2", {"n": 64}),
 ]
 
 

@@ -12,7 +12,7 @@ from helpers import dense_theta_pattern, make_gpu_op
 pytestmark = pytest.mark.gpu
 
 CASES = [("small-1d", {}), ("small-2d", {"n": 32, "levels": 3}), ("small-2d", {"n": 32, "levels": 3, "order": 1}),
-         ("small-2d", {"n": 64, "levels": 4, "delta": 3})]
+         ("small-2d", {"n": 64, "levels": 4, "delta": 3}), ("op1", {"n": 32, "levels": 3})]
 
 
 @pytest.fixture(scope="module")
