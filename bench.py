@@ -299,6 +299,50 @@ def run_fista(pw, g, op, rank, dev, stream, iters):
     return out
 
 
+def run_sweep(pw, rank, dev, stream, sides=(128, 256, 512, 1024)):
+    """Assembly times of the stand-ins for the paper's two blurs (Section 4.1; Symmlet 6,
+    L = 4, op1: m = 5 / 19x19, op2: m = 25 / 25x25) on square images of side 2^7..2^10 (the
+    paper's timing sweep goes to 2^12 with its thresholded, much sparser matrix; the exact
+    pattern at 2^12 would need ~300 GB).  FP32 Theta, no BF16 copy, CUDA events around
+    pc_assemble, inputs larger than L2 from side 256 on."""
+    import torch
+    import pc_inputs as P
+    out = []
+    for name in ("op1", "op2"):
+        for n in sides:
+            rec = {"operator": name, "side": n}
+            g = None
+            try:
+                op = P.workload(name, n=n, seed_offset=rank)
+                g = pw.PCOperator(pw.desc_of(op, pw.PC_FP32, 0), torch.tensor(op.u, dtype=torch.float32, device=dev),
+                                  torch.tensor(op.v, dtype=torch.float32, device=dev))
+                for _ in range(2):
+                    g.assemble()
+                ts = []
+                for _ in range(3):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    g.assemble()
+                    b.record(stream)
+                    torch.cuda.synchronize()
+                    ts.append(a.elapsed_time(b))
+                g.sync()
+                ms = float(np.median(ts))
+                rec.update({"N": op.N, "m": op.m, "stencil": 2 * op.r + 1, "nnz": g.nnz, "assemble_ms": ms,
+                            "entries_per_s": g.nnz / (ms * 1e-3),
+                            "hbm_gbs_algorithmic": (4 * g.nnz + 4 * op.m * op.N) / (ms * 1e-3) / 1e9})
+            except Exception as e:                  # recorded, not fatal to the bench line
+                rec["error"] = str(e)[:200]
+            finally:
+                if g is not None:
+                    try:
+                        g.close()
+                    except Exception:
+                        pass
+            out.append(rec)
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_2005_09870_gb300 as pw
@@ -509,6 +553,10 @@ def run_ours(args, rank, world, local_rank):
                                  "sample": f"{cols1} columns on one core, {wall1:.1f} s"},
                "full_theta_s_extrapolated": nnz / rate}
 
+    sweep = None
+    if not args.no_sweep:
+        sweep = run_sweep(pw, rank, dev, stream)
+
     clocks = clk.summary()
     if rank == 0:
         line = {
@@ -524,6 +572,7 @@ def run_ours(args, rank, world, local_rank):
             "bwd_ms": bwd_ms,
             "batch": batch_info,
             "fista": fista,
+            "symmlet6_sweep": sweep,
             "roofline": roof,
             "roofline_fp32": roof_fp32,
             "cpu_baseline": cpu,
@@ -550,6 +599,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-fista", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--fista-iters", type=int, default=50)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
