@@ -269,6 +269,14 @@ pc_status pc_info(pc_handle h, int64_t* nnz, int64_t* device_bytes);
  * and of the row offsets (int64, N+1).  Valid until pc_destroy. */
 pc_status pc_theta(pc_handle h, void** values, void** values_bf16, int64_t** row_ptr);
 
+/* Host copy of Theta (Section 3.2: Theta[mu, lambda] = <psi_mu, H psi_lambda>, rows = outputs)
+ * in CSR form with ascending columns in every row, in either operator order: row_ptr (N + 1),
+ * cols (nnz) and vals (nnz, double; the FP32 or FP64 stored values, not the BF16 copy), all
+ * caller-owned host arrays.  Copies the values to the host (synchronises `stream`) and sorts
+ * on one host thread: meant for inspection and for operators of modest size.
+ * PC_ERR_NOT_ASSEMBLED before the first assembly; PC_ERR_INVALID_ARG for NULL arrays. */
+pc_status pc_export(pc_handle h, int64_t* row_ptr, int64_t* cols, double* vals, void* stream);
+
 /* Storage position of Theta[mu, lambda] for n pairs (host arrays), -1 when outside the
  * pattern.  Host only; no device work. */
 pc_status pc_lookup(pc_handle h, int64_t n, const int64_t* mu, const int64_t* lambda,

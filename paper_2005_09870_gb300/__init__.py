@@ -75,6 +75,7 @@ _sig = {
     "pc_power_norm": ([_H, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
     "pc_fista": ([_H, _P, _P, _P, _P, ctypes.c_int, ctypes.c_double, _P], ctypes.c_int),
     "pc_filter_taps": ([ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "pc_export": ([_H, _I64P, _I64P, ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
 }
 for _name, (_args, _ret) in _sig.items():
     _f = getattr(_lib, _name)
@@ -97,6 +98,17 @@ def desc_of(op, precision=PC_FP32, store_bf16=0) -> pc_desc:
     order and optionally family)."""
     return make_desc(op.d, op.n, op.levels, op.delta, op.m, op.r, op.gap, op.order, precision, store_bf16,
                      getattr(op, "family", 0))
+
+
+def pc_export(h, nnz, N, stream=None):
+    """Theta as host CSR arrays (row_ptr, cols, vals), ascending columns per row."""
+    import numpy as np
+    row_ptr = np.zeros(N + 1, dtype=np.int64)
+    cols = np.zeros(nnz, dtype=np.int64)
+    vals = np.zeros(nnz, dtype=np.float64)
+    _check(_lib.pc_export(h, row_ptr.ctypes.data_as(_I64P), cols.ctypes.data_as(_I64P),
+                          vals.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream(stream)), h)
+    return row_ptr, cols, vals
 
 
 def pc_filter_taps(family: int, delta: int):
@@ -357,6 +369,10 @@ class PCOperator:
         dv = t.empty((self.desc.m, self.N), dtype=self.dtype, device="cuda")
         pc_backward(self.h, dtheta, du, dv, stream)
         return du, dv
+
+    def export(self, stream=None):
+        """(row_ptr, cols, vals) of Theta on the host (CSR, ascending columns)."""
+        return pc_export(self.h, self.nnz, self.N, stream)
 
     def lookup(self, mu, lam):
         return pc_lookup(self.h, mu, lam)

@@ -1952,6 +1952,77 @@ pc_status pc_lookup(pc_handle h, int64_t n, const int64_t* mu, const int64_t* la
     return PC_OK;
 }
 
+pc_status pc_export(pc_handle h, int64_t* row_ptr, int64_t* cols, double* vals, void* stream)
+{
+    if (!h) return fail(nullptr, PC_ERR_INVALID_ARG, "handle is NULL");
+    if (!h->assembled) return fail(h, PC_ERR_NOT_ASSEMBLED, "pc_export before pc_assemble");
+    if (!row_ptr || !cols || !vals) return fail(h, PC_ERR_INVALID_ARG, "row_ptr, cols and vals must not be NULL");
+    const int64_t N = h->N, nnz = h->nnz;
+    // stored values to the host, as double
+    std::vector<double> sv((size_t)nnz);
+    if (h->desc.precision == PC_FP64) {
+        PC_CUDA(h, cudaMemcpyAsync(sv.data(), h->theta_d, sizeof(double) * nnz, cudaMemcpyDeviceToHost,
+                                   (cudaStream_t)stream));
+        PC_CUDA(h, cudaStreamSynchronize((cudaStream_t)stream));
+    } else {
+        std::vector<float> f((size_t)nnz);
+        PC_CUDA(h, cudaMemcpyAsync(f.data(), h->theta_d, sizeof(float) * nnz, cudaMemcpyDeviceToHost,
+                                   (cudaStream_t)stream));
+        PC_CUDA(h, cudaStreamSynchronize((cudaStream_t)stream));
+        for (int64_t i = 0; i < nnz; ++i) sv[(size_t)i] = f[(size_t)i];
+    }
+    // the pattern is symmetric, so row mu of Theta has as many entries as stored row mu
+    for (int64_t i = 0; i <= N; ++i) row_ptr[i] = h->row_ptr_h[(size_t)i];
+    Geo g = geo_of(&h->desc);
+    const bool conv_first = h->desc.order == PC_ORDER_CONV_THEN_MULT;   // stored row = column of Theta
+    std::vector<int64_t> cursor;
+    if (conv_first) cursor.assign(h->row_ptr_h.begin(), h->row_ptr_h.end() - 1);
+    std::vector<std::pair<int64_t, double>> row;
+    for (int64_t s = 0; s < N; ++s) {
+        int b, l0, l1;
+        decode(g, s, &b, &l0, &l1);
+        const Band Bo = band_info(g.d, g.n, g.L, b);
+        int64_t pos = h->row_ptr_h[(size_t)s];
+        row.clear();
+        for (int b2 = 0; b2 < g.nb; ++b2) {
+            if (!block_kept(g.d, g.n, g.L, g.gap, b, b2)) continue;
+            const Band B2 = band_info(g.d, g.n, g.L, b2);
+            int f0 = 0, W0 = 1, f1, W1;
+            stencil(Bo.j, Bo.e1, l1, B2.j, B2.e1, g.r, g.Lf, g.n, g.gap < 0, &f1, &W1);
+            if (g.d == 2) stencil(Bo.j, Bo.e0, l0, B2.j, B2.e0, g.r, g.Lf, g.n, g.gap < 0, &f0, &W0);
+            for (int a = 0; a < W0; ++a)
+                for (int c = 0; c < W1; ++c) {
+                    const int64_t col =
+                        B2.off + (int64_t)pmod(f0 + a, B2.nj) * ((g.d == 2) ? B2.nj : 0) + pmod(f1 + c, B2.nj);
+                    row.emplace_back(col, sv[(size_t)pos++]);
+                }
+        }
+        if (pos != h->row_ptr_h[(size_t)s + 1]) return fail(h, PC_ERR_DEVICE, "internal: row %lld length", (long long)s);
+        if (!conv_first) {
+            // Theta's row s: sort by column
+            std::sort(row.begin(), row.end(),
+                      [](const std::pair<int64_t, double>& x, const std::pair<int64_t, double>& y) {
+                          return x.first < y.first;
+                      });
+            int64_t o = h->row_ptr_h[(size_t)s];
+            for (const auto& e : row) {
+                cols[o] = e.first;
+                vals[o++] = e.second;
+            }
+        } else {
+            // Theta[col, s]: appended to row col; s ascends, so every row ends up sorted
+            for (const auto& e : row) {
+                const int64_t o = cursor[(size_t)e.first]++;
+                if (o >= h->row_ptr_h[(size_t)e.first + 1])
+                    return fail(h, PC_ERR_DEVICE, "internal: pattern not symmetric at row %lld", (long long)e.first);
+                cols[o] = s;
+                vals[o] = e.second;
+            }
+        }
+    }
+    return PC_OK;
+}
+
 pc_status pc_sync(pc_handle h, void* stream)
 {
     if (!h) return fail(nullptr, PC_ERR_INVALID_ARG, "handle is NULL");
