@@ -40,7 +40,7 @@ def _random_G(op, g, seed):
                                      ("small-2d", {"n": 32, "levels": 4, "r": 4}), ("small-2d", {"n": 64, "levels": 4, "gap": 1}),
                                      ("small-2d", {"n": 32, "levels": 3, "delta": 3}),
                                      ("small-2d", {"n": 32, "levels": 3, "delta": 1}),
-                                     ("small-2d", {"n": 32, "levels": 3, "delta": 6, "family": 1}),   # Symmlet 6
+                                     ("small-2d", {"n": 32, "levels": 3, "delta": 4, "family": 1}),   # Symmlet 4
                                      ("c1", {})])
 @pytest.mark.parametrize("precision", [0, 1], ids=["fp32", "fp64"])
 def test_backward_matches_oracle(pw, name, kw, precision):

@@ -46,9 +46,9 @@ def test_partition_of_unity_with_point_kernels_is_identity(pw, order, family, de
     # every stored row holds exactly one 1 (its diagonal) and zeros elsewhere
     pos = g.lookup(np.arange(op.N, dtype=np.int64), np.arange(op.N, dtype=np.int64))
     assert np.all(pos >= 0)
-    assert np.abs(vals[pos] - 1.0).max() < 2e-6
+    assert np.abs(vals[pos] - 1.0).max() <= 1e-5      # the FP32 bar: 1e-5 of max |Theta| = 1
     vals[pos] = 0.0
-    assert np.abs(vals).max() < 2e-6
+    assert np.abs(vals).max() <= 1e-5
     g.close()
 
 
@@ -70,7 +70,7 @@ def test_multiplier_is_symmetric(pw):
     a = _entries(pw, g, op, mus, lams)
     b = _entries(pw, g, op, lams, mus)          # the pattern is symmetric
     scale = np.abs(a).max()
-    assert np.abs(a - b).max() <= 2e-6 * scale
+    assert np.abs(a - b).max() <= 1e-5 * scale
     g.close()
 
 
@@ -99,5 +99,5 @@ def test_convolution_subbands_are_circulant(pw):
         x = _entries(pw, g, op, [int(mu)] * lam.size, lam)
         y = _entries(pw, g, op, [shift(mu)] * lam.size, [shift(l) for l in lam])
         worst = max(worst, float(np.abs(x - y).max()))
-    assert worst <= 2e-6 * float(np.abs(g.values().double().cpu().numpy()).max())
+    assert worst <= 1e-5 * float(np.abs(g.values().double().cpu().numpy()).max())
     g.close()
