@@ -65,8 +65,6 @@ struct pc_op {
     void* dF_d = nullptr;  // backward scratch: dL/dF
     void* dG_d = nullptr;  // backward scratch: dL/dG
     void* S_d = nullptr;   // 2-D: stage-1 values s of every row (assembly), then dL/ds (backward)
-    int* sblk_d = nullptr;  // first k_s_rows block of each band
-    int sblk_total = 0;
     void* od_d = nullptr;   // device copy of the operator descriptor for k_s_rows
     unsigned long long* amask_d = nullptr;  // backward scratch: active terms per row (2-D)
     int64_t Stotal = 0;
@@ -1120,7 +1118,7 @@ pc_status build_window_list(pc_op* h, cudaStream_t st)
 void free_all(pc_op* h)
 {
     void* ptrs[] = {h->u_d,  h->v_d,        h->taps64_d,  h->wav64_d,  h->tapsT_d, h->wavT_d, h->F_d,
-                    h->G_d,  h->dF_d, h->dG_d, h->S_d, h->amask_d, h->wl_d, h->cnt_d, h->dfoff_d, h->q_items_d, h->q_items_b_d, h->q_op_d, h->q_counter_d, h->row_ptr_d,  h->theta_d,   h->theta16_d, h->xsplit_d, h->sblk_d, h->od_d, h->masks_d, h->err_d, h->fista_d, h->bdesc_d, h->boff_d, h->thetaT_d};
+                    h->G_d,  h->dF_d, h->dG_d, h->S_d, h->amask_d, h->wl_d, h->cnt_d, h->dfoff_d, h->q_items_d, h->q_items_b_d, h->q_op_d, h->q_counter_d, h->row_ptr_d,  h->theta_d,   h->theta16_d, h->xsplit_d, h->od_d, h->masks_d, h->err_d, h->fista_d, h->bdesc_d, h->boff_d, h->thetaT_d};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -1686,21 +1684,11 @@ pc_status pc_create(const pc_desc* desc, const void* u, const void* v, void* str
     if (D.store_bf16 && (st = dev_alloc(h, &h->theta16_d, sizeof(__nv_bfloat16) * h->nnz))) return bail(st);
     if (D.store_bf16 && (st = dev_alloc(h, &h->xsplit_d, sizeof(unsigned) * 16 * h->N))) return bail(st);
     if (D.dim == 2) {
-        // s scratch (stage 1 of the assembly, dL/ds of the backward) and the k_s_rows grid
-        std::vector<int> sblk(h->nb + 1, 0);
-        int64_t tot = 0;
-        for (int b = 0; b < h->nb; ++b) {
-            sblk[b] = (int)tot;
-            const int64_t RR = (int64_t)h->bd.band[b].R0 * h->bd.band[b].R1;
-            tot += band_rows(g, b) * ((RR + 255) / 256);
-        }
-        sblk[h->nb] = (int)tot;
-        h->sblk_total = (int)tot;
-        if ((st = dev_alloc(h, &h->S_d, h->esz * h->Stotal)) || (st = dev_alloc(h, &h->sblk_d, sizeof(int) * (h->nb + 1))) ||
+        // s scratch (stage 1 of the assembly, dL/ds of the backward) and the device copy of the
+        // operator view that k_s_rows reads
+        if ((st = dev_alloc(h, &h->S_d, h->esz * h->Stotal)) ||
             (st = dev_alloc(h, &h->od_d, std::max(sizeof(OpDev<double>), sizeof(OpDev<float>)))))
             return bail(st);
-        if (cudaMemcpy(h->sblk_d, sblk.data(), sizeof(int) * (h->nb + 1), cudaMemcpyHostToDevice) != cudaSuccess)
-            return bail(fail(h, PC_ERR_CUDA, "upload failed"));
     }
     cudaError_t e;
     if ((e = cudaMemcpyAsync(h->taps64_d, h->h, sizeof(double) * h->Lf, cudaMemcpyHostToDevice, s)) ||
