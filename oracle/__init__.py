@@ -52,6 +52,7 @@ def _load():
         lib.or_jacobi.argtypes = [D, _dp, _dp]
         lib.or_power_norm.argtypes = [D, _dp, _dp, I, _dp]
         lib.or_fista.argtypes = [D, _dp, _dp, _dp, _dp, I, ctypes.c_double, _dp]
+        lib.or_alg1_dense.argtypes = [I, I, I, I, I, I, I, _dp, _dp, ctypes.c_double, _dp, _i64p, _dp]
         _lib = lib
     return _lib
 
@@ -196,3 +197,18 @@ def fista(T, z0, w, iters, tau, z_init=None, sigma=None):
     z = np.zeros(N) if z_init is None else np.array(z_init, dtype=np.float64).reshape(-1)
     _check(_load().or_fista(N, Tp, z0p, wp, sp, int(iters), float(tau), z.ctypes.data_as(_dp)), "fista")
     return z
+
+
+def alg1_dense(op, eta, u=None, v=None):
+    """Algorithm 1 with thresholding on dense matrices (N <= 4096): returns (Theta~ (N, N),
+    entries kept per A~_k, threshold per k)."""
+    u, up = _d(op.u if u is None else u)
+    v, vp = _d(op.v if v is None else v)
+    N = op.N
+    T = np.zeros((N, N))
+    nnz = np.zeros(u.shape[0], dtype=np.int64)
+    tau = np.zeros(u.shape[0])
+    rc = _load().or_alg1_dense(op.d, op.n, op.levels, _opcode(op), u.shape[0], op.r, op.order, up, vp, float(eta),
+                               T.ctypes.data_as(_dp), nnz.ctypes.data_as(_i64p), tau.ctypes.data_as(_dp))
+    _check(rc, "alg1_dense")
+    return T, nnz, tau

@@ -708,6 +708,96 @@ int or_fista(int64_t N, const double *T, const double *z0, const double *w, cons
     return 0;
 }
 
+/* ------------------------------------------------------------------------------------
+ * Algorithm 1 (Section 3.2) with thresholding, on dense matrices (small N only).
+ *   eps_k = eta / (m ||v_k||_inf);  A_k = Psi^* U_k Psi;  B_k = Psi^* V_k Psi;
+ *   A~_k = A_k with the entries below a threshold tau_k set to 0, tau_k the largest value
+ *          whose discarded part D_k has Schur bound sqrt(||D_k||_1 ||D_k||_inf) <= eps_k
+ *          (so ||A_k - A~_k||_2 <= eps_k; bisection on tau, 80 halvings);
+ *   Theta~ = sum_k A~_k B_k  (paper order; B_k A~_k in the convolution-first order).
+ * Since ||B_k||_2 = ||v_k||_inf, ||Theta - Theta~||_2 <= sum_k eps_k ||v_k||_inf = eta.
+ * theta: N x N row-major Theta~[mu * N + lambda]; nnz_a[k] = entries kept in A~_k;
+ * tau[k] = the threshold.  Returns 0, or -1 on bad input or allocation failure.
+ * ------------------------------------------------------------------------------------ */
+static double schur_discard(int64_t N, const double *A, double t, double *rs, double *cs)
+{
+    for (int64_t i = 0; i < N; ++i) { rs[i] = 0.0; cs[i] = 0.0; }
+    for (int64_t i = 0; i < N; ++i)
+        for (int64_t j = 0; j < N; ++j) {
+            const double a = fabs(A[i * N + j]);
+            if (a < t) { rs[i] += a; cs[j] += a; }
+        }
+    double mr = 0.0, mc = 0.0;
+    for (int64_t i = 0; i < N; ++i) { mr = fmax(mr, rs[i]); mc = fmax(mc, cs[i]); }
+    return sqrt(mr * mc);
+}
+
+int or_alg1_dense(int d, int n, int L, int wcode, int m, int r, int order, const double *u, const double *v,
+                  double eta, double *theta, int64_t *nnz_a, double *tau)
+{
+    const int64_t N = (d == 1) ? n : (int64_t)n * n;
+    const int64_t Ku = (d == 1) ? (2 * r + 1) : (int64_t)(2 * r + 1) * (2 * r + 1);
+    if (N > 4096 || m < 1 || eta < 0.0) return -1;
+    double *colsA = malloc(sizeof(double) * N * N), *colsB = malloc(sizeof(double) * N * N);
+    double *A = malloc(sizeof(double) * N * N), *B = malloc(sizeof(double) * N * N);
+    double *ones = malloc(sizeof(double) * N), *rs = malloc(sizeof(double) * N), *cs = malloc(sizeof(double) * N);
+    int64_t *all = malloc(sizeof(int64_t) * N);
+    if (!colsA || !colsB || !A || !B || !ones || !rs || !cs || !all) {
+        free(colsA); free(colsB); free(A); free(B); free(ones); free(rs); free(cs); free(all);
+        return -1;
+    }
+    for (int64_t i = 0; i < N; ++i) { ones[i] = 1.0; all[i] = i; }
+    for (int64_t i = 0; i < N * N; ++i) theta[i] = 0.0;
+    const double delta1 = 1.0;   /* the point kernel of the multiplier */
+    int rc = 0;
+    for (int k = 0; k < m && rc == 0; ++k) {
+        double vmax = 0.0;
+        for (int64_t x = 0; x < N; ++x) vmax = fmax(vmax, fabs(v[k * N + x]));
+        /* A_k = Psi^* U_k Psi (columns of the one-term operator u_k * (1 . f)) */
+        rc |= or_theta_columns(d, n, L, wcode, 1, r, 0, u + k * Ku, ones, N, all, colsA, 0);
+        /* B_k = Psi^* V_k Psi (columns of the one-term operator delta * (v_k . f)) */
+        rc |= or_theta_columns(d, n, L, wcode, 1, 0, 0, &delta1, v + k * N, N, all, colsB, 0);
+        if (rc) break;
+        for (int64_t mu = 0; mu < N; ++mu)
+            for (int64_t la = 0; la < N; ++la) {
+                A[mu * N + la] = colsA[la * N + mu];
+                B[mu * N + la] = colsB[la * N + mu];
+            }
+        /* threshold by bisection on tau */
+        const double eps = (vmax > 0.0) ? eta / (m * vmax) : 1e300;
+        double amax = 0.0;
+        for (int64_t i = 0; i < N * N; ++i) amax = fmax(amax, fabs(A[i]));
+        double t;
+        const double top = amax * (1.0 + 1e-15) + 1e-300;
+        if (schur_discard(N, A, top, rs, cs) <= eps) {
+            t = top;
+        } else {
+            double lo = 0.0, hi = top;
+            for (int it = 0; it < 80; ++it) {
+                const double mid = 0.5 * (lo + hi);
+                if (schur_discard(N, A, mid, rs, cs) <= eps) lo = mid; else hi = mid;
+            }
+            t = lo;
+        }
+        tau[k] = t;
+        int64_t kept = 0;
+        for (int64_t i = 0; i < N * N; ++i) {
+            if (fabs(A[i]) < t) A[i] = 0.0; else ++kept;
+        }
+        nnz_a[k] = kept;
+        /* C_k = A~_k B_k (paper order) or B_k A~_k (convolution first), accumulated */
+        const double *P1 = (order == 0) ? A : B, *P2 = (order == 0) ? B : A;
+        for (int64_t mu = 0; mu < N; ++mu)
+            for (int64_t q = 0; q < N; ++q) {
+                const double a = P1[mu * N + q];
+                if (a == 0.0) continue;
+                for (int64_t la = 0; la < N; ++la) theta[mu * N + la] += a * P2[q * N + la];
+            }
+    }
+    free(colsA); free(colsB); free(A); free(B); free(ones); free(rs); free(cs); free(all);
+    return rc ? -1 : 0;
+}
+
 int or_max_threads(void)
 {
 #ifdef _OPENMP
