@@ -7,7 +7,7 @@
  * or  H f = sum_{k=1..m} v_k . (u_k * f)          (PC_ORDER_CONV_THEN_MULT)
  * on periodic 1-D signals or 2-D images of side n, and the library assembles
  *     Theta = Psi^* H Psi,   Theta[mu, lambda] = <psi_mu, H psi_lambda>      (Section 3.2)
- * in an orthonormal periodic Daubechies basis (Section 2), keeping only the entries of a
+ * in an orthonormal periodic Daubechies or Symmlet basis (Section 2), keeping only the entries of a
  * prescribed pattern: | |mu| - |lambda| | <= gap (the band rule (i) of Remark 5.3) and, on
  * each axis, supp psi_lambda within distance r (the kernel radius) of supp psi_mu on the
  * torus (the support test of Section 5.2; entries failing it are exactly zero).
@@ -20,7 +20,8 @@
  *     input's coefficients to the output's.
  *   - Kernels u_k are (2r+1)^d stencils, row-major, centre index = offset 0:
  *     (u * f)(y) = sum_t u(t) f(y - t).  Windows v_k are n^d pixels.
- *   - Daubechies filters: minimum-phase low-pass h with 2*delta taps, sum sqrt(2);
+ *   - Filters: low-pass h with 2*delta taps on [0, 2 delta - 1], sum sqrt(2) -- Daubechies'
+ *     minimum-phase factor or the least-asymmetric (Symmlet) one, see pc_filter_taps;
  *     g[i] = (-1)^(1-i) h[1-i] (Section 2.1).
  *
  * Storage of Theta ("stencil-ELL").  Rows of the stored matrix S are the filtered-side
@@ -35,7 +36,8 @@
  * outside a buffer, a work queue that overran) set a device flag read by pc_sync().
  *
  * Ownership.  The handle owns the device buffers it allocates (Theta, filtered wavelets,
- * plans, scratch).  The caller owns every pointer it passes (inputs, x, y, dtheta, du, dv).
+ * plans, scratch, and the solver's transposed copy and vectors once a solver call ran).  The
+ * caller owns every pointer it passes (inputs, x, y, dtheta, du, dv, z0, w, sigma, z).
  */
 #ifndef PCWAVE_H
 #define PCWAVE_H
@@ -70,7 +72,7 @@ typedef struct {
     int dim;       /* 1 or 2 */
     int n;         /* side of the periodic grid, a power of two >= 2 */
     int levels;    /* L >= 1 with n >> L >= 1 (the paper's J when L = log2 n) */
-    int delta;     /* Daubechies order (vanishing moments), 1..10; 2*delta taps (db2 = 2, db4 = 4) */
+    int delta;     /* filter order (vanishing moments), 1..10; 2*delta taps (db2 = 2, db4 = 4, sym6 = 6) */
     int m;         /* number of product-convolution terms, 1..256 */
     int radius;    /* kernel radius r >= 0: kernels are (2r+1)^dim */
     int gap;       /* band rule: keep | |mu| - |lambda| | <= gap; -1 keeps every entry (dense) */
