@@ -2,8 +2,10 @@
 
 Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline / reference leg may
 import this package.  It shares no code with the CUDA path.  The arithmetic lives in
-pc_oracle.c (plain double-precision loops following the paper's Algorithm 2 and the
-definitions of Sections 1-3); this file only compiles and calls it.
+pc_oracle.c (plain double-precision loops following the paper's Algorithm 2, the
+definitions of Sections 1-3, the thresholded Algorithm 1, the Symmlet filters and the FISTA
+iterations of the deblurring appendix); this file only compiles and calls it.  pc_svir.py
+(numpy) holds the randomized-SVD construction of a product-convolution expansion.
 """
 from __future__ import annotations
 
