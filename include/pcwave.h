@@ -182,10 +182,12 @@ pc_status pc_apply_adjoint(pc_handle h, const void* x, void* y, int nrhs, int ld
  * sigma = 1/pc_jacobi(): FISTA-WP).  z holds z^(0) = y^(1) on entry and z^(iters) on return;
  * z0 (the observed image's wavelet coefficients) and the weights w (>= 0) are inputs.
  * tau > 0 (convergence needs tau <= 1 / pc_power_norm(sigma)).  Asynchronous; three kernel
- * launches per iteration in the paper's order (Theta y - z0 with g cleared, the scatter of
- * Theta^T r into g, the update), five in the convolution-first order.  The first call on a
- * handle also builds per-row column-block descriptors (8 bytes per row and kept block).
- * PC_ERR_INVALID_ARG for NULL z0/w/z, iters < 0 or tau <= 0. */
+ * launches per iteration (r = Theta y - z0, g = Theta^T r, the update), both products
+ * gathering over stored rows: the one against the stored direction reads a transposed copy
+ * of the values (the pattern is symmetric).  The first solver call on a handle builds per-row
+ * column-block descriptors (12 bytes per row and kept block), and the first after each
+ * assembly rebuilds the transposed copy (4 bytes per entry in FP32, 8 in FP64; pc_jacobi and
+ * pc_power_norm build them too).  PC_ERR_INVALID_ARG for NULL z0/w/z, iters < 0 or tau <= 0. */
 pc_status pc_jacobi(pc_handle h, void* diag, void* stream);
 pc_status pc_power_norm(pc_handle h, const void* sigma, int iters, double* norm2, void* stream);
 pc_status pc_fista(pc_handle h, const void* z0, const void* w, const void* sigma, void* z, int iters,
