@@ -9,6 +9,11 @@ of the whole hot path:
   pc_apply     (y = Theta x, 16 right-hand sides, BF16 Theta, FP32 accumulation)
   pc_backward  (dL/du, dL/dv for L = 1/2 ||Theta||^2, i.e. dL/dTheta = Theta)
 `value` = Theta entries per second of the whole step (nnz / step time, summed over ranks).
+The end of the line summarises the metric's own numbers: the batched FP32 assembly of 64
+uneven operators against the plain FP64 assembly of each (`batch_c4`), the large 1024^2
+workload (`c5_1024`: assembly, BF16 apply to 16 right-hand sides, backward), the single-operator
+FP32 vs FP64 assembly (`assembly_c2`), every result's error against the FP64 oracle
+(`errors_vs_oracle`) and the backward time (`bwd_ms`).
 
 --impl reference times the FP64 CPU oracle (the paper's Algorithm 2) on the machine's host
 cores, on a bounded sample of columns of the same workload, in the same unit.
@@ -212,15 +217,21 @@ def job_value(world, units_per_rank, ms):
     return world * units_per_rank / (ms * 1e-3)
 
 
+def bench_config(world):
+    """The `config` of both arms' lines (the same dict, so that the two lines compare)."""
+    return {"workload": WORKLOAD, "nrhs": 16, "l2": "flushed between steps (256 MB write, untimed)",
+            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}
+
+
 def run_reference(args, rank, world):
-    """The oracle arm: FP64 CPU Algorithm 2 on the host cores, rank 0 only."""
+    """The oracle arm: FP64 CPU Algorithm 2 on the host cores, rank 0 only.  Loads only the
+    oracle's library."""
     if rank != 0:
         return
     import oracle
     import pc_inputs as P
     oracle.build()
     op = P.workload(args.workload)
-    import paper_2005_09870_gb300 as pw  # noqa: F401  (nnz from the planner for the unit only)
     rng = np.random.default_rng(7)
     threads = oracle.max_threads()
     ncols = max(threads, 16)
@@ -239,7 +250,7 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD},
+        "data": "synthetic", "config": bench_config(world),
         "cpu_baseline": {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"{ncols} uniformly drawn columns per step, Algorithm 2 in FP64"},
         "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -301,11 +312,11 @@ def run_fista(pw, g, op, rank, dev, stream, iters):
     return out
 
 
-def run_sweep(pw, rank, dev, stream, sides=(128, 256, 512, 1024)):
+def run_sweep(pw, rank, dev, stream, sides=(128, 256, 512, 1024, 2048)):
     """Assembly times of the stand-ins for the paper's two blurs (Section 4.1; Symmlet 6,
-    L = 4, op1: m = 5 / 19x19, op2: m = 25 / 25x25) on square images of side 2^7..2^10 (the
+    L = 4, op1: m = 5 / 19x19, op2: m = 25 / 25x25) on square images of side 2^7..2^11 (the
     paper's timing sweep goes to 2^12 with its thresholded, much sparser matrix; the exact
-    pattern at 2^12 would need ~300 GB).  FP32 Theta, no BF16 copy, CUDA events around
+    pattern at 2^12 would need ~270 GB for its FP32 values alone).  FP32 Theta, no BF16 copy, CUDA events around
     pc_assemble, inputs larger than L2 from side 256 on."""
     import torch
     import pc_inputs as P
@@ -345,6 +356,249 @@ def run_sweep(pw, rank, dev, stream, sides=(128, 256, 512, 1024)):
     return out
 
 
+# ---------------- the oracle leg: CPU baseline and per-result errors against the FP64 oracle ----------------
+# Everything below runs outside the timed regions; it is the one part of the GPU arm that calls
+# the oracle (test infrastructure), and only to time it and to compare results with it.
+def _stratified(op, seed, per_band=1, bands=None):
+    """Seeded indices: per_band per band (band b of `bands`, default all), canonical order."""
+    rng = np.random.default_rng(seed)
+    n, L, d = op.n, op.levels, op.d
+    starts = [(0, (n >> L) ** d)]
+    for j in range(L, 0, -1):
+        nb = (n >> j) ** d
+        for t in range(1 if d == 1 else 3):
+            starts.append(((n >> j) if d == 1 else nb * (1 + t), nb))
+    pick = []
+    for b, (off, size) in enumerate(starts):
+        if bands is None or b in bands:
+            pick += (off + rng.integers(0, size, per_band)).tolist()
+    return np.array(sorted(set(pick)), dtype=np.int64)
+
+
+def oracle_column_error(g, op, cols, nthreads=0):
+    """max |Theta - Theta_oracle| / max |Theta_oracle| over the pattern entries of `cols`,
+    gathering only those entries from the device."""
+    import torch
+    import oracle
+    T = oracle.theta_columns(op, cols, nthreads=nthreads)
+    vals = g.values()
+    err = ref = 0.0
+    for c, lam in enumerate(cols):
+        mus = np.nonzero(oracle.pattern_column(op, int(lam)))[0].astype(np.int64)
+        pos = g.lookup(mus, np.full(mus.size, lam, dtype=np.int64))
+        if (pos < 0).any():
+            return float("inf")
+        got = vals[torch.as_tensor(pos, device=vals.device)].double().cpu().numpy()
+        err = max(err, float(np.abs(got - T[c][mus]).max(initial=0.0)))
+        ref = max(ref, float(np.abs(T[c][mus]).max(initial=0.0)))
+    return err / ref if ref else 0.0
+
+
+def _flipped(op):
+    """Mirrored kernels and the other order: column mu of its Theta is row mu of op's
+    (Theta_0(u)^T = Theta_1(flip u))."""
+    import copy
+    o = copy.copy(op)
+    o.u = np.ascontiguousarray(op.u[:, ::-1])
+    o.order = 1 - op.order
+    return o
+
+
+def oracle_apply_error(op, x, y, rows, nthreads=0):
+    """max over right-hand sides of ||y - Theta_oracle x|| / ||Theta_oracle x|| on `rows`."""
+    import oracle
+    R = oracle.theta_columns(_flipped(op), rows, nthreads=nthreads)
+    ref = np.zeros((rows.size, x.shape[1]))
+    for i, mu in enumerate(rows):
+        mask = oracle.pattern_column(op, int(mu))      # the pattern is symmetric
+        ref[i] = R[i][mask] @ x[mask]
+    got = y[rows]
+    return float((np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0)).max())
+
+
+def oracle_grad_error(pw, g, op, cols, seed, nthreads=0):
+    """Seeded N(0,1) dL/dTheta on the pattern entries of `cols`: the GPU's dL/du, dL/dv against
+    the oracle's adjoint, element-wise: max |g - g_ref| / max |g_ref| over du and dv."""
+    import torch
+    import oracle
+    import pc_inputs as P
+    G = np.zeros((cols.size, op.N))
+    Gd = torch.zeros(g.nnz, dtype=g.dtype, device="cuda")
+    for c, lam in enumerate(cols):
+        mus = np.nonzero(oracle.pattern_column(op, int(lam)))[0].astype(np.int64)
+        vals = P.normal(seed + c, mus.size)
+        G[c, mus] = vals
+        pos = g.lookup(mus, np.full(mus.size, lam, dtype=np.int64))
+        Gd[torch.as_tensor(pos, device="cuda")] = torch.tensor(vals, dtype=g.dtype, device="cuda")
+    du, dv = g.backward(Gd)
+    g.sync()
+    du_ref, dv_ref = oracle.theta_grad(op, cols, G, nthreads=nthreads)
+    e = [float(np.abs(a.double().cpu().numpy() - b).max() / np.abs(b).max()) for a, b in ((du, du_ref), (dv, dv_ref))]
+    del Gd
+    return max(e)
+
+
+def fd_grad_error(pw, nparams=8, seed=3):
+    """Differentiation workload (2-D 128^2, db4, L=3, m=9, 11x11 kernels): the GPU's FP32 gradient
+    (forward and backward on the device) of L = ||Theta_P(u) - Theta_P(u_target)||^2 over a
+    seeded sample of columns, against FP64 central differences (step 1e-6) of the same loss
+    evaluated by the oracle, on `nparams` seeded parameters (half kernel taps, half window pixels
+    inside a sampled column's support): max per parameter of |g - fd| / max(|fd|, 1e-3 max|g|)."""
+    import torch
+    import oracle
+    import pc_inputs as P
+    op = P.workload("c3")
+    tgt = P.workload("c3")
+    tgt.u = op.extra["u_target"]
+    cols = _stratified(op, 9, per_band=3)
+    masks = np.array([oracle.pattern_column(op, int(lam)) for lam in cols])
+    Tt = oracle.theta_columns(tgt, cols)
+
+    def loss(u, v):
+        return float((((oracle.theta_columns(op, cols, u=u, v=v) - Tt) * masks) ** 2).sum())
+
+    mk = lambda o: pw.PCOperator(pw.desc_of(o), torch.tensor(o.u, dtype=torch.float32, device="cuda"),
+                                 torch.tensor(o.v, dtype=torch.float32, device="cuda"))
+    g, t = mk(op), mk(tgt)
+    g.assemble()
+    t.assemble()
+    mus = np.arange(op.N, dtype=np.int64)
+    pos = np.concatenate([g.lookup(mus[m], np.full(int(m.sum()), lam, dtype=np.int64)) for lam, m in zip(cols, masks)])
+    pd = torch.as_tensor(pos, device="cuda")
+    G = torch.zeros(g.nnz, dtype=torch.float32, device="cuda")
+    G[pd] = 2.0 * (g.values()[pd] - t.values()[pd])
+    du, dv = g.backward(G)
+    g.sync()
+    du, dv = du.double().cpu().numpy(), dv.double().cpu().numpy()
+    scale = max(np.abs(du).max(), np.abs(dv).max())
+    rng = np.random.default_rng(P.BASE_SEED + seed)
+    h, worst = 1e-6, 0.0
+    for i in range(nparams):
+        k = int(rng.integers(op.m))
+        u0, v0 = op.u.copy(), op.v.copy()
+        if i % 2 == 0:
+            tp = int(rng.integers(op.u.shape[1]))
+            up, um = u0.copy(), u0.copy()
+            up[k, tp] += h
+            um[k, tp] -= h
+            fd, got = (loss(up, v0) - loss(um, v0)) / (2 * h), du[k, tp]
+        else:
+            lam = int(cols[int(rng.integers(cols.size))])
+            e = np.zeros(op.N)
+            e[lam] = 1.0
+            supp = np.nonzero(oracle.idwt(op.d, op.n, op.levels, op.delta, e))[0]
+            x = int(supp[int(rng.integers(supp.size))])
+            vp, vm = v0.copy(), v0.copy()
+            vp[k, x] += h
+            vm[k, x] -= h
+            fd, got = (loss(u0, vp) - loss(u0, vm)) / (2 * h), dv[k, x]
+        worst = max(worst, abs(got - fd) / max(abs(fd), 1e-3 * scale))
+    g.close()
+    t.close()
+    return worst, nparams
+
+
+def _ev(stream, fn, reps=3, flush=None):
+    """Median CUDA-event time (ms) of fn() on `stream` over `reps` runs (L2 flushed before each)."""
+    import torch
+    ts = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts))
+
+
+def run_batch(pw, rank, dev, stream, flush, check):
+    """Batched FP32 assembly of the 64 uneven operators (one CUDA graph) against the plain
+    FP64 assembly of each operator alone; errors against the oracle on two seeded columns per
+    operator (one from the finest band, one from any band)."""
+    import torch
+    import pc_inputs as P
+    bops = P.batch_workload(64, seed_offset=rank)
+    bg = [pw.PCOperator(pw.desc_of(o, pw.PC_FP32, 0), torch.tensor(o.u, dtype=torch.float32, device=dev),
+                        torch.tensor(o.v, dtype=torch.float32, device=dev)) for o in bops]
+    bnnz = sum(x.nnz for x in bg)
+    batch = pw.PCBatch(bg)                 # plans the queue, runs once, captures the graph
+    for _ in range(2):
+        batch.run()
+    batch_ms = _ev(stream, batch.run, reps=5, flush=flush)
+    for x in bg:
+        x.sync()
+    items = batch.items
+    err = None
+    if check and rank == 0:
+        err = 0.0
+        for i, (o, x) in enumerate(zip(bops, bg)):
+            nb = 1 + o.levels * (1 if o.d == 1 else 3)
+            cols = np.concatenate([_stratified(o, 40 + i, 1, bands={nb - 1}), _stratified(o, 80 + i, 1)])[:2]
+            err = max(err, oracle_column_error(x, o, cols))
+    batch.close()
+    for x in bg:
+        x.close()
+    del bg
+    # plain FP64: one operator per assembly call, the same kernels instantiated in FP64
+    f64 = 0.0
+    for o in bops:
+        x = pw.PCOperator(pw.desc_of(o, pw.PC_FP64, 0), torch.tensor(o.u, dtype=torch.float64, device=dev),
+                          torch.tensor(o.v, dtype=torch.float64, device=dev))
+        x.assemble()
+        f64 += _ev(stream, x.assemble, reps=1, flush=flush)
+        x.close()
+    peak, _ = _peaks()
+    gbs = 4 * bnnz / (batch_ms * 1e-3) / 1e9
+    return {"ops": 64, "nnz": bnnz, "items": items, "fp32_ms": round(batch_ms, 3),
+            "entries_per_s": bnnz / (batch_ms * 1e-3), "hbm_gbs_alg": round(gbs, 1), "hbm_frac": round(gbs / peak, 4),
+            "fp64_plain_ms": round(f64, 2), "vs_fp64_plain": round(f64 / batch_ms, 2),
+            "max_rel_err": err, "tol": 1e-5}
+
+
+def run_c5(pw, dev, stream, flush, check):
+    """The large workload (2-D 1024^2, db4, L=5, m=64, 31x31 Gaussian * motion kernels): FP32
+    assembly with its BF16 copy, the BF16 apply to 16 right-hand sides, the backward; errors
+    against the oracle on seeded columns / rows of the finest and coarsest bands."""
+    import torch
+    import pc_inputs as P
+    op = P.workload("c5")
+    g = pw.PCOperator(pw.desc_of(op, pw.PC_FP32, 1), torch.tensor(op.u, dtype=torch.float32, device=dev),
+                      torch.tensor(op.v, dtype=torch.float32, device=dev))
+    pw.pc_autotune(g.h)
+    nrhs = 16
+    xh = P.normal(P.BASE_SEED + 98, op.N * nrhs).reshape(op.N, nrhs)
+    x = torch.tensor(xh, dtype=torch.float32, device=dev)
+    y = torch.empty_like(x)
+    K = (2 * op.r + 1) ** 2
+    du = torch.empty((op.m, K), dtype=torch.float32, device=dev)
+    dv = torch.empty((op.m, op.N), dtype=torch.float32, device=dev)
+    g.assemble()
+    asm = _ev(stream, g.assemble, flush=flush)
+    app = _ev(stream, lambda: pw.pc_apply(g.h, x, y, nrhs), flush=flush)
+    th = g.values()
+    bwd = _ev(stream, lambda: pw.pc_backward(g.h, th, du, dv), flush=flush)
+    g.sync()
+    peak, _ = _peaks()
+    out = {"nnz": g.nnz, "assemble_ms": round(asm, 2), "entries_per_s": g.nnz / (asm * 1e-3),
+           "hbm_frac_alg": round(6 * g.nnz / (asm * 1e-3) / 1e9 / peak, 4),
+           "apply16_bf16_ms": round(app, 2), "bwd_ms": round(bwd, 2)}
+    if check:
+        nb = 1 + 3 * op.levels
+        cols = np.concatenate([_stratified(op, 51, 2, bands={nb - 1}), _stratified(op, 52, 1, bands={0})])
+        out["asm_err"] = oracle_column_error(g, op, cols)
+        pw.pc_apply(g.h, x, y, nrhs)
+        torch.cuda.synchronize()
+        yh = y.double().cpu().numpy()
+        out["apply_err"] = oracle_apply_error(op, xh, yh, _stratified(op, 53, 2))
+        out["bwd_err"] = oracle_grad_error(pw, g, op, _stratified(op, 54, 2, bands={nb - 1}), P.BASE_SEED + 700,
+                                           nthreads=4)
+    g.close()
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_2005_09870_gb300 as pw
@@ -361,8 +615,8 @@ def run_ours(args, rank, world, local_rank):
         pw.pc_autotune(g.h)                 # per-band thread-group shapes (untimed setup)
     nnz = g.nnz
     nrhs = 16
-    x = torch.tensor(P.normal(P.BASE_SEED + 99 + rank, op.N * nrhs), dtype=torch.float32,
-                     device=dev).reshape(op.N, nrhs)
+    xh = P.normal(P.BASE_SEED + 99 + rank, op.N * nrhs).reshape(op.N, nrhs)
+    x = torch.tensor(xh, dtype=torch.float32, device=dev)
     y = torch.empty_like(x)
     K = (2 * op.r + 1) ** op.d
     du = torch.empty((op.m, K), dtype=torch.float32, device=dev)
@@ -404,6 +658,7 @@ def run_ours(args, rank, world, local_rank):
     ms = max_over_ranks(float(step_ms.mean()), dev, world)
     prep_ms, rows_ms, apply_ms, bwd_ms = (float(a) for a in ph.mean(axis=0))
     value = job_value(world, nnz, ms)
+    y_step = y.double().cpu().numpy()
 
     # ---------------- end to end through the C-ABI with host buffers ----------------
     u_h = torch.tensor(op.u, dtype=torch.float32).pin_memory()
@@ -437,88 +692,30 @@ def run_ours(args, rank, world, local_rank):
     g64 = pw.PCOperator(pw.desc_of(op, pw.PC_FP64, 0), u64, v64)
     for _ in range(2):
         g64.assemble()
-    f64_ms = []
-    for _ in range(3):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        g64.assemble()
-        b.record(stream)
-        torch.cuda.synchronize()
-        f64_ms.append(a.elapsed_time(b))
+    fp64_asm_ms = _ev(stream, g64.assemble, flush=flush)
     fp32_asm_ms = prep_ms + rows_ms
-    fp64_asm_ms = float(np.mean(f64_ms))
-    # accuracy of both on seeded columns against the oracle (outside the timed region)
-    acc = {}
-    if rank == 0 and not args.no_check:
-        import oracle
-        cols = np.random.default_rng(3).integers(0, op.N, size=8)
-        T = oracle.theta_columns(op, cols)
-        mus = np.arange(op.N, dtype=np.int64)
-        v32 = g.values().double().cpu().numpy()
-        v64h = g64.values().cpu().numpy()
-        e32 = e64 = ref = 0.0
-        for c, lam in enumerate(cols):
-            pos = g.lookup(mus, np.full(op.N, lam, dtype=np.int64))
-            m = pos >= 0
-            e32 = max(e32, np.abs(v32[pos[m]] - T[c][mus[m]]).max())
-            e64 = max(e64, np.abs(v64h[pos[m]] - T[c][mus[m]]).max())
-            ref = max(ref, np.abs(T[c][mus[m]]).max())
-        acc = {"fp32_max_rel_err": e32 / ref, "fp64_max_rel_err": e64 / ref, "columns_checked": 8}
+    check = rank == 0 and not args.no_check
+    err = {}
+    if check:
+        cols = _stratified(op, 3, per_band=1)
+        err["assembly_fp32"] = oracle_column_error(g, op, cols)
+        err["assembly_fp64"] = oracle_column_error(g64, op, cols)
+        err["apply_bf16"] = oracle_apply_error(op, xh, y_step, _stratified(op, 4, per_band=1))
+        err["bwd_vs_oracle"] = oracle_grad_error(pw, g, op, _stratified(op, 5, per_band=1, bands={0, 12}),
+                                                 P.BASE_SEED + 800)
+        fd, npar = fd_grad_error(pw)
+        err["grad_vs_fd_c3"] = fd
+        err["tol"] = {"assembly_fp32": 1e-5, "assembly_fp64": 1e-12, "apply_bf16": 1e-2, "bwd_vs_oracle": 1e-5,
+                      "grad_vs_fd_c3": 1e-4}
+        err["how"] = (f"oracle (FP64 Algorithm 2) on seeded columns of every band (assembly), rows of every band "
+                      f"(apply, 16 RHS), seeded dL/dTheta on 2 columns (backward, element-wise); FD: {npar} "
+                      f"parameters of the 128^2 differentiation workload, oracle loss, step 1e-6")
     g64.close()
 
     # ---------------- wavelet-domain deblurring (Section 4.3) on the assembled Theta ----------------
     fista = None
     if not args.no_fista:
         fista = run_fista(pw, g, op, rank, dev, stream, args.fista_iters)
-
-    # ---------------- batched FP32 vs plain FP64 on 64 uneven operators ----------------
-    batch_info = None
-    if not args.no_batch:
-        bops = P.batch_workload(64, seed_offset=rank)
-        bg = [pw.PCOperator(pw.desc_of(o, pw.PC_FP32, 0), torch.tensor(o.u, dtype=torch.float32, device=dev),
-                            torch.tensor(o.v, dtype=torch.float32, device=dev)) for o in bops]
-        bnnz = sum(x.nnz for x in bg)
-        batch = pw.PCBatch(bg)                 # plans the queue, runs once, captures the graph
-        for _ in range(2):
-            batch.run()
-        bt = []
-        for _ in range(3):
-            flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            batch.run()
-            b.record(stream)
-            torch.cuda.synchronize()
-            bt.append(a.elapsed_time(b))
-        for x in bg:
-            x.sync()
-        batch_ms = float(np.median(bt))
-        items = batch.items
-        batch.close()
-        for x in bg:
-            x.close()
-        del bg
-        # plain FP64: one operator per assembly call, the same kernels instantiated in FP64
-        f64 = 0.0
-        for o in bops:
-            x = pw.PCOperator(pw.desc_of(o, pw.PC_FP64, 0), torch.tensor(o.u, dtype=torch.float64, device=dev),
-                              torch.tensor(o.v, dtype=torch.float64, device=dev))
-            x.assemble()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            x.assemble()
-            b.record(stream)
-            torch.cuda.synchronize()
-            f64 += a.elapsed_time(b)
-            x.close()
-        batch_info = {"workload": "64 operators: 32 1-D (n=2^10..2^16) + 32 2-D (64^2..512^2), m 4..25, "
-                                  "kernel widths 5..31, db2/db4, L 3..6; one persistent launch per kernel kind (1-D, "
-                                  "db2, db4 templates), side by side, in one CUDA graph",
-                      "nnz": bnnz, "work_items": items, "fp32_batched_ms": batch_ms,
-                      "fp32_batched_entries_per_s": bnnz / (batch_ms * 1e-3),
-                      "fp64_plain_ms": f64, "fp64_plain_entries_per_s": bnnz / (f64 * 1e-3),
-                      "fp32_batched_vs_fp64_plain_factor": f64 / batch_ms}
 
     # ---------------- roofline of the dominant kernel (fused row assembly) ----------------
     peak, peak_kind = _peaks()
@@ -532,8 +729,7 @@ def run_ours(args, rank, world, local_rank):
         except Exception:
             traffic = None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel": "stage 1 of the assembly: k_s_rows (s of every row) + k_assemble_batch "
-                                   "(localized transforms, one persistent launch over all row bands)",
+            "traffic": traffic, "kernel": "stage 1 of the assembly (window sums + localized transforms)",
             "peak_kind": peak_kind}
     flops = assembly_flops(op) if op.d == 2 else None
     roof_fp32 = None
@@ -541,9 +737,15 @@ def run_ours(args, rank, world, local_rank):
         tf = flops / (rows_ms * 1e-3) / 1e12
         roof_fp32 = {"bound": "alu", "achieved": tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": tf / FP32_PEAK_TFLOPS, "flops": flops,
-                     "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
-                     "note": "algorithmic FP32 work of stage 1 (window sums + localized transforms, "
-                             "compensation terms not counted)"}
+                     "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"}
+    g.close()
+    del flush
+    torch.cuda.empty_cache()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    # ---------------- batched FP32 vs plain FP64 on 64 uneven operators ----------------
+    batch_info = None if args.no_batch else run_batch(pw, rank, dev, stream, flush, check)
+    c5 = None if args.no_c5 else run_c5(pw, dev, stream, flush, check)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -561,31 +763,35 @@ def run_ours(args, rank, world, local_rank):
 
     clocks = clk.summary()
     if rank == 0:
+        r4 = lambda z: None if z is None else float(f"{z:.4g}")
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nnz": nnz, "nrhs": nrhs, "l2": "flushed between steps (256 MB write, untimed)",
-                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
-            "phases_ms": {"prepare": prep_ms, "assemble_rows": rows_ms, "apply_16rhs": apply_ms, "backward": bwd_ms},
-            "assembly": {"entries_per_s": nnz / (fp32_asm_ms * 1e-3), "ms": fp32_asm_ms,
-                         "fp64_ms": fp64_asm_ms, "fp64_entries_per_s": nnz / (fp64_asm_ms * 1e-3),
-                         "fp32_vs_fp64_factor": fp64_asm_ms / fp32_asm_ms, **acc},
-            "bwd_ms": bwd_ms,
-            "batch": batch_info,
-            "fista": fista,
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "nnz": nnz,
+            "config": bench_config(world),
+            # details first; the driver's record keeps the end of the line
             "symmlet6_sweep": sweep,
-            "roofline": roof,
+            "fista": fista,
             "roofline_fp32": roof_fp32,
+            "phases_ms": {"prepare": prep_ms, "assemble_rows": rows_ms, "apply_16rhs": apply_ms, "backward": bwd_ms},
+            "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": e2e_ms},
             "gpu_launches": int(launches),
             "gpu_launches_per_step": launches / args.steps,
             "clocks": clocks,
+            # summary of the metric's own numbers, last
+            "c5_1024": c5,
+            "batch_c4": batch_info,
+            "assembly_c2": {"fp32_ms": r4(fp32_asm_ms), "fp64_plain_ms": r4(fp64_asm_ms),
+                            "fp32_vs_fp64": r4(fp64_asm_ms / fp32_asm_ms),
+                            "entries_per_s": r4(nnz / (fp32_asm_ms * 1e-3)),
+                            "stage1_hbm_frac": r4(achieved / peak)},
+            "errors_vs_oracle": {k: (r4(v) if isinstance(v, float) else v) for k, v in err.items()},
+            "bwd_ms": r4(bwd_ms),
         }
         print(json.dumps(line), flush=True)
-    g.close()
 
 
 def main():
@@ -602,6 +808,7 @@ def main():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-fista", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-c5", action="store_true")
     ap.add_argument("--fista-iters", type=int, default=50)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -220,8 +220,10 @@ pc_status pc_backward(pc_handle h, const void* dtheta, void* du, void* dv, void*
  * element times the sizes of its filtered wavelets and their first-pass products);
  * otherwise PC_ERR_UNSUPPORTED with the required size in pc_last_error().
  * Set-up: the first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before any stream
- * capture.  Sharing: all calls on a device use the same array and it keeps the last call's
+ * (cudaGetSymbolAddress) with that device current and keeps it for the life of the process;
+ * make that first call before any stream capture.  The kept address does not survive
+ * cudaDeviceReset (which unloads the library's device code): do not call this entry point
+ * after resetting a device it has already run on.  Sharing: all calls on a device use the same array and it keeps the last call's
  * contents (the call clears what must start at zero).  Calls that overlap on the GPU (two
  * streams, two host threads, two handles) race on it: order them. */
 #define PC_NOALLOC_SCRATCH_BYTES (8u << 20)

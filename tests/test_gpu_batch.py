@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import pc_inputs as P
-from helpers import compare_columns, make_gpu_op, sample_columns
+from helpers import compare_columns, compare_columns_dev, make_gpu_op, sample_columns
 
 pytestmark = pytest.mark.gpu
 
@@ -78,3 +78,32 @@ def test_autotune_keeps_values(pw):
     assert torch.equal(g.values(), before)
     err, ref = compare_columns(g, op, sample_columns(op, per_band=2))
     assert err <= 1e-5 * ref
+
+
+def test_full_batch_workload_vs_oracle(pw):
+    """The batching workload at its own size: 64 operators (32 1-D with n = 2^10..2^16, 32 2-D
+    with side 64..512; m 4..25, kernel widths 5..31, db2/db4, L 3..6) assembled by one batch
+    (persistent launches captured in a CUDA graph), then replayed.  Every operator is checked
+    against the FP64 oracle (Algorithm 2) on columns stratified over its bands (first, last and
+    one seeded translate of each band): element-wise within 1e-5 of max|Theta|, with the stored
+    pattern equal to the oracle's (over every row for two columns per operator, and every
+    oracle entry present for the others)."""
+    import torch
+    ops = P.batch_workload(64)
+    gs = [make_gpu_op(pw, op) for op in ops]
+    batch = pw.PCBatch(gs)
+    batch.run()
+    torch.cuda.synchronize()
+    worst = 0.0
+    for i, (g, op) in enumerate(zip(gs, ops)):
+        g.sync()
+        cols = sample_columns(op, per_band=1, seed=100 + i)
+        err, ref = compare_columns_dev(g, op, cols[:2], full_pattern=True)
+        e2, r2 = compare_columns_dev(g, op, cols[2:], full_pattern=False)
+        rel = max(err, e2) / max(ref, r2)
+        worst = max(worst, rel)
+        assert rel <= 1e-5, (op.name, op.d, op.n, op.m, op.r, op.delta, op.levels, rel)
+    batch.close()
+    for g in gs:
+        g.close()
+    print(f"batch workload: worst max rel err {worst:.2e} over 64 operators")
