@@ -10,6 +10,8 @@
 // produce CH low-pass and CH high-pass outputs per work item (taps unrolled, LF = filter
 // length as a template parameter; shorter filters run zero-padded).
 #pragma once
+#include <type_traits>
+
 #include "pcw_kernels.cuh"
 
 namespace pcw {
@@ -152,6 +154,67 @@ __device__ __forceinline__ void pass_lo(const T* in, int lstride, int stride, Ra
     }
 }
 
+// floor(x / w) for 0 <= x < 2^20 and 1 <= w < 2^12, from a reciprocal of w: (x + 1/2) / w is at
+// least 1/(2w) away from an integer, far more than the rounding of the product.
+__device__ __forceinline__ int div_small(int x, float inv_w) { return __float2int_rz(((float)x + 0.5f) * inv_w); }
+
+// Stores the W0 x W1 window of a shared-memory array z (row pitch pz) row-major to th[0 ..
+// W0 W1) and, when t16 is set, its BF16 copy.  The destination is split at its 16-byte
+// boundaries: up to 3 leading and 3 trailing entries are stored one by one, the groups of 4
+// between them as one 16-byte FP32 store and one 8-byte BF16 store each.  A group's 4 source
+// entries are consecutive in z except where the window row ends (W1 >= 4 here).
+__device__ __forceinline__ void store_window_f32(float* th, __nv_bfloat16* t16, const float* z, int pz, int W0,
+                                                 int W1, int tid, int gt)
+{
+    const int tot = W0 * W1;
+    const float inv = 1.0f / (float)W1;
+    const int head = min(tot, (int)((4u - ((unsigned)(size_t)th >> 2)) & 3u));
+    const int ng = (tot - head) >> 2;
+    const int tail0 = head + 4 * ng;
+    // leading and trailing entries
+    if (tid < 6) {
+        const int e = tid < 3 ? tid : tail0 + tid - 3;
+        if ((tid < 3 && e < head) || (tid >= 3 && e < tot)) {
+            const int a = div_small(e, inv), b = e - a * W1;
+            const float val = z[a * pz + b];
+            th[e] = val;
+            if (t16) t16[e] = __float2bfloat16_rn(val);
+        }
+    }
+    if (ng <= tid) return;
+    // groups: thread tid takes groups tid, tid + gt, ...; (a, b) is the window position of
+    // the group's first entry, advanced by 4 gt entries per step
+    int e = head + 4 * tid;
+    int a = div_small(e, inv), b = e - a * W1;
+    const int da = div_small(4 * gt, inv), db = 4 * gt - da * W1;
+    const float* zp = z + a * pz + b;
+    const int dz = da * pz + db, wrapz = pz - W1;
+    float4* th4 = reinterpret_cast<float4*>(th + head);
+    uint2* t4 = t16 ? reinterpret_cast<uint2*>(t16 + head) : nullptr;
+    for (int g = tid; g < ng; g += gt) {
+        const int left = W1 - b;  // entries of the group before the window row ends
+        float4 v;
+        v.x = zp[0];
+        v.y = zp[left > 1 ? 1 : 1 + wrapz];
+        v.z = zp[left > 2 ? 2 : 2 + wrapz];
+        v.w = zp[left > 3 ? 3 : 3 + wrapz];
+        th4[g] = v;
+        if (t4) {
+            const __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
+            uint2 w;
+            w.x = *reinterpret_cast<const unsigned*>(&lo);
+            w.y = *reinterpret_cast<const unsigned*>(&hi);
+            t4[g] = w;
+        }
+        b += db;
+        zp += dz;
+        if (b >= W1) {
+            b -= W1;
+            zp += wrapz;
+        }
+    }
+}
+
 // Copies the stencil window of one column band from its coefficient array (pitch pz) to the
 // row's storage (and the BF16 copy), which holds the window row-major.
 template <typename T>
@@ -166,6 +229,12 @@ __device__ __forceinline__ void write_win(const OpDev<T>& op, const T* Zb, int p
     st.init(tid, gt, W1);
     if (!r0.full && !r1.full && op.gap >= 0) {
         const T* z = Zb + (f0 - r0.lo) * pz + (f1 - r1.lo);  // inside the array (checked by the planner)
+        if constexpr (std::is_same<T, float>::value) {
+            if (W1 >= 4) {
+                store_window_f32(th, t16, z, pz, W0, W1, tid, gt);
+                return;
+            }
+        }
         for (int idx = tid; idx < tot; idx += gt, st.next()) {
             const T val = z[st.a * pz + st.b];
             th[idx] = val;
@@ -184,50 +253,79 @@ __device__ __forceinline__ void write_win(const OpDev<T>& op, const T* Zb, int p
 
 // Stage 1 of every stored 2-D row in one launch: s(q) = sum over the window list of pixel
 // g + q of v_k * F_{k,b}(q) (the windows nonzero there, in increasing k), compensated,
-// written to op.sf + Soff[b] + rl * RR + q.  One CTA per stored row (blockIdx.x = canonical
-// row index); its threads walk the region positions.
+// written to op.sf + Soff[b] + rl * RR + q.  One warp per stored row (canonical order, eight
+// rows per CTA); its lanes walk the region positions.  Indices are 32-bit: a region, a
+// window list (slots x N) and a band's F stay far below 2^31 elements.
+template <typename T, int SMAX>
+__device__ __forceinline__ T s_pixel(const WSlot<T>* __restrict__ wp, int N, int S, const T* __restrict__ F0,
+                                     int RR, int q)
+{
+    // all slot loads first, then the F loads, then the compensated sum over the terms
+    WSlot<T> w[SMAX];
+#pragma unroll
+    for (int sl = 0; sl < SMAX; ++sl)
+        if (sl < S) w[sl] = load_slot(wp + sl * N);
+    T f[SMAX];
+#pragma unroll
+    for (int sl = 0; sl < SMAX; ++sl) f[sl] = (sl < S) ? __ldg(F0 + (int64_t)w[sl].k * RR + q) : T(0);
+    T acc = (S > 0) ? w[0].v * f[0] : T(0), c = T(0);
+#pragma unroll
+    for (int sl = 1; sl < SMAX; ++sl)
+        if (sl < S) kahan_add(acc, c, w[sl].v * f[sl]);
+    return acc;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_s_rows(const OpDev<T>* __restrict__ opd)
 {
-    __shared__ const T* F0s;
-    __shared__ T* outs;
-    __shared__ int g0s, g1s, c1s, RRs;
+    __shared__ int64_t boff_s[MAXB];
     const OpDev<T>& op = *opd;  // device copy (refreshed before each run, also inside graphs)
-    const int n = op.n, nm = n - 1;
-    if (threadIdx.x == 0) {
-        const int64_t srow = blockIdx.x;
-        int b = op.nb - 1;
-        while (b > 0 && band_info(2, n, op.L, b).off > srow) --b;
-        const Band Bo = band_info(2, n, op.L, b);
-        const int rl = (int)(srow - Bo.off);
-        const int lg = log2i(Bo.nj);
-        const Range R0 = region0(Bo.j, Bo.e0, rl >> lg, op.r, op.Lf, n);
-        const Range R1 = region0(Bo.j, Bo.e1, rl & (Bo.nj - 1), op.r, op.Lf, n);
-        g0s = pmod(R0.lo, n);
-        g1s = pmod(R1.lo, n);
-        c1s = R1.cnt;
-        RRs = R0.cnt * R1.cnt;
-        F0s = op.F + op.Foff[b];
-        outs = op.sf + op.Soff[b] + (int64_t)rl * RRs;
-    }
+    const int n = op.n, nm = n - 1, nb = op.nb;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) boff_s[b] = band_info(2, n, op.L, b).off;
     __syncthreads();
-    const int g0 = g0s, g1 = g1s, c1 = c1s, RR = RRs;
-    const T* F0 = F0s;
-    T* out = outs;
+    const int lane = threadIdx.x & 31;
+    const int64_t srow = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (srow >= op.N) return;
+    // band of the row: the last band that starts at or before it (offsets increase with b)
+    const unsigned m1 = __ballot_sync(0xffffffffu, lane < nb && boff_s[lane] <= srow);
+    const unsigned m2 = __ballot_sync(0xffffffffu, lane + 32 < nb && boff_s[min(lane + 32, MAXB - 1)] <= srow);
+    const int b = m2 ? 63 - __clz(m2) : 31 - __clz(m1);
+    const Band Bo = band_info(2, n, op.L, b);
+    const int rl = (int)(srow - Bo.off);
+    const int lg = log2i(Bo.nj);
+    const Range R0 = region0(Bo.j, Bo.e0, rl >> lg, op.r, op.Lf, n);
+    const Range R1 = region0(Bo.j, Bo.e1, rl & (Bo.nj - 1), op.r, op.Lf, n);
+    const int g0 = pmod(R0.lo, n), g1 = pmod(R1.lo, n), c1 = R1.cnt;
+    const int RR = R0.cnt * c1;
+    const T* F0 = op.F + op.Foff[b];
+    T* out = op.sf + op.Soff[b] + (int64_t)rl * RR;
     const WSlot<T>* wl = reinterpret_cast<const WSlot<T>*>(op.wl);
-    const int S = op.wl_slots;
-    const int64_t N = op.N;
-    Stepper st;  // a = q0, b = q1
-    st.init(threadIdx.x, blockDim.x, c1);
-    for (int q = threadIdx.x; q < RR; q += blockDim.x, st.next()) {
-        const int64_t pix = (int64_t)((g0 + st.a) & nm) * n + ((g1 + st.b) & nm);
-        T s = T(0), c = T(0);
-#pragma unroll 2
-        for (int sl = 0; sl < S; ++sl) {
-            const WSlot<T> w = load_slot(wl + (int64_t)sl * N + pix);
-            if (w.v != T(0)) kahan_add(s, c, w.v * __ldg(F0 + (int64_t)w.k * RR + q));
+    const int S = op.wl_slots, N = (int)op.N;
+    // (a, b) = (q0, q1) of position q, advanced by 32 positions per step
+    const float inv = 1.0f / (float)c1;
+    int qa = div_small(lane, inv), qb = lane - qa * c1;
+    const int da = div_small(32, inv), db = 32 - da * c1;
+    for (int q = lane; q < RR; q += 32) {
+        const int pix = ((g0 + qa) & nm) * n + ((g1 + qb) & nm);
+        const WSlot<T>* wp = wl + pix;
+        T val;
+        if (S <= 4)
+            val = s_pixel<T, 4>(wp, N, S, F0, RR, q);
+        else {
+            T acc = T(0), c = T(0);
+            for (int sl = 0; sl < S; ++sl) {
+                const WSlot<T> w = load_slot(wp + sl * N);
+                if (w.v != T(0)) kahan_add(acc, c, w.v * __ldg(F0 + (int64_t)w.k * RR + q));
+            }
+            val = acc;
         }
-        out[q] = s;
+        out[q] = val;
+        qa += da;
+        qb += db;
+        if (qb >= c1) {
+            qb -= c1;
+            ++qa;
+        }
     }
 }
 
@@ -437,26 +535,27 @@ __device__ __forceinline__ void asm2d_row(const OpDev<T>& op, const AsmCfg& cfg,
             const int nr = first ? min(B, A0.cnt - r0) : p0.cnt;
             if (first) {
                 if (bi == 0 && !lo_only) zero_gaps<T, 2 * LF - 2>(arena, mg, B, A1.cnt, XP, tid, gt);
-                // s rows computed for all rows beforehand (k_s_rows): RD loads in flight
-                constexpr int RD = 4;
+                // s rows computed for all rows beforehand (k_s_rows), copied asynchronously
+                // (cp.async: no register round trip, every copy of the thread in flight at once)
                 const T* sr = op.sf + op.Soff[cfg.b] + (int64_t)rl * RR + r0 * A1.cnt;
                 const int tot = nr * A1.cnt;
-                Stepper sq;  // a = row, b = column
-                sq.init(tid, gt, A1.cnt);
-                for (int i0 = tid; i0 < tot; i0 += RD * gt) {
-                    T val[RD];
-                    int xi[RD];
-#pragma unroll
-                    for (int u = 0; u < RD; ++u) {
-                        const int e = i0 + u * gt;
-                        xi[u] = sq.a * XP + sq.b;
-                        val[u] = (e < tot) ? __ldg(sr + e) : T(0);
-                        sq.next();
+                const float inv = 1.0f / (float)A1.cnt;
+                int qa = div_small(tid, inv), qb = tid - qa * A1.cnt;
+                const int da = div_small(gt, inv), db = gt - da * A1.cnt;
+                for (int e = tid; e < tot; e += gt) {
+                    const unsigned dst = (unsigned)__cvta_generic_to_shared(xs0 + qa * XP + qb);
+                    if constexpr (sizeof(T) == 4)
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(sr + e) : "memory");
+                    else
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(sr + e) : "memory");
+                    qa += da;
+                    qb += db;
+                    if (qb >= A1.cnt) {
+                        qb -= A1.cnt;
+                        ++qa;
                     }
-#pragma unroll
-                    for (int u = 0; u < RD; ++u)
-                        if (i0 + u * gt < tot) xs0[xi[u]] = val[u];
                 }
+                asm volatile("cp.async.wait_all;" ::: "memory");
                 group_sync(gt, gid);
             }
             if (lo_only) {

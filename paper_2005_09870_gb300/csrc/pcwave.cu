@@ -121,6 +121,11 @@ struct pc_batch {
     // from and joined back into the run's stream by events
     std::vector<cudaStream_t> side;
     std::vector<cudaEvent_t> fork, join;
+    // every operator's stage 0 and stage-1 sums run on one of these streams (round robin),
+    // forked from the run's stream by prep_fork and joined back before the persistent launches
+    std::vector<cudaStream_t> prep;
+    std::vector<cudaEvent_t> prep_join;
+    cudaEvent_t prep_fork = nullptr;
 };
 
 namespace {
@@ -593,7 +598,7 @@ pc_status s_rows_t(pc_op* h, const OpDev<T>& od, cudaStream_t st, const OpDev<T>
         PC_CUDA(h, cudaMemcpyAsync(h->od_d, &od, sizeof(od), cudaMemcpyHostToDevice, st));
         od_dev = (const OpDev<T>*)h->od_d;
     }
-    k_s_rows<T><<<(int)h->N, 256, 0, st>>>(od_dev);
+    k_s_rows<T><<<(int)((h->N + 7) / 8), 256, 0, st>>>(od_dev);
     count_launch();
     PC_CUDA(h, cudaGetLastError());
     return PC_OK;
@@ -1187,16 +1192,26 @@ pc_status build_queue(pc_op* h)
     return PC_OK;
 }
 
-// Enqueues one run of a batch on st: every operator's stage 0, the queue reset, the
-// persistent kernel.
+// Enqueues one run of a batch on st: every operator's stage 0 and stage-1 sums (spread over
+// the prep streams, so that the small launches of different operators overlap), the queue
+// resets, the persistent kernels.
 pc_status batch_enqueue(pc_batch* B, cudaStream_t st)
 {
+    const size_t np = B->prep.size();
+    if (np && cudaEventRecord(B->prep_fork, st) != cudaSuccess) return PC_ERR_CUDA;
+    for (size_t p = 0; p < np; ++p)
+        if (cudaStreamWaitEvent(B->prep[p], B->prep_fork, 0) != cudaSuccess) return PC_ERR_CUDA;
     for (size_t i = 0; i < B->ops.size(); ++i) {
         pc_op* h = B->ops[i];
-        pc_status ps = prepare_t<float>(h, st);
-        if (ps == PC_OK) ps = s_rows_t<float>(h, B->od[i], st, B->ops_d + i);
+        cudaStream_t sp = np ? B->prep[i % np] : st;
+        pc_status ps = prepare_t<float>(h, sp);
+        if (ps == PC_OK) ps = s_rows_t<float>(h, B->od[i], sp, B->ops_d + i);
         if (ps != PC_OK) return ps;
     }
+    for (size_t p = 0; p < np; ++p)
+        if (cudaEventRecord(B->prep_join[p], B->prep[p]) != cudaSuccess ||
+            cudaStreamWaitEvent(st, B->prep_join[p], 0) != cudaSuccess)
+            return PC_ERR_CUDA;
     if (cudaMemsetAsync(B->counter_d, 0, sizeof(int) * B->groups.size(), st) != cudaSuccess) return PC_ERR_CUDA;
     const size_t ng = B->groups.size();
     if (ng > 1 && cudaEventRecord(B->fork[0], st) != cudaSuccess) return PC_ERR_CUDA;
@@ -1227,6 +1242,9 @@ void batch_free(pc_batch* B)
     if (B->graph) cudaGraphDestroy(B->graph);
     if (B->cap) cudaStreamDestroy(B->cap);
     for (cudaStream_t s : B->side) cudaStreamDestroy(s);
+    for (cudaStream_t s : B->prep) cudaStreamDestroy(s);
+    for (cudaEvent_t e : B->prep_join) cudaEventDestroy(e);
+    if (B->prep_fork) cudaEventDestroy(B->prep_fork);
     for (cudaEvent_t e : B->fork) cudaEventDestroy(e);
     for (cudaEvent_t e : B->join) cudaEventDestroy(e);
     if (B->ops_d) cudaFree(B->ops_d);
@@ -1311,6 +1329,25 @@ pc_status batch_build(pc_handle* ops, int count, cudaStream_t st, bool capture, 
                 return fail(nullptr, PC_ERR_CUDA, "batch setup: %s", cudaGetErrorString(e));
             }
             B->join.push_back(ev);
+        }
+        if (count > 1) {
+            if ((e = cudaEventCreateWithFlags(&B->prep_fork, cudaEventDisableTiming)) != cudaSuccess) {
+                batch_free(B);
+                return fail(nullptr, PC_ERR_CUDA, "batch setup: %s", cudaGetErrorString(e));
+            }
+            for (int p = 0; p < std::min(count, 8); ++p) {
+                cudaStream_t s2;
+                if ((e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking)) != cudaSuccess) {
+                    batch_free(B);
+                    return fail(nullptr, PC_ERR_CUDA, "batch setup: %s", cudaGetErrorString(e));
+                }
+                B->prep.push_back(s2);
+                if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) {
+                    batch_free(B);
+                    return fail(nullptr, PC_ERR_CUDA, "batch setup: %s", cudaGetErrorString(e));
+                }
+                B->prep_join.push_back(ev);
+            }
         }
     }
     // one eager run (sets up every kernel), then capture the same sequence

@@ -4,11 +4,11 @@ It serves callers that cannot call cudaMalloc: a framework that has reserved the
 for its own pool allocator, or a training loop that cannot afford the implicit device
 synchronisation of an allocation.  Its scratch is one static device array that every call on a
 device shares.  The tests below call it first on a freshly created handle (so no scratch of
-pc_backward exists yet) and check that it allocates nothing (the handle's device bytes, torch's
-allocator are unchanged), then that its dL/du and dL/dv match the
-FP64 oracle's adjoint element-wise and pc_backward's results, on two calls in a row with
-different dL/dTheta (no state leaks from one call into the next), for FP32 and FP64 handles,
-1-D and 2-D operators and several filter templates.  An operator whose scratch exceeds the
+pc_backward exists yet) and check that it allocates nothing (the handle's device bytes and
+torch's allocated bytes are unchanged), then that its dL/du and dL/dv match the FP64 oracle's
+adjoint element-wise and pc_backward's results, on two calls in a row with different dL/dTheta
+(no state leaks from one call into the next), for FP32 and FP64 handles, 1-D and 2-D operators
+and several filter templates.  An operator whose scratch exceeds the
 array's size gets PC_ERR_UNSUPPORTED with the size it needs, and its outputs are left alone.
 This file is collected last so that a failure here stops a `-x` run only after every other test.
 """
