@@ -31,15 +31,20 @@ __device__ __forceinline__ void kahan_add<float>(float& s, float& c, float x)
     s = t;
 }
 
-// Steps (a, b) through a row-major count x W grid by gt per iteration (no divisions in loops).
+// floor(x / w) for 0 <= x < 2^21 and 1 <= w < 2^24, from a reciprocal of w: (x + 1/2) / w lies at
+// least 1/(2w) from an integer, and the float product errs by under 2^-21 (x + 1/2) / w.
+__device__ __forceinline__ int div_small(int x, float inv_w) { return __float2int_rz(((float)x + 0.5f) * inv_w); }
+
+// Steps (a, b) through a row-major count x W grid by gt per iteration (no divisions).
 struct Stepper {
     int a, b, da, db, W;
     __device__ __forceinline__ void init(int start, int step, int w)
     {
         W = w;
-        a = start / w;
+        const float inv = 1.0f / (float)w;
+        a = div_small(start, inv);
         b = start - a * w;
-        da = step / w;
+        da = div_small(step, inv);
         db = step - da * w;
     }
     __device__ __forceinline__ void next()
@@ -154,66 +159,35 @@ __device__ __forceinline__ void pass_lo(const T* in, int lstride, int stride, Ra
     }
 }
 
-// floor(x / w) for 0 <= x < 2^20 and 1 <= w < 2^12, from a reciprocal of w: (x + 1/2) / w is at
-// least 1/(2w) away from an integer, far more than the rounding of the product.
-__device__ __forceinline__ int div_small(int x, float inv_w) { return __float2int_rz(((float)x + 0.5f) * inv_w); }
 
-// Stores the W0 x W1 window of a shared-memory array z (row pitch pz) row-major to th[0 ..
-// W0 W1) and, when t16 is set, its BF16 copy.  The destination is split at its 16-byte
-// boundaries: up to 3 leading and 3 trailing entries are stored one by one, the groups of 4
-// between them as one 16-byte FP32 store and one 8-byte BF16 store each.  A group's 4 source
-// entries are consecutive in z except where the window row ends (W1 >= 4 here).
-__device__ __forceinline__ void store_window_f32(float* th, __nv_bfloat16* t16, const float* z, int pz, int W0,
-                                                 int W1, int tid, int gt)
-{
-    const int tot = W0 * W1;
-    const float inv = 1.0f / (float)W1;
-    const int head = min(tot, (int)((4u - ((unsigned)(size_t)th >> 2)) & 3u));
-    const int ng = (tot - head) >> 2;
-    const int tail0 = head + 4 * ng;
-    // leading and trailing entries
-    if (tid < 6) {
-        const int e = tid < 3 ? tid : tail0 + tid - 3;
-        if ((tid < 3 && e < head) || (tid >= 3 && e < tot)) {
-            const int a = div_small(e, inv), b = e - a * W1;
-            const float val = z[a * pz + b];
-            th[e] = val;
-            if (t16) t16[e] = __float2bfloat16_rn(val);
-        }
+// Position stepping over a W0 x W1 window held in a shared-memory array of row pitch pz, for
+// copies between the window and a row's storage (the window row-major and contiguous there).
+// A thread takes entries e, e + step, e + 2 step, ... (consecutive entries on consecutive
+// threads: coalesced in global memory, free of bank conflicts in shared memory); zi is the
+// shared-memory offset of its current entry, advanced without divisions.
+struct WinStep {
+    int zi, b, dz, db, wrapz, W1;
+    __device__ __forceinline__ void init(int e, int step, int pz, int w1)
+    {
+        W1 = w1;
+        const float inv = 1.0f / (float)w1;
+        const int a = div_small(e, inv), da = div_small(step, inv);
+        b = e - a * w1;
+        db = step - da * w1;
+        zi = a * pz + b;
+        dz = da * pz + db;
+        wrapz = pz - w1;
     }
-    if (ng <= tid) return;
-    // groups: thread tid takes groups tid, tid + gt, ...; (a, b) is the window position of
-    // the group's first entry, advanced by 4 gt entries per step
-    int e = head + 4 * tid;
-    int a = div_small(e, inv), b = e - a * W1;
-    const int da = div_small(4 * gt, inv), db = 4 * gt - da * W1;
-    const float* zp = z + a * pz + b;
-    const int dz = da * pz + db, wrapz = pz - W1;
-    float4* th4 = reinterpret_cast<float4*>(th + head);
-    uint2* t4 = t16 ? reinterpret_cast<uint2*>(t16 + head) : nullptr;
-    for (int g = tid; g < ng; g += gt) {
-        const int left = W1 - b;  // entries of the group before the window row ends
-        float4 v;
-        v.x = zp[0];
-        v.y = zp[left > 1 ? 1 : 1 + wrapz];
-        v.z = zp[left > 2 ? 2 : 2 + wrapz];
-        v.w = zp[left > 3 ? 3 : 3 + wrapz];
-        th4[g] = v;
-        if (t4) {
-            const __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
-            uint2 w;
-            w.x = *reinterpret_cast<const unsigned*>(&lo);
-            w.y = *reinterpret_cast<const unsigned*>(&hi);
-            t4[g] = w;
-        }
+    __device__ __forceinline__ void next()
+    {
         b += db;
-        zp += dz;
+        zi += dz;
         if (b >= W1) {
             b -= W1;
-            zp += wrapz;
+            zi += wrapz;
         }
     }
-}
+};
 
 // Copies the stencil window of one column band from its coefficient array (pitch pz) to the
 // row's storage (and the BF16 copy), which holds the window row-major.
@@ -225,22 +199,19 @@ __device__ __forceinline__ void write_win(const OpDev<T>& op, const T* Zb, int p
     if (tot <= 0) return;
     T* th = op.theta + dst;
     __nv_bfloat16* t16 = op.theta16 ? op.theta16 + dst : nullptr;
-    Stepper st;
-    st.init(tid, gt, W1);
     if (!r0.full && !r1.full && op.gap >= 0) {
         const T* z = Zb + (f0 - r0.lo) * pz + (f1 - r1.lo);  // inside the array (checked by the planner)
-        if constexpr (std::is_same<T, float>::value) {
-            if (W1 >= 4) {
-                store_window_f32(th, t16, z, pz, W0, W1, tid, gt);
-                return;
-            }
-        }
-        for (int idx = tid; idx < tot; idx += gt, st.next()) {
-            const T val = z[st.a * pz + st.b];
+        WinStep ws;
+        ws.init(tid, gt, pz, W1);
+        for (int idx = tid; idx < tot; idx += gt) {
+            const T val = z[ws.zi];
             th[idx] = val;
             if (t16) t16[idx] = __float2bfloat16_rn((float)val);
+            ws.next();
         }
     } else {
+        Stepper st;
+        st.init(tid, gt, W1);
         for (int idx = tid; idx < tot; idx += gt, st.next()) {
             const int p0 = pmod(f0 + st.a - r0.lo, nj), p1 = pmod(f1 + st.b - r1.lo, nj);
             const bool ok = (r0.full || p0 < r0.cnt) && (r1.full || p1 < r1.cnt);
@@ -256,28 +227,11 @@ __device__ __forceinline__ void write_win(const OpDev<T>& op, const T* Zb, int p
 // written to op.sf + Soff[b] + rl * RR + q.  One warp per stored row (canonical order, eight
 // rows per CTA); its lanes walk the region positions.  Indices are 32-bit: a region, a
 // window list (slots x N) and a band's F stay far below 2^31 elements.
-template <typename T, int SMAX>
-__device__ __forceinline__ T s_pixel(const WSlot<T>* __restrict__ wp, int N, int S, const T* __restrict__ F0,
-                                     int RR, int q)
-{
-    // all slot loads first, then the F loads, then the compensated sum over the terms
-    WSlot<T> w[SMAX];
-#pragma unroll
-    for (int sl = 0; sl < SMAX; ++sl)
-        if (sl < S) w[sl] = load_slot(wp + sl * N);
-    T f[SMAX];
-#pragma unroll
-    for (int sl = 0; sl < SMAX; ++sl) f[sl] = (sl < S) ? __ldg(F0 + (int64_t)w[sl].k * RR + q) : T(0);
-    T acc = (S > 0) ? w[0].v * f[0] : T(0), c = T(0);
-#pragma unroll
-    for (int sl = 1; sl < SMAX; ++sl)
-        if (sl < S) kahan_add(acc, c, w[sl].v * f[sl]);
-    return acc;
-}
-
 template <typename T>
 __global__ void __launch_bounds__(256) k_s_rows(const OpDev<T>* __restrict__ opd)
 {
+    constexpr int PX = 4;    // positions per lane and step, all their loads in flight together
+    constexpr int SMAX = 4;  // window-list slots handled by the unrolled path
     __shared__ int64_t boff_s[MAXB];
     const OpDev<T>& op = *opd;  // device copy (refreshed before each run, also inside graphs)
     const int n = op.n, nm = n - 1, nb = op.nb;
@@ -301,30 +255,55 @@ __global__ void __launch_bounds__(256) k_s_rows(const OpDev<T>* __restrict__ opd
     T* out = op.sf + op.Soff[b] + (int64_t)rl * RR;
     const WSlot<T>* wl = reinterpret_cast<const WSlot<T>*>(op.wl);
     const int S = op.wl_slots, N = (int)op.N;
-    // (a, b) = (q0, q1) of position q, advanced by 32 positions per step
+    // (qa, qb) = (q0, q1) of position q, advanced by 32 positions at a time
     const float inv = 1.0f / (float)c1;
     int qa = div_small(lane, inv), qb = lane - qa * c1;
     const int da = div_small(32, inv), db = 32 - da * c1;
-    for (int q = lane; q < RR; q += 32) {
-        const int pix = ((g0 + qa) & nm) * n + ((g1 + qb) & nm);
-        const WSlot<T>* wp = wl + pix;
-        T val;
-        if (S <= 4)
-            val = s_pixel<T, 4>(wp, N, S, F0, RR, q);
-        else {
-            T acc = T(0), c = T(0);
-            for (int sl = 0; sl < S; ++sl) {
-                const WSlot<T> w = load_slot(wp + sl * N);
-                if (w.v != T(0)) kahan_add(acc, c, w.v * __ldg(F0 + (int64_t)w.k * RR + q));
+    for (int q = lane; q < RR; q += 32 * PX) {
+        int pix[PX];
+#pragma unroll
+        for (int u = 0; u < PX; ++u) {
+            pix[u] = ((g0 + qa) & nm) * n + ((g1 + qb) & nm);
+            qa += da;
+            qb += db;
+            if (qb >= c1) {
+                qb -= c1;
+                ++qa;
             }
-            val = acc;
         }
-        out[q] = val;
-        qa += da;
-        qb += db;
-        if (qb >= c1) {
-            qb -= c1;
-            ++qa;
+        if (S <= SMAX) {
+            WSlot<T> w[PX][SMAX];
+#pragma unroll
+            for (int u = 0; u < PX; ++u)
+#pragma unroll
+                for (int sl = 0; sl < SMAX; ++sl)
+                    if (sl < S && q + 32 * u < RR) w[u][sl] = load_slot(wl + sl * N + pix[u]);
+                    else w[u][sl] = WSlot<T>{0, T(0)};
+            T f[PX][SMAX];
+#pragma unroll
+            for (int u = 0; u < PX; ++u)
+#pragma unroll
+                for (int sl = 0; sl < SMAX; ++sl)
+                    f[u][sl] = (w[u][sl].v != T(0)) ? __ldg(F0 + (int64_t)w[u][sl].k * RR + q + 32 * u) : T(0);
+#pragma unroll
+            for (int u = 0; u < PX; ++u) {
+                T acc = w[u][0].v * f[u][0], c = T(0);
+#pragma unroll
+                for (int sl = 1; sl < SMAX; ++sl)
+                    if (sl < S) kahan_add(acc, c, w[u][sl].v * f[u][sl]);
+                if (q + 32 * u < RR) out[q + 32 * u] = acc;
+            }
+        } else {
+#pragma unroll 1
+            for (int u = 0; u < PX; ++u) {
+                if (q + 32 * u >= RR) break;
+                T acc = T(0), c = T(0);
+                for (int sl = 0; sl < S; ++sl) {
+                    const WSlot<T> w = load_slot(wl + sl * N + pix[u]);
+                    if (w.v != T(0)) kahan_add(acc, c, w.v * __ldg(F0 + (int64_t)w.k * RR + q + 32 * u));
+                }
+                out[q + 32 * u] = acc;
+            }
         }
     }
 }
@@ -375,9 +354,9 @@ __device__ __forceinline__ bool row2_meta(const OpDev<T>& op, const Row2& R, int
 #pragma unroll
         for (int w = 0; w < MAXW; ++w) mw[w] = 0ull;
         const int ts0 = op.ts0, ts1 = op.ts1;
-        const int s0 = R.g0 / ts0, s1 = R.g1 / ts1;
+        const int s0 = terms ? R.g0 / ts0 : 0, s1 = terms ? R.g1 / ts1 : 0;
         const int nt0 = terms ? min(op.tpa0, (R.g0 % ts0 + R.A0.cnt + ts0 - 1) / ts0) : 0;
-        const int nt1 = min(op.tpa1, (R.g1 % ts1 + R.A1.cnt + ts1 - 1) / ts1);
+        const int nt1 = terms ? min(op.tpa1, (R.g1 % ts1 + R.A1.cnt + ts1 - 1) / ts1) : 0;
         for (int i = lane; i < nt0 * nt1; i += 32) {
             const int i0 = i / nt1;
             const int t0 = (s0 + i0) % op.tpa0, t1 = (s1 + i - i0 * nt1) % op.tpa1;
@@ -386,13 +365,25 @@ __device__ __forceinline__ bool row2_meta(const OpDev<T>& op, const Row2& R, int
             for (int w = 0; w < MAXW; ++w)
                 if (w < op.mwords) mw[w] |= mp[w];
         }
-        // block counts: lane b2 (and b2 + 32); exclusive scan in canonical band order
+        // stencil windows and block counts: lane b2 (and b2 + 32); exclusive scan of the counts
+        // in canonical band order
         int total = 0;
+        const int dense = op.gap < 0;
         for (int base = 0; base < op.nb; base += 32) {
             const int b2 = base + lane;
             int cnt = 0;
-            if (b2 < op.nb && block_kept(2, n, L, op.gap, b, b2))
-                cnt = (int)block_count(2, n, L, op.Lf, op.r, op.gap, b, R.l0, R.l1, b2);
+            if (b2 < op.nb && block_kept(2, n, L, op.gap, b, b2)) {
+                const Band B2 = band_info(2, n, L, b2);
+                int f0, W0, f1, W1;
+                stencil(R.j, R.Bo.e0, R.l0, B2.j, B2.e0, op.r, op.Lf, n, dense, &f0, &W0);
+                stencil(R.j, R.Bo.e1, R.l1, B2.j, B2.e1, op.r, op.Lf, n, dense, &f1, &W1);
+                int* w = meta + WIN_OFF + 4 * b2;
+                w[0] = f0;
+                w[1] = W0;
+                w[2] = f1;
+                w[3] = W1;
+                cnt = W0 * W1;
+            }
             int x = cnt;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -441,9 +432,11 @@ __device__ __forceinline__ void write_level(const OpDev<T>& op, const Row2& R, c
     for (int t = 0; t < tmax; ++t) {
         const int b2 = (t == 3) ? 0 : band_of_level(2, L, jj, t);
         const int e0 = (t == 3) ? 0 : (t >= 1 ? 1 : 0), e1 = (t == 3) ? 0 : (t == 1 ? 0 : 1);
-        int f0, W0, f1, W1;
-        stencil(R.j, R.Bo.e0, R.l0, jj, e0, op.r, op.Lf, n, dense, &f0, &W0);
-        stencil(R.j, R.Bo.e1, R.l1, jj, e1, op.r, op.Lf, n, dense, &f1, &W1);
+        (void)e0;
+        (void)e1;
+        (void)dense;
+        const int* w = meta + WIN_OFF + 4 * b2;
+        const int f0 = w[0], W0 = w[1], f1 = w[2], W1 = w[3];
         write_win(op, (t == 3) ? LL : D + t * dq, (t == 3) ? LP : q1r.cnt, q0r, q1r, nj, f0, W0, f1, W1,
                   R.row_base + meta[b2], tid, gt);
     }

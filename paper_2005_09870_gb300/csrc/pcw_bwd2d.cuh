@@ -120,27 +120,25 @@ __device__ __forceinline__ void read_win(const OpDev<T>& op, const T* __restrict
     const int tot = W0 * W1;
     if (tot <= 0) return;
     const T* g = Gr + src;
-    Stepper st;
-    st.init(tid, gt, W1);
     if (!r0.full && !r1.full && op.gap >= 0) {
         T* z = Zb + (f0 - r0.lo) * pz + (f1 - r1.lo);
-        // RD loads in flight per thread before their stores
+        // RD loads in flight per thread before their stores; positions stepped without divisions
         constexpr int RD = 4;
+        WinStep ws;
+        ws.init(tid, gt, pz, W1);
         for (int i0 = tid; i0 < tot; i0 += RD * gt) {
             T val[RD];
-            int zi[RD];
+#pragma unroll
+            for (int u = 0; u < RD; ++u) val[u] = (i0 + u * gt < tot) ? __ldg(g + i0 + u * gt) : T(0);
 #pragma unroll
             for (int u = 0; u < RD; ++u) {
-                const bool ok = i0 + u * gt < tot;
-                zi[u] = st.a * pz + st.b;
-                val[u] = ok ? __ldg(g + i0 + u * gt) : T(0);
-                st.next();
+                if (i0 + u * gt < tot) z[ws.zi] = val[u];
+                ws.next();
             }
-#pragma unroll
-            for (int u = 0; u < RD; ++u)
-                if (i0 + u * gt < tot) z[zi[u]] = val[u];
         }
     } else {
+        Stepper st;
+        st.init(tid, gt, W1);
         for (int idx = tid; idx < tot; idx += gt, st.next()) {
             const int p0 = pmod(f0 + st.a - r0.lo, nj), p1 = pmod(f1 + st.b - r1.lo, nj);
             if ((r0.full || p0 < r0.cnt) && (r1.full || p1 < r1.cnt)) Zb[p0 * pz + p1] = g[idx];
@@ -160,9 +158,11 @@ __device__ __forceinline__ void read_level(const OpDev<T>& op, const Row2& R, co
     for (int t = 0; t < tmax; ++t) {
         const int b2 = (t == 3) ? 0 : band_of_level(2, L, jj, t);
         const int e0 = (t == 3) ? 0 : (t >= 1 ? 1 : 0), e1 = (t == 3) ? 0 : (t == 1 ? 0 : 1);
-        int f0, W0, f1, W1;
-        stencil(R.j, R.Bo.e0, R.l0, jj, e0, op.r, op.Lf, n, dense, &f0, &W0);
-        stencil(R.j, R.Bo.e1, R.l1, jj, e1, op.r, op.Lf, n, dense, &f1, &W1);
+        (void)e0;
+        (void)e1;
+        (void)dense;
+        const int* w = meta + WIN_OFF + 4 * b2;
+        const int f0 = w[0], W0 = w[1], f1 = w[2], W1 = w[3];
         read_win(op, Gth, Z + ((t == 3) ? 0 : (1 + t) * zq), q1r.cnt, q0r, q1r, nj, f0, W0, f1, W1,
                  R.row_base + meta[b2], tid, gt);
     }

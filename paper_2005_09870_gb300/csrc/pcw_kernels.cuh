@@ -506,9 +506,12 @@ __device__ __forceinline__ void asm1d_row(const OpDev<T>& op, const AsmCfg& cfg,
 
 // Shared-memory layout of the row kernels: filters (cfg.filt elements of T) | per group a meta
 // area of META_INTS ints | per group an arena of cfg.arena elements of T.
-constexpr int META_INTS = 112;  // block offsets [MAXB+1], active terms (bytes) [64 ints], count
-constexpr int ACT_OFF = MAXB + 1;
+// meta area of a 2-D row group: block offsets [MAXB + 1], the stencil window of every kept
+// column band (f0, W0, f1, W1) [4 MAXB], active terms (bytes) [64 ints], their count
+constexpr int WIN_OFF = MAXB + 1;
+constexpr int ACT_OFF = WIN_OFF + 4 * MAXB;
 constexpr int NACT_OFF = ACT_OFF + 64;
+constexpr int META_INTS = (NACT_OFF + 1 + 3) / 4 * 4;
 static_assert(NACT_OFF < META_INTS, "meta layout");
 
 template <typename T>
