@@ -227,11 +227,38 @@ __device__ __forceinline__ void write_win(const OpDev<T>& op, const T* Zb, int p
 // written to op.sf + Soff[b] + rl * RR + q.  One warp per stored row (canonical order, eight
 // rows per CTA); its lanes walk the region positions.  Indices are 32-bit: a region, a
 // window list (slots x N) and a band's F stay far below 2^31 elements.
+// PX region positions of one lane with NS window-list slots (NS = the operator's slot count):
+// every slot and F load unconditional (unused slots hold (k, v) = (0, 0) and positions past the
+// region are clamped to its last one, so every address is valid), then the compensated sums.
+template <typename T, int NS, int PX>
+__device__ __forceinline__ void s_positions(const WSlot<T>* __restrict__ wl, int N, const T* __restrict__ F0, int RR,
+                                            const int (&pix)[PX], int q, T* __restrict__ out)
+{
+    WSlot<T> w[PX][NS];
+#pragma unroll
+    for (int u = 0; u < PX; ++u)
+#pragma unroll
+        for (int sl = 0; sl < NS; ++sl) w[u][sl] = load_slot(wl + (pix[u] + sl * N));
+    T f[PX][NS];
+#pragma unroll
+    for (int u = 0; u < PX; ++u) {
+        const int qu = min(q + 32 * u, RR - 1);
+#pragma unroll
+        for (int sl = 0; sl < NS; ++sl) f[u][sl] = __ldg(F0 + ((int)w[u][sl].k * RR + qu));
+    }
+#pragma unroll
+    for (int u = 0; u < PX; ++u) {
+        T acc = w[u][0].v * f[u][0], c = T(0);
+#pragma unroll
+        for (int sl = 1; sl < NS; ++sl) kahan_add(acc, c, w[u][sl].v * f[u][sl]);
+        if (q + 32 * u < RR) out[q + 32 * u] = acc;
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_s_rows(const OpDev<T>* __restrict__ opd)
 {
-    constexpr int PX = 4;    // positions per lane and step, all their loads in flight together
-    constexpr int SMAX = 4;  // window-list slots handled by the unrolled path
+    constexpr int PX = 4;  // positions per lane and step, all their loads in flight together
     __shared__ int64_t boff_s[MAXB];
     const OpDev<T>& op = *opd;  // device copy (refreshed before each run, also inside graphs)
     const int n = op.n, nm = n - 1, nb = op.nb;
@@ -271,39 +298,23 @@ __global__ void __launch_bounds__(256) k_s_rows(const OpDev<T>* __restrict__ opd
                 ++qa;
             }
         }
-        if (S <= SMAX) {
-            WSlot<T> w[PX][SMAX];
+        switch (S) {
+            case 1: s_positions<T, 1, PX>(wl, N, F0, RR, pix, q, out); break;
+            case 2: s_positions<T, 2, PX>(wl, N, F0, RR, pix, q, out); break;
+            case 3: s_positions<T, 3, PX>(wl, N, F0, RR, pix, q, out); break;
+            case 4: s_positions<T, 4, PX>(wl, N, F0, RR, pix, q, out); break;
+            default:
 #pragma unroll
-            for (int u = 0; u < PX; ++u)
-#pragma unroll
-                for (int sl = 0; sl < SMAX; ++sl)
-                    if (sl < S && q + 32 * u < RR) w[u][sl] = load_slot(wl + sl * N + pix[u]);
-                    else w[u][sl] = WSlot<T>{0, T(0)};
-            T f[PX][SMAX];
-#pragma unroll
-            for (int u = 0; u < PX; ++u)
-#pragma unroll
-                for (int sl = 0; sl < SMAX; ++sl)
-                    f[u][sl] = (w[u][sl].v != T(0)) ? __ldg(F0 + (int64_t)w[u][sl].k * RR + q + 32 * u) : T(0);
-#pragma unroll
-            for (int u = 0; u < PX; ++u) {
-                T acc = w[u][0].v * f[u][0], c = T(0);
-#pragma unroll
-                for (int sl = 1; sl < SMAX; ++sl)
-                    if (sl < S) kahan_add(acc, c, w[u][sl].v * f[u][sl]);
-                if (q + 32 * u < RR) out[q + 32 * u] = acc;
-            }
-        } else {
-#pragma unroll 1
-            for (int u = 0; u < PX; ++u) {
-                if (q + 32 * u >= RR) break;
-                T acc = T(0), c = T(0);
-                for (int sl = 0; sl < S; ++sl) {
-                    const WSlot<T> w = load_slot(wl + sl * N + pix[u]);
-                    if (w.v != T(0)) kahan_add(acc, c, w.v * __ldg(F0 + (int64_t)w.k * RR + q + 32 * u));
+                for (int u = 0; u < PX; ++u) {
+                    if (q + 32 * u < RR) {
+                        T acc = T(0), c = T(0);
+                        for (int sl = 0; sl < S; ++sl) {
+                            const WSlot<T> w = load_slot(wl + (pix[u] + sl * N));
+                            if (w.v != T(0)) kahan_add(acc, c, w.v * __ldg(F0 + ((int)w.k * RR + q + 32 * u)));
+                        }
+                        out[q + 32 * u] = acc;
+                    }
                 }
-                out[q + 32 * u] = acc;
-            }
         }
     }
 }

@@ -388,8 +388,12 @@ __global__ void __launch_bounds__(256) k_bwd_dv4(const __grid_constant__ BwdDev 
                                                  const float* __restrict__ S, float* __restrict__ dv)
 {
     const int n = bd.n;
-    const int kbase = blockIdx.z * 4 * NQ;
-    const int x0 = blockIdx.y * 16 + threadIdx.y, x1 = blockIdx.x * 16 + threadIdx.x;
+    // blockIdx.x = pixel tile column * zc + term group: the zc CTAs of a tile are adjacent in
+    // launch order, so that they run together and share the tile's dL/ds reads through L2
+    const int zc = (bd.m + 4 * NQ - 1) / (4 * NQ);
+    const int tx = blockIdx.x / zc;
+    const int kbase = (blockIdx.x - tx * zc) * 4 * NQ;
+    const int x0 = blockIdx.y * 16 + threadIdx.y, x1 = tx * 16 + threadIdx.x;
     if (x0 >= n || x1 >= n) return;
     float4 acc[NQ];
 #pragma unroll

@@ -963,8 +963,10 @@ pc_status backward_core(pc_op* h, const T* G, T* du, T* dv, T* dF, T* dG, cudaSt
             int maxRR = 0;
             for (int b = 0; b < h->nb; ++b) maxRR = std::max(maxRR, h->bd.band[b].R0 * h->bd.band[b].R1);
             k_transpose_F<<<dim3((maxRR + 255) / 256, h->nb), 256, 0, st>>>(h->bd, (const float*)h->F_d, FT);
-            constexpr int NQ = 2;  // float4 term groups per thread
-            k_bwd_dv4<NQ><<<dim3((D.n + 15) / 16, (D.n + 15) / 16, (D.m + 4 * NQ - 1) / (4 * NQ)), dim3(16, 16), 0,
+            // two float4 term groups (8 terms) per thread: wider groups load each dL/ds value fewer
+            // times but hold more registers, and measured slower on the 1024^2 workload
+            constexpr int NQ = 2;
+            k_bwd_dv4<NQ><<<dim3((D.n + 15) / 16 * ((D.m + 4 * NQ - 1) / (4 * NQ)), (D.n + 15) / 16, 1), dim3(16, 16), 0,
                             st>>>(h->bd, FT, S, dv);
             count_launch(2);
         } else {
@@ -973,8 +975,9 @@ pc_status backward_core(pc_op* h, const T* G, T* du, T* dv, T* dF, T* dG, cudaSt
             count_launch();
         }
         {
-            // one launch over all bands: blocks (band, 128 region positions, 32 rows)
-            const int chunk = 32;
+            // one launch over all bands: blocks (band, 128 region positions, a chunk of rows); larger
+            // operators take longer chunks (fewer blocks and fewer atomic adds per dL/dF entry)
+            const int chunk = h->N >= ((int64_t)1 << 20) ? 128 : h->N >= ((int64_t)1 << 16) ? 64 : 32;
             int offs[MAXB + 1];
             int tot = 0;
             for (int b = 0; b < h->nb; ++b) {
@@ -1659,6 +1662,10 @@ pc_status pc_create(const pc_desc* desc, const void* u, const void* v, void* str
         fb.R0 = (D.dim == 2) ? std::min(U, D.n) : 1;
         fb.Foff = Fo;
         fb.Goff = Go;
+        // the window sums index a band's filtered wavelets with 32-bit offsets
+        if ((int64_t)D.m * fb.R0 * fb.R1 >= ((int64_t)1 << 31))
+            return bail(fail(h, PC_ERR_UNSUPPORTED, "band %d: %d terms x %d x %d region exceed 2^31 elements", b, D.m,
+                             fb.R0, fb.R1));
         Fo += (int64_t)D.m * fb.R0 * fb.R1;
         Go += (int64_t)D.m * ((D.dim == 2) ? h->K : 1) * fb.U1;
     }

@@ -131,3 +131,34 @@ def test_large_backward_vs_oracle(large):
     e1 = assert_elementwise(du.double().cpu().numpy(), du_ref, 1e-5, "dL/du")
     e2 = assert_elementwise(dv.double().cpu().numpy(), dv_ref, 1e-5, "dL/dv")
     print(f"c5 backward vs oracle: max err / max|g| du {e1:.2e} dv {e2:.2e}")
+
+
+@pytest.mark.parametrize("name,kw", [("op2", {"n": 512}), ("c5", {"n": 512, "levels": 4})],
+                         ids=["m25-512", "m64-512"])
+def test_backward_many_terms_vs_oracle(name, kw):
+    """Operators with many terms (25 Symmlet-6 terms and 64 terms on 512^2, several groups of
+    terms in the dL/dv gather): seeded dL/dTheta on one column per band, dL/du and dL/dv against
+    the oracle's adjoint element-wise within 1e-5 of the largest magnitude."""
+    import torch
+    import oracle
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2005_09870_gb300 as pw
+    op = P.workload(name, **kw)
+    g = make_gpu_op(pw, op)
+    cols = _band_columns(op, 24)
+    G = np.zeros((cols.size, op.N))
+    G_d = torch.zeros(g.nnz, dtype=torch.float32, device="cuda")
+    for c, lam in enumerate(cols):
+        mus = np.nonzero(oracle.pattern_column(op, int(lam)))[0].astype(np.int64)
+        vals = P.normal(P.BASE_SEED + 650 + c, mus.size)
+        G[c, mus] = vals
+        pos = g.lookup(mus, np.full(mus.size, lam, dtype=np.int64))
+        assert (pos >= 0).all()
+        G_d[torch.tensor(pos, device="cuda")] = torch.tensor(vals, dtype=torch.float32, device="cuda")
+    du, dv = g.backward(G_d)
+    g.sync()
+    du_ref, dv_ref = oracle.theta_grad(op, cols, G, nthreads=8)
+    assert_elementwise(du.double().cpu().numpy(), du_ref, 1e-5, "dL/du")
+    assert_elementwise(dv.double().cpu().numpy(), dv_ref, 1e-5, "dL/dv")
+    g.close()
