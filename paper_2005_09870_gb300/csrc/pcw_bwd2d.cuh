@@ -5,7 +5,7 @@
 //           dL/dTheta entries, written to the scratch S (band b at Soff[b], row rl at
 //           + rl * RR_b, region row-major);
 //   phase 2 (k_bwd_dv4, k_bwd_dv for FP64): dL/dv_k(x) = sum_b sum_{rows l covering x}
-//           F_{k,b}(x - t_l) S_{b,l}(x - t_l), one thread per pixel, no atomics;
+//           F_{k,b}(x - t_l) S_{b,l}(x - t_l), a gather (no atomics), one thread per pixel;
 //   phase 3 (k_bwd_dF_wl, k_bwd_dF without window lists): dL/dF_{k,b}(q) =
 //           sum_l v_k(t_l + q) S_{b,l}(q), chunks of rows per CTA, one atomic per (k, q, chunk).
 // The adjoint of F = kappa_k * rho_b (dL/dkappa_k) then runs in k_dfilt_pass2 / pass1.
@@ -122,19 +122,17 @@ __device__ __forceinline__ void read_win(const OpDev<T>& op, const T* __restrict
     const T* g = Gr + src;
     if (!r0.full && !r1.full && op.gap >= 0) {
         T* z = Zb + (f0 - r0.lo) * pz + (f1 - r1.lo);
-        // RD loads in flight per thread before their stores; positions stepped without divisions
-        constexpr int RD = 4;
+        // asynchronous copies (cp.async): every copy of the thread in flight at once, no register
+        // round trip; read_level waits for them.  Positions stepped without divisions.
         WinStep ws;
         ws.init(tid, gt, pz, W1);
-        for (int i0 = tid; i0 < tot; i0 += RD * gt) {
-            T val[RD];
-#pragma unroll
-            for (int u = 0; u < RD; ++u) val[u] = (i0 + u * gt < tot) ? __ldg(g + i0 + u * gt) : T(0);
-#pragma unroll
-            for (int u = 0; u < RD; ++u) {
-                if (i0 + u * gt < tot) z[ws.zi] = val[u];
-                ws.next();
-            }
+        for (int i = tid; i < tot; i += gt) {
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(z + ws.zi);
+            if constexpr (sizeof(T) == 4)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(g + i) : "memory");
+            else
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(g + i) : "memory");
+            ws.next();
         }
     } else {
         Stepper st;
@@ -166,6 +164,7 @@ __device__ __forceinline__ void read_level(const OpDev<T>& op, const Row2& R, co
         read_win(op, Gth, Z + ((t == 3) ? 0 : (1 + t) * zq), q1r.cnt, q0r, q1r, nj, f0, W0, f1, W1,
                  R.row_base + meta[b2], tid, gt);
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");  // this thread's window copies have landed
 }
 
 // Phase 1, one stored 2-D row by one thread group (same plan, arenas and filter area as the
@@ -383,13 +382,14 @@ __global__ void k_transpose_F(const __grid_constant__ BwdDev bd, const float* __
 }
 
 // Phase 2 on the term-contiguous copy: 4 * NQ terms per thread, read as NQ float4 per translate.
+// Phase 2 (FP32).  One thread per pixel and 4 NQ terms (blockIdx.x = tile column * zc + term
+// group: the zc blocks of a 16 x 16 pixel tile are adjacent in launch order, so that they run
+// together and share the tile's dL/ds reads through L2).
 template <int NQ>
 __global__ void __launch_bounds__(256) k_bwd_dv4(const __grid_constant__ BwdDev bd, const float* __restrict__ FT,
                                                  const float* __restrict__ S, float* __restrict__ dv)
 {
     const int n = bd.n;
-    // blockIdx.x = pixel tile column * zc + term group: the zc CTAs of a tile are adjacent in
-    // launch order, so that they run together and share the tile's dL/ds reads through L2
     const int zc = (bd.m + 4 * NQ - 1) / (4 * NQ);
     const int tx = blockIdx.x / zc;
     const int kbase = (blockIdx.x - tx * zc) * 4 * NQ;
@@ -414,15 +414,15 @@ __global__ void __launch_bounds__(256) k_bwd_dv4(const __grid_constant__ BwdDev 
 #pragma unroll 2
             for (int l1 = l1lo; l1 <= l1hi; ++l1) {
                 const int q = q0 * B.R1 + (a1 - (l1 << lg));
-                const float s = __ldg(Sb + (rb + (l1 & njm)) * RR + q);
+                const float sv = __ldg(Sb + (rb + (l1 & njm)) * RR + q);
 #pragma unroll
                 for (int g = 0; g < NQ; ++g) {
                     if (g < ng) {
                         const float4 f = __ldg(Fa + (int64_t)g * RR + q);
-                        acc[g].x = fmaf(f.x, s, acc[g].x);
-                        acc[g].y = fmaf(f.y, s, acc[g].y);
-                        acc[g].z = fmaf(f.z, s, acc[g].z);
-                        acc[g].w = fmaf(f.w, s, acc[g].w);
+                        acc[g].x = fmaf(f.x, sv, acc[g].x);
+                        acc[g].y = fmaf(f.y, sv, acc[g].y);
+                        acc[g].z = fmaf(f.z, sv, acc[g].z);
+                        acc[g].w = fmaf(f.w, sv, acc[g].w);
                     }
                 }
             }
