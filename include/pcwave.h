@@ -265,6 +265,30 @@ pc_status pc_batch_assemble(pc_handle* ops, int count, void* stream);
 pc_status pc_autotune(pc_handle h, void* stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Building an expansion.
+ * --------------------------------------------------------------------------------------- */
+
+/* Product-convolution expansion of a space-varying operator from its space-varying impulse
+ * response (SVIR), by randomized SVD (Section 2.4: the best rank-m approximation of the SVIR in
+ * Frobenius norm gives the expansion; Halko, Martinsson and Tropp's randomized range finder).
+ *   S: N x K, FP32, device, row-major: S[x * K + t] is the response at stencil offset t (a
+ *      (2r+1)^d stencil, row-major, centre = offset 0) to a unit source at pixel x, so that
+ *      (H f)(x + t) = sum_x f(x) S[x, t] on the torus.
+ *   omega: K x l test matrix (FP32, device, row-major; the caller draws it, e.g. N(0,1)),
+ *      l = m + oversampling, 1 <= m <= l <= min(64, K); power_iters >= 0 refinements
+ *      Q <- orth(S orth(S^T Q)).
+ * Computes Q = orth(S omega) (refined), B = Q^T S, B = U diag(s) W^T (FP64 on the host) and
+ * writes u_k = W[:, k] (u: m x K) and v_k = s_k (Q U)[:, k] (v: m x N), both FP32 device,
+ * caller-owned: S ~ sum_k v_k u_k^T, and (u, v) are the kernels and windows of pc_create in
+ * the paper's order.  Directions of the sketch below 1e-12 of its largest are dropped, and
+ * terms past the sketch's numerical rank come out zero.  sing (host, l doubles, may be NULL)
+ * receives s.  The tall products run as cuBLAS FP32 GEMMs on `stream`; the call allocates
+ * device scratch (about (N + 2K) l floats) and a cuBLAS handle, and synchronises `stream`.
+ * PC_ERR_INVALID_ARG for NULL pointers or sizes out of range. */
+pc_status pc_svir_expansion(const float* S, int64_t N, int K, int m, int l, int power_iters, const float* omega,
+                            float* u, float* v, double* sing, void* stream);
+
+/* ---------------------------------------------------------------------------------------
  * Inspection.
  * --------------------------------------------------------------------------------------- */
 

@@ -76,6 +76,8 @@ _sig = {
     "pc_fista": ([_H, _P, _P, _P, _P, ctypes.c_int, ctypes.c_double, _P], ctypes.c_int),
     "pc_filter_taps": ([ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "pc_export": ([_H, _I64P, _I64P, ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
+    "pc_svir_expansion": ([_P, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P,
+                           ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
 }
 for _name, (_args, _ret) in _sig.items():
     _f = getattr(_lib, _name)
@@ -109,6 +111,21 @@ def pc_export(h, nnz, N, stream=None):
     _check(_lib.pc_export(h, row_ptr.ctypes.data_as(_I64P), cols.ctypes.data_as(_I64P),
                           vals.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream(stream)), h)
     return row_ptr, cols, vals
+
+
+def pc_svir_expansion(S, m, omega, power_iters=2, stream=None):
+    """Rank-m product-convolution expansion of an SVIR S (N x K, FP32 CUDA tensor) by randomized
+    SVD with the test matrix omega (K x l, FP32 CUDA tensor): returns (u (m x K), v (m x N),
+    singular values of the projected matrix (l,), numpy)."""
+    t = _torch()
+    N, K = S.shape
+    l = omega.shape[1]
+    u = t.empty((m, K), dtype=t.float32, device=S.device)
+    v = t.empty((m, N), dtype=t.float32, device=S.device)
+    sing = np.zeros(l)
+    _check(_lib.pc_svir_expansion(_ptr(S), int(N), int(K), int(m), int(l), int(power_iters), _ptr(omega), _ptr(u),
+                                  _ptr(v), sing.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream(stream)))
+    return u, v, sing
 
 
 def pc_filter_taps(family: int, delta: int):

@@ -30,7 +30,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         return LIB
     tmp = LIB + f".{os.getpid()}.tmp"
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-           "-cudart", "shared", "-o", tmp, os.path.join(SRC, "pcwave.cu"), *extra]
+           "-cudart", "shared", "-o", tmp, os.path.join(SRC, "pcwave.cu"), "-lcublas", *extra]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)

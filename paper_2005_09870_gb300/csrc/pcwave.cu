@@ -21,6 +21,7 @@
 #include "pcw_asm2d.cuh"
 #include "pcw_bwd2d.cuh"
 #include "pcw_taps.h"
+#include "pcw_svir_gpu.cuh"
 
 using namespace pcw;
 
@@ -2070,5 +2071,76 @@ pc_status pc_sync(pc_handle h, void* stream)
 }
 
 const char* pc_last_error(pc_handle h) { return h ? h->err.c_str() : g_noh_error.c_str(); }
+
+pc_status pc_svir_expansion(const float* S, int64_t N, int K, int m, int l, int power_iters, const float* omega,
+                            float* u, float* v, double* sing, void* stream)
+{
+    if (!S || !omega || !u || !v || N < 1 || K < 1 || m < 1 || l < m || l > 64 || l > K || power_iters < 0 ||
+        N > ((int64_t)1 << 30))
+        return fail(nullptr, PC_ERR_INVALID_ARG, "pc_svir_expansion: bad arguments (need 1 <= m <= l <= min(64, K))");
+    SvirWork w;
+    w.st = (cudaStream_t)stream;
+    float *Y = nullptr, *Z = nullptr, *Bm = nullptr, *Ut = nullptr;
+    auto cleanup = [&]() {
+        for (void* p : {(void*)Y, (void*)Z, (void*)Bm, (void*)Ut, (void*)w.G, (void*)w.T, (void*)w.tmp})
+            if (p) cudaFree(p);
+        if (w.hb) cublasDestroy(w.hb);
+    };
+    auto bad = [&](pc_status st, const std::string& msg) {
+        cleanup();
+        return fail(nullptr, st, "pc_svir_expansion: %s", msg.c_str());
+    };
+    const int64_t rows = std::max<int64_t>(N, K);
+    if (cudaMalloc(&Y, sizeof(float) * N * l) || cudaMalloc(&Z, sizeof(float) * (size_t)K * l) ||
+        cudaMalloc(&Bm, sizeof(float) * (size_t)l * K) || cudaMalloc(&Ut, sizeof(float) * (size_t)m * l) ||
+        cudaMalloc(&w.G, sizeof(float) * l * l) || cudaMalloc(&w.T, sizeof(float) * l * l) ||
+        cudaMalloc(&w.tmp, sizeof(float) * rows * l))
+        return bad(PC_ERR_OOM, "device allocation failed");
+    if (cublasCreate(&w.hb) != CUBLAS_STATUS_SUCCESS || cublasSetStream(w.hb, w.st) != CUBLAS_STATUS_SUCCESS ||
+        cublasSetMathMode(w.hb, CUBLAS_PEDANTIC_MATH) != CUBLAS_STATUS_SUCCESS)
+        return bad(PC_ERR_CUDA, "cuBLAS set-up failed");
+    // range finder: Y = S Omega, orthonormalised; power iterations Z = S^T Q, Y = S Z
+    if (gemm_rm(w.hb, false, false, (int)N, l, K, S, K, omega, l, Y, l) != CUBLAS_STATUS_SUCCESS)
+        return bad(PC_ERR_CUDA, "cuBLAS product S Omega failed");
+    int r = svir_orthonormalise(w, Y, N, l, l);
+    if (!r) return bad(PC_ERR_CUDA, w.err);
+    for (int it = 0; it < power_iters; ++it) {
+        if (gemm_rm(w.hb, true, false, K, r, (int)N, S, K, Y, l, Z, l) != CUBLAS_STATUS_SUCCESS)
+            return bad(PC_ERR_CUDA, "cuBLAS product S^T Q failed");
+        int rz = svir_orthonormalise(w, Z, K, r, l);
+        if (!rz) return bad(PC_ERR_CUDA, w.err);
+        if (gemm_rm(w.hb, false, false, (int)N, rz, K, S, K, Z, l, Y, l) != CUBLAS_STATUS_SUCCESS)
+            return bad(PC_ERR_CUDA, "cuBLAS product S Z failed");
+        r = svir_orthonormalise(w, Y, N, rz, l);
+        if (!r) return bad(PC_ERR_CUDA, w.err);
+    }
+    // projected matrix B = Q^T S (r x K), its SVD on the host in FP64
+    if (gemm_rm(w.hb, true, false, r, K, (int)N, Y, l, S, K, Bm, K) != CUBLAS_STATUS_SUCCESS)
+        return bad(PC_ERR_CUDA, "cuBLAS product Q^T S failed");
+    std::vector<float> bf((size_t)r * K);
+    if (cudaMemcpyAsync(bf.data(), Bm, sizeof(float) * bf.size(), cudaMemcpyDeviceToHost, w.st) != cudaSuccess ||
+        cudaStreamSynchronize(w.st) != cudaSuccess)
+        return bad(PC_ERR_CUDA, "copy of the projected matrix failed");
+    std::vector<double> B(bf.begin(), bf.end()), sv, U, W;
+    jacobi_svd(B, r, K, &sv, &U, &W);
+    // u_k = W[:, k]; v_k = s_k (Q U)[:, k], as v (m x N) = (U[:, :m] diag(s))^T Q^T; terms past the
+    // numerical rank of the sketch are zero
+    const int mm = std::min(m, r);
+    std::vector<float> uh((size_t)m * K, 0.0f), ut((size_t)m * l, 0.0f);
+    for (int k = 0; k < mm; ++k) {
+        for (int t = 0; t < K; ++t) uh[(size_t)k * K + t] = (float)W[(size_t)t * r + k];
+        for (int j = 0; j < r; ++j) ut[(size_t)k * l + j] = (float)(U[(size_t)j * r + k] * sv[k]);
+    }
+    if (cudaMemcpyAsync(u, uh.data(), sizeof(float) * uh.size(), cudaMemcpyHostToDevice, w.st) != cudaSuccess ||
+        cudaMemcpyAsync(Ut, ut.data(), sizeof(float) * ut.size(), cudaMemcpyHostToDevice, w.st) != cudaSuccess)
+        return bad(PC_ERR_CUDA, "copy of the factors failed");
+    if (gemm_rm(w.hb, false, true, m, (int)N, r, Ut, l, Y, l, v, (int)N) != CUBLAS_STATUS_SUCCESS)
+        return bad(PC_ERR_CUDA, "cuBLAS product for v failed");
+    if (cudaStreamSynchronize(w.st) != cudaSuccess) return bad(PC_ERR_CUDA, "stream synchronisation failed");
+    if (sing)
+        for (int i = 0; i < l; ++i) sing[i] = i < r ? sv[i] : 0.0;
+    cleanup();
+    return PC_OK;
+}
 
 }  // extern "C"
