@@ -120,6 +120,30 @@ def assembly_flops(op, phases=8):
     return total
 
 
+def _csrc_sha():
+    """SHA-256 of the CUDA sources (names and contents), to tell whether a profile still applies."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_2005_09870_gb300", "csrc")
+    hsh = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        hsh.update(f.encode())
+        hsh.update(open(os.path.join(d, f), "rb").read())
+    return hsh.hexdigest()
+
+
+def profile_traffic(kernels):
+    """DRAM bytes (read + write) per launch of the named kernels of the 256^2 workload, summed,
+    from the committed ncu summary profiles/traffic_c2.json; None when that capture was taken on
+    other CUDA sources than the ones built now, or is missing."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "profiles", "traffic_c2.json")))
+        if d.get("csrc_sha256") != _csrc_sha():
+            return None
+        return int(sum(d["kernels"][k]["dram_bytes_per_launch"] for k in kernels))
+    except Exception:
+        return None
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
@@ -717,20 +741,22 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_fista:
         fista = run_fista(pw, g, op, rank, dev, stream, args.fista_iters)
 
-    # ---------------- roofline of the dominant kernel (fused row assembly) ----------------
+    # ---------------- rooflines: stage 1 of the assembly (the metric's kernels) and the backward ----------------
     peak, peak_kind = _peaks()
     alg_bytes = nnz * (4 + 2) + op.m * op.N * 4     # Theta FP32 + BF16 written once, windows read once
     achieved = alg_bytes / (rows_ms * 1e-3) / 1e9
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "assemble_c2_traffic.json")
-    if os.path.exists(tpath):
-        try:
-            traffic = json.load(open(tpath)).get("bytes_per_launch_set")
-        except Exception:
-            traffic = None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel": "stage 1 of the assembly (window sums + localized transforms)",
+            "traffic": profile_traffic(["k_s_rows", "k_assemble_batch"]), "alg_bytes": alg_bytes,
+            "kernel": "stage 1 of the assembly: k_s_rows (window sums) + k_assemble_batch (localized transforms)",
             "peak_kind": peak_kind}
+    # backward: dL/dTheta read once, dL/dv written and the windows read once, dL/du written
+    K = (2 * op.r + 1) ** op.d
+    bwd_alg = 4 * nnz + 8 * op.m * op.N + 4 * op.m * K
+    bwd_gbs = bwd_alg / (bwd_ms * 1e-3) / 1e9
+    roof_bwd = {"bound": "hbm", "achieved": bwd_gbs, "peak": peak, "unit": "GB/s", "frac": bwd_gbs / peak,
+                "traffic": profile_traffic(["k_backward_queue", "k_bwd_dv4", "k_bwd_dF_wl"]), "alg_bytes": bwd_alg,
+                "kernel": "pc_backward: k_backward_queue (adjoint rows) + k_bwd_dv4 (dL/dv) + k_bwd_dF_wl (dL/dF) "
+                          "+ the small adjoint of the filtered wavelets", "peak_kind": peak_kind}
     flops = assembly_flops(op) if op.d == 2 else None
     roof_fp32 = None
     if flops:
@@ -775,6 +801,7 @@ def run_ours(args, rank, world, local_rank):
             "roofline_fp32": roof_fp32,
             "phases_ms": {"prepare": prep_ms, "assemble_rows": rows_ms, "apply_16rhs": apply_ms, "backward": bwd_ms},
             "roofline": roof,
+            "roofline_bwd": roof_bwd,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": e2e_ms},

@@ -382,10 +382,11 @@ __global__ void k_transpose_F(const __grid_constant__ BwdDev bd, const float* __
 }
 
 // Phase 2 on the term-contiguous copy: 4 * NQ terms per thread, read as NQ float4 per translate.
-// Phase 2 (FP32).  One thread per pixel and 4 NQ terms (blockIdx.x = tile column * zc + term
-// group: the zc blocks of a 16 x 16 pixel tile are adjacent in launch order, so that they run
-// together and share the tile's dL/ds reads through L2).
-template <int NQ>
+// Phase 2 (FP32).  One thread per pixel and 4 NQ terms; a block covers a TX x (256 / TX) pixel
+// tile (TX consecutive pixels along axis 1 per block row, so that a warp's dL/ds and F loads are
+// contiguous), and blockIdx.x = tile column * zc + term group: the zc blocks of a tile are
+// adjacent in launch order, so that they run together and share the tile's dL/ds reads through L2.
+template <int NQ, int TX>
 __global__ void __launch_bounds__(256) k_bwd_dv4(const __grid_constant__ BwdDev bd, const float* __restrict__ FT,
                                                  const float* __restrict__ S, float* __restrict__ dv)
 {
@@ -393,7 +394,7 @@ __global__ void __launch_bounds__(256) k_bwd_dv4(const __grid_constant__ BwdDev 
     const int zc = (bd.m + 4 * NQ - 1) / (4 * NQ);
     const int tx = blockIdx.x / zc;
     const int kbase = (blockIdx.x - tx * zc) * 4 * NQ;
-    const int x0 = blockIdx.y * 16 + threadIdx.y, x1 = tx * 16 + threadIdx.x;
+    const int x0 = blockIdx.y * (256 / TX) + threadIdx.y, x1 = tx * TX + threadIdx.x;
     if (x0 >= n || x1 >= n) return;
     float4 acc[NQ];
 #pragma unroll

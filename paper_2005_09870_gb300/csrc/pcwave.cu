@@ -964,10 +964,14 @@ pc_status backward_core(pc_op* h, const T* G, T* du, T* dv, T* dF, T* dG, cudaSt
             int maxRR = 0;
             for (int b = 0; b < h->nb; ++b) maxRR = std::max(maxRR, h->bd.band[b].R0 * h->bd.band[b].R1);
             k_transpose_F<<<dim3((maxRR + 255) / 256, h->nb), 256, 0, st>>>(h->bd, (const float*)h->F_d, FT);
-            // 8 terms per thread, 16 x 16 pixel tiles
+            // 8 terms per thread, 32 x 8 pixel tiles (16 x 16 below 32 pixels a side)
             constexpr int NQ = 2;
-            k_bwd_dv4<NQ><<<dim3((D.n + 15) / 16 * ((D.m + 4 * NQ - 1) / (4 * NQ)), (D.n + 15) / 16, 1),
-                                dim3(16, 16), 0, st>>>(h->bd, FT, S, dv);
+            const int zc = (D.m + 4 * NQ - 1) / (4 * NQ);
+            if (D.n >= 32)
+                k_bwd_dv4<NQ, 32><<<dim3((D.n + 31) / 32 * zc, (D.n + 7) / 8, 1), dim3(32, 8), 0, st>>>(h->bd, FT, S, dv);
+            else
+                k_bwd_dv4<NQ, 16><<<dim3((D.n + 15) / 16 * zc, (D.n + 15) / 16, 1), dim3(16, 16), 0, st>>>(h->bd, FT, S,
+                                                                                                       dv);
             count_launch(2);
         } else {
             k_bwd_dv<T, KC><<<dim3((D.n + 15) / 16, (D.n + 15) / 16, (D.m + KC - 1) / KC), dim3(16, 16), 0, st>>>(
