@@ -746,8 +746,8 @@ def run_ours(args, rank, world, local_rank):
     alg_bytes = nnz * (4 + 2) + op.m * op.N * 4     # Theta FP32 + BF16 written once, windows read once
     achieved = alg_bytes / (rows_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": profile_traffic(["k_s_rows", "k_assemble_batch"]), "alg_bytes": alg_bytes,
-            "kernel": "stage 1 of the assembly: k_s_rows (window sums) + k_assemble_batch (localized transforms)",
+            "traffic": profile_traffic(["k_s_tiles", "k_assemble_batch"]), "alg_bytes": alg_bytes,
+            "kernel": "stage 1 of the assembly: k_s_tiles (window sums) + k_assemble_batch (localized transforms)",
             "peak_kind": peak_kind}
     # backward: dL/dTheta read once, dL/dv written and the windows read once, dL/du written
     K = (2 * op.r + 1) ** op.d

@@ -1,6 +1,6 @@
 // 2-D row assembly and its adjoint, register-blocked.
 //
-// Stage 1 (k_s_rows, one launch over all rows): s(q) = sum_k v_k(g + q) F_{k,b}(q) over the
+// Stage 1 (k_s_tiles, one launch over all rows): s(q) = sum_k v_k(g + q) F_{k,b}(q) over the
 // windows nonzero at each pixel, compensated over k (FP32), into the s scratch.
 // Stage 2, one stored row per thread group (gt threads; several groups per CTA): the row's s,
 //   level 1 (or LL of level k0 by the scaling filter phi_{k0} at stride 2^k0 for rows whose
@@ -227,94 +227,116 @@ __device__ __forceinline__ void write_win(const OpDev<T>& op, const T* Zb, int p
 // written to op.sf + Soff[b] + rl * RR + q.  One warp per stored row (canonical order, eight
 // rows per CTA); its lanes walk the region positions.  Indices are 32-bit: a region, a
 // window list (slots x N) and a band's F stay far below 2^31 elements.
-// PX region positions of one lane with NS window-list slots (NS = the operator's slot count):
-// every slot and F load unconditional (unused slots hold (k, v) = (0, 0) and positions past the
-// region are clamped to its last one, so every address is valid), then the compensated sums.
-template <typename T, int NS, int PX>
-__device__ __forceinline__ void s_positions(const WSlot<T>* __restrict__ wl, int N, const T* __restrict__ F0, int RR,
-                                            const int (&pix)[PX], int q, T* __restrict__ out)
+// Tiles of the window sums: T consecutive rows of one band along axis 1 (same l0).  Their
+// regions, shifted by 2^j from row to row, cover a union of R0 x (R1 + (T - 1) 2^j) pixels
+// (axis 1 unwrapped: a pixel the union meets twice counts twice); a block walks the union once,
+// loads each pixel's window list once and produces s for every row of the tile whose region
+// holds the pixel.
+struct STiles {
+    int T;                    // rows per tile along axis 1
+    int tile_off[MAXB + 1];   // first tile of each band (bands in canonical order)
+};
+
+// s of the rows t in [t_lo, t_hi] of a tile at one union pixel, with NS window-list slots: the
+// slots are loaded once, then for each row its F values (all loads first) and the compensated
+// sum over the slots.
+template <typename T, int NS>
+__device__ __forceinline__ void s_tile_pixel(const WSlot<T>* __restrict__ wp, int N, const T* __restrict__ F0, int RR,
+                                             int qbase, int sq, int t_lo, int t_hi, T* __restrict__ out)
 {
-    WSlot<T> w[PX][NS];
+    WSlot<T> w[NS];
 #pragma unroll
-    for (int u = 0; u < PX; ++u)
+    for (int sl = 0; sl < NS; ++sl) w[sl] = load_slot(wp + sl * N);
+    for (int t = t_lo; t <= t_hi; ++t) {
+        const int q = qbase - t * sq;  // position in row t's region
+        T f[NS];
 #pragma unroll
-        for (int sl = 0; sl < NS; ++sl) w[u][sl] = load_slot(wl + (pix[u] + sl * N));
-    T f[PX][NS];
+        for (int sl = 0; sl < NS; ++sl) f[sl] = __ldg(F0 + ((int)w[sl].k * RR + q));
+        T acc = w[0].v * f[0], c = T(0);
 #pragma unroll
-    for (int u = 0; u < PX; ++u) {
-        const int qu = min(q + 32 * u, RR - 1);
-#pragma unroll
-        for (int sl = 0; sl < NS; ++sl) f[u][sl] = __ldg(F0 + ((int)w[u][sl].k * RR + qu));
-    }
-#pragma unroll
-    for (int u = 0; u < PX; ++u) {
-        T acc = w[u][0].v * f[u][0], c = T(0);
-#pragma unroll
-        for (int sl = 1; sl < NS; ++sl) kahan_add(acc, c, w[u][sl].v * f[u][sl]);
-        if (q + 32 * u < RR) out[q + 32 * u] = acc;
+        for (int sl = 1; sl < NS; ++sl) kahan_add(acc, c, w[sl].v * f[sl]);
+        out[(int64_t)t * RR + q] = acc;
     }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_s_rows(const OpDev<T>* __restrict__ opd)
+__global__ void __launch_bounds__(256) k_s_tiles(const OpDev<T>* __restrict__ opd, const __grid_constant__ STiles tl)
 {
-    constexpr int PX = 4;  // positions per lane and step, all their loads in flight together
-    __shared__ int64_t boff_s[MAXB];
+    __shared__ int b_s;
     const OpDev<T>& op = *opd;  // device copy (refreshed before each run, also inside graphs)
     const int n = op.n, nm = n - 1, nb = op.nb;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) boff_s[b] = band_info(2, n, op.L, b).off;
+    if (threadIdx.x < 32) {
+        // band of the tile: the last band whose first tile is at or before it
+        const int lane = threadIdx.x;
+        const unsigned m1 = __ballot_sync(0xffffffffu, lane < nb && tl.tile_off[lane] <= (int)blockIdx.x);
+        const unsigned m2 =
+            __ballot_sync(0xffffffffu, lane + 32 < nb && tl.tile_off[min(lane + 32, MAXB)] <= (int)blockIdx.x);
+        if (lane == 0) b_s = m2 ? 63 - __clz(m2) : 31 - __clz(m1);
+    }
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int64_t srow = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (srow >= op.N) return;
-    // band of the row: the last band that starts at or before it (offsets increase with b)
-    const unsigned m1 = __ballot_sync(0xffffffffu, lane < nb && boff_s[lane] <= srow);
-    const unsigned m2 = __ballot_sync(0xffffffffu, lane + 32 < nb && boff_s[min(lane + 32, MAXB - 1)] <= srow);
-    const int b = m2 ? 63 - __clz(m2) : 31 - __clz(m1);
+    const int b = b_s;
     const Band Bo = band_info(2, n, op.L, b);
-    const int rl = (int)(srow - Bo.off);
-    const int lg = log2i(Bo.nj);
-    const Range R0 = region0(Bo.j, Bo.e0, rl >> lg, op.r, op.Lf, n);
-    const Range R1 = region0(Bo.j, Bo.e1, rl & (Bo.nj - 1), op.r, op.Lf, n);
-    const int g0 = pmod(R0.lo, n), g1 = pmod(R1.lo, n), c1 = R1.cnt;
-    const int RR = R0.cnt * c1;
+    const int nt1 = (Bo.nj + tl.T - 1) / tl.T;
+    const int tb = blockIdx.x - tl.tile_off[b];
+    const int l0 = tb / nt1, l1s = (tb - l0 * nt1) * tl.T;
+    const int nr = min(tl.T, Bo.nj - l1s);
+    const Range R0 = region0(Bo.j, Bo.e0, l0, op.r, op.Lf, n);
+    const Range R1 = region0(Bo.j, Bo.e1, l1s, op.r, op.Lf, n);  // the tile's first row
+    const int lg = Bo.j, sq = 1 << lg;
+    const int c1 = R1.cnt, RR = R0.cnt * c1;
+    const bool full1 = R1.full;
+    const int U1 = full1 ? n : c1 + (nr - 1) * sq;
+    const int g0 = pmod(R0.lo, n), g1 = pmod(R1.lo, n);
     const T* F0 = op.F + op.Foff[b];
-    T* out = op.sf + op.Soff[b] + (int64_t)rl * RR;
+    T* out = op.sf + op.Soff[b] + ((int64_t)l0 * Bo.nj + l1s) * RR;
     const WSlot<T>* wl = reinterpret_cast<const WSlot<T>*>(op.wl);
     const int S = op.wl_slots, N = (int)op.N;
-    // (qa, qb) = (q0, q1) of position q, advanced by 32 positions at a time
-    const float inv = 1.0f / (float)c1;
-    int qa = div_small(lane, inv), qb = lane - qa * c1;
-    const int da = div_small(32, inv), db = 32 - da * c1;
-    for (int q = lane; q < RR; q += 32 * PX) {
-        int pix[PX];
-#pragma unroll
-        for (int u = 0; u < PX; ++u) {
-            pix[u] = ((g0 + qa) & nm) * n + ((g1 + qb) & nm);
-            qa += da;
-            qb += db;
-            if (qb >= c1) {
-                qb -= c1;
-                ++qa;
+    const int tot = R0.cnt * U1;
+    const float inv = 1.0f / (float)U1;
+    int a = div_small(threadIdx.x, inv), c = threadIdx.x - a * U1;
+    const int da = div_small(blockDim.x, inv), dc = blockDim.x - da * U1;
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+        const int pix = ((g0 + a) & nm) * n + ((g1 + c) & nm);
+        // rows of the tile whose region holds union column c: c - t 2^j in [0, c1)
+        int t_lo, t_hi, qbase;
+        if (full1) {
+            // every row covers every pixel; row t's column is (c - t 2^j) mod n, handled row by row
+            for (int t = 0; t < nr; ++t) {
+                const int q = a * c1 + ((c - t * sq) & nm);
+                T acc = T(0), cc = T(0);
+                for (int sl = 0; sl < S; ++sl) {
+                    const WSlot<T> w = load_slot(wl + (pix + sl * N));
+                    if (w.v != T(0)) kahan_add(acc, cc, w.v * __ldg(F0 + ((int)w.k * RR + q)));
+                }
+                out[(int64_t)t * RR + q] = acc;
+            }
+        } else {
+            t_lo = max(0, -((-(c - c1 + 1)) >> lg));
+            t_hi = min(nr - 1, c >> lg);
+            qbase = a * c1 + c;
+            const WSlot<T>* wp = wl + pix;
+            switch (S) {
+                case 1: s_tile_pixel<T, 1>(wp, N, F0, RR, qbase, sq, t_lo, t_hi, out); break;
+                case 2: s_tile_pixel<T, 2>(wp, N, F0, RR, qbase, sq, t_lo, t_hi, out); break;
+                case 3: s_tile_pixel<T, 3>(wp, N, F0, RR, qbase, sq, t_lo, t_hi, out); break;
+                case 4: s_tile_pixel<T, 4>(wp, N, F0, RR, qbase, sq, t_lo, t_hi, out); break;
+                default:
+                    for (int t = t_lo; t <= t_hi; ++t) {
+                        const int q = qbase - t * sq;
+                        T acc = T(0), cc = T(0);
+                        for (int sl = 0; sl < S; ++sl) {
+                            const WSlot<T> w = load_slot(wp + sl * N);
+                            if (w.v != T(0)) kahan_add(acc, cc, w.v * __ldg(F0 + ((int)w.k * RR + q)));
+                        }
+                        out[(int64_t)t * RR + q] = acc;
+                    }
             }
         }
-        switch (S) {
-            case 1: s_positions<T, 1, PX>(wl, N, F0, RR, pix, q, out); break;
-            case 2: s_positions<T, 2, PX>(wl, N, F0, RR, pix, q, out); break;
-            case 3: s_positions<T, 3, PX>(wl, N, F0, RR, pix, q, out); break;
-            case 4: s_positions<T, 4, PX>(wl, N, F0, RR, pix, q, out); break;
-            default:
-#pragma unroll
-                for (int u = 0; u < PX; ++u) {
-                    if (q + 32 * u < RR) {
-                        T acc = T(0), c = T(0);
-                        for (int sl = 0; sl < S; ++sl) {
-                            const WSlot<T> w = load_slot(wl + (pix[u] + sl * N));
-                            if (w.v != T(0)) kahan_add(acc, c, w.v * __ldg(F0 + ((int)w.k * RR + q + 32 * u)));
-                        }
-                        out[q + 32 * u] = acc;
-                    }
-                }
+        a += da;
+        c += dc;
+        if (c >= U1) {
+            c -= U1;
+            ++a;
         }
     }
 }
@@ -481,7 +503,7 @@ __device__ __forceinline__ void asm2d_row(const OpDev<T>& op, const AsmCfg& cfg,
     T* const arena_end = arena + cfg.arena;
     const int A = cfg.arena;
     const Row2 R = row2_setup(op, cfg.b, rl);
-    if (!row2_meta(op, R, cfg.b, meta, tid, gt, gid, false)) return;  // s comes from k_s_rows: no term list
+    if (!row2_meta(op, R, cfg.b, meta, tid, gt, gid, false)) return;  // s comes from k_s_tiles: no term list
     const int k0 = R.k0;
     const int lenk = (k0 > 0) ? wav_len(k0, Lf) : 0;
 
@@ -539,7 +561,7 @@ __device__ __forceinline__ void asm2d_row(const OpDev<T>& op, const AsmCfg& cfg,
             const int nr = first ? min(B, A0.cnt - r0) : p0.cnt;
             if (first) {
                 if (bi == 0 && !lo_only) zero_gaps<T, 2 * LF - 2>(arena, mg, B, A1.cnt, XP, tid, gt);
-                // s rows computed for all rows beforehand (k_s_rows), copied asynchronously
+                // s rows computed for all rows beforehand (k_s_tiles), copied asynchronously
                 // (cp.async: no register round trip, every copy of the thread in flight at once)
                 const T* sr = op.sf + op.Soff[cfg.b] + (int64_t)rl * RR + r0 * A1.cnt;
                 const int tot = nr * A1.cnt;

@@ -66,7 +66,7 @@ struct pc_op {
     void* dF_d = nullptr;  // backward scratch: dL/dF
     void* dG_d = nullptr;  // backward scratch: dL/dG
     void* S_d = nullptr;   // 2-D: stage-1 values s of every row (assembly), then dL/ds (backward)
-    void* od_d = nullptr;   // device copy of the operator descriptor for k_s_rows
+    void* od_d = nullptr;   // device copy of the operator descriptor for k_s_tiles
     unsigned long long* amask_d = nullptr;  // backward scratch: active terms per row (2-D)
     int64_t Stotal = 0;
     int64_t FTtotal = 0;  // term-contiguous copy of F (FP32 backward), after dG in its scratch
@@ -590,7 +590,7 @@ pc_status prepare_t(pc_op* h, cudaStream_t st)
     return PC_OK;
 }
 
-// Stage 1 of every 2-D row (k_s_rows) into the s scratch, before the row kernels.
+// Stage 1 of every 2-D row (k_s_tiles) into the s scratch, before the row kernels.
 template <typename T>
 pc_status s_rows_t(pc_op* h, const OpDev<T>& od, cudaStream_t st, const OpDev<T>* od_dev = nullptr)
 {
@@ -599,7 +599,17 @@ pc_status s_rows_t(pc_op* h, const OpDev<T>& od, cudaStream_t st, const OpDev<T>
         PC_CUDA(h, cudaMemcpyAsync(h->od_d, &od, sizeof(od), cudaMemcpyHostToDevice, st));
         od_dev = (const OpDev<T>*)h->od_d;
     }
-    k_s_rows<T><<<(int)((h->N + 7) / 8), 256, 0, st>>>(od_dev);
+    // tiles of 8 consecutive rows along axis 1 (fewer in bands narrower than that)
+    STiles tl{};
+    tl.T = 8;
+    int tiles = 0;
+    for (int b = 0; b < h->nb; ++b) {
+        const Band B = band_info(2, h->desc.n, h->desc.levels, b);
+        tl.tile_off[b] = tiles;
+        tiles += B.nj * ((B.nj + tl.T - 1) / tl.T);
+    }
+    tl.tile_off[h->nb] = tiles;
+    k_s_tiles<T><<<tiles, 256, 0, st>>>(od_dev, tl);
     count_launch();
     PC_CUDA(h, cudaGetLastError());
     return PC_OK;
@@ -1316,7 +1326,7 @@ pc_status batch_build(pc_handle* ops, int count, cudaStream_t st, bool capture, 
         q.grid = persistent_grid(queue_kernel(q.kind), B->smem);
     }
     B->kernels_per_run = 6 * count + (int)B->groups.size();
-    for (pc_op* h : B->ops) B->kernels_per_run += (h->desc.dim == 2 && h->S_d) ? 1 : 0;  // k_s_rows
+    for (pc_op* h : B->ops) B->kernels_per_run += (h->desc.dim == 2 && h->S_d) ? 1 : 0;  // k_s_tiles
     {
         cudaEvent_t ev;
         if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) {
@@ -1733,7 +1743,7 @@ pc_status pc_create(const pc_desc* desc, const void* u, const void* v, void* str
     if (D.store_bf16 && (st = dev_alloc(h, &h->xsplit_d, sizeof(unsigned) * 16 * h->N))) return bail(st);
     if (D.dim == 2) {
         // s scratch (stage 1 of the assembly, dL/ds of the backward) and the device copy of the
-        // operator view that k_s_rows reads
+        // operator view that k_s_tiles reads
         if ((st = dev_alloc(h, &h->S_d, h->esz * h->Stotal)) ||
             (st = dev_alloc(h, &h->od_d, std::max(sizeof(OpDev<double>), sizeof(OpDev<float>)))))
             return bail(st);
