@@ -540,6 +540,27 @@ __global__ void __launch_bounds__(128) k_bwd_dF(const __grid_constant__ BwdDev b
 // Phase 3 with the per-pixel window lists: the same blocks as k_bwd_dF, but a region position
 // visits only the (at most `slots`) windows nonzero at its pixel; each thread keeps the m
 // partial sums of its position in its own column of shared memory ([m][128]).
+// Rows of one dL/dF block at one region position q: for each row, the dL/ds value and the NS
+// window-list slots of its pixel, accumulated into the thread's column of acc (acc[k * 128]).
+template <typename T, int NS>
+__device__ __forceinline__ void dF_rows(const WSlot<T>* __restrict__ wl, int N, const T* __restrict__ Sq, int RR,
+                                        int rbeg, int rend, int lgn, int njm, int lg, int p0, int p1, int nm, int n,
+                                        T* acc)
+{
+#pragma unroll 2
+    for (int rl = rbeg; rl < rend; ++rl) {
+        const int l0 = rl >> lgn, l1 = rl & njm;
+        const int pix = (((l0 << lg) + p0) & nm) * n + (((l1 << lg) + p1) & nm);
+        const T sv = __ldg(Sq + (int64_t)rl * RR);
+        WSlot<T> w[NS];
+#pragma unroll
+        for (int sl = 0; sl < NS; ++sl) w[sl] = load_slot(wl + (pix + sl * N));
+#pragma unroll
+        for (int sl = 0; sl < NS; ++sl)
+            if (w[sl].v != T(0)) acc[(int)w[sl].k * 128] += w[sl].v * sv;
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(128) k_bwd_dF_wl(const __grid_constant__ BwdDev bd, const WSlot<T>* __restrict__ wl,
                                                    int slots, const T* __restrict__ S, T* __restrict__ dF,
@@ -557,22 +578,29 @@ __global__ void __launch_bounds__(128) k_bwd_dF_wl(const __grid_constant__ BwdDe
     const int q = qb * 128 + threadIdx.x;
     if (q >= RR) return;
     const int n = bd.n, lg = B.j, m = bd.m;
-    const int64_t N = bd.N;
+    const int N = (int)bd.N;
     for (int k = 0; k < m; ++k) acc[k * 128] = T(0);
     const int q0 = q / B.R1, q1 = q - q0 * B.R1;
     const int rows = B.nj * B.nj;
     const int rbeg = cb * chunk, rend = min(rows, rbeg + chunk);
     const int lgn = log2i(B.nj);
-#pragma unroll 2
-    for (int rl = rbeg; rl < rend; ++rl) {
-        const int l0 = rl >> lgn, l1 = rl & (B.nj - 1);
-        const int gy = ((l0 << lg) + B.P0 + q0) & (n - 1), gx = ((l1 << lg) + B.P1 + q1) & (n - 1);
-        const int64_t pix = (int64_t)gy * n + gx;
-        const T sv = __ldg(S + B.Soff + (int64_t)rl * RR + q);
-        for (int sl = 0; sl < slots; ++sl) {
-            const WSlot<T> w = load_slot(wl + (int64_t)sl * N + pix);
-            if (w.v != T(0)) acc[w.k * 128] += w.v * sv;
-        }
+    const T* Sq = S + B.Soff + q;  // row rl's value at + rl * RR
+    const int p0 = B.P0 + q0, p1 = B.P1 + q1, nm = n - 1, njm = B.nj - 1;
+    switch (slots) {
+        case 1: dF_rows<T, 1>(wl, N, Sq, RR, rbeg, rend, lgn, njm, lg, p0, p1, nm, n, acc); break;
+        case 2: dF_rows<T, 2>(wl, N, Sq, RR, rbeg, rend, lgn, njm, lg, p0, p1, nm, n, acc); break;
+        case 3: dF_rows<T, 3>(wl, N, Sq, RR, rbeg, rend, lgn, njm, lg, p0, p1, nm, n, acc); break;
+        case 4: dF_rows<T, 4>(wl, N, Sq, RR, rbeg, rend, lgn, njm, lg, p0, p1, nm, n, acc); break;
+        default:
+            for (int rl = rbeg; rl < rend; ++rl) {
+                const int l0 = rl >> lgn, l1 = rl & njm;
+                const int pix = (((l0 << lg) + p0) & nm) * n + (((l1 << lg) + p1) & nm);
+                const T sv = __ldg(Sq + (int64_t)rl * RR);
+                for (int sl = 0; sl < slots; ++sl) {
+                    const WSlot<T> w = load_slot(wl + (pix + sl * N));
+                    if (w.v != T(0)) acc[(int)w.k * 128] += w.v * sv;
+                }
+            }
     }
     for (int k = 0; k < m; ++k) {
         const T a = acc[k * 128];

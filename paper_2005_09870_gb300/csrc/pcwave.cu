@@ -974,14 +974,16 @@ pc_status backward_core(pc_op* h, const T* G, T* du, T* dv, T* dF, T* dG, cudaSt
             int maxRR = 0;
             for (int b = 0; b < h->nb; ++b) maxRR = std::max(maxRR, h->bd.band[b].R0 * h->bd.band[b].R1);
             k_transpose_F<<<dim3((maxRR + 255) / 256, h->nb), 256, 0, st>>>(h->bd, (const float*)h->F_d, FT);
-            // 8 terms per thread, 32 x 8 pixel tiles (16 x 16 below 32 pixels a side)
-            constexpr int NQ = 2;
-            const int zc = (D.m + 4 * NQ - 1) / (4 * NQ);
-            if (D.n >= 32)
-                k_bwd_dv4<NQ, 32><<<dim3((D.n + 31) / 32 * zc, (D.n + 7) / 8, 1), dim3(32, 8), 0, st>>>(h->bd, FT, S, dv);
+            // 32 x 8 pixel tiles (16 x 16 below 32 pixels a side); 16 terms per thread when that
+            // still gives >= 2048 blocks (each dL/ds value is loaded once per group of terms), else 8
+            const int tiles32 = ((D.n + 31) / 32) * ((D.n + 7) / 8), zc4 = (D.m + 15) / 16, zc2 = (D.m + 7) / 8;
+            if (D.n >= 32 && D.m > 8 && tiles32 * zc4 >= 2048)
+                k_bwd_dv4<4, 32><<<dim3((D.n + 31) / 32 * zc4, (D.n + 7) / 8, 1), dim3(32, 8), 0, st>>>(h->bd, FT, S, dv);
+            else if (D.n >= 32)
+                k_bwd_dv4<2, 32><<<dim3((D.n + 31) / 32 * zc2, (D.n + 7) / 8, 1), dim3(32, 8), 0, st>>>(h->bd, FT, S, dv);
             else
-                k_bwd_dv4<NQ, 16><<<dim3((D.n + 15) / 16 * zc, (D.n + 15) / 16, 1), dim3(16, 16), 0, st>>>(h->bd, FT, S,
-                                                                                                       dv);
+                k_bwd_dv4<2, 16><<<dim3((D.n + 15) / 16 * zc2, (D.n + 15) / 16, 1), dim3(16, 16), 0, st>>>(h->bd, FT, S,
+                                                                                                      dv);
             count_launch(2);
         } else {
             k_bwd_dv<T, KC><<<dim3((D.n + 15) / 16, (D.n + 15) / 16, (D.m + KC - 1) / KC), dim3(16, 16), 0, st>>>(
