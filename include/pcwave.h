@@ -316,6 +316,46 @@ pc_status pc_lookup(pc_handle h, int64_t n, const int64_t* mu, const int64_t* la
  * for counting the launches inside a timed region. */
 int64_t pc_launch_counter(void);
 
+/* ---------------------------------------------------------------------------------------
+ * Thresholded Algorithm 1 (Section 3.2): a sparse eta-approximation of Theta.
+ *
+ * For k = 1..m: A_k = Psi^* U_k Psi (U_k: convolution with u_k), thresholded at tau_k to
+ * A~_k, times B_k = Psi^* V_k Psi (V_k = diag(v_k)), accumulated: Theta~ = sum_k A~_k B_k.
+ * Threshold: tau_k is the largest value whose discarded part D = A_k restricted to the entries
+ * |a| < tau_k has Schur bound sqrt(||D||_1 ||D||_inf) <= eps_k = eta / (m ||v_k||_inf), found
+ * by 80 bisection steps on [0, top] with top = max|A_k| (1 + 1e-15) + 1e-300 (taken outright when
+ * top itself satisfies the bound, i.e. everything is discarded; eps_k is 1e300 for v_k = 0).
+ * Since ||B_k||_2 = ||v_k||_inf (Section 5.5), ||Theta - Theta~||_2 <= eta.
+ * Theta~ is stored on the support the products can reach (Section 5.3): row mu holds the
+ * coefficients lambda whose wavelet meets the union of the supports of the wavelets kept in
+ * row mu of any A~_k (entries there may be zero).  The rows of A_k fall into 2^(levels dim)
+ * classes whose rows are translates (sub-band circulant structure), and every stage works per
+ * class: no N x N matrix is formed.
+ * --------------------------------------------------------------------------------------- */
+typedef struct pc_alg1* pc_alg1_handle;
+
+/* Runs Algorithm 1 on the device and keeps Theta~ in the handle.  desc: dim, n, levels,
+ * delta, family, m, radius as for pc_create; order must be PC_ORDER_MULT_THEN_CONV (the other
+ * order's matrix is the transpose of this one's for the flipped kernels u_k(-t)) and precision
+ * PC_FP64 (every stage in FP64); gap and store_bf16 are ignored.  u: m x (2r+1)^dim, v: m x n^dim,
+ * FP64, host or device (copied).  eta >= 0.  Synchronous on `stream`.  PC_ERR_INVALID_ARG for
+ * NULL pointers, eta < 0 or a descriptor out of range, PC_ERR_UNSUPPORTED for the other order,
+ * PC_FP32 or more than 2^16 row classes (dim * levels > 16), PC_ERR_OOM when the generator,
+ * product or Theta~ storage does not fit. */
+pc_status pc_alg1_create(const pc_desc* desc, const double* u, const double* v, double eta, void* stream,
+                         pc_alg1_handle* out);
+
+/* nnz: stored entries of Theta~; tau[m]: the thresholds; kept[m]: nonzero entries of A~_k
+ * (over the whole N x N matrix); stage_ms[4]: device time of the generator rows, the thresholds,
+ * the synthesis of the kept rows and the products.  Any pointer may be NULL. */
+pc_status pc_alg1_info(pc_alg1_handle h, int64_t* nnz, double* tau, int64_t* kept, double* stage_ms);
+
+/* Host CSR copy of Theta~ in canonical order: row_ptr (N + 1), cols and vals (nnz each; columns
+ * of a row in storage order, unsorted), caller-owned host memory.  Synchronous. */
+pc_status pc_alg1_export(pc_alg1_handle h, int64_t* row_ptr, int64_t* cols, double* vals);
+
+void pc_alg1_destroy(pc_alg1_handle h);
+
 /* Waits for `stream`, then reports any device-side fault flagged since the last call
  * (PC_ERR_DEVICE) and clears it. */
 pc_status pc_sync(pc_handle h, void* stream);

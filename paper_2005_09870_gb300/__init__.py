@@ -78,6 +78,11 @@ _sig = {
     "pc_export": ([_H, _I64P, _I64P, ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
     "pc_svir_expansion": ([_P, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P,
                            ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
+    "pc_alg1_create": ([_DP, _P, _P, ctypes.c_double, _P, ctypes.POINTER(_H)], ctypes.c_int),
+    "pc_alg1_info": ([_H, _I64P, ctypes.POINTER(ctypes.c_double), _I64P, ctypes.POINTER(ctypes.c_double)],
+                     ctypes.c_int),
+    "pc_alg1_export": ([_H, _I64P, _I64P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "pc_alg1_destroy": ([_H], None),
 }
 for _name, (_args, _ret) in _sig.items():
     _f = getattr(_lib, _name)
@@ -126,6 +131,67 @@ def pc_svir_expansion(S, m, omega, power_iters=2, stream=None):
     _check(_lib.pc_svir_expansion(_ptr(S), int(N), int(K), int(m), int(l), int(power_iters), _ptr(omega), _ptr(u),
                                   _ptr(v), sing.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream(stream)))
     return u, v, sing
+
+
+class PCAlg1:
+    """Thresholded Algorithm 1 (pc_alg1_create): Theta~ = sum_k A~_k B_k within eta of Theta in
+    the 2-norm, built on the device.  u (m x K) and v (m x N) are FP64 (numpy or CUDA tensors);
+    desc as for pc_create with order 0.  Attributes: nnz, tau (m,), kept (m,), stage_ms (4,)."""
+
+    def __init__(self, desc: pc_desc, u, v, eta: float, stream=None):
+        self.h = _H()
+        self.m = int(desc.m)
+        self.N = int(desc.n) ** int(desc.dim)
+        self._keep = []
+        _check(_lib.pc_alg1_create(ctypes.byref(desc), self._f64(u), self._f64(v), float(eta), _stream(stream),
+                                   ctypes.byref(self.h)))
+        self._keep = []
+        nnz = ctypes.c_int64()
+        self.tau = np.zeros(self.m)
+        self.kept = np.zeros(self.m, dtype=np.int64)
+        self.stage_ms = np.zeros(4)
+        _check(_lib.pc_alg1_info(self.h, ctypes.byref(nnz), self.tau.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                 self.kept.ctypes.data_as(_I64P),
+                                 self.stage_ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        self.nnz = int(nnz.value)
+
+    def _f64(self, a):
+        if hasattr(a, "is_cuda"):
+            t = _torch()
+            a = a.to(t.float64).contiguous()
+            self._keep.append(a)
+            return _ptr(a) if a.is_cuda else a.data_ptr()
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        self._keep.append(a)
+        return a.ctypes.data
+
+    def export(self):
+        """Host CSR (row_ptr, cols, vals) in canonical row order."""
+        row_ptr = np.zeros(self.N + 1, dtype=np.int64)
+        cols = np.zeros(max(self.nnz, 1), dtype=np.int64)
+        vals = np.zeros(max(self.nnz, 1), dtype=np.float64)
+        _check(_lib.pc_alg1_export(self.h, row_ptr.ctypes.data_as(_I64P), cols.ctypes.data_as(_I64P),
+                                   vals.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return row_ptr, cols[:self.nnz], vals[:self.nnz]
+
+    def dense(self):
+        """Theta~ as a dense N x N numpy array (small N)."""
+        row_ptr, cols, vals = self.export()
+        T = np.zeros((self.N, self.N))
+        rows = np.repeat(np.arange(self.N), np.diff(row_ptr))
+        np.add.at(T, (rows, cols), vals)
+        return T
+
+    def close(self):
+        if self.h:
+            _lib.pc_alg1_destroy(self.h)
+            self.h = _H()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def pc_filter_taps(family: int, delta: int):

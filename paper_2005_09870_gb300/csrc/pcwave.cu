@@ -22,6 +22,7 @@
 #include "pcw_bwd2d.cuh"
 #include "pcw_taps.h"
 #include "pcw_svir_gpu.cuh"
+#include "pcw_alg1.cuh"
 
 using namespace pcw;
 
@@ -2157,6 +2158,541 @@ pc_status pc_svir_expansion(const float* S, int64_t N, int K, int m, int l, int 
         for (int i = 0; i < l; ++i) sing[i] = i < r ? sv[i] : 0.0;
     cleanup();
     return PC_OK;
+}
+
+}  // extern "C"
+
+// =========================================================================================
+// Thresholded Algorithm 1 (Section 3.2): Theta~ = sum_k A~_k B_k, see pcw_alg1.cuh
+// =========================================================================================
+struct pc_alg1 {
+    int D = 1, n = 0, J = 0, Lf = 0, m = 0, r = 0, ncls = 0, nJ = 0, rows = 0;
+    int64_t N = 0, nnz = 0;
+    double eta = 0.0;
+    std::vector<pcw::alg1::A1Class> cls;
+    std::vector<int> band_cbase;  // first class of each canonical band
+    std::vector<double> tau;
+    std::vector<int64_t> kept;
+    double stage_ms[4] = {0, 0, 0, 0};
+    double* theta_d = nullptr;
+    std::string err = "no error";
+};
+
+namespace {
+
+using pcw::alg1::A1Class;
+using pcw::alg1::A1Params;
+using pcw::alg1::Ax;
+
+// Canonical band b of a basis with levels J: level, types (e0, e1) and the offset of its first
+// coefficient.  Band 0 is the approximation of level J; then levels J..1, in 2-D the detail
+// bands (0,1), (1,0), (1,1).
+struct BandId {
+    int j, e0, e1;
+    int64_t off;
+};
+
+std::vector<BandId> canonical_bands(int D, int n, int J)
+{
+    std::vector<BandId> out;
+    const int64_t nJ = n >> J;
+    out.push_back({J, 0, 0, 0});
+    for (int l = J; l >= 1; --l) {
+        const int64_t nl = n >> l;
+        if (D == 2) {
+            out.push_back({l, 0, 1, nl * nl});
+            out.push_back({l, 1, 0, 2 * nl * nl});
+            out.push_back({l, 1, 1, 3 * nl * nl});
+        } else {
+            out.push_back({l, 1, 0, nl});
+        }
+    }
+    (void)nJ;
+    return out;
+}
+
+// Calls f(band index, level, e0, e1, offset in the row, box0, box1) for the segments of a row.
+template <class Fn>
+void host_segments(int D, int J, const Ax (*bx)[pcw::alg1::A1_MAXJ + 1], const int* offl, Fn f)
+{
+    f(0, J, 0, 0, 0, bx[0][J], bx[1][J]);
+    int band = 1;
+    for (int l = J; l >= 1; --l) {
+        const int sz = bx[0][l].w * bx[1][l].w;
+        if (D == 2) {
+            f(band++, l, 0, 1, offl[l], bx[0][l], bx[1][l]);
+            f(band++, l, 1, 0, offl[l] + sz, bx[0][l], bx[1][l]);
+            f(band++, l, 1, 1, offl[l] + 2 * sz, bx[0][l], bx[1][l]);
+        } else {
+            f(band++, l, 1, 0, offl[l], bx[0][l], bx[1][l]);
+        }
+    }
+}
+
+struct DevBufs {
+    std::vector<void*> ptrs;
+    ~DevBufs()
+    {
+        for (void* p : ptrs)
+            if (p) cudaFree(p);
+    }
+    template <class T>
+    bool alloc(T** p, size_t count)
+    {
+        *p = nullptr;
+        if (cudaMalloc((void**)p, sizeof(T) * std::max<size_t>(count, 1)) != cudaSuccess) return false;
+        ptrs.push_back(*p);
+        return true;
+    }
+};
+
+// Launch shape of a CTA-per-item kernel with `per_cta` doubles of scratch: dynamic shared memory
+// when it fits (grid from the occupancy), else one global slab per CTA (grid of 2 per SM).
+struct ScratchPlan {
+    bool smem = true;
+    int grid = 1;
+    size_t bytes = 0;
+};
+
+template <class K>
+ScratchPlan plan_scratch(K kernel, long long items, size_t per_cta)
+{
+    ScratchPlan sp;
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    sp.bytes = per_cta * sizeof(double);
+    if (sp.bytes <= 200 * 1024) {
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.bytes);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, pcw::alg1::A1_THREADS, sp.bytes);
+        sp.grid = (int)std::min<long long>(items, (long long)std::max(per_sm, 1) * sms);
+    } else {
+        sp.smem = false;
+        sp.grid = (int)std::min<long long>(items, 2LL * sms);
+    }
+    sp.grid = std::max(sp.grid, 1);
+    return sp;
+}
+
+pc_status a1_fail(pc_alg1* h, pc_status st, const std::string& msg)
+{
+    if (h) h->err = msg;
+    return fail(nullptr, st, "pc_alg1_create: %s", msg.c_str());
+}
+
+template <int D>
+pc_status alg1_run(pc_alg1* h, const pc_desc* desc, const double* u, const double* v, cudaStream_t st)
+{
+    using namespace pcw::alg1;
+    const int n = h->n, J = h->J, Lf = h->Lf, m = h->m, r = h->r, ncls = h->ncls;
+    const int64_t N = h->N;
+    DevBufs db;
+    auto oom = [&]() { return a1_fail(h, PC_ERR_OOM, "device allocation failed"); };
+    auto cuda_err = [&](const char* what) { return a1_fail(h, PC_ERR_CUDA, std::string(what) + " failed"); };
+
+    // taps and 1-D factor tables
+    A1Params P{};
+    P.D = D;
+    P.n = n;
+    P.J = J;
+    P.Lf = Lf;
+    P.r = r;
+    P.m = m;
+    P.ncls = ncls;
+    P.nJ = h->nJ;
+    P.N = N;
+    double hh[64];
+    if (pcw::filter_taps(desc->family, desc->delta, hh) != Lf) return a1_fail(h, PC_ERR_INVALID_ARG, "filter taps");
+    for (int i = 0; i < Lf; ++i) P.h[i] = hh[i];
+    for (int i = 2 - Lf; i <= 1; ++i) P.g[i - (2 - Lf)] = (((1 - i) % 2 == 0) ? 1.0 : -1.0) * hh[1 - i];
+    std::vector<std::vector<double>> phi, psi;
+    factor_tables(hh, Lf, J, &phi, &psi);
+    std::vector<double> tab;
+    for (int j = 1; j <= J; ++j) {
+        P.tab_len[j] = (int)phi[j].size();
+        P.tab_off[j][0] = (int)tab.size();
+        tab.insert(tab.end(), phi[j].begin(), phi[j].end());
+        P.tab_off[j][1] = (int)tab.size();
+        tab.insert(tab.end(), psi[j].begin(), psi[j].end());
+    }
+
+    // classes with their generator boxes (the support of F widened by r), in canonical band order
+    const std::vector<BandId> bands = canonical_bands(D, n, J);
+    h->band_cbase.clear();
+    h->cls.clear();
+    int64_t gtotal = 0;
+    for (const BandId& b : bands) {
+        h->band_cbase.push_back((int)h->cls.size());
+        const int ph = 1 << (J - b.j);
+        for (int p0 = 0; p0 < ph; ++p0)
+            for (int p1 = 0; p1 < (D == 2 ? ph : 1); ++p1) {
+                A1Class c{};
+                c.j = b.j;
+                c.e0 = b.e0;
+                c.e1 = (D == 2) ? b.e1 : 0;
+                c.p0 = p0;
+                c.p1 = p1;
+                c.rows = h->rows;
+                const int len = ((1 << b.j) - 1) * (Lf - 1) + 1;
+                Ax b0[2];
+                const int ee[2] = {c.e0, c.e1}, pp[2] = {p0, p1};
+                for (int d = 0; d < 2; ++d) {
+                    if (d >= D) {
+                        b0[d] = {0, 1};
+                        continue;
+                    }
+                    const int s = factor_start(b.j, ee[d], pp[d], Lf);
+                    b0[d] = (len + 2 * r >= n) ? Ax{0, n} : Ax{s - r, len + 2 * r};
+                }
+                c.glen = chain(D, n, J, Lf, b0, c.g, c.goffl);
+                c.goff = gtotal;
+                gtotal += c.glen;
+                h->cls.push_back(c);
+            }
+    }
+    h->band_cbase.push_back((int)h->cls.size());
+    if ((int)h->cls.size() != ncls) return a1_fail(h, PC_ERR_INVALID_ARG, "class count");
+    P.gtotal = gtotal;
+
+    // segments: the entries of each row class grouped by column class (class of the entry's
+    // position: band, y mod 2^(J - l) per axis), and the segments of each column class
+    std::vector<int> perm((size_t)gtotal), seg_len, seg_row_off(ncls + 1, 0), seg_cc;
+    std::vector<long long> seg_start;
+    for (int c = 0; c < ncls; ++c) {
+        const A1Class& C = h->cls[c];
+        std::vector<std::pair<int, int>> keyed;
+        keyed.reserve(C.glen);
+        host_segments(D, J, C.g, C.goffl, [&](int band, int l, int, int, int off, Ax b0, Ax b1) {
+            const int ph = 1 << (J - l);
+            for (int i0 = 0; i0 < b0.w; ++i0)
+                for (int i1 = 0; i1 < b1.w; ++i1) {
+                    const int q0 = (b0.a + i0) & (ph - 1), q1 = (D == 2) ? ((b1.a + i1) & (ph - 1)) : 0;
+                    const int cc = h->band_cbase[band] + (D == 2 ? q0 * ph + q1 : q0);
+                    keyed.push_back({cc, off + i0 * b1.w + i1});
+                }
+        });
+        std::sort(keyed.begin(), keyed.end());
+        seg_row_off[c] = (int)seg_len.size();
+        for (size_t i = 0; i < keyed.size(); ++i) {
+            perm[(size_t)C.goff + i] = keyed[i].second;
+            if (i == 0 || keyed[i].first != keyed[i - 1].first) {
+                seg_cc.push_back(keyed[i].first);
+                seg_start.push_back(C.goff + (long long)i);
+                seg_len.push_back(0);
+            }
+            seg_len.back()++;
+        }
+    }
+    const int nseg = (int)seg_len.size();
+    seg_row_off[ncls] = nseg;
+    std::vector<int> colseg_off(ncls + 1, 0), colseg(nseg);
+    for (int s = 0; s < nseg; ++s) colseg_off[seg_cc[s] + 1]++;
+    for (int c = 0; c < ncls; ++c) colseg_off[c + 1] += colseg_off[c];
+    {
+        std::vector<int> fill(colseg_off.begin(), colseg_off.end() - 1);
+        for (int s = 0; s < nseg; ++s) colseg[fill[seg_cc[s]]++] = s;
+    }
+
+    // device buffers
+    double *tab_d, *u_d, *v_d, *G_d, *segsum_d, *st_d, *vmax_d, *amax_d;
+    A1Class* cls_d;
+    int *perm_d, *seglen_d, *segrow_d, *colo_d, *cols_d, *done_d, *rbox_d;
+    long long *segst_d, *kept_d;
+    const int K = (D == 2) ? (2 * r + 1) * (2 * r + 1) : 2 * r + 1;
+    if (!db.alloc(&tab_d, tab.size()) || !db.alloc(&cls_d, ncls) || !db.alloc(&u_d, (size_t)m * K) ||
+        !db.alloc(&v_d, (size_t)m * N) || !db.alloc(&G_d, (size_t)m * gtotal) || !db.alloc(&perm_d, gtotal) ||
+        !db.alloc(&seglen_d, nseg) || !db.alloc(&segrow_d, ncls + 1) || !db.alloc(&colo_d, ncls + 1) ||
+        !db.alloc(&cols_d, nseg) || !db.alloc(&segst_d, nseg) || !db.alloc(&segsum_d, (size_t)m * nseg) ||
+        !db.alloc(&st_d, 6 * (size_t)m) || !db.alloc(&done_d, m) || !db.alloc(&vmax_d, m) || !db.alloc(&amax_d, m) ||
+        !db.alloc(&kept_d, (size_t)m * ncls) || !db.alloc(&rbox_d, 4 * (size_t)ncls))
+        return oom();
+    if (cudaMemcpyAsync(tab_d, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, st) ||
+        cudaMemcpyAsync(cls_d, h->cls.data(), sizeof(A1Class) * ncls, cudaMemcpyHostToDevice, st) ||
+        cudaMemcpyAsync(u_d, u, sizeof(double) * m * K, cudaMemcpyDefault, st) ||
+        cudaMemcpyAsync(v_d, v, sizeof(double) * m * N, cudaMemcpyDefault, st) ||
+        cudaMemcpyAsync(perm_d, perm.data(), sizeof(int) * gtotal, cudaMemcpyHostToDevice, st) ||
+        cudaMemcpyAsync(seglen_d, seg_len.data(), sizeof(int) * nseg, cudaMemcpyHostToDevice, st) ||
+        cudaMemcpyAsync(segrow_d, seg_row_off.data(), sizeof(int) * (ncls + 1), cudaMemcpyHostToDevice, st) ||
+        cudaMemcpyAsync(colo_d, colseg_off.data(), sizeof(int) * (ncls + 1), cudaMemcpyHostToDevice, st) ||
+        cudaMemcpyAsync(cols_d, colseg.data(), sizeof(int) * nseg, cudaMemcpyHostToDevice, st) ||
+        cudaMemcpyAsync(segst_d, seg_start.data(), sizeof(long long) * nseg, cudaMemcpyHostToDevice, st))
+        return cuda_err("upload");
+    P.cls = cls_d;
+    P.tab = tab_d;
+    P.u = u_d;
+    P.v = v_d;
+    P.G = G_d;
+
+    cudaEvent_t ev[5];
+    for (auto& e : ev) cudaEventCreate(&e);
+    struct EvGuard {
+        cudaEvent_t* e;
+        ~EvGuard()
+        {
+            for (int i = 0; i < 5; ++i) cudaEventDestroy(e[i]);
+        }
+    } evg{ev};
+    cudaEventRecord(ev[0], st);
+
+    // stage 1: generator rows (scratch: two level buffers, the work buffer, factor samples)
+    {
+        long long sA = 1, sT = 1, sR = 1;
+        for (const A1Class& C : h->cls) {
+            for (int l = 0; l <= J; ++l) sA = std::max<long long>(sA, (long long)C.g[0][l].w * C.g[1][l].w);
+            for (int l = 0; l < J; ++l) sT = std::max<long long>(sT, 2LL * C.g[0][l].w * C.g[1][l + 1].w);
+            sT = std::max<long long>(sT, (long long)(2 * r + 1) * C.g[1][0].w);
+            sR = std::max<long long>(sR, C.g[0][0].w + C.g[1][0].w + 4LL * r);
+        }
+        P.sA = sA;
+        P.sT = sT;
+        P.sR = sR;
+        const long long items = (long long)ncls * m;
+        const ScratchPlan sp = plan_scratch(k_a1_generators<D>, items, 2 * sA + sT + sR);
+        double* slab = nullptr;
+        if (!sp.smem && !db.alloc(&slab, (size_t)sp.grid * (2 * sA + sT + sR))) return oom();
+        k_a1_generators<D><<<sp.grid, A1_THREADS, sp.smem ? sp.bytes : 0, st>>>(P, slab);
+        count_launch();
+        k_a1_absmax<<<m, 256, 0, st>>>(v_d, N, N, vmax_d);
+        k_a1_absmax<<<m, 256, 0, st>>>(G_d, gtotal, gtotal, amax_d);
+        count_launch(2);
+        if (cudaGetLastError() != cudaSuccess) return cuda_err("generator launch");
+    }
+    cudaEventRecord(ev[1], st);
+
+    // stage 2: thresholds by bisection on the Schur bound (the rule of the oracle's reading)
+    std::vector<double> vmax(m), amax(m), eps(m), top(m);
+    if (cudaMemcpyAsync(vmax.data(), vmax_d, sizeof(double) * m, cudaMemcpyDeviceToHost, st) ||
+        cudaMemcpyAsync(amax.data(), amax_d, sizeof(double) * m, cudaMemcpyDeviceToHost, st) ||
+        cudaStreamSynchronize(st))
+        return cuda_err("generator stage");
+    for (int k = 0; k < m; ++k) {
+        eps[k] = vmax[k] > 0.0 ? h->eta / (m * vmax[k]) : 1e300;
+        top[k] = amax[k] * (1.0 + 1e-15) + 1e-300;
+    }
+    double *eps_d = st_d, *top_d = st_d + m, *lo_d = st_d + 2 * m, *hi_d = st_d + 3 * m, *tq_d = st_d + 4 * m,
+           *tau_d = st_d + 5 * m;
+    if (cudaMemcpyAsync(eps_d, eps.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st) ||
+        cudaMemcpyAsync(top_d, top.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st) ||
+        cudaMemcpyAsync(tq_d, top.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st) ||
+        cudaMemsetAsync(done_d, 0, sizeof(int) * m, st))
+        return cuda_err("threshold set-up");
+    {
+        const int last = 80;
+        int dev = 0, sms = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int grid = (int)std::min<long long>((long long)ncls * m, 8LL * sms);
+        for (int step = 0; step <= last; ++step) {
+            k_a1_segsum<<<grid, A1_THREADS, 0, st>>>(P, perm_d, segst_d, seglen_d, segrow_d, nseg, tq_d, segsum_d);
+            k_a1_bisect<<<m, 256, 0, st>>>(ncls, nseg, segrow_d, colo_d, cols_d, segsum_d, eps_d, top_d, lo_d, hi_d,
+                                           tq_d, tau_d, done_d, step, last);
+            count_launch(2);
+        }
+        if (cudaGetLastError() != cudaSuccess) return cuda_err("threshold launch");
+    }
+    P.tau = tau_d;
+    h->tau.assign(m, 0.0);
+    std::vector<int> rbox_init(4 * (size_t)ncls);
+    for (int c = 0; c < ncls; ++c) {
+        rbox_init[4 * c] = rbox_init[4 * c + 2] = INT_MAX;
+        rbox_init[4 * c + 1] = rbox_init[4 * c + 3] = INT_MIN;
+    }
+    if (cudaMemcpyAsync(rbox_d, rbox_init.data(), sizeof(int) * rbox_init.size(), cudaMemcpyHostToDevice, st))
+        return cuda_err("support set-up");
+    {
+        const int grid = (int)std::min<long long>((long long)ncls * m, 1024);
+        k_a1_support<D><<<grid, A1_THREADS, 0, st>>>(P, kept_d, rbox_d);
+        count_launch();
+        if (cudaGetLastError() != cudaSuccess) return cuda_err("support launch");
+    }
+    std::vector<long long> keptc((size_t)m * ncls);
+    std::vector<int> rbox(4 * (size_t)ncls);
+    if (cudaMemcpyAsync(h->tau.data(), tau_d, sizeof(double) * m, cudaMemcpyDeviceToHost, st) ||
+        cudaMemcpyAsync(keptc.data(), kept_d, sizeof(long long) * keptc.size(), cudaMemcpyDeviceToHost, st) ||
+        cudaMemcpyAsync(rbox.data(), rbox_d, sizeof(int) * rbox.size(), cudaMemcpyDeviceToHost, st) ||
+        cudaStreamSynchronize(st))
+        return cuda_err("threshold stage");
+    cudaEventRecord(ev[2], st);
+
+    // product boxes: R per class (the union of the kept supports, or the period), its chain
+    h->kept.assign(m, 0);
+    int64_t ftotal = 0, ttotal = 0;
+    long long sA = 1, sT = 1;
+    for (int c = 0; c < ncls; ++c) {
+        A1Class& C = h->cls[c];
+        long long any = 0;
+        for (int k = 0; k < m; ++k) {
+            any += keptc[(size_t)k * ncls + c];
+            h->kept[k] += keptc[(size_t)k * ncls + c] * h->rows;
+        }
+        if (!any) {
+            C.rsize = C.tlen = 0;
+            C.foff = ftotal;
+            C.toff = ttotal;
+            continue;
+        }
+        Ax b0[2];
+        for (int d = 0; d < 2; ++d) {
+            if (d >= D) {
+                b0[d] = {0, 1};
+                continue;
+            }
+            const long long lo = rbox[4 * c + 2 * d], hi = rbox[4 * c + 2 * d + 1];
+            b0[d] = (hi - lo + 1 >= n) ? Ax{0, n} : Ax{(int)lo, (int)(hi - lo + 1)};
+        }
+        C.tlen = chain(D, n, J, Lf, b0, C.c, C.coffl);
+        C.rsize = b0[0].w * b0[1].w;
+        C.foff = ftotal;
+        C.toff = ttotal;
+        ftotal += (int64_t)m * C.rsize;
+        ttotal += (int64_t)h->rows * C.tlen;
+        for (int l = 0; l <= J; ++l) sA = std::max<long long>(sA, (long long)C.c[0][l].w * C.c[1][l].w);
+        for (int l = 0; l < J; ++l) sT = std::max<long long>(sT, 2LL * C.c[0][l].w * C.c[1][l + 1].w);
+    }
+    h->nnz = ttotal;
+    double* Fb_d;
+    if (!db.alloc(&Fb_d, ftotal)) return oom();
+    if (cudaMalloc(&h->theta_d, sizeof(double) * std::max<int64_t>(ttotal, 1)) != cudaSuccess) {
+        h->theta_d = nullptr;
+        return oom();
+    }
+    if (cudaMemcpyAsync(cls_d, h->cls.data(), sizeof(A1Class) * ncls, cudaMemcpyHostToDevice, st))
+        return cuda_err("class upload");
+    P.Fb = Fb_d;
+    P.theta = h->theta_d;
+    P.sA = sA;
+    P.sT = sT;
+    P.sR = 0;
+
+    // stage 3: F~ per (class, term); stage 4: the rows of Theta~
+    {
+        const ScratchPlan sp = plan_scratch(k_a1_synth<D>, (long long)ncls * m, 2 * sA + sT);
+        double* slab = nullptr;
+        if (!sp.smem && !db.alloc(&slab, (size_t)sp.grid * (2 * sA + sT))) return oom();
+        k_a1_synth<D><<<sp.grid, A1_THREADS, sp.smem ? sp.bytes : 0, st>>>(P, slab);
+        count_launch();
+        if (cudaGetLastError() != cudaSuccess) return cuda_err("synthesis launch");
+    }
+    cudaEventRecord(ev[3], st);
+    {
+        const long long items = (long long)ncls * h->rows;
+        const ScratchPlan sp = plan_scratch(k_a1_product<D>, items, 2 * sA + sT);
+        double* slab = nullptr;
+        if (!sp.smem && !db.alloc(&slab, (size_t)sp.grid * (2 * sA + sT))) return oom();
+        k_a1_product<D><<<sp.grid, A1_THREADS, sp.smem ? sp.bytes : 0, st>>>(P, slab);
+        count_launch();
+        if (cudaGetLastError() != cudaSuccess) return cuda_err("product launch");
+    }
+    cudaEventRecord(ev[4], st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_err("Algorithm 1");
+    for (int i = 0; i < 4; ++i) {
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+        h->stage_ms[i] = ms;
+    }
+    return PC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pc_status pc_alg1_create(const pc_desc* desc, const double* u, const double* v, double eta, void* stream,
+                         pc_alg1_handle* out)
+{
+    if (!desc || !u || !v || !out || !(eta >= 0.0) || !std::isfinite(eta))
+        return fail(nullptr, PC_ERR_INVALID_ARG, "pc_alg1_create: NULL pointer or eta not finite and >= 0");
+    *out = nullptr;
+    const pc_desc& d = *desc;
+    if ((d.dim != 1 && d.dim != 2) || d.n < 2 || (d.n & (d.n - 1)) || d.levels < 1 ||
+        d.levels > pcw::alg1::A1_MAXJ || (d.n >> d.levels) < 1 || d.delta < 1 || d.delta > 10 || d.m < 1 ||
+        d.m > 256 || d.radius < 0 || 2 * d.radius + 1 > d.n || (d.family != 0 && d.family != 1))
+        return fail(nullptr, PC_ERR_INVALID_ARG, "pc_alg1_create: descriptor out of range");
+    if (d.order != PC_ORDER_MULT_THEN_CONV)
+        return fail(nullptr, PC_ERR_UNSUPPORTED,
+                    "pc_alg1_create: only the paper's order (the other is the transpose with flipped kernels)");
+    if (d.precision != PC_FP64) return fail(nullptr, PC_ERR_UNSUPPORTED, "pc_alg1_create: FP64 only");
+    if (d.dim * d.levels > 16) return fail(nullptr, PC_ERR_UNSUPPORTED, "pc_alg1_create: more than 2^16 classes");
+    pc_alg1* h = new (std::nothrow) pc_alg1;
+    if (!h) return fail(nullptr, PC_ERR_OOM, "pc_alg1_create: host allocation failed");
+    h->D = d.dim;
+    h->n = d.n;
+    h->J = d.levels;
+    h->Lf = 2 * d.delta;
+    h->m = d.m;
+    h->r = d.radius;
+    h->nJ = d.n >> d.levels;
+    h->rows = (d.dim == 2) ? h->nJ * h->nJ : h->nJ;
+    h->ncls = 1 << (d.dim * d.levels);
+    h->N = (d.dim == 2) ? (int64_t)d.n * d.n : d.n;
+    h->eta = eta;
+    pc_status s = (d.dim == 2) ? alg1_run<2>(h, desc, u, v, (cudaStream_t)stream)
+                               : alg1_run<1>(h, desc, u, v, (cudaStream_t)stream);
+    if (s != PC_OK) {
+        pc_alg1_destroy(h);
+        return s;
+    }
+    *out = h;
+    return PC_OK;
+}
+
+pc_status pc_alg1_info(pc_alg1_handle h, int64_t* nnz, double* tau, int64_t* kept, double* stage_ms)
+{
+    if (!h) return fail(nullptr, PC_ERR_INVALID_ARG, "pc_alg1_info: NULL handle");
+    if (nnz) *nnz = h->nnz;
+    for (int k = 0; k < h->m; ++k) {
+        if (tau) tau[k] = h->tau[k];
+        if (kept) kept[k] = h->kept[k];
+    }
+    if (stage_ms)
+        for (int i = 0; i < 4; ++i) stage_ms[i] = h->stage_ms[i];
+    return PC_OK;
+}
+
+pc_status pc_alg1_export(pc_alg1_handle h, int64_t* row_ptr, int64_t* cols, double* vals)
+{
+    if (!h || !row_ptr || (h->nnz && (!cols || !vals)))
+        return fail(nullptr, PC_ERR_INVALID_ARG, "pc_alg1_export: NULL pointer");
+    std::vector<double> t((size_t)h->nnz);
+    if (h->nnz && cudaMemcpy(t.data(), h->theta_d, sizeof(double) * h->nnz, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(nullptr, PC_ERR_CUDA, "pc_alg1_export: copy failed");
+    const int D = h->D, n = h->n, J = h->J, nJ = h->nJ;
+    const std::vector<BandId> bands = canonical_bands(D, n, J);
+    int64_t pos = 0;
+    row_ptr[0] = 0;
+    int64_t mu = 0;
+    for (size_t b = 0; b < bands.size(); ++b) {
+        const int j = bands[b].j, nl = n >> j, ph = 1 << (J - j);
+        for (int x0 = 0; x0 < nl; ++x0)
+            for (int x1 = 0; x1 < (D == 2 ? nl : 1); ++x1, ++mu) {
+                const int c = h->band_cbase[b] + (D == 2 ? (x0 & (ph - 1)) * ph + (x1 & (ph - 1)) : (x0 & (ph - 1)));
+                const int t0 = x0 >> (J - j), t1 = (D == 2) ? x1 >> (J - j) : 0;
+                const A1Class& C = h->cls[c];
+                const double* row = t.data() + C.toff + (int64_t)(D == 2 ? t0 * nJ + t1 : t0) * C.tlen;
+                if (C.tlen)
+                    host_segments(D, J, C.c, C.coffl, [&](int band, int l, int, int, int off, Ax b0, Ax b1) {
+                        const int nlb = n >> l, sh = J - l;
+                        for (int i0 = 0; i0 < b0.w; ++i0)
+                            for (int i1 = 0; i1 < b1.w; ++i1) {
+                                const int y0 = (b0.a + i0 + (t0 << sh)) & (nlb - 1);
+                                const int y1 = (D == 2) ? ((b1.a + i1 + (t1 << sh)) & (nlb - 1)) : 0;
+                                cols[pos] = bands[band].off + (D == 2 ? (int64_t)y0 * nlb + y1 : y0);
+                                vals[pos] = row[off + i0 * b1.w + i1];
+                                ++pos;
+                            }
+                    });
+                row_ptr[mu + 1] = pos;
+            }
+    }
+    return PC_OK;
+}
+
+void pc_alg1_destroy(pc_alg1_handle h)
+{
+    if (!h) return;
+    if (h->theta_d) cudaFree(h->theta_d);
+    delete h;
 }
 
 }  // extern "C"

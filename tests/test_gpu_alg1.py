@@ -1,0 +1,215 @@
+"""The GPU's thresholded Algorithm 1 (Section 3.2; pc_alg1_create) against the FP64 oracle's
+dense Algorithm 1 (oracle.alg1_dense, reading R21) on the same seeded operators.
+
+Where several results are correct.  The threshold tau_k ends next to the magnitude of one entry of
+A_k; entries whose magnitudes are equal (the translates of a row, and coincident values) can fall
+on either side between two FP64 evaluations that round differently.  So every case checks:
+  - tau_k against the oracle's (relative 1e-9), the kept counts against the oracle's up to the
+    entries tied with tau (|a| within 1e-12 of tau); at eta ~ 0 the threshold falls among the
+    rounding-noise entries (below 1e-13 max|A_k|), which count as tied;
+  - Theta~ element-wise against sum_k (A_k restricted to |a| >= tau_k(GPU)) B_k built from the
+    oracle's dense A_k = Psi^T U_k Psi and B_k = Psi^T V_k Psi (numpy products), with an allowance
+    for the tied entries only: |dT| <= 1e-12 max|Theta| + sum_k |A_k on ties| |B_k|;
+  - where no entry is tied (every tie-free case), Theta~ against the oracle's own Theta~
+    element-wise at 1e-12;
+  - the guarantee ||Theta - Theta~||_2 <= eta (Section 5.5) with Theta from the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import pc_inputs as P
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pw():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2005_09870_gb300 as m
+    return m
+
+
+def _tiny(d, n, L, delta, r, m, seed=0, family=0):
+    N, K = n ** d, (2 * r + 1) ** d
+    u = P.normal(P.BASE_SEED + 100 + seed, m * K).reshape(m, K)
+    v = P.uniform(P.BASE_SEED + 200 + seed, m * N).reshape(m, N) + 0.1
+    return P.Operator("tiny", d, n, delta, L, r, u, v, gap=-1, family=family)
+
+
+def _smooth(d, n, L, delta, r, g, family=0):
+    """Gaussian kernels of growing width on hat windows (the smooth operators of Section 4.1)."""
+    u = np.stack([P.gaussian_kernel(d, r, 0.8 + 0.6 * k).reshape(-1) for k in range(g ** d)])
+    v = P.hat_windows(d, n, g)
+    return P.Operator("smooth", d, n, delta, L, r, u, v, gap=-1, family=family)
+
+
+def _one_term(op, u, v, r):
+    return P.Operator("term", op.d, op.n, op.delta, op.levels, r, u[None, :], v[None, :], gap=-1,
+                      family=op.family)
+
+
+def _dense_parts(op):
+    """The oracle's dense A_k and B_k (row-major N x N) for every term."""
+    N = op.N
+    cols = np.arange(N)
+    A, B = [], []
+    for k in range(op.m):
+        A.append(oracle.theta_columns(_one_term(op, op.u[k], np.ones(N), op.r), cols).T.copy())
+        B.append(oracle.theta_columns(_one_term(op, np.ones(1), op.v[k], 0), cols).T.copy())
+    return A, B
+
+
+def _run(pw, op, eta):
+    desc = pw.make_desc(op.d, op.n, op.levels, op.delta, op.m, op.r, gap=-1, order=0, precision=pw.PC_FP64,
+                        family=op.family)
+    a = pw.PCAlg1(desc, op.u, op.v, eta)
+    T = a.dense()
+    out = (T, a.kept.copy(), a.tau.copy(), a.nnz)
+    a.close()
+    return out
+
+
+def _check_case(pw, op, eta, strict_when_untied=True):
+    T, kept, tau, nnz = _run(pw, op, eta)
+    To, kept_o, tau_o = oracle.alg1_dense(op, eta)
+    A, B = _dense_parts(op)
+    scale = max(np.abs(To).max(), 1e-300)
+    expect = np.zeros_like(T)
+    allow = np.zeros_like(T)
+    tied_any = False
+    for k in range(op.m):
+        a = np.abs(A[k])
+        amax = a.max()
+        top = amax * (1 + 1e-15) + 1e-300
+        noise = 1e-13 * amax
+        ties = (np.abs(a - tau[k]) <= 1e-12 * tau[k]) & (a > 0)
+        if tau_o[k] <= noise or tau[k] <= noise:
+            # eta ~ 0: the threshold sits among rounding-noise entries (exact zeros of A_k that
+            # each FP64 evaluation leaves at its own ~1e-17 level), which both sides may keep
+            assert tau[k] <= noise and tau_o[k] <= noise, (k, tau[k], tau_o[k])
+            amb = ties | ((a > 0) & (a <= noise))
+        else:
+            # the GPU's threshold: the oracle's within the bisection's resolution, or the top
+            assert abs(tau[k] - tau_o[k]) <= 1e-9 * tau_o[k] or (tau[k] >= amax and tau_o[k] >= amax), \
+                (k, tau[k], tau_o[k])
+            amb = ties
+        tied_any |= bool(amb.any())
+        keep = (a >= tau[k]) & (a > 0)
+        n_amb = int(np.count_nonzero(amb))
+        assert abs(int(kept[k]) - int(np.count_nonzero(keep))) <= n_amb, (k, kept[k])
+        if tau_o[k] > 0.0:
+            assert abs(int(kept[k]) - int(kept_o[k])) <= n_amb, (k, kept[k], kept_o[k])
+        else:
+            # a zero threshold (the bisection never left lo = 0) keeps every entry, zeros included
+            assert kept_o[k] == op.N * op.N and kept[k] <= op.N * op.N
+        expect += np.where(keep & ~amb, A[k], 0.0) @ B[k]
+        if amb.any():
+            allow += np.where(amb, a, 0.0) @ np.abs(B[k])
+        if tau[k] < top:
+            # the kept part is what the threshold certifies: discarded Schur bound within eps_k
+            D = np.where(a < tau[k] * (1 - 1e-12), a, 0.0)
+            eps = eta / (op.m * np.abs(op.v[k]).max())
+            assert np.sqrt(D.sum(0).max() * D.sum(1).max()) <= eps * (1 + 1e-9) + 1e-12 * amax
+    err = np.abs(T - expect)
+    assert np.all(err <= 1e-12 * scale + allow * (1 + 1e-9)), err.max() / scale
+    if strict_when_untied and not tied_any:
+        assert np.array_equal(kept, kept_o)
+        assert np.abs(T - To).max() <= 1e-12 * scale, np.abs(T - To).max() / scale
+    return T, To
+
+
+CASES = [
+    # d, n, L, delta, r, m, family
+    (1, 32, 3, 2, 2, 2, 0),
+    (1, 64, 4, 4, 3, 3, 0),
+    (1, 1024, 5, 4, 4, 3, 0),
+    (1, 256, 8, 2, 3, 2, 0),        # L = log2 n: every row its own class
+    (2, 16, 2, 2, 1, 2, 0),
+    (2, 32, 3, 3, 2, 3, 0),
+    (2, 32, 3, 3, 2, 2, 1),         # Symmlet 6
+    (2, 32, 5, 2, 1, 2, 0),         # L = log2 n
+]
+
+
+@pytest.mark.parametrize("eta", [0.0, 1e-3, 1e-1, 1e3])
+@pytest.mark.parametrize("d,n,L,delta,r,m,family", CASES)
+def test_alg1_matches_oracle(pw, d, n, L, delta, r, m, family, eta):
+    op = _tiny(d, n, L, delta, r, m, seed=d * 7 + n + L, family=family)
+    T, To = _check_case(pw, op, eta)
+    if eta >= 1e3:
+        assert not np.any(T)
+
+
+def test_alg1_4096_pixels(pw):
+    """A 64 x 64 image, three levels, db2, radius 3: several CTAs per class and full-period boxes
+    at the coarse levels."""
+    op = _tiny(2, 64, 3, 2, 3, 2, seed=5)
+    _check_case(pw, op, 1e-2)
+
+
+@pytest.mark.parametrize("d,n,L,delta,r,g", [(1, 256, 5, 3, 8, 4), (2, 32, 3, 2, 4, 2)])
+def test_alg1_guarantee(pw, d, n, L, delta, r, g):
+    """||Theta - Theta~||_2 <= eta on smooth operators, with fewer kept entries of A~_k and
+    larger thresholds as eta grows."""
+    op = _smooth(d, n, L, delta, r, g)
+    Theta = oracle.theta_columns(op, np.arange(op.N)).T
+    prev = None
+    for eta in (1e-6, 1e-4, 1e-2, 1e-1):
+        T, kept, tau, nnz = _run(pw, op, eta)
+        assert np.linalg.norm(Theta - T, 2) <= eta * (1 + 1e-9), eta
+        if prev is not None:
+            assert nnz <= prev[0] and np.all(kept <= prev[1]) and np.all(tau >= prev[2])
+        prev = (nnz, kept, tau)
+
+
+def test_alg1_storage_shrinks_with_eta(pw):
+    """A 128 x 128 smooth operator: the stored support follows the thresholds (boxes narrower
+    than the period), so Theta~ holds a part of N^2 and less as eta grows."""
+    op = _smooth(2, 128, 3, 2, 4, 2)
+    nnzs = []
+    desc = pw.make_desc(2, 128, 3, 2, op.m, 4, gap=-1, precision=pw.PC_FP64)
+    for eta in (1e-6, 1e-3, 1e-1):
+        a = pw.PCAlg1(desc, op.u, op.v, eta)
+        nnzs.append(a.nnz)
+        a.close()
+    assert nnzs[0] >= nnzs[1] >= nnzs[2] and nnzs[2] < 0.9 * nnzs[0]
+    assert nnzs[0] < op.N * op.N // 4, nnzs
+
+
+def test_alg1_eta_zero_is_theta(pw):
+    op = _tiny(2, 32, 3, 3, 2, 3, seed=11)
+    T, _, _, _ = _run(pw, op, 0.0)
+    Theta = oracle.theta_columns(op, np.arange(op.N)).T
+    assert np.abs(T - Theta).max() <= 1e-12 * np.abs(Theta).max()
+
+
+def test_alg1_device_inputs_and_zero_window(pw):
+    """Inputs from device memory give the same Theta~; a zero window contributes nothing."""
+    import torch
+    op = _tiny(2, 16, 2, 2, 1, 3, seed=3)
+    op.v[1] = 0.0
+    T_host, kept_h, tau_h, _ = _run(pw, op, 1e-3)
+    desc = pw.make_desc(2, 16, 2, 2, 3, 1, gap=-1, precision=pw.PC_FP64)
+    a = pw.PCAlg1(desc, torch.tensor(op.u, device="cuda"), torch.tensor(op.v, device="cuda"), 1e-3)
+    assert np.array_equal(a.dense(), T_host)
+    assert np.array_equal(a.kept, kept_h) and np.array_equal(a.tau, tau_h)
+    assert a.kept[1] == 0
+    a.close()
+
+
+def test_alg1_rejects(pw):
+    op = _tiny(2, 16, 2, 2, 1, 2)
+    bad_order = pw.make_desc(2, 16, 2, 2, 2, 1, gap=-1, order=1, precision=pw.PC_FP64)
+    with pytest.raises(pw.PCError) as e:
+        pw.PCAlg1(bad_order, op.u, op.v, 1e-3)
+    assert e.value.status == pw.PC_ERR_UNSUPPORTED
+    fp32 = pw.make_desc(2, 16, 2, 2, 2, 1, gap=-1, precision=pw.PC_FP32)
+    with pytest.raises(pw.PCError) as e:
+        pw.PCAlg1(fp32, op.u, op.v, 1e-3)
+    assert e.value.status == pw.PC_ERR_UNSUPPORTED
+    ok = pw.make_desc(2, 16, 2, 2, 2, 1, gap=-1, precision=pw.PC_FP64)
+    with pytest.raises(pw.PCError) as e:
+        pw.PCAlg1(ok, op.u, op.v, -1.0)
+    assert e.value.status == pw.PC_ERR_INVALID_ARG
