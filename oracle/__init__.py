@@ -54,7 +54,7 @@ def _load():
         lib.or_jacobi.argtypes = [D, _dp, _dp]
         lib.or_power_norm.argtypes = [D, _dp, _dp, I, _dp]
         lib.or_fista.argtypes = [D, _dp, _dp, _dp, _dp, I, ctypes.c_double, _dp]
-        lib.or_alg1_dense.argtypes = [I, I, I, I, I, I, I, _dp, _dp, ctypes.c_double, _dp, _i64p, _dp]
+        lib.or_alg1_dense.argtypes = [I, I, I, I, I, I, I, _dp, _dp, ctypes.c_double, I, _dp, _i64p, _dp]
         _lib = lib
     return _lib
 
@@ -201,9 +201,10 @@ def fista(T, z0, w, iters, tau, z_init=None, sigma=None):
     return z
 
 
-def alg1_dense(op, eta, u=None, v=None):
+def alg1_dense(op, eta, u=None, v=None, rule=0):
     """Algorithm 1 with thresholding on dense matrices (N <= 4096): returns (Theta~ (N, N),
-    entries kept per A~_k, threshold per k)."""
+    entries kept per A~_k, threshold per k).  rule 0: the Schur-certified threshold; rule 1:
+    tau_k = eps_k."""
     u, up = _d(op.u if u is None else u)
     v, vp = _d(op.v if v is None else v)
     N = op.N
@@ -211,6 +212,6 @@ def alg1_dense(op, eta, u=None, v=None):
     nnz = np.zeros(u.shape[0], dtype=np.int64)
     tau = np.zeros(u.shape[0])
     rc = _load().or_alg1_dense(op.d, op.n, op.levels, _opcode(op), u.shape[0], op.r, op.order, up, vp, float(eta),
-                               T.ctypes.data_as(_dp), nnz.ctypes.data_as(_i64p), tau.ctypes.data_as(_dp))
+                               int(rule), T.ctypes.data_as(_dp), nnz.ctypes.data_as(_i64p), tau.ctypes.data_as(_dp))
     _check(rc, "alg1_dense")
     return T, nnz, tau

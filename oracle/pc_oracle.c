@@ -711,11 +711,12 @@ int or_fista(int64_t N, const double *T, const double *z0, const double *w, cons
 /* ------------------------------------------------------------------------------------
  * Algorithm 1 (Section 3.2) with thresholding, on dense matrices (small N only).
  *   eps_k = eta / (m ||v_k||_inf);  A_k = Psi^* U_k Psi;  B_k = Psi^* V_k Psi;
- *   A~_k = A_k with the entries below a threshold tau_k set to 0, tau_k the largest value
- *          whose discarded part D_k has Schur bound sqrt(||D_k||_1 ||D_k||_inf) <= eps_k
- *          (so ||A_k - A~_k||_2 <= eps_k; bisection on tau, 80 halvings);
+ *   A~_k = A_k with the entries below a threshold tau_k set to 0.  rule 0: tau_k the largest
+ *          value whose discarded part D_k has Schur bound sqrt(||D_k||_1 ||D_k||_inf) <= eps_k
+ *          (so ||A_k - A~_k||_2 <= eps_k; bisection on tau, 80 halvings).  rule 1: tau_k = eps_k
+ *          (the threshold step read as a plain cut at eps_k; no 2-norm certificate);
  *   Theta~ = sum_k A~_k B_k  (paper order; B_k A~_k in the convolution-first order).
- * Since ||B_k||_2 = ||v_k||_inf, ||Theta - Theta~||_2 <= sum_k eps_k ||v_k||_inf = eta.
+ * Rule 0: since ||B_k||_2 = ||v_k||_inf, ||Theta - Theta~||_2 <= sum_k eps_k ||v_k||_inf = eta.
  * theta: N x N row-major Theta~[mu * N + lambda]; nnz_a[k] = entries kept in A~_k;
  * tau[k] = the threshold.  Returns 0, or -1 on bad input or allocation failure.
  * ------------------------------------------------------------------------------------ */
@@ -733,11 +734,11 @@ static double schur_discard(int64_t N, const double *A, double t, double *rs, do
 }
 
 int or_alg1_dense(int d, int n, int L, int wcode, int m, int r, int order, const double *u, const double *v,
-                  double eta, double *theta, int64_t *nnz_a, double *tau)
+                  double eta, int rule, double *theta, int64_t *nnz_a, double *tau)
 {
     const int64_t N = (d == 1) ? n : (int64_t)n * n;
     const int64_t Ku = (d == 1) ? (2 * r + 1) : (int64_t)(2 * r + 1) * (2 * r + 1);
-    if (N > 4096 || m < 1 || eta < 0.0) return -1;
+    if (N > 4096 || m < 1 || eta < 0.0 || (rule != 0 && rule != 1)) return -1;
     double *colsA = malloc(sizeof(double) * N * N), *colsB = malloc(sizeof(double) * N * N);
     double *A = malloc(sizeof(double) * N * N), *B = malloc(sizeof(double) * N * N);
     double *ones = malloc(sizeof(double) * N), *rs = malloc(sizeof(double) * N), *cs = malloc(sizeof(double) * N);
@@ -769,7 +770,9 @@ int or_alg1_dense(int d, int n, int L, int wcode, int m, int r, int order, const
         for (int64_t i = 0; i < N * N; ++i) amax = fmax(amax, fabs(A[i]));
         double t;
         const double top = amax * (1.0 + 1e-15) + 1e-300;
-        if (schur_discard(N, A, top, rs, cs) <= eps) {
+        if (rule == 1) {
+            t = eps;
+        } else if (schur_discard(N, A, top, rs, cs) <= eps) {
             t = top;
         } else {
             double lo = 0.0, hi = top;

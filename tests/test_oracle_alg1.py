@@ -82,3 +82,32 @@ def test_large_eta_discards_everything():
     T, nnz, _ = oracle.alg1_dense(op, eta)
     assert np.all(nnz == 0) and np.all(T == 0.0)
     assert np.linalg.norm(Theta, 2) <= eta
+
+
+@pytest.mark.parametrize("make", ["tiny", "smooth"])
+def test_hard_rule_is_a_plain_cut(make):
+    """Rule 1 (tau_k = eps_k): the kept entries are exactly those of A_k = Psi^T U_k Psi (dense,
+    from the independent cascade basis) with |a| >= eps_k, and Theta~ = sum_k A~_k B_k with
+    B_k = Psi^T diag(v_k) Psi, both orders."""
+    for order in (0, 1):
+        op = tiny(1, 64, 4, 4, 3, 3, order=order) if make == "tiny" else _smooth(1, 128, 5, 4, 6, 4, order=order)
+        Psi = dense_psi(op.d, op.n, op.levels, op.delta)
+        N, K = op.N, 2 * op.r + 1
+        eta = 2e-3
+        T, nnz, tau = oracle.alg1_dense(op, eta, rule=1)
+        ref = np.zeros((N, N))
+        for k in range(op.m):
+            U = np.zeros((N, N))
+            for t in range(-op.r, op.r + 1):
+                U[(np.arange(N) + t) % N, np.arange(N)] += op.u[k, t + op.r]
+            A = Psi.T @ U @ Psi
+            B = Psi.T @ np.diag(op.v[k]) @ Psi
+            eps = eta / (op.m * np.abs(op.v[k]).max())
+            assert tau[k] == eps
+            # entries within rounding of eps may go either way between this A and the oracle's
+            assert np.count_nonzero(np.abs(A) >= eps * (1 + 1e-9)) <= nnz[k] <= np.count_nonzero(np.abs(A) >= eps * (1 - 1e-9))
+            At = np.where(np.abs(A) >= eps, A, 0.0)
+            assert np.abs(A - At).max() < eps
+            assert nnz[k] < np.count_nonzero(np.abs(A) > 1e-14 * np.abs(A).max())   # the cut drops entries
+            ref += At @ B if order == 0 else B @ At
+        assert np.abs(T - ref).max() < 1e-12 * np.abs(ref).max()
