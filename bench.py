@@ -380,6 +380,83 @@ def run_sweep(pw, rank, dev, stream, sides=(128, 256, 512, 1024, 2048)):
     return out
 
 
+# The paper's Algorithm 1 decomposition times in seconds (FP64 on a 12-core CPU, eta = 5e-4,
+# Symmlet 6; the timing-vs-N figure of Section 4.2), for context beside the GPU's.
+PAPER_ALG1_S = {"op1": {128: 3.35, 256: 15.7, 512: 78.3, 1024: 430.9, 2048: 2292.0, 4096: 13048.0},
+                "op2": {128: 14.9, 256: 72.6, 512: 345.8, 1024: 1816.6, 2048: 9747.7, 4096: 56192.9}}
+
+
+def run_alg1(pw, rank, dev, check, sides=(128, 256, 512, 1024)):
+    """Thresholded Algorithm 1 on the GPU (pc_alg1_create, Section 3.2) on the stand-ins for the
+    paper's two blurs: eta = 5e-4 with the plain cut tau_k = eps_k, FP32 products, sides
+    2^7..2^10 beside the paper's Algorithm 1 times (beyond 2^10 Theta~ does not fit: rows that
+    keep a coarse wavelet reach its whole support); the time against eta at 256^2 for both
+    threshold rules (the paper's timing-vs-precision figure); and, when checking, the max error of
+    a small case against the oracle's dense Algorithm 1.  Each call is synchronous; wall time
+    around it (host planning and the allocation of Theta~ included) and the device time of its
+    four stages (CUDA events)."""
+    import time
+    import torch
+    import pc_inputs as P
+
+    def one(name, n, eta, rule):
+        rec = {"operator": name, "side": n, "eta": eta, "rule": "hard" if rule else "schur"}
+        a = None
+        try:
+            op = P.workload(name, n=n, seed_offset=rank)
+            desc = pw.make_desc(2, n, op.levels, op.delta, op.m, op.r, gap=-1, precision=pw.PC_FP32,
+                                family=op.family)
+            u = torch.tensor(op.u, device=dev)
+            v = torch.tensor(op.v, device=dev)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            a = pw.PCAlg1(desc, u, v, eta, rule=rule)
+            wall = time.perf_counter() - t0
+            rec.update({"N": op.N, "m": op.m, "s": round(wall, 4),
+                        "stage_ms": {k: round(float(x), 3) for k, x in
+                                     zip(("generators", "thresholds", "synthesis", "products"), a.stage_ms)},
+                        "nnz": a.nnz, "entries_per_row": round(a.nnz / op.N, 1),
+                        "kept_per_row_per_term": round(float(a.kept.sum()) / op.N / op.m, 1)})
+        except Exception as e:                       # recorded, not fatal to the bench line
+            rec["error"] = str(e)[:160]
+        finally:
+            if a is not None:
+                a.close()
+        return rec
+
+    one("op1", 128, 5e-4, 1)                         # first call: module set-up
+    out = {"sweep": [], "vs_eta_256": []}
+    for name in ("op1", "op2"):
+        for n in sides:
+            rec = one(name, n, 5e-4, 1)
+            rec["paper_alg1_s"] = PAPER_ALG1_S[name][n]
+            if "s" in rec:
+                rec["paper_over_gpu"] = round(rec["paper_alg1_s"] / rec["s"], 1)
+            out["sweep"].append(rec)
+    for eta in (1e-2, 1e-3, 1e-4):
+        for rule in (0, 1):
+            for name in ("op1", "op2"):
+                out["vs_eta_256"].append(one(name, 256, eta, rule))
+    if check:
+        import oracle
+        errs = {}
+        for rule in (0, 1):
+            n, m, r = 32, 3, 2
+            u = P.normal(P.BASE_SEED + 901, m * (2 * r + 1) ** 2).reshape(m, -1)
+            v = P.uniform(P.BASE_SEED + 902, m * n * n).reshape(m, -1) + 0.1
+            op = P.Operator("alg1-check", 2, n, 3, 3, r, u, v, gap=-1)
+            To, _, _ = oracle.alg1_dense(op, 1e-3, rule=rule)
+            for fp32 in (False, True):
+                desc = pw.make_desc(2, n, 3, 3, m, r, gap=-1, precision=pw.PC_FP32 if fp32 else pw.PC_FP64)
+                a = pw.PCAlg1(desc, u, v, 1e-3, rule=rule)
+                T = a.dense()
+                a.close()
+                errs[f"{'hard' if rule else 'schur'}_{'fp32' if fp32 else 'fp64'}"] = \
+                    float(np.abs(T - To).max() / np.abs(To).max())
+        out["max_rel_err_vs_oracle_32x32"] = errs
+    return out
+
+
 # ---------------- the oracle leg: CPU baseline and per-result errors against the FP64 oracle ----------------
 # Everything below runs outside the timed regions; it is the one part of the GPU arm that calls
 # the oracle (test infrastructure), and only to time it and to compare results with it.
@@ -786,6 +863,9 @@ def run_ours(args, rank, world, local_rank):
     sweep = None
     if not args.no_sweep:
         sweep = run_sweep(pw, rank, dev, stream)
+    alg1 = None
+    if not args.no_alg1:
+        alg1 = run_alg1(pw, rank, dev, check)
 
     clocks = clk.summary()
     if rank == 0:
@@ -797,6 +877,7 @@ def run_ours(args, rank, world, local_rank):
             "config": bench_config(world),
             # details first; the driver's record keeps the end of the line
             "symmlet6_sweep": sweep,
+            "alg1_thresholded": alg1,
             "fista": fista,
             "roofline_fp32": roof_fp32,
             "phases_ms": {"prepare": prep_ms, "assemble_rows": rows_ms, "apply_16rhs": apply_ms, "backward": bwd_ms},
@@ -836,6 +917,7 @@ def main():
     ap.add_argument("--no-fista", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-c5", action="store_true")
+    ap.add_argument("--no-alg1", action="store_true")
     ap.add_argument("--fista-iters", type=int, default=50)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -334,15 +334,24 @@ int64_t pc_launch_counter(void);
  * --------------------------------------------------------------------------------------- */
 typedef struct pc_alg1* pc_alg1_handle;
 
+/* Threshold rules for A_k: PC_ALG1_SCHUR is the certified rule above; PC_ALG1_HARD drops the
+ * entries below eps_k itself (tau_k = eps_k, the threshold step read literally), which keeps far
+ * fewer entries but certifies only max|A_k - A~_k| < eps_k, not the 2-norm bound. */
+typedef enum { PC_ALG1_SCHUR = 0, PC_ALG1_HARD = 1 } pc_alg1_rule;
+
 /* Runs Algorithm 1 on the device and keeps Theta~ in the handle.  desc: dim, n, levels,
  * delta, family, m, radius as for pc_create; order must be PC_ORDER_MULT_THEN_CONV (the other
- * order's matrix is the transpose of this one's for the flipped kernels u_k(-t)) and precision
- * PC_FP64 (every stage in FP64); gap and store_bf16 are ignored.  u: m x (2r+1)^dim, v: m x n^dim,
- * FP64, host or device (copied).  eta >= 0.  Synchronous on `stream`.  PC_ERR_INVALID_ARG for
- * NULL pointers, eta < 0 or a descriptor out of range, PC_ERR_UNSUPPORTED for the other order,
- * PC_FP32 or more than 2^16 row classes (dim * levels > 16), PC_ERR_OOM when the generator,
- * product or Theta~ storage does not fit. */
-pc_status pc_alg1_create(const pc_desc* desc, const double* u, const double* v, double eta, void* stream,
+ * order's matrix is the transpose of this one's for the flipped kernels u_k(-t)); rule is a
+ * pc_alg1_rule; gap and
+ * store_bf16 are ignored.  The generator rows, thresholds and the synthesis of the kept rows run
+ * in FP64 in either precision (so both precisions keep the same entries); PC_FP64 forms the
+ * products s~ = sum_k v_k F~_k and their transforms in FP64 and stores Theta~ in FP64, PC_FP32
+ * in FP32 with the sum over k compensated (Kahan), Theta~ in FP32.  u: m x (2r+1)^dim,
+ * v: m x n^dim, FP64, host or device (copied).  eta >= 0.  Synchronous on `stream`.
+ * PC_ERR_INVALID_ARG for NULL pointers, eta < 0, an unknown rule or a descriptor out of range,
+ * PC_ERR_UNSUPPORTED for the other order or more than 2^16 row classes (dim * levels > 16),
+ * PC_ERR_OOM when the generator, product or Theta~ storage does not fit. */
+pc_status pc_alg1_create(const pc_desc* desc, const double* u, const double* v, double eta, int rule, void* stream,
                          pc_alg1_handle* out);
 
 /* nnz: stored entries of Theta~; tau[m]: the thresholds; kept[m]: nonzero entries of A~_k

@@ -95,9 +95,21 @@ struct A1Params {
     const double* tau;           // m thresholds
     double* Fb;                  // F~ per class: m x |R|
     double* theta;               // Theta~ rows
-    long long sA, sT, sR;        // scratch layout of a CTA (doubles): two level buffers, a
+    long long sA, sT, sR;        // scratch layout of a CTA (elements): two level buffers, a
                                  // work buffer, the 1-D factor samples
+    // FP32 products (Theta~ in FP32): the taps, windows, F~ and Theta~ in single precision
+    float hf[A1_MAXLF], gf[A1_MAXLF];
+    const float* v32;
+    float* Fb32;
+    float* theta32;
 };
+
+template <class T> __device__ __forceinline__ T tap_h(const A1Params& P, int i);
+template <> __device__ __forceinline__ double tap_h<double>(const A1Params& P, int i) { return P.h[i]; }
+template <> __device__ __forceinline__ float tap_h<float>(const A1Params& P, int i) { return P.hf[i]; }
+template <class T> __device__ __forceinline__ T tap_g(const A1Params& P, int i);
+template <> __device__ __forceinline__ double tap_g<double>(const A1Params& P, int i) { return P.g[i]; }
+template <> __device__ __forceinline__ float tap_g<float>(const A1Params& P, int i) { return P.gf[i]; }
 
 // ---------------------------------------------------------------------------------------
 // Host geometry
@@ -160,29 +172,31 @@ inline int chain(int D, int n, int J, int Lf, const Ax b0[2], Ax out[2][A1_MAXJ 
 
 // Value at unwrapped position p of a line stored on box b with period M (a power of two):
 // zero unless p is an image of a stored position.
-__device__ __forceinline__ double at(const double* line, int stride, Ax b, int M, int p)
+template <class T>
+__device__ __forceinline__ T at(const T* line, int stride, Ax b, int M, int p)
 {
     const int k = (p - b.a) & (M - 1);
-    return k < b.w ? line[(long long)k * stride] : 0.0;
+    return k < b.w ? line[(long long)k * stride] : T(0);
 }
 
 // One analysis level of a 2-D box signal X (b0.w x b1.w, row-major, period M): the next
 // approximation into Y (nb0.w x nb1.w) and the detail bands (0,1), (1,0), (1,1) into out,
 // out + sz, out + 2 sz (sz = nb0.w nb1.w); T holds 2 b0.w nb1.w.  Axis 1 first, then axis 0.
-__device__ void analysis2(const A1Params& P, const double* X, Ax b0, Ax b1, int M, Ax nb0, Ax nb1, double* T,
-                          double* Y, double* out)
+template <class F>
+__device__ void analysis2(const A1Params& P, const F* X, Ax b0, Ax b1, int M, Ax nb0, Ax nb1, F* T, F* Y,
+                          F* out)
 {
     const int Lf = P.Lf;
     const int n01 = b0.w * nb1.w;
     for (int idx = threadIdx.x; idx < n01; idx += blockDim.x) {
         const int r = idx / nb1.w, q = idx - r * nb1.w;
         const int base = 2 * (nb1.a + q);
-        const double* line = X + (long long)r * b1.w;
-        double lo = 0.0, hi = 0.0;
+        const F* line = X + (long long)r * b1.w;
+        F lo = 0, hi = 0;
         for (int i = 2 - Lf; i < Lf; ++i) {
-            const double x = at(line, 1, b1, M, base + i);
-            if (i >= 0) lo = fma(P.h[i], x, lo);
-            if (i <= 1) hi = fma(P.g[i - (2 - Lf)], x, hi);
+            const F x = at(line, 1, b1, M, base + i);
+            if (i >= 0) lo = fma(tap_h<F>(P, i), x, lo);
+            if (i <= 1) hi = fma(tap_g<F>(P, i - (2 - Lf)), x, hi);
         }
         T[idx] = lo;
         T[n01 + idx] = hi;
@@ -192,16 +206,16 @@ __device__ void analysis2(const A1Params& P, const double* X, Ax b0, Ax b1, int 
     for (int idx = threadIdx.x; idx < sz; idx += blockDim.x) {
         const int r = idx / nb1.w, q = idx - r * nb1.w;
         const int base = 2 * (nb0.a + r);
-        double ll = 0.0, d01 = 0.0, d10 = 0.0, d11 = 0.0;
+        F ll = 0, d01 = 0, d10 = 0, d11 = 0;
         for (int i = 2 - Lf; i < Lf; ++i) {
-            const double xl = at(T + q, nb1.w, b0, M, base + i);
-            const double xh = at(T + n01 + q, nb1.w, b0, M, base + i);
+            const F xl = at(T + q, nb1.w, b0, M, base + i);
+            const F xh = at(T + n01 + q, nb1.w, b0, M, base + i);
             if (i >= 0) {
-                ll = fma(P.h[i], xl, ll);
-                d01 = fma(P.h[i], xh, d01);
+                ll = fma(tap_h<F>(P, i), xl, ll);
+                d01 = fma(tap_h<F>(P, i), xh, d01);
             }
             if (i <= 1) {
-                const double gi = P.g[i - (2 - Lf)];
+                const F gi = tap_g<F>(P, i - (2 - Lf));
                 d10 = fma(gi, xl, d10);
                 d11 = fma(gi, xh, d11);
             }
@@ -215,16 +229,17 @@ __device__ void analysis2(const A1Params& P, const double* X, Ax b0, Ax b1, int 
 }
 
 // One analysis level of a 1-D box signal.
-__device__ void analysis1(const A1Params& P, const double* X, Ax b, int M, Ax nb, double* Y, double* out)
+template <class F>
+__device__ void analysis1(const A1Params& P, const F* X, Ax b, int M, Ax nb, F* Y, F* out)
 {
     const int Lf = P.Lf;
     for (int idx = threadIdx.x; idx < nb.w; idx += blockDim.x) {
         const int base = 2 * (nb.a + idx);
-        double lo = 0.0, hi = 0.0;
+        F lo = 0, hi = 0;
         for (int i = 2 - Lf; i < Lf; ++i) {
-            const double x = at(X, 1, b, M, base + i);
-            if (i >= 0) lo = fma(P.h[i], x, lo);
-            if (i <= 1) hi = fma(P.g[i - (2 - Lf)], x, hi);
+            const F x = at(X, 1, b, M, base + i);
+            if (i >= 0) lo = fma(tap_h<F>(P, i), x, lo);
+            if (i <= 1) hi = fma(tap_g<F>(P, i - (2 - Lf)), x, hi);
         }
         Y[idx] = lo;
         out[idx] = hi;
@@ -329,9 +344,9 @@ __device__ inline void load_class(const A1Class* src, A1Class* dst)
 // Analysis chain over the boxes bx (levels 0..J) from X, into a row (approximation of level J
 // at 0, detail bands of level l at offl[l]).  X and Y are swapped between levels; returns the
 // buffer holding the approximation.
-template <int D>
-__device__ double* analysis_chain(const A1Params& P, double* X, double* Y, double* T, const Ax (*bx)[A1_MAXJ + 1],
-                                  const int* offl, double* row)
+template <int D, class F>
+__device__ F* analysis_chain(const A1Params& P, F* X, F* Y, F* T, const Ax (*bx)[A1_MAXJ + 1], const int* offl,
+                             F* row)
 {
     for (int l = 0; l < P.J; ++l) {
         const int M = P.n >> l;
@@ -339,7 +354,7 @@ __device__ double* analysis_chain(const A1Params& P, double* X, double* Y, doubl
             analysis2(P, X, bx[0][l], bx[1][l], M, bx[0][l + 1], bx[1][l + 1], T, Y, row + offl[l + 1]);
         else
             analysis1(P, X, bx[0][l], M, bx[0][l + 1], Y, row + offl[l + 1]);
-        double* t = X;
+        F* t = X;
         X = Y;
         Y = t;
     }
@@ -416,6 +431,13 @@ __global__ void __launch_bounds__(A1_THREADS) k_a1_generators(const __grid_const
         __syncthreads();
         analysis_chain<D>(P, A, B, T, C.g, C.goffl, P.G + (long long)k * P.gtotal + C.goff);
     }
+}
+
+// FP32 copy of n values.
+__global__ void k_a1_tof32(const double* x, float* y, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = (float)x[i];
 }
 
 // Max |x| over each of gridDim.x runs of len values (stride apart): out[blockIdx.x].
@@ -648,21 +670,42 @@ __global__ void __launch_bounds__(A1_THREADS) k_a1_synth(const __grid_constant__
             X = Y;
             Y = t;
         }
-        double* out = P.Fb + C.foff + (long long)k * C.rsize;
-        for (int idx = threadIdx.x; idx < C.rsize; idx += blockDim.x) out[idx] = X[idx];
+        if (P.Fb32) {
+            float* out = P.Fb32 + C.foff + (long long)k * C.rsize;
+            for (int idx = threadIdx.x; idx < C.rsize; idx += blockDim.x) out[idx] = (float)X[idx];
+        } else {
+            double* out = P.Fb + C.foff + (long long)k * C.rsize;
+            for (int idx = threadIdx.x; idx < C.rsize; idx += blockDim.x) out[idx] = X[idx];
+        }
         __syncthreads();
     }
 }
 
 // Stage 4: the rows of Theta~.  One CTA per row (class c, translate t): s~ = sum_k v_k . F~_{k,c}
-// on R shifted by 2^J t, then its analysis chain on the class's product boxes.
-template <int D>
-__global__ void __launch_bounds__(A1_THREADS) k_a1_product(const __grid_constant__ A1Params P, double* gscratch)
+// on R shifted by 2^J t, then its analysis chain on the class's product boxes.  F = double: FP64
+// throughout; F = float: FP32 windows, F~ and transform, the sum over k compensated (Kahan).
+template <class F> struct ProdIO;
+template <> struct ProdIO<double> {
+    static __device__ const double* v(const A1Params& P) { return P.v; }
+    static __device__ const double* fb(const A1Params& P) { return P.Fb; }
+    static __device__ double* theta(const A1Params& P) { return P.theta; }
+};
+template <> struct ProdIO<float> {
+    static __device__ const float* v(const A1Params& P) { return P.v32; }
+    static __device__ const float* fb(const A1Params& P) { return P.Fb32; }
+    static __device__ float* theta(const A1Params& P) { return P.theta32; }
+};
+
+template <int D, class F>
+__global__ void __launch_bounds__(A1_THREADS) k_a1_product(const __grid_constant__ A1Params P, F* gscratch)
 {
-    extern __shared__ double smem[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ A1Class C;
-    double* S = gscratch ? gscratch + (long long)blockIdx.x * (2 * P.sA + P.sT) : smem;
-    double *X = S, *Y = S + P.sA, *T = S + 2 * P.sA;
+    F* S = gscratch ? gscratch + (long long)blockIdx.x * (2 * P.sA + P.sT) : reinterpret_cast<F*>(smem_raw);
+    F *X = S, *Y = S + P.sA, *T = S + 2 * P.sA;
+    const F* V = ProdIO<F>::v(P);
+    const F* FB = ProdIO<F>::fb(P);
+    F* TH = ProdIO<F>::theta(P);
     const int rows = (D == 2) ? P.nJ * P.nJ : P.nJ;
     const long long total = (long long)P.ncls * rows;
     for (long long item = blockIdx.x; item < total; item += gridDim.x) {
@@ -671,17 +714,27 @@ __global__ void __launch_bounds__(A1_THREADS) k_a1_product(const __grid_constant
         if (C.tlen == 0) continue;
         const int t0 = (D == 2) ? t / P.nJ : t, t1 = (D == 2) ? t - t0 * P.nJ : 0;
         const Ax R0 = C.c[0][0], R1 = C.c[1][0];
-        const double* F = P.Fb + C.foff;
+        const F* Fc = FB + C.foff;
         for (int idx = threadIdx.x; idx < C.rsize; idx += blockDim.x) {
             const int i0 = idx / R1.w, i1 = idx - i0 * R1.w;
             const int x0 = (R0.a + i0 + (t0 << P.J)) & (P.n - 1);
             const long long pix = (D == 2) ? (long long)x0 * P.n + ((R1.a + i1 + (t1 << P.J)) & (P.n - 1)) : x0;
-            double s = 0.0;
-            for (int k = 0; k < P.m; ++k) s = fma(P.v[(long long)k * P.N + pix], F[(long long)k * C.rsize + idx], s);
+            F s = 0, comp = 0;
+            for (int k = 0; k < P.m; ++k) {
+                const F term = V[(long long)k * P.N + pix] * Fc[(long long)k * C.rsize + idx];
+                if (sizeof(F) == 4) {
+                    const F y = term - comp;
+                    const F z = s + y;
+                    comp = (z - s) - y;
+                    s = z;
+                } else {
+                    s += term;
+                }
+            }
             X[idx] = s;
         }
         __syncthreads();
-        analysis_chain<D>(P, X, Y, T, C.c, C.coffl, P.theta + C.toff + (long long)t * C.tlen);
+        analysis_chain<D>(P, X, Y, T, C.c, C.coffl, TH + C.toff + (long long)t * C.tlen);
     }
 }
 

@@ -2174,7 +2174,9 @@ struct pc_alg1 {
     std::vector<double> tau;
     std::vector<int64_t> kept;
     double stage_ms[4] = {0, 0, 0, 0};
-    double* theta_d = nullptr;
+    bool fp32 = false;            // Theta~ in FP32 (products in FP32), else FP64
+    int rule = PC_ALG1_SCHUR;     // threshold rule
+    void* theta_d = nullptr;
     std::string err = "no error";
 };
 
@@ -2240,7 +2242,11 @@ struct DevBufs {
     bool alloc(T** p, size_t count)
     {
         *p = nullptr;
-        if (cudaMalloc((void**)p, sizeof(T) * std::max<size_t>(count, 1)) != cudaSuccess) return false;
+        if (cudaMalloc((void**)p, sizeof(T) * std::max<size_t>(count, 1)) != cudaSuccess) {
+            *p = nullptr;
+            (void)cudaGetLastError();  // an allocation failure is reported by status, not left pending
+            return false;
+        }
         ptrs.push_back(*p);
         return true;
     }
@@ -2255,13 +2261,13 @@ struct ScratchPlan {
 };
 
 template <class K>
-ScratchPlan plan_scratch(K kernel, long long items, size_t per_cta)
+ScratchPlan plan_scratch(K kernel, long long items, size_t per_cta, size_t elem = sizeof(double))
 {
     ScratchPlan sp;
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    sp.bytes = per_cta * sizeof(double);
+    sp.bytes = per_cta * elem;
     if (sp.bytes <= 200 * 1024) {
         cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.bytes);
         int per_sm = 0;
@@ -2306,6 +2312,10 @@ pc_status alg1_run(pc_alg1* h, const pc_desc* desc, const double* u, const doubl
     if (pcw::filter_taps(desc->family, desc->delta, hh) != Lf) return a1_fail(h, PC_ERR_INVALID_ARG, "filter taps");
     for (int i = 0; i < Lf; ++i) P.h[i] = hh[i];
     for (int i = 2 - Lf; i <= 1; ++i) P.g[i - (2 - Lf)] = (((1 - i) % 2 == 0) ? 1.0 : -1.0) * hh[1 - i];
+    for (int i = 0; i < Lf; ++i) {
+        P.hf[i] = (float)P.h[i];
+        P.gf[i] = (float)P.g[i];
+    }
     std::vector<std::vector<double>> phi, psi;
     factor_tables(hh, Lf, J, &phi, &psi);
     std::vector<double> tab;
@@ -2386,6 +2396,7 @@ pc_status alg1_run(pc_alg1* h, const pc_desc* desc, const double* u, const doubl
     }
     const int nseg = (int)seg_len.size();
     seg_row_off[ncls] = nseg;
+
     std::vector<int> colseg_off(ncls + 1, 0), colseg(nseg);
     for (int s = 0; s < nseg; ++s) colseg_off[seg_cc[s] + 1]++;
     for (int c = 0; c < ncls; ++c) colseg_off[c + 1] += colseg_off[c];
@@ -2477,7 +2488,11 @@ pc_status alg1_run(pc_alg1* h, const pc_desc* desc, const double* u, const doubl
         cudaMemcpyAsync(tq_d, top.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st) ||
         cudaMemsetAsync(done_d, 0, sizeof(int) * m, st))
         return cuda_err("threshold set-up");
-    {
+    if (h->rule == PC_ALG1_HARD) {
+        // tau_k = eps_k (everything for a zero window)
+        if (cudaMemcpyAsync(tau_d, eps.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st))
+            return cuda_err("threshold set-up");
+    } else {
         const int last = 80;
         int dev = 0, sms = 1;
         cudaGetDevice(&dev);
@@ -2551,16 +2566,27 @@ pc_status alg1_run(pc_alg1* h, const pc_desc* desc, const double* u, const doubl
         for (int l = 0; l < J; ++l) sT = std::max<long long>(sT, 2LL * C.c[0][l].w * C.c[1][l + 1].w);
     }
     h->nnz = ttotal;
-    double* Fb_d;
-    if (!db.alloc(&Fb_d, ftotal)) return oom();
-    if (cudaMalloc(&h->theta_d, sizeof(double) * std::max<int64_t>(ttotal, 1)) != cudaSuccess) {
+    const size_t esz = h->fp32 ? sizeof(float) : sizeof(double);
+    if (h->fp32) {
+        float* v32;
+        if (!db.alloc(&P.Fb32, ftotal) || !db.alloc(&v32, (size_t)m * N)) return oom();
+        k_a1_tof32<<<1024, 256, 0, st>>>(v_d, v32, (long long)m * N);
+        count_launch();
+        P.v32 = v32;
+    } else if (!db.alloc(&P.Fb, ftotal)) {
+        return oom();
+    }
+    if (cudaMalloc(&h->theta_d, esz * std::max<int64_t>(ttotal, 1)) != cudaSuccess) {
         h->theta_d = nullptr;
+        (void)cudaGetLastError();
         return oom();
     }
     if (cudaMemcpyAsync(cls_d, h->cls.data(), sizeof(A1Class) * ncls, cudaMemcpyHostToDevice, st))
         return cuda_err("class upload");
-    P.Fb = Fb_d;
-    P.theta = h->theta_d;
+    if (h->fp32)
+        P.theta32 = (float*)h->theta_d;
+    else
+        P.theta = (double*)h->theta_d;
     P.sA = sA;
     P.sT = sT;
     P.sR = 0;
@@ -2577,10 +2603,17 @@ pc_status alg1_run(pc_alg1* h, const pc_desc* desc, const double* u, const doubl
     cudaEventRecord(ev[3], st);
     {
         const long long items = (long long)ncls * h->rows;
-        const ScratchPlan sp = plan_scratch(k_a1_product<D>, items, 2 * sA + sT);
-        double* slab = nullptr;
-        if (!sp.smem && !db.alloc(&slab, (size_t)sp.grid * (2 * sA + sT))) return oom();
-        k_a1_product<D><<<sp.grid, A1_THREADS, sp.smem ? sp.bytes : 0, st>>>(P, slab);
+        if (h->fp32) {
+            const ScratchPlan sp = plan_scratch(k_a1_product<D, float>, items, 2 * sA + sT, sizeof(float));
+            float* slab = nullptr;
+            if (!sp.smem && !db.alloc(&slab, (size_t)sp.grid * (2 * sA + sT))) return oom();
+            k_a1_product<D, float><<<sp.grid, A1_THREADS, sp.smem ? sp.bytes : 0, st>>>(P, slab);
+        } else {
+            const ScratchPlan sp = plan_scratch(k_a1_product<D, double>, items, 2 * sA + sT);
+            double* slab = nullptr;
+            if (!sp.smem && !db.alloc(&slab, (size_t)sp.grid * (2 * sA + sT))) return oom();
+            k_a1_product<D, double><<<sp.grid, A1_THREADS, sp.smem ? sp.bytes : 0, st>>>(P, slab);
+        }
         count_launch();
         if (cudaGetLastError() != cudaSuccess) return cuda_err("product launch");
     }
@@ -2598,11 +2631,13 @@ pc_status alg1_run(pc_alg1* h, const pc_desc* desc, const double* u, const doubl
 
 extern "C" {
 
-pc_status pc_alg1_create(const pc_desc* desc, const double* u, const double* v, double eta, void* stream,
+pc_status pc_alg1_create(const pc_desc* desc, const double* u, const double* v, double eta, int rule, void* stream,
                          pc_alg1_handle* out)
 {
-    if (!desc || !u || !v || !out || !(eta >= 0.0) || !std::isfinite(eta))
-        return fail(nullptr, PC_ERR_INVALID_ARG, "pc_alg1_create: NULL pointer or eta not finite and >= 0");
+    if (!desc || !u || !v || !out || !(eta >= 0.0) || !std::isfinite(eta) ||
+        (rule != PC_ALG1_SCHUR && rule != PC_ALG1_HARD))
+        return fail(nullptr, PC_ERR_INVALID_ARG,
+                    "pc_alg1_create: NULL pointer, eta not finite and >= 0, or an unknown rule");
     *out = nullptr;
     const pc_desc& d = *desc;
     if ((d.dim != 1 && d.dim != 2) || d.n < 2 || (d.n & (d.n - 1)) || d.levels < 1 ||
@@ -2612,7 +2647,8 @@ pc_status pc_alg1_create(const pc_desc* desc, const double* u, const double* v, 
     if (d.order != PC_ORDER_MULT_THEN_CONV)
         return fail(nullptr, PC_ERR_UNSUPPORTED,
                     "pc_alg1_create: only the paper's order (the other is the transpose with flipped kernels)");
-    if (d.precision != PC_FP64) return fail(nullptr, PC_ERR_UNSUPPORTED, "pc_alg1_create: FP64 only");
+    if (d.precision != PC_FP64 && d.precision != PC_FP32)
+        return fail(nullptr, PC_ERR_INVALID_ARG, "pc_alg1_create: unknown precision");
     if (d.dim * d.levels > 16) return fail(nullptr, PC_ERR_UNSUPPORTED, "pc_alg1_create: more than 2^16 classes");
     pc_alg1* h = new (std::nothrow) pc_alg1;
     if (!h) return fail(nullptr, PC_ERR_OOM, "pc_alg1_create: host allocation failed");
@@ -2627,6 +2663,8 @@ pc_status pc_alg1_create(const pc_desc* desc, const double* u, const double* v, 
     h->ncls = 1 << (d.dim * d.levels);
     h->N = (d.dim == 2) ? (int64_t)d.n * d.n : d.n;
     h->eta = eta;
+    h->fp32 = d.precision == PC_FP32;
+    h->rule = rule;
     pc_status s = (d.dim == 2) ? alg1_run<2>(h, desc, u, v, (cudaStream_t)stream)
                                : alg1_run<1>(h, desc, u, v, (cudaStream_t)stream);
     if (s != PC_OK) {
@@ -2655,8 +2693,17 @@ pc_status pc_alg1_export(pc_alg1_handle h, int64_t* row_ptr, int64_t* cols, doub
     if (!h || !row_ptr || (h->nnz && (!cols || !vals)))
         return fail(nullptr, PC_ERR_INVALID_ARG, "pc_alg1_export: NULL pointer");
     std::vector<double> t((size_t)h->nnz);
-    if (h->nnz && cudaMemcpy(t.data(), h->theta_d, sizeof(double) * h->nnz, cudaMemcpyDeviceToHost) != cudaSuccess)
-        return fail(nullptr, PC_ERR_CUDA, "pc_alg1_export: copy failed");
+    if (h->nnz) {
+        cudaError_t e;
+        if (h->fp32) {
+            std::vector<float> tf((size_t)h->nnz);
+            e = cudaMemcpy(tf.data(), h->theta_d, sizeof(float) * h->nnz, cudaMemcpyDeviceToHost);
+            for (size_t i = 0; i < tf.size(); ++i) t[i] = tf[i];
+        } else {
+            e = cudaMemcpy(t.data(), h->theta_d, sizeof(double) * h->nnz, cudaMemcpyDeviceToHost);
+        }
+        if (e != cudaSuccess) return fail(nullptr, PC_ERR_CUDA, "pc_alg1_export: copy failed");
+    }
     const int D = h->D, n = h->n, J = h->J, nJ = h->nJ;
     const std::vector<BandId> bands = canonical_bands(D, n, J);
     int64_t pos = 0;

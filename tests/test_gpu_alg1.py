@@ -1,5 +1,6 @@
 """The GPU's thresholded Algorithm 1 (Section 3.2; pc_alg1_create) against the FP64 oracle's
-dense Algorithm 1 (oracle.alg1_dense, reading R21) on the same seeded operators.
+dense Algorithm 1 (oracle.alg1_dense, reading R21: the Schur-certified rule 0 and the plain cut
+tau_k = eps_k, rule 1) on the same seeded operators.
 
 Where several results are correct.  The threshold tau_k ends next to the magnitude of one entry of
 A_k; entries whose magnitudes are equal (the translates of a row, and coincident values) can fall
@@ -61,19 +62,20 @@ def _dense_parts(op):
     return A, B
 
 
-def _run(pw, op, eta):
-    desc = pw.make_desc(op.d, op.n, op.levels, op.delta, op.m, op.r, gap=-1, order=0, precision=pw.PC_FP64,
-                        family=op.family)
-    a = pw.PCAlg1(desc, op.u, op.v, eta)
+def _run(pw, op, eta, fp32=False, rule=0):
+    desc = pw.make_desc(op.d, op.n, op.levels, op.delta, op.m, op.r, gap=-1, order=0,
+                        precision=pw.PC_FP32 if fp32 else pw.PC_FP64, family=op.family)
+    a = pw.PCAlg1(desc, op.u, op.v, eta, rule=rule)
     T = a.dense()
     out = (T, a.kept.copy(), a.tau.copy(), a.nnz)
     a.close()
     return out
 
 
-def _check_case(pw, op, eta, strict_when_untied=True):
-    T, kept, tau, nnz = _run(pw, op, eta)
-    To, kept_o, tau_o = oracle.alg1_dense(op, eta)
+def _check_case(pw, op, eta, strict_when_untied=True, fp32=False, rule=0):
+    tol = 1e-5 if fp32 else 1e-12
+    T, kept, tau, nnz = _run(pw, op, eta, fp32, rule)
+    To, kept_o, tau_o = oracle.alg1_dense(op, eta, rule=rule)
     A, B = _dense_parts(op)
     scale = max(np.abs(To).max(), 1e-300)
     expect = np.zeros_like(T)
@@ -85,7 +87,10 @@ def _check_case(pw, op, eta, strict_when_untied=True):
         top = amax * (1 + 1e-15) + 1e-300
         noise = 1e-13 * amax
         ties = (np.abs(a - tau[k]) <= 1e-12 * tau[k]) & (a > 0)
-        if tau_o[k] <= noise or tau[k] <= noise:
+        if rule == 1:
+            assert tau[k] == tau_o[k], (k, tau[k], tau_o[k])      # both eta / (m max|v_k|)
+            amb = ties
+        elif tau_o[k] <= noise or tau[k] <= noise:
             # eta ~ 0: the threshold sits among rounding-noise entries (exact zeros of A_k that
             # each FP64 evaluation leaves at its own ~1e-17 level), which both sides may keep
             assert tau[k] <= noise and tau_o[k] <= noise, (k, tau[k], tau_o[k])
@@ -107,16 +112,16 @@ def _check_case(pw, op, eta, strict_when_untied=True):
         expect += np.where(keep & ~amb, A[k], 0.0) @ B[k]
         if amb.any():
             allow += np.where(amb, a, 0.0) @ np.abs(B[k])
-        if tau[k] < top:
+        if rule == 0 and tau[k] < top:
             # the kept part is what the threshold certifies: discarded Schur bound within eps_k
             D = np.where(a < tau[k] * (1 - 1e-12), a, 0.0)
             eps = eta / (op.m * np.abs(op.v[k]).max())
             assert np.sqrt(D.sum(0).max() * D.sum(1).max()) <= eps * (1 + 1e-9) + 1e-12 * amax
     err = np.abs(T - expect)
-    assert np.all(err <= 1e-12 * scale + allow * (1 + 1e-9)), err.max() / scale
+    assert np.all(err <= tol * scale + allow * (1 + 1e-9)), err.max() / scale
     if strict_when_untied and not tied_any:
         assert np.array_equal(kept, kept_o)
-        assert np.abs(T - To).max() <= 1e-12 * scale, np.abs(T - To).max() / scale
+        assert np.abs(T - To).max() <= tol * scale, np.abs(T - To).max() / scale
     return T, To
 
 
@@ -142,11 +147,29 @@ def test_alg1_matches_oracle(pw, d, n, L, delta, r, m, family, eta):
         assert not np.any(T)
 
 
-def test_alg1_4096_pixels(pw):
+@pytest.mark.parametrize("eta", [1e-4, 1e-2, 1e-1])
+@pytest.mark.parametrize("d,n,L,delta,r,m,family", CASES)
+def test_alg1_hard_rule_matches_oracle(pw, d, n, L, delta, r, m, family, eta):
+    """The plain cut tau_k = eps_k (rule 1), FP64 and FP32 products."""
+    op = _tiny(d, n, L, delta, r, m, seed=d * 7 + n + L, family=family)
+    _check_case(pw, op, eta, rule=1)
+    _check_case(pw, op, eta, rule=1, fp32=True)
+
+
+@pytest.mark.parametrize("eta", [1e-3, 1e-1])
+@pytest.mark.parametrize("d,n,L,delta,r,m,family", [CASES[1], CASES[2], CASES[5], CASES[6], CASES[7]])
+def test_alg1_fp32_matches_oracle(pw, d, n, L, delta, r, m, family, eta):
+    """FP32 products (the same FP64 thresholds): Theta~ within 1e-5 of max|Theta~| element-wise."""
+    op = _tiny(d, n, L, delta, r, m, seed=d * 7 + n + L, family=family)
+    _check_case(pw, op, eta, fp32=True)
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_alg1_4096_pixels(pw, fp32):
     """A 64 x 64 image, three levels, db2, radius 3: several CTAs per class and full-period boxes
     at the coarse levels."""
     op = _tiny(2, 64, 3, 2, 3, 2, seed=5)
-    _check_case(pw, op, 1e-2)
+    _check_case(pw, op, 1e-2, fp32=fp32)
 
 
 @pytest.mark.parametrize("d,n,L,delta,r,g", [(1, 256, 5, 3, 8, 4), (2, 32, 3, 2, 4, 2)])
@@ -205,11 +228,30 @@ def test_alg1_rejects(pw):
     with pytest.raises(pw.PCError) as e:
         pw.PCAlg1(bad_order, op.u, op.v, 1e-3)
     assert e.value.status == pw.PC_ERR_UNSUPPORTED
-    fp32 = pw.make_desc(2, 16, 2, 2, 2, 1, gap=-1, precision=pw.PC_FP32)
+    bad_prec = pw.make_desc(2, 16, 2, 2, 2, 1, gap=-1, precision=7)
     with pytest.raises(pw.PCError) as e:
-        pw.PCAlg1(fp32, op.u, op.v, 1e-3)
-    assert e.value.status == pw.PC_ERR_UNSUPPORTED
+        pw.PCAlg1(bad_prec, op.u, op.v, 1e-3)
+    assert e.value.status == pw.PC_ERR_INVALID_ARG
     ok = pw.make_desc(2, 16, 2, 2, 2, 1, gap=-1, precision=pw.PC_FP64)
     with pytest.raises(pw.PCError) as e:
         pw.PCAlg1(ok, op.u, op.v, -1.0)
     assert e.value.status == pw.PC_ERR_INVALID_ARG
+    with pytest.raises(pw.PCError) as e:
+        pw.PCAlg1(ok, op.u, op.v, 1e-3, rule=2)
+    assert e.value.status == pw.PC_ERR_INVALID_ARG
+
+
+def test_alg1_oversize_reports_oom_and_leaves_the_context_usable(pw):
+    """A 2048 x 2048 Symmlet-6 operator at eta = 5e-4 needs ~10^11 stored entries (rows reach the
+    coarse wavelets' supports): PC_ERR_OOM, no pending CUDA error, and the next calls work."""
+    import torch
+    op = P.workload("op1", n=2048)
+    desc = pw.make_desc(2, 2048, op.levels, op.delta, op.m, op.r, gap=-1, precision=pw.PC_FP32, family=op.family)
+    with pytest.raises(pw.PCError) as e:
+        pw.PCAlg1(desc, op.u, op.v, 5e-4, rule=pw.PC_ALG1_HARD)
+    assert e.value.status == pw.PC_ERR_OOM
+    x = torch.ones(1 << 20, device="cuda")
+    assert float(x.sum()) == float(1 << 20)
+    small = _tiny(2, 16, 2, 2, 1, 2, seed=4)
+    T, _, _, _ = _run(pw, small, 1e-3)
+    assert np.isfinite(T).all()
