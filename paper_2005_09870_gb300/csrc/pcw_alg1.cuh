@@ -97,11 +97,16 @@ struct A1Params {
     double* theta;               // Theta~ rows
     long long sA, sT, sR;        // scratch layout of a CTA (elements): two level buffers, a
                                  // work buffer, the 1-D factor samples
-    // FP32 products (Theta~ in FP32): the taps, windows, F~ and Theta~ in single precision
+    // FP32 products (Theta~ in FP32): the taps, F~ and Theta~ in single precision
     float hf[A1_MAXLF], gf[A1_MAXLF];
-    const float* v32;
     float* Fb32;
     float* theta32;
+    // per-pixel lists of the terms whose window is nonzero there (slot-major, wslots x N; k = -1
+    // ends a list), with the window values in the products' precision
+    int wslots;
+    const int* wk;
+    const double* wv64;
+    const float* wv32;
 };
 
 template <class T> __device__ __forceinline__ T tap_h(const A1Params& P, int i);
@@ -182,21 +187,63 @@ __device__ __forceinline__ T at(const T* line, int stride, Ax b, int M, int p)
 // One analysis level of a 2-D box signal X (b0.w x b1.w, row-major, period M): the next
 // approximation into Y (nb0.w x nb1.w) and the detail bands (0,1), (1,0), (1,1) into out,
 // out + sz, out + 2 sz (sz = nb0.w nb1.w); T holds 2 b0.w nb1.w.  Axis 1 first, then axis 0.
+// Filter taps as seen by the transforms: LF > 0 holds the LF taps of h and g in registers (the
+// loops over them unroll); LF = 0 reads them from the parameters with the run-time length.
+template <class F, int LF>
+struct Taps {
+    F h[LF], g[LF];
+    __device__ explicit Taps(const A1Params& P)
+    {
+#pragma unroll
+        for (int i = 0; i < LF; ++i) {
+            h[i] = tap_h<F>(P, i);
+            g[i] = tap_g<F>(P, i);
+        }
+    }
+    __device__ int lf() const { return LF; }
+    __device__ F H(int i) const { return h[i]; }
+    __device__ F G(int i) const { return g[i]; }  // g at index i - (2 - Lf)
+};
 template <class F>
-__device__ void analysis2(const A1Params& P, const F* X, Ax b0, Ax b1, int M, Ax nb0, Ax nb1, F* T, F* Y,
-                          F* out)
+struct Taps<F, 0> {
+    const A1Params& P;
+    __device__ explicit Taps(const A1Params& p) : P(p) {}
+    __device__ int lf() const { return P.Lf; }
+    __device__ F H(int i) const { return tap_h<F>(P, i); }
+    __device__ F G(int i) const { return tap_g<F>(P, i); }
+};
+
+// One analysis level of a 2-D box signal X (b0.w x b1.w, row-major, period M): the next
+// approximation into Y (nb0.w x nb1.w) and the detail bands (0,1), (1,0), (1,1) into out,
+// out + sz, out + 2 sz (sz = nb0.w nb1.w); T holds 2 b0.w nb1.w.  Axis 1 first, then axis 0.
+// An output whose taps all fall on stored positions reads them unchecked (at() would return the
+// same values); the others go through at().
+template <class F, int LF = 0>
+__device__ void analysis2(const A1Params& P, const F* X, Ax b0, Ax b1, int M, Ax nb0, Ax nb1, F* T, F* Y, F* out)
 {
-    const int Lf = P.Lf;
+    const Taps<F, LF> tp(P);
+    const int Lf = tp.lf();
     const int n01 = b0.w * nb1.w;
     for (int idx = threadIdx.x; idx < n01; idx += blockDim.x) {
         const int r = idx / nb1.w, q = idx - r * nb1.w;
         const int base = 2 * (nb1.a + q);
         const F* line = X + (long long)r * b1.w;
         F lo = 0, hi = 0;
-        for (int i = 2 - Lf; i < Lf; ++i) {
-            const F x = at(line, 1, b1, M, base + i);
-            if (i >= 0) lo = fma(tap_h<F>(P, i), x, lo);
-            if (i <= 1) hi = fma(tap_g<F>(P, i - (2 - Lf)), x, hi);
+        const int k0 = base + 2 - Lf - b1.a;
+        if (k0 >= 0 && k0 + 2 * Lf - 3 < b1.w) {
+            const F* xp = line + k0;
+#pragma unroll
+            for (int i = 2 - Lf; i < Lf; ++i) {
+                const F x = xp[i - (2 - Lf)];
+                if (i >= 0) lo = fma(tp.H(i), x, lo);
+                if (i <= 1) hi = fma(tp.G(i - (2 - Lf)), x, hi);
+            }
+        } else {
+            for (int i = 2 - Lf; i < Lf; ++i) {
+                const F x = at(line, 1, b1, M, base + i);
+                if (i >= 0) lo = fma(tp.H(i), x, lo);
+                if (i <= 1) hi = fma(tp.G(i - (2 - Lf)), x, hi);
+            }
         }
         T[idx] = lo;
         T[n01 + idx] = hi;
@@ -207,17 +254,37 @@ __device__ void analysis2(const A1Params& P, const F* X, Ax b0, Ax b1, int M, Ax
         const int r = idx / nb1.w, q = idx - r * nb1.w;
         const int base = 2 * (nb0.a + r);
         F ll = 0, d01 = 0, d10 = 0, d11 = 0;
-        for (int i = 2 - Lf; i < Lf; ++i) {
-            const F xl = at(T + q, nb1.w, b0, M, base + i);
-            const F xh = at(T + n01 + q, nb1.w, b0, M, base + i);
-            if (i >= 0) {
-                ll = fma(tap_h<F>(P, i), xl, ll);
-                d01 = fma(tap_h<F>(P, i), xh, d01);
+        const int k0 = base + 2 - Lf - b0.a;
+        if (k0 >= 0 && k0 + 2 * Lf - 3 < b0.w) {
+            const F* tl = T + (long long)k0 * nb1.w + q;
+            const F* th = tl + n01;
+#pragma unroll
+            for (int i = 2 - Lf; i < Lf; ++i) {
+                const long long o = (long long)(i - (2 - Lf)) * nb1.w;
+                const F xl = tl[o], xh = th[o];
+                if (i >= 0) {
+                    ll = fma(tp.H(i), xl, ll);
+                    d01 = fma(tp.H(i), xh, d01);
+                }
+                if (i <= 1) {
+                    const F gi = tp.G(i - (2 - Lf));
+                    d10 = fma(gi, xl, d10);
+                    d11 = fma(gi, xh, d11);
+                }
             }
-            if (i <= 1) {
-                const F gi = tap_g<F>(P, i - (2 - Lf));
-                d10 = fma(gi, xl, d10);
-                d11 = fma(gi, xh, d11);
+        } else {
+            for (int i = 2 - Lf; i < Lf; ++i) {
+                const F xl = at(T + q, nb1.w, b0, M, base + i);
+                const F xh = at(T + n01 + q, nb1.w, b0, M, base + i);
+                if (i >= 0) {
+                    ll = fma(tp.H(i), xl, ll);
+                    d01 = fma(tp.H(i), xh, d01);
+                }
+                if (i <= 1) {
+                    const F gi = tp.G(i - (2 - Lf));
+                    d10 = fma(gi, xl, d10);
+                    d11 = fma(gi, xh, d11);
+                }
             }
         }
         Y[idx] = ll;
@@ -229,17 +296,28 @@ __device__ void analysis2(const A1Params& P, const F* X, Ax b0, Ax b1, int M, Ax
 }
 
 // One analysis level of a 1-D box signal.
-template <class F>
+template <class F, int LF = 0>
 __device__ void analysis1(const A1Params& P, const F* X, Ax b, int M, Ax nb, F* Y, F* out)
 {
-    const int Lf = P.Lf;
+    const Taps<F, LF> tp(P);
+    const int Lf = tp.lf();
     for (int idx = threadIdx.x; idx < nb.w; idx += blockDim.x) {
         const int base = 2 * (nb.a + idx);
         F lo = 0, hi = 0;
-        for (int i = 2 - Lf; i < Lf; ++i) {
-            const F x = at(X, 1, b, M, base + i);
-            if (i >= 0) lo = fma(tap_h<F>(P, i), x, lo);
-            if (i <= 1) hi = fma(tap_g<F>(P, i - (2 - Lf)), x, hi);
+        const int k0 = base + 2 - Lf - b.a;
+        if (k0 >= 0 && k0 + 2 * Lf - 3 < b.w) {
+#pragma unroll
+            for (int i = 2 - Lf; i < Lf; ++i) {
+                const F x = X[k0 + i - (2 - Lf)];
+                if (i >= 0) lo = fma(tp.H(i), x, lo);
+                if (i <= 1) hi = fma(tp.G(i - (2 - Lf)), x, hi);
+            }
+        } else {
+            for (int i = 2 - Lf; i < Lf; ++i) {
+                const F x = at(X, 1, b, M, base + i);
+                if (i >= 0) lo = fma(tp.H(i), x, lo);
+                if (i <= 1) hi = fma(tp.G(i - (2 - Lf)), x, hi);
+            }
         }
         Y[idx] = lo;
         out[idx] = hi;
@@ -344,16 +422,16 @@ __device__ inline void load_class(const A1Class* src, A1Class* dst)
 // Analysis chain over the boxes bx (levels 0..J) from X, into a row (approximation of level J
 // at 0, detail bands of level l at offl[l]).  X and Y are swapped between levels; returns the
 // buffer holding the approximation.
-template <int D, class F>
+template <int D, class F, int LF = 0>
 __device__ F* analysis_chain(const A1Params& P, F* X, F* Y, F* T, const Ax (*bx)[A1_MAXJ + 1], const int* offl,
                              F* row)
 {
     for (int l = 0; l < P.J; ++l) {
         const int M = P.n >> l;
         if (D == 2)
-            analysis2(P, X, bx[0][l], bx[1][l], M, bx[0][l + 1], bx[1][l + 1], T, Y, row + offl[l + 1]);
+            analysis2<F, LF>(P, X, bx[0][l], bx[1][l], M, bx[0][l + 1], bx[1][l + 1], T, Y, row + offl[l + 1]);
         else
-            analysis1(P, X, bx[0][l], M, bx[0][l + 1], Y, row + offl[l + 1]);
+            analysis1<F, LF>(P, X, bx[0][l], M, bx[0][l + 1], Y, row + offl[l + 1]);
         F* t = X;
         X = Y;
         Y = t;
@@ -433,11 +511,29 @@ __global__ void __launch_bounds__(A1_THREADS) k_a1_generators(const __grid_const
     }
 }
 
-// FP32 copy of n values.
-__global__ void k_a1_tof32(const double* x, float* y, long long n)
+// Per-pixel lists of the terms with v_k(x) != 0: pass 0 counts the longest list (atomicMax), pass
+// 1 writes the lists (increasing k, -1 after the last) and the window values.
+__global__ void k_a1_wlist(const double* v, int m, long long N, int slots, int* maxcnt, int* wk, double* wv64,
+                           float* wv32)
 {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        y[i] = (float)x[i];
+    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < N; x += (long long)gridDim.x * blockDim.x) {
+        int cnt = 0;
+        for (int k = 0; k < m; ++k) {
+            const double a = v[(long long)k * N + x];
+            if (a == 0.0) continue;
+            if (slots > 0 && cnt < slots) {
+                wk[(long long)cnt * N + x] = k;
+                if (wv64) wv64[(long long)cnt * N + x] = a;
+                if (wv32) wv32[(long long)cnt * N + x] = (float)a;
+            }
+            ++cnt;
+        }
+        if (slots > 0) {
+            if (cnt < slots) wk[(long long)cnt * N + x] = -1;
+        } else {
+            atomicMax(maxcnt, cnt);
+        }
+    }
 }
 
 // Max |x| over each of gridDim.x runs of len values (stride apart): out[blockIdx.x].
@@ -682,35 +778,39 @@ __global__ void __launch_bounds__(A1_THREADS) k_a1_synth(const __grid_constant__
 }
 
 // Stage 4: the rows of Theta~.  One CTA per row (class c, translate t): s~ = sum_k v_k . F~_{k,c}
-// on R shifted by 2^J t, then its analysis chain on the class's product boxes.  F = double: FP64
+// on R shifted by 2^J t (over the terms whose window is nonzero at the pixel, in increasing k),
+// then its analysis chain on the class's product boxes.  F = double: FP64
 // throughout; F = float: FP32 windows, F~ and transform, the sum over k compensated (Kahan).
+// LF > 0: instantiated for one filter length (taps in registers).  The CTAs take the rows of the
+// classes clist[0 .. nlist).
 template <class F> struct ProdIO;
 template <> struct ProdIO<double> {
-    static __device__ const double* v(const A1Params& P) { return P.v; }
+    static __device__ const double* wv(const A1Params& P) { return P.wv64; }
     static __device__ const double* fb(const A1Params& P) { return P.Fb; }
     static __device__ double* theta(const A1Params& P) { return P.theta; }
 };
 template <> struct ProdIO<float> {
-    static __device__ const float* v(const A1Params& P) { return P.v32; }
+    static __device__ const float* wv(const A1Params& P) { return P.wv32; }
     static __device__ const float* fb(const A1Params& P) { return P.Fb32; }
     static __device__ float* theta(const A1Params& P) { return P.theta32; }
 };
 
-template <int D, class F>
-__global__ void __launch_bounds__(A1_THREADS) k_a1_product(const __grid_constant__ A1Params P, F* gscratch)
+template <int D, class F, int LF = 0>
+__global__ void __launch_bounds__(A1_THREADS) k_a1_product(const __grid_constant__ A1Params P, const int* clist,
+                                                           int nlist, F* gscratch)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ A1Class C;
     F* S = gscratch ? gscratch + (long long)blockIdx.x * (2 * P.sA + P.sT) : reinterpret_cast<F*>(smem_raw);
     F *X = S, *Y = S + P.sA, *T = S + 2 * P.sA;
-    const F* V = ProdIO<F>::v(P);
+    const F* WV = ProdIO<F>::wv(P);
     const F* FB = ProdIO<F>::fb(P);
     F* TH = ProdIO<F>::theta(P);
     const int rows = (D == 2) ? P.nJ * P.nJ : P.nJ;
-    const long long total = (long long)P.ncls * rows;
+    const long long total = (long long)nlist * rows;
     for (long long item = blockIdx.x; item < total; item += gridDim.x) {
-        const int c = (int)(item / rows), t = (int)(item - (long long)c * rows);
-        load_class(P.cls + c, &C);
+        const int ci = (int)(item / rows), t = (int)(item - (long long)ci * rows);
+        load_class(P.cls + clist[ci], &C);
         if (C.tlen == 0) continue;
         const int t0 = (D == 2) ? t / P.nJ : t, t1 = (D == 2) ? t - t0 * P.nJ : 0;
         const Ax R0 = C.c[0][0], R1 = C.c[1][0];
@@ -720,8 +820,10 @@ __global__ void __launch_bounds__(A1_THREADS) k_a1_product(const __grid_constant
             const int x0 = (R0.a + i0 + (t0 << P.J)) & (P.n - 1);
             const long long pix = (D == 2) ? (long long)x0 * P.n + ((R1.a + i1 + (t1 << P.J)) & (P.n - 1)) : x0;
             F s = 0, comp = 0;
-            for (int k = 0; k < P.m; ++k) {
-                const F term = V[(long long)k * P.N + pix] * Fc[(long long)k * C.rsize + idx];
+            for (int sl = 0; sl < P.wslots; ++sl) {
+                const int k = P.wk[(long long)sl * P.N + pix];
+                if (k < 0) break;
+                const F term = WV[(long long)sl * P.N + pix] * Fc[(long long)k * C.rsize + idx];
                 if (sizeof(F) == 4) {
                     const F y = term - comp;
                     const F z = s + y;
@@ -734,7 +836,7 @@ __global__ void __launch_bounds__(A1_THREADS) k_a1_product(const __grid_constant
             X[idx] = s;
         }
         __syncthreads();
-        analysis_chain<D>(P, X, Y, T, C.c, C.coffl, TH + C.toff + (long long)t * C.tlen);
+        analysis_chain<D, F, LF>(P, X, Y, T, C.c, C.coffl, TH + C.toff + (long long)t * C.tlen);
     }
 }
 

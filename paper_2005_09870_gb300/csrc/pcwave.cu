@@ -2568,13 +2568,32 @@ pc_status alg1_run(pc_alg1* h, const pc_desc* desc, const double* u, const doubl
     h->nnz = ttotal;
     const size_t esz = h->fp32 ? sizeof(float) : sizeof(double);
     if (h->fp32) {
-        float* v32;
-        if (!db.alloc(&P.Fb32, ftotal) || !db.alloc(&v32, (size_t)m * N)) return oom();
-        k_a1_tof32<<<1024, 256, 0, st>>>(v_d, v32, (long long)m * N);
-        count_launch();
-        P.v32 = v32;
+        if (!db.alloc(&P.Fb32, ftotal)) return oom();
     } else if (!db.alloc(&P.Fb, ftotal)) {
         return oom();
+    }
+    {
+        // per-pixel lists of the nonzero windows (a hat window is nonzero on a few of the m)
+        int* cnt_d;
+        int slots = 0;
+        if (!db.alloc(&cnt_d, 1)) return oom();
+        if (cudaMemsetAsync(cnt_d, 0, sizeof(int), st)) return cuda_err("window lists");
+        k_a1_wlist<<<1024, 256, 0, st>>>(v_d, m, N, 0, cnt_d, nullptr, nullptr, nullptr);
+        if (cudaMemcpyAsync(&slots, cnt_d, sizeof(int), cudaMemcpyDeviceToHost, st) || cudaStreamSynchronize(st))
+            return cuda_err("window lists");
+        slots = std::max(slots, 1);
+        int* wk;
+        double* wv64 = nullptr;
+        float* wv32 = nullptr;
+        if (!db.alloc(&wk, (size_t)slots * N) ||
+            (h->fp32 ? !db.alloc(&wv32, (size_t)slots * N) : !db.alloc(&wv64, (size_t)slots * N)))
+            return oom();
+        k_a1_wlist<<<1024, 256, 0, st>>>(v_d, m, N, slots, cnt_d, wk, wv64, wv32);
+        count_launch(2);
+        P.wslots = slots;
+        P.wk = wk;
+        P.wv64 = wv64;
+        P.wv32 = wv32;
     }
     if (cudaMalloc(&h->theta_d, esz * std::max<int64_t>(ttotal, 1)) != cudaSuccess) {
         h->theta_d = nullptr;
@@ -2602,19 +2621,54 @@ pc_status alg1_run(pc_alg1* h, const pc_desc* desc, const double* u, const doubl
     }
     cudaEventRecord(ev[3], st);
     {
-        const long long items = (long long)ncls * h->rows;
-        if (h->fp32) {
-            const ScratchPlan sp = plan_scratch(k_a1_product<D, float>, items, 2 * sA + sT, sizeof(float));
-            float* slab = nullptr;
-            if (!sp.smem && !db.alloc(&slab, (size_t)sp.grid * (2 * sA + sT))) return oom();
-            k_a1_product<D, float><<<sp.grid, A1_THREADS, sp.smem ? sp.bytes : 0, st>>>(P, slab);
-        } else {
-            const ScratchPlan sp = plan_scratch(k_a1_product<D, double>, items, 2 * sA + sT);
-            double* slab = nullptr;
-            if (!sp.smem && !db.alloc(&slab, (size_t)sp.grid * (2 * sA + sT))) return oom();
-            k_a1_product<D, double><<<sp.grid, A1_THREADS, sp.smem ? sp.bytes : 0, st>>>(P, slab);
+        // two launches: the classes whose buffers fit in 100 KB of shared memory (two CTAs per
+        // SM), and the others with a global slab per CTA
+        const size_t esz4 = h->fp32 ? sizeof(float) : sizeof(double);
+        std::vector<int> lists[2];
+        long long mA[2] = {1, 1}, mT[2] = {1, 1};
+        for (int c = 0; c < ncls; ++c) {
+            const A1Class& C = h->cls[c];
+            if (!C.tlen) continue;
+            long long cA = 1, cT = 1;
+            for (int l = 0; l <= J; ++l) cA = std::max<long long>(cA, (long long)C.c[0][l].w * C.c[1][l].w);
+            for (int l = 0; l < J; ++l) cT = std::max<long long>(cT, 2LL * C.c[0][l].w * C.c[1][l + 1].w);
+            const int w = (size_t)(2 * cA + cT) * esz4 <= 100 * 1024 ? 0 : 1;
+            lists[w].push_back(c);
+            mA[w] = std::max(mA[w], cA);
+            mT[w] = std::max(mT[w], cT);
         }
-        count_launch();
+        auto kern32 = k_a1_product<D, float, 0>;
+        if (D == 2) {
+            // FP32 2-D products for the common filter lengths with the taps in registers
+            if (Lf == 4) kern32 = k_a1_product<D, float, 4>;
+            if (Lf == 6) kern32 = k_a1_product<D, float, 6>;
+            if (Lf == 8) kern32 = k_a1_product<D, float, 8>;
+            if (Lf == 12) kern32 = k_a1_product<D, float, 12>;
+        }
+        for (int w = 0; w < 2; ++w) {
+            if (lists[w].empty()) continue;
+            int* cl_d = nullptr;
+            if (!db.alloc(&cl_d, lists[w].size())) return oom();
+            if (cudaMemcpyAsync(cl_d, lists[w].data(), sizeof(int) * lists[w].size(), cudaMemcpyHostToDevice, st))
+                return cuda_err("class list");
+            P.sA = mA[w];
+            P.sT = mT[w];
+            const long long per = 2 * mA[w] + mT[w];
+            const long long items = (long long)lists[w].size() * h->rows;
+            const int nl = (int)lists[w].size();
+            if (h->fp32) {
+                const ScratchPlan sp = plan_scratch(kern32, items, per, sizeof(float));
+                float* slab = nullptr;
+                if (!sp.smem && !db.alloc(&slab, (size_t)sp.grid * per)) return oom();
+                kern32<<<sp.grid, A1_THREADS, sp.smem ? sp.bytes : 0, st>>>(P, cl_d, nl, slab);
+            } else {
+                const ScratchPlan sp = plan_scratch(k_a1_product<D, double>, items, per);
+                double* slab = nullptr;
+                if (!sp.smem && !db.alloc(&slab, (size_t)sp.grid * per)) return oom();
+                k_a1_product<D, double><<<sp.grid, A1_THREADS, sp.smem ? sp.bytes : 0, st>>>(P, cl_d, nl, slab);
+            }
+            count_launch();
+        }
         if (cudaGetLastError() != cudaSuccess) return cuda_err("product launch");
     }
     cudaEventRecord(ev[4], st);

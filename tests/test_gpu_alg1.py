@@ -165,11 +165,12 @@ def test_alg1_fp32_matches_oracle(pw, d, n, L, delta, r, m, family, eta):
 
 
 @pytest.mark.parametrize("fp32", [False, True])
-def test_alg1_4096_pixels(pw, fp32):
-    """A 64 x 64 image, three levels, db2, radius 3: several CTAs per class and full-period boxes
-    at the coarse levels."""
-    op = _tiny(2, 64, 3, 2, 3, 2, seed=5)
-    _check_case(pw, op, 1e-2, fp32=fp32)
+@pytest.mark.parametrize("L,r,rule,eta", [(3, 3, 0, 1e-2), (2, 1, 1, 1e-3), (3, 1, 1, 1e-2)])
+def test_alg1_4096_pixels(pw, fp32, L, r, rule, eta):
+    """A 64 x 64 image, db2: support boxes narrower than the image (the unchecked interior taps)
+    next to full-period ones at the coarse levels."""
+    op = _tiny(2, 64, L, 2, r, 2, seed=5 + L + r)
+    _check_case(pw, op, eta, fp32=fp32, rule=rule)
 
 
 @pytest.mark.parametrize("d,n,L,delta,r,g", [(1, 256, 5, 3, 8, 4), (2, 32, 3, 2, 4, 2)])
