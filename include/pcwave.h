@@ -363,6 +363,12 @@ pc_status pc_alg1_info(pc_alg1_handle h, int64_t* nnz, double* tau, int64_t* kep
  * of a row in storage order, unsorted), caller-owned host memory.  Synchronous. */
 pc_status pc_alg1_export(pc_alg1_handle h, int64_t* row_ptr, int64_t* cols, double* vals);
 
+/* One row of Theta~ (canonical index `row`): with cols and vals NULL, *count receives its length;
+ * otherwise cols and vals (host, *count entries at least) receive the columns (storage order) and
+ * values and *count the length.  Synchronous.  PC_ERR_INVALID_ARG for a row outside [0, N) or
+ * buffers shorter than the row. */
+pc_status pc_alg1_row(pc_alg1_handle h, int64_t row, int64_t* cols, double* vals, int64_t* count);
+
 void pc_alg1_destroy(pc_alg1_handle h);
 
 /* Waits for `stream`, then reports any device-side fault flagged since the last call

@@ -83,6 +83,7 @@ _sig = {
     "pc_alg1_info": ([_H, _I64P, ctypes.POINTER(ctypes.c_double), _I64P, ctypes.POINTER(ctypes.c_double)],
                      ctypes.c_int),
     "pc_alg1_export": ([_H, _I64P, _I64P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "pc_alg1_row": ([_H, _I64, _I64P, ctypes.POINTER(ctypes.c_double), _I64P], ctypes.c_int),
     "pc_alg1_destroy": ([_H], None),
 }
 for _name, (_args, _ret) in _sig.items():
@@ -175,6 +176,16 @@ class PCAlg1:
         _check(_lib.pc_alg1_export(self.h, row_ptr.ctypes.data_as(_I64P), cols.ctypes.data_as(_I64P),
                                    vals.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return row_ptr, cols[:self.nnz], vals[:self.nnz]
+
+    def row(self, mu: int):
+        """Row mu of Theta~: (columns, values), storage order."""
+        cnt = ctypes.c_int64(0)
+        _check(_lib.pc_alg1_row(self.h, int(mu), None, None, ctypes.byref(cnt)))
+        cols = np.zeros(max(cnt.value, 1), dtype=np.int64)
+        vals = np.zeros(max(cnt.value, 1))
+        _check(_lib.pc_alg1_row(self.h, int(mu), cols.ctypes.data_as(_I64P),
+                                vals.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(cnt)))
+        return cols[:cnt.value], vals[:cnt.value]
 
     def dense(self):
         """Theta~ as a dense N x N numpy array (small N)."""

@@ -2621,18 +2621,19 @@ pc_status alg1_run(pc_alg1* h, const pc_desc* desc, const double* u, const doubl
     }
     cudaEventRecord(ev[3], st);
     {
-        // two launches: the classes whose buffers fit in 100 KB of shared memory (two CTAs per
-        // SM), and the others with a global slab per CTA
+        // up to three launches: the classes whose buffers fit in 100 KB of shared memory (two
+        // CTAs per SM), in 200 KB (one), and the others with a global slab per CTA
         const size_t esz4 = h->fp32 ? sizeof(float) : sizeof(double);
-        std::vector<int> lists[2];
-        long long mA[2] = {1, 1}, mT[2] = {1, 1};
+        std::vector<int> lists[3];
+        long long mA[3] = {1, 1, 1}, mT[3] = {1, 1, 1};
         for (int c = 0; c < ncls; ++c) {
             const A1Class& C = h->cls[c];
             if (!C.tlen) continue;
             long long cA = 1, cT = 1;
             for (int l = 0; l <= J; ++l) cA = std::max<long long>(cA, (long long)C.c[0][l].w * C.c[1][l].w);
             for (int l = 0; l < J; ++l) cT = std::max<long long>(cT, 2LL * C.c[0][l].w * C.c[1][l + 1].w);
-            const int w = (size_t)(2 * cA + cT) * esz4 <= 100 * 1024 ? 0 : 1;
+            const size_t need = (size_t)(2 * cA + cT) * esz4;
+            const int w = need <= 100 * 1024 ? 0 : need <= 200 * 1024 ? 1 : 2;
             lists[w].push_back(c);
             mA[w] = std::max(mA[w], cA);
             mT[w] = std::max(mT[w], cT);
@@ -2645,7 +2646,7 @@ pc_status alg1_run(pc_alg1* h, const pc_desc* desc, const double* u, const doubl
             if (Lf == 8) kern32 = k_a1_product<D, float, 8>;
             if (Lf == 12) kern32 = k_a1_product<D, float, 12>;
         }
-        for (int w = 0; w < 2; ++w) {
+        for (int w = 0; w < 3; ++w) {
             if (lists[w].empty()) continue;
             int* cl_d = nullptr;
             if (!db.alloc(&cl_d, lists[w].size())) return oom();
@@ -2742,50 +2743,89 @@ pc_status pc_alg1_info(pc_alg1_handle h, int64_t* nnz, double* tau, int64_t* kep
     return PC_OK;
 }
 
+// Class, translate and the columns of row mu (canonical) of Theta~; vals from the row's stored
+// values `row` (host).  Returns the entry count.
+static int64_t alg1_row_entries(const pc_alg1* h, int64_t mu, const std::vector<BandId>& bands, int* cls_out,
+                                int64_t* toff_out, const double* row, int64_t* cols, double* vals)
+{
+    const int D = h->D, n = h->n, J = h->J, nJ = h->nJ;
+    size_t b = 0;
+    while (b + 1 < bands.size() && bands[b + 1].off <= mu) ++b;
+    const int j = bands[b].j, nl = n >> j, ph = 1 << (J - j);
+    const int64_t pos = mu - bands[b].off;
+    const int x0 = (D == 2) ? (int)(pos / nl) : (int)pos, x1 = (D == 2) ? (int)(pos % nl) : 0;
+    const int c = h->band_cbase[b] + (D == 2 ? (x0 & (ph - 1)) * ph + (x1 & (ph - 1)) : (x0 & (ph - 1)));
+    const int t0 = x0 >> (J - j), t1 = (D == 2) ? x1 >> (J - j) : 0;
+    const A1Class& C = h->cls[c];
+    if (cls_out) *cls_out = c;
+    if (toff_out) *toff_out = C.toff + (int64_t)(D == 2 ? t0 * nJ + t1 : t0) * C.tlen;
+    if (!cols) return C.tlen;
+    int64_t k = 0;
+    if (C.tlen)
+        host_segments(D, J, C.c, C.coffl, [&](int band, int l, int, int, int off, Ax b0, Ax b1) {
+            const int nlb = n >> l, sh = J - l;
+            for (int i0 = 0; i0 < b0.w; ++i0)
+                for (int i1 = 0; i1 < b1.w; ++i1) {
+                    const int y0 = (b0.a + i0 + (t0 << sh)) & (nlb - 1);
+                    const int y1 = (D == 2) ? ((b1.a + i1 + (t1 << sh)) & (nlb - 1)) : 0;
+                    cols[k] = bands[band].off + (D == 2 ? (int64_t)y0 * nlb + y1 : y0);
+                    if (vals) vals[k] = row[off + i0 * b1.w + i1];
+                    ++k;
+                }
+        });
+    return k;
+}
+
+// Copies n values of Theta~ from element offset `off` of the device array into host doubles.
+static cudaError_t alg1_copy_values(const pc_alg1* h, int64_t off, int64_t n, double* out)
+{
+    if (n <= 0) return cudaSuccess;
+    if (h->fp32) {
+        std::vector<float> tf((size_t)n);
+        const cudaError_t e = cudaMemcpy(tf.data(), (const float*)h->theta_d + off, sizeof(float) * n,
+                                         cudaMemcpyDeviceToHost);
+        for (int64_t i = 0; i < n; ++i) out[i] = tf[(size_t)i];
+        return e;
+    }
+    return cudaMemcpy(out, (const double*)h->theta_d + off, sizeof(double) * n, cudaMemcpyDeviceToHost);
+}
+
 pc_status pc_alg1_export(pc_alg1_handle h, int64_t* row_ptr, int64_t* cols, double* vals)
 {
     if (!h || !row_ptr || (h->nnz && (!cols || !vals)))
         return fail(nullptr, PC_ERR_INVALID_ARG, "pc_alg1_export: NULL pointer");
     std::vector<double> t((size_t)h->nnz);
-    if (h->nnz) {
-        cudaError_t e;
-        if (h->fp32) {
-            std::vector<float> tf((size_t)h->nnz);
-            e = cudaMemcpy(tf.data(), h->theta_d, sizeof(float) * h->nnz, cudaMemcpyDeviceToHost);
-            for (size_t i = 0; i < tf.size(); ++i) t[i] = tf[i];
-        } else {
-            e = cudaMemcpy(t.data(), h->theta_d, sizeof(double) * h->nnz, cudaMemcpyDeviceToHost);
-        }
-        if (e != cudaSuccess) return fail(nullptr, PC_ERR_CUDA, "pc_alg1_export: copy failed");
-    }
-    const int D = h->D, n = h->n, J = h->J, nJ = h->nJ;
-    const std::vector<BandId> bands = canonical_bands(D, n, J);
+    if (alg1_copy_values(h, 0, h->nnz, t.data()) != cudaSuccess)
+        return fail(nullptr, PC_ERR_CUDA, "pc_alg1_export: copy failed");
+    const std::vector<BandId> bands = canonical_bands(h->D, h->n, h->J);
     int64_t pos = 0;
     row_ptr[0] = 0;
-    int64_t mu = 0;
-    for (size_t b = 0; b < bands.size(); ++b) {
-        const int j = bands[b].j, nl = n >> j, ph = 1 << (J - j);
-        for (int x0 = 0; x0 < nl; ++x0)
-            for (int x1 = 0; x1 < (D == 2 ? nl : 1); ++x1, ++mu) {
-                const int c = h->band_cbase[b] + (D == 2 ? (x0 & (ph - 1)) * ph + (x1 & (ph - 1)) : (x0 & (ph - 1)));
-                const int t0 = x0 >> (J - j), t1 = (D == 2) ? x1 >> (J - j) : 0;
-                const A1Class& C = h->cls[c];
-                const double* row = t.data() + C.toff + (int64_t)(D == 2 ? t0 * nJ + t1 : t0) * C.tlen;
-                if (C.tlen)
-                    host_segments(D, J, C.c, C.coffl, [&](int band, int l, int, int, int off, Ax b0, Ax b1) {
-                        const int nlb = n >> l, sh = J - l;
-                        for (int i0 = 0; i0 < b0.w; ++i0)
-                            for (int i1 = 0; i1 < b1.w; ++i1) {
-                                const int y0 = (b0.a + i0 + (t0 << sh)) & (nlb - 1);
-                                const int y1 = (D == 2) ? ((b1.a + i1 + (t1 << sh)) & (nlb - 1)) : 0;
-                                cols[pos] = bands[band].off + (D == 2 ? (int64_t)y0 * nlb + y1 : y0);
-                                vals[pos] = row[off + i0 * b1.w + i1];
-                                ++pos;
-                            }
-                    });
-                row_ptr[mu + 1] = pos;
-            }
+    for (int64_t mu = 0; mu < h->N; ++mu) {
+        int64_t toff = 0;
+        alg1_row_entries(h, mu, bands, nullptr, &toff, nullptr, nullptr, nullptr);
+        pos += alg1_row_entries(h, mu, bands, nullptr, nullptr, t.data() + toff, cols + pos, vals + pos);
+        row_ptr[mu + 1] = pos;
     }
+    return PC_OK;
+}
+
+pc_status pc_alg1_row(pc_alg1_handle h, int64_t row, int64_t* cols, double* vals, int64_t* count)
+{
+    if (!h || !count || row < 0 || row >= h->N)
+        return fail(nullptr, PC_ERR_INVALID_ARG, "pc_alg1_row: NULL handle or count, or row out of range");
+    const std::vector<BandId> bands = canonical_bands(h->D, h->n, h->J);
+    int64_t toff = 0;
+    const int64_t len = alg1_row_entries(h, row, bands, nullptr, &toff, nullptr, nullptr, nullptr);
+    if (!cols && !vals) {
+        *count = len;
+        return PC_OK;
+    }
+    if (!cols || !vals || *count < len)
+        return fail(nullptr, PC_ERR_INVALID_ARG, "pc_alg1_row: buffers missing or shorter than the row");
+    std::vector<double> t((size_t)len);
+    if (alg1_copy_values(h, toff, len, t.data()) != cudaSuccess)
+        return fail(nullptr, PC_ERR_CUDA, "pc_alg1_row: copy failed");
+    *count = alg1_row_entries(h, row, bands, nullptr, nullptr, t.data(), cols, vals);
     return PC_OK;
 }
 

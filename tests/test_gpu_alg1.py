@@ -256,3 +256,74 @@ def test_alg1_oversize_reports_oom_and_leaves_the_context_usable(pw):
     small = _tiny(2, 16, 2, 2, 1, 2, seed=4)
     T, _, _, _ = _run(pw, small, 1e-3)
     assert np.isfinite(T).all()
+
+
+def _oracle_rows(op, tau, rows):
+    """Rows of sum_k A~_k B_k from the oracle's transforms (FP64, full periodic length): row mu is
+    Psi^*(sum_k v_k . Psi A~_k[mu, :]) since B_k = Psi^* diag(v_k) Psi, with A_k[mu, :] = Psi^* F
+    and F(z) = sum_t u_k(t) psi_mu(z + t); A~_k keeps |a| >= tau_k.  Returns, per row, the row and
+    the number of its A_k entries within 1e-9 of tau_k (tied entries)."""
+    d, n, L, r = op.d, op.n, op.levels, op.r
+    K1 = 2 * r + 1
+    shape = (n, n) if d == 2 else (n,)
+    out = []
+    for mu in rows:
+        e = np.zeros(op.N)
+        e[mu] = 1.0
+        psi = oracle.idwt(d, n, L, op.delta, e, family=op.family).reshape(shape)
+        s = np.zeros(op.N)
+        ties = 0
+        for k in range(op.m):
+            uk = op.u[k].reshape((K1, K1) if d == 2 else (K1,))
+            F = np.zeros(shape)
+            if d == 2:
+                for t0 in range(-r, r + 1):
+                    for t1 in range(-r, r + 1):
+                        if uk[t0 + r, t1 + r] != 0.0:
+                            F += uk[t0 + r, t1 + r] * np.roll(psi, (-t0, -t1), (0, 1))
+            else:
+                for t in range(-r, r + 1):
+                    F += uk[t + r] * np.roll(psi, -t)
+            a = oracle.dwt(d, n, L, op.delta, F.reshape(-1), family=op.family)
+            ties += int(np.count_nonzero(np.abs(np.abs(a) - tau[k]) <= 1e-9 * tau[k]))
+            Ft = oracle.idwt(d, n, L, op.delta, np.where(np.abs(a) >= tau[k], a, 0.0), family=op.family)
+            s += op.v[k] * Ft
+        out.append((oracle.dwt(d, n, L, op.delta, s, family=op.family), ties))
+    return out
+
+
+@pytest.mark.parametrize("name,fp32", [("op1", True), ("op2", True), ("op1", False)])
+def test_alg1_rows_at_256(pw, name, fp32):
+    """The Symmlet-6 stand-ins at 256^2 (the benchmark's case; support boxes too large for shared
+    memory, so the global-scratch product path runs), eta = 5e-4, the plain cut: sampled rows of
+    every level against the oracle's transforms, element-wise; the columns the GPU does not store
+    are zero there."""
+    op = P.workload(name, n=256)
+    desc = pw.make_desc(2, 256, op.levels, op.delta, op.m, op.r, gap=-1,
+                        precision=pw.PC_FP32 if fp32 else pw.PC_FP64, family=op.family)
+    a = pw.PCAlg1(desc, op.u, op.v, 5e-4, rule=pw.PC_ALG1_HARD)
+    eps = 5e-4 / (op.m * np.abs(op.v).max(1))
+    assert np.array_equal(a.tau, eps)
+    n, L = 256, op.levels
+    nL = n >> L
+    rows = [3 * nL + 5,                                    # approximation
+            nL * nL + 7 * nL + 2,                           # level L, band (0,1)
+            3 * (n >> 2) ** 2 + 11 * (n >> 2) + 40,        # level 2, band (1,1)
+            (n >> 1) ** 2 + 77 * (n >> 1) + 101,           # level 1, band (0,1)
+            2 * (n >> 1) ** 2 + 128 * (n >> 1) - 1]        # level 1, band (1,0), last column
+    checked = 0
+    for mu, (ref, ties) in zip(rows, _oracle_rows(op, a.tau, rows)):
+        if ties:
+            continue
+        cols, vals = a.row(mu)
+        scale = np.abs(ref).max()
+        got = np.zeros(op.N)
+        got[cols] = vals
+        tol = 1e-5 if fp32 else 1e-12
+        assert np.abs(got - ref).max() <= tol * scale, (mu, np.abs(got - ref).max() / scale)
+        off = np.ones(op.N, dtype=bool)
+        off[cols] = False
+        assert np.abs(ref[off]).max(initial=0.0) <= 1e-12 * scale
+        checked += 1
+    assert checked >= 4
+    a.close()
