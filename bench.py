@@ -386,11 +386,12 @@ PAPER_ALG1_S = {"op1": {128: 3.35, 256: 15.7, 512: 78.3, 1024: 430.9, 2048: 2292
                 "op2": {128: 14.9, 256: 72.6, 512: 345.8, 1024: 1816.6, 2048: 9747.7, 4096: 56192.9}}
 
 
-def run_alg1(pw, rank, dev, check, sides=(128, 256, 512, 1024)):
+def run_alg1(pw, rank, dev, check, sides=(128, 256, 512, 1024), discard_sides=(2048, 4096)):
     """Thresholded Algorithm 1 on the GPU (pc_alg1_create, Section 3.2) on the stand-ins for the
     paper's two blurs: eta = 5e-4 with the plain cut tau_k = eps_k, FP32 products, sides
-    2^7..2^10 beside the paper's Algorithm 1 times (beyond 2^10 Theta~ does not fit: rows that
-    keep a coarse wavelet reach its whole support); the time against eta at 256^2 for both
+    2^7..2^10 beside the paper's Algorithm 1 times, and 2^11, 2^12 with every row formed into a
+    reused buffer and Theta~ not kept (PC_ALG1_DISCARD: it would need 0.8-3 TB; rows that keep a
+    coarse wavelet reach its whole support); the time against eta at 256^2 for both
     threshold rules (the paper's timing-vs-precision figure); and, when checking, the max error of
     a small case against the oracle's dense Algorithm 1.  Each call is synchronous; wall time
     around it (host planning and the allocation of Theta~ included) and the device time of its
@@ -399,8 +400,10 @@ def run_alg1(pw, rank, dev, check, sides=(128, 256, 512, 1024)):
     import torch
     import pc_inputs as P
 
-    def one(name, n, eta, rule):
+    def one(name, n, eta, rule, flags=0):
         rec = {"operator": name, "side": n, "eta": eta, "rule": "hard" if rule else "schur"}
+        if flags:
+            rec["theta_kept"] = False
         a = None
         try:
             op = P.workload(name, n=n, seed_offset=rank)
@@ -410,7 +413,7 @@ def run_alg1(pw, rank, dev, check, sides=(128, 256, 512, 1024)):
             v = torch.tensor(op.v, device=dev)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            a = pw.PCAlg1(desc, u, v, eta, rule=rule)
+            a = pw.PCAlg1(desc, u, v, eta, rule=rule, flags=flags)
             wall = time.perf_counter() - t0
             rec.update({"N": op.N, "m": op.m, "s": round(wall, 4),
                         "stage_ms": {k: round(float(x), 3) for k, x in
@@ -427,8 +430,8 @@ def run_alg1(pw, rank, dev, check, sides=(128, 256, 512, 1024)):
     one("op1", 128, 5e-4, 1)                         # first call: module set-up
     out = {"sweep": [], "vs_eta_256": []}
     for name in ("op1", "op2"):
-        for n in sides:
-            rec = one(name, n, 5e-4, 1)
+        for n in tuple(sides) + tuple(discard_sides):
+            rec = one(name, n, 5e-4, 1, pw.PC_ALG1_DISCARD if n in discard_sides else 0)
             rec["paper_alg1_s"] = PAPER_ALG1_S[name][n]
             if "s" in rec:
                 rec["paper_over_gpu"] = round(rec["paper_alg1_s"] / rec["s"], 1)

@@ -339,20 +339,26 @@ typedef struct pc_alg1* pc_alg1_handle;
  * fewer entries but certifies only max|A_k - A~_k| < eps_k, not the 2-norm bound. */
 typedef enum { PC_ALG1_SCHUR = 0, PC_ALG1_HARD = 1 } pc_alg1_rule;
 
+/* Flags.  PC_ALG1_DISCARD: every row of Theta~ is formed, into one device buffer of at most 8 GB
+ * (or the largest class's rows) that the groups of row classes overwrite in turn, and the matrix
+ * is not kept: the thresholds, counts and stage times remain, pc_alg1_export and pc_alg1_row
+ * return PC_ERR_UNSUPPORTED.  For timing sizes whose Theta~ exceeds the device. */
+enum { PC_ALG1_DISCARD = 1 };
+
 /* Runs Algorithm 1 on the device and keeps Theta~ in the handle.  desc: dim, n, levels,
  * delta, family, m, radius as for pc_create; order must be PC_ORDER_MULT_THEN_CONV (the other
  * order's matrix is the transpose of this one's for the flipped kernels u_k(-t)); rule is a
- * pc_alg1_rule; gap and
+ * pc_alg1_rule, flags 0 or PC_ALG1_DISCARD; gap and
  * store_bf16 are ignored.  The generator rows, thresholds and the synthesis of the kept rows run
  * in FP64 in either precision (so both precisions keep the same entries); PC_FP64 forms the
  * products s~ = sum_k v_k F~_k and their transforms in FP64 and stores Theta~ in FP64, PC_FP32
  * in FP32 with the sum over k compensated (Kahan), Theta~ in FP32.  u: m x (2r+1)^dim,
  * v: m x n^dim, FP64, host or device (copied).  eta >= 0.  Synchronous on `stream`.
- * PC_ERR_INVALID_ARG for NULL pointers, eta < 0, an unknown rule or a descriptor out of range,
+ * PC_ERR_INVALID_ARG for NULL pointers, eta < 0, an unknown rule or flag or a descriptor out of range,
  * PC_ERR_UNSUPPORTED for the other order or more than 2^16 row classes (dim * levels > 16),
  * PC_ERR_OOM when the generator, product or Theta~ storage does not fit. */
-pc_status pc_alg1_create(const pc_desc* desc, const double* u, const double* v, double eta, int rule, void* stream,
-                         pc_alg1_handle* out);
+pc_status pc_alg1_create(const pc_desc* desc, const double* u, const double* v, double eta, int rule, int flags,
+                         void* stream, pc_alg1_handle* out);
 
 /* nnz: stored entries of Theta~; tau[m]: the thresholds; kept[m]: nonzero entries of A~_k
  * (over the whole N x N matrix); stage_ms[4]: device time of the generator rows, the thresholds,

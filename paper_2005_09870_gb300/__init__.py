@@ -25,6 +25,7 @@ PC_OK, PC_ERR_INVALID_ARG, PC_ERR_UNSUPPORTED, PC_ERR_OOM, PC_ERR_CUDA, PC_ERR_T
 PC_ORDER_MULT_THEN_CONV, PC_ORDER_CONV_THEN_MULT = 0, 1
 PC_FP32, PC_FP64 = 0, 1
 PC_ALG1_SCHUR, PC_ALG1_HARD = 0, 1
+PC_ALG1_DISCARD = 1
 _STATUS = ["PC_OK", "PC_ERR_INVALID_ARG", "PC_ERR_UNSUPPORTED", "PC_ERR_OOM", "PC_ERR_CUDA",
            "PC_ERR_TIMEOUT", "PC_ERR_NOT_ASSEMBLED", "PC_ERR_DEVICE"]
 
@@ -79,7 +80,8 @@ _sig = {
     "pc_export": ([_H, _I64P, _I64P, ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
     "pc_svir_expansion": ([_P, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P,
                            ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
-    "pc_alg1_create": ([_DP, _P, _P, ctypes.c_double, ctypes.c_int, _P, ctypes.POINTER(_H)], ctypes.c_int),
+    "pc_alg1_create": ([_DP, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(_H)],
+                       ctypes.c_int),
     "pc_alg1_info": ([_H, _I64P, ctypes.POINTER(ctypes.c_double), _I64P, ctypes.POINTER(ctypes.c_double)],
                      ctypes.c_int),
     "pc_alg1_export": ([_H, _I64P, _I64P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
@@ -141,12 +143,12 @@ class PCAlg1:
     u (m x K) and v (m x N) are FP64 (numpy or CUDA tensors); desc as for pc_create with
     order 0.  Attributes: nnz, tau (m,), kept (m,), stage_ms (4,)."""
 
-    def __init__(self, desc: pc_desc, u, v, eta: float, rule: int = 0, stream=None):
+    def __init__(self, desc: pc_desc, u, v, eta: float, rule: int = 0, flags: int = 0, stream=None):
         self.h = _H()
         self.m = int(desc.m)
         self.N = int(desc.n) ** int(desc.dim)
         self._keep = []
-        _check(_lib.pc_alg1_create(ctypes.byref(desc), self._f64(u), self._f64(v), float(eta), int(rule),
+        _check(_lib.pc_alg1_create(ctypes.byref(desc), self._f64(u), self._f64(v), float(eta), int(rule), int(flags),
                                    _stream(stream), ctypes.byref(self.h)))
         self._keep = []
         nnz = ctypes.c_int64()

@@ -95,6 +95,7 @@ struct A1Params {
     const double* tau;           // m thresholds
     double* Fb;                  // F~ per class: m x |R|
     double* theta;               // Theta~ rows
+    long long tbase;             // value offset of the Theta~ buffer's first element
     long long sA, sT, sR;        // scratch layout of a CTA (elements): two level buffers, a
                                  // work buffer, the 1-D factor samples
     // FP32 products (Theta~ in FP32): the taps, F~ and Theta~ in single precision
@@ -836,7 +837,7 @@ __global__ void __launch_bounds__(A1_THREADS) k_a1_product(const __grid_constant
             X[idx] = s;
         }
         __syncthreads();
-        analysis_chain<D, F, LF>(P, X, Y, T, C.c, C.coffl, TH + C.toff + (long long)t * C.tlen);
+        analysis_chain<D, F, LF>(P, X, Y, T, C.c, C.coffl, TH + (C.toff - P.tbase) + (long long)t * C.tlen);
     }
 }
 

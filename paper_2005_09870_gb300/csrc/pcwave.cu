@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <atomic>
 #include <mutex>
@@ -2175,6 +2176,7 @@ struct pc_alg1 {
     std::vector<int64_t> kept;
     double stage_ms[4] = {0, 0, 0, 0};
     bool fp32 = false;            // Theta~ in FP32 (products in FP32), else FP64
+    bool discard = false;         // rows formed into one reused buffer, Theta~ not kept
     int rule = PC_ALG1_SCHUR;     // threshold rule
     void* theta_d = nullptr;
     std::string err = "no error";
@@ -2595,7 +2597,15 @@ pc_status alg1_run(pc_alg1* h, const pc_desc* desc, const double* u, const doubl
         P.wv64 = wv64;
         P.wv32 = wv32;
     }
-    if (cudaMalloc(&h->theta_d, esz * std::max<int64_t>(ttotal, 1)) != cudaSuccess) {
+    // Theta~ storage; with PC_ALG1_DISCARD one buffer of at most 8 GB (or the largest class) that
+    // every group of classes overwrites in turn
+    int64_t tcap = std::max<int64_t>(ttotal, 1);
+    if (h->discard) {
+        int64_t big = 1;
+        for (const A1Class& C : h->cls) big = std::max<int64_t>(big, (int64_t)h->rows * C.tlen);
+        tcap = std::max(big, std::min<int64_t>(tcap, (int64_t)(8LL << 30) / (int64_t)esz));
+    }
+    if (cudaMalloc(&h->theta_d, esz * tcap) != cudaSuccess) {
         h->theta_d = nullptr;
         (void)cudaGetLastError();
         return oom();
@@ -2646,17 +2656,46 @@ pc_status alg1_run(pc_alg1* h, const pc_desc* desc, const double* u, const doubl
             if (Lf == 8) kern32 = k_a1_product<D, float, 8>;
             if (Lf == 12) kern32 = k_a1_product<D, float, 12>;
         }
-        for (int w = 0; w < 3; ++w) {
-            if (lists[w].empty()) continue;
-            int* cl_d = nullptr;
-            if (!db.alloc(&cl_d, lists[w].size())) return oom();
-            if (cudaMemcpyAsync(cl_d, lists[w].data(), sizeof(int) * lists[w].size(), cudaMemcpyHostToDevice, st))
-                return cuda_err("class list");
+        // groups of consecutive classes whose rows fit the Theta~ buffer (one group unless discarding)
+        std::vector<int> group(ncls, 0);
+        std::vector<int64_t> gbase(1, 0);
+        {
+            int64_t used = 0;
+            for (int c = 0; c < ncls; ++c) {
+                const int64_t sz = (int64_t)h->rows * h->cls[c].tlen;
+                if (used + sz > tcap && used > 0) {
+                    gbase.push_back(h->cls[c].toff);
+                    used = 0;
+                }
+                group[c] = (int)gbase.size() - 1;
+                used += sz;
+            }
+        }
+        std::vector<int> order;
+        std::vector<std::array<int64_t, 3>> runs;  // (group, tier, start in order)
+        for (int g = 0; g < (int)gbase.size(); ++g)
+            for (int w = 0; w < 3; ++w) {
+                const size_t start = order.size();
+                for (int c : lists[w])
+                    if (group[c] == g) order.push_back(c);
+                if (order.size() > start) runs.push_back({g, w, (int64_t)start});
+            }
+        int* order_d = nullptr;
+        if (!db.alloc(&order_d, order.size())) return oom();
+        if (!order.empty() &&
+            cudaMemcpyAsync(order_d, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice, st))
+            return cuda_err("class list");
+        for (size_t ri = 0; ri < runs.size(); ++ri) {
+            const int g = (int)runs[ri][0], w = (int)runs[ri][1];
+            const int64_t start = runs[ri][2];
+            const int64_t end = ri + 1 < runs.size() ? runs[ri + 1][2] : (int64_t)order.size();
+            int* cl_d = order_d + start;
+            P.tbase = gbase[g];
             P.sA = mA[w];
             P.sT = mT[w];
             const long long per = 2 * mA[w] + mT[w];
-            const long long items = (long long)lists[w].size() * h->rows;
-            const int nl = (int)lists[w].size();
+            const int nl = (int)(end - start);
+            const long long items = (long long)nl * h->rows;
             if (h->fp32) {
                 const ScratchPlan sp = plan_scratch(kern32, items, per, sizeof(float));
                 float* slab = nullptr;
@@ -2686,13 +2725,13 @@ pc_status alg1_run(pc_alg1* h, const pc_desc* desc, const double* u, const doubl
 
 extern "C" {
 
-pc_status pc_alg1_create(const pc_desc* desc, const double* u, const double* v, double eta, int rule, void* stream,
-                         pc_alg1_handle* out)
+pc_status pc_alg1_create(const pc_desc* desc, const double* u, const double* v, double eta, int rule, int flags,
+                         void* stream, pc_alg1_handle* out)
 {
     if (!desc || !u || !v || !out || !(eta >= 0.0) || !std::isfinite(eta) ||
-        (rule != PC_ALG1_SCHUR && rule != PC_ALG1_HARD))
+        (rule != PC_ALG1_SCHUR && rule != PC_ALG1_HARD) || (flags & ~PC_ALG1_DISCARD))
         return fail(nullptr, PC_ERR_INVALID_ARG,
-                    "pc_alg1_create: NULL pointer, eta not finite and >= 0, or an unknown rule");
+                    "pc_alg1_create: NULL pointer, eta not finite and >= 0, an unknown rule or flag");
     *out = nullptr;
     const pc_desc& d = *desc;
     if ((d.dim != 1 && d.dim != 2) || d.n < 2 || (d.n & (d.n - 1)) || d.levels < 1 ||
@@ -2720,6 +2759,7 @@ pc_status pc_alg1_create(const pc_desc* desc, const double* u, const double* v, 
     h->eta = eta;
     h->fp32 = d.precision == PC_FP32;
     h->rule = rule;
+    h->discard = (flags & PC_ALG1_DISCARD) != 0;
     pc_status s = (d.dim == 2) ? alg1_run<2>(h, desc, u, v, (cudaStream_t)stream)
                                : alg1_run<1>(h, desc, u, v, (cudaStream_t)stream);
     if (s != PC_OK) {
@@ -2794,6 +2834,7 @@ pc_status pc_alg1_export(pc_alg1_handle h, int64_t* row_ptr, int64_t* cols, doub
 {
     if (!h || !row_ptr || (h->nnz && (!cols || !vals)))
         return fail(nullptr, PC_ERR_INVALID_ARG, "pc_alg1_export: NULL pointer");
+    if (h->discard) return fail(nullptr, PC_ERR_UNSUPPORTED, "pc_alg1_export: Theta~ was not kept");
     std::vector<double> t((size_t)h->nnz);
     if (alg1_copy_values(h, 0, h->nnz, t.data()) != cudaSuccess)
         return fail(nullptr, PC_ERR_CUDA, "pc_alg1_export: copy failed");
@@ -2813,6 +2854,7 @@ pc_status pc_alg1_row(pc_alg1_handle h, int64_t row, int64_t* cols, double* vals
 {
     if (!h || !count || row < 0 || row >= h->N)
         return fail(nullptr, PC_ERR_INVALID_ARG, "pc_alg1_row: NULL handle or count, or row out of range");
+    if (h->discard) return fail(nullptr, PC_ERR_UNSUPPORTED, "pc_alg1_row: Theta~ was not kept");
     const std::vector<BandId> bands = canonical_bands(h->D, h->n, h->J);
     int64_t toff = 0;
     const int64_t len = alg1_row_entries(h, row, bands, nullptr, &toff, nullptr, nullptr, nullptr);

@@ -327,3 +327,25 @@ def test_alg1_rows_at_256(pw, name, fp32):
         checked += 1
     assert checked >= 4
     a.close()
+
+
+def test_alg1_discard_mode(pw):
+    """PC_ALG1_DISCARD on the 256^2 op1 stand-in (FP32 Theta~ of ~10 GB, two groups of classes
+    in the 8 GB buffer): the same thresholds, kept counts and stored-entry count as the kept run,
+    and the matrix calls refuse."""
+    import torch
+    op = P.workload("op1", n=256)
+    desc = pw.make_desc(2, 256, op.levels, op.delta, op.m, op.r, gap=-1, precision=pw.PC_FP32, family=op.family)
+    a = pw.PCAlg1(desc, op.u, op.v, 5e-4, rule=pw.PC_ALG1_HARD)
+    b = pw.PCAlg1(desc, op.u, op.v, 5e-4, rule=pw.PC_ALG1_HARD, flags=pw.PC_ALG1_DISCARD)
+    assert a.nnz * 4 > (8 << 30)
+    assert np.array_equal(a.tau, b.tau) and np.array_equal(a.kept, b.kept) and a.nnz == b.nnz
+    for call in (lambda: b.row(0), b.export):
+        with pytest.raises(pw.PCError) as e:
+            call()
+        assert e.value.status == pw.PC_ERR_UNSUPPORTED
+    cols, vals = a.row(1000)
+    assert len(cols) > 0 and np.isfinite(vals).all()
+    a.close()
+    b.close()
+    assert float(torch.ones(8, device="cuda").sum()) == 8.0
