@@ -387,7 +387,7 @@ PAPER_ALG1_S = {"op1": {128: 3.35, 256: 15.7, 512: 78.3, 1024: 430.9, 2048: 2292
 
 
 def run_alg1(pw, rank, dev, check, sides=(128, 256, 512, 1024), discard_sides=(2048, 4096), ops=("op1", "op2"),
-             vs_eta=True):
+             vs_eta=True, eta=5e-4):
     """Thresholded Algorithm 1 on the GPU (pc_alg1_create, Section 3.2) on the stand-ins for the
     paper's two blurs: eta = 5e-4 with the plain cut tau_k = eps_k, FP32 products, sides
     2^7..2^10 beside the paper's Algorithm 1 times, and 2^11, 2^12 with every row formed into a
@@ -432,9 +432,9 @@ def run_alg1(pw, rank, dev, check, sides=(128, 256, 512, 1024), discard_sides=(2
     out = {"sweep": [], "vs_eta_256": []}
     for name in ops:
         for n in tuple(sides) + tuple(discard_sides):
-            rec = one(name, n, 5e-4, 1, pw.PC_ALG1_DISCARD if n in discard_sides else 0)
-            rec["paper_alg1_s"] = PAPER_ALG1_S[name][n]
-            if "s" in rec:
+            rec = one(name, n, eta, 1, pw.PC_ALG1_DISCARD if n in discard_sides else 0)
+            rec["paper_alg1_s"] = PAPER_ALG1_S[name][n] if eta == 5e-4 else None
+            if "s" in rec and rec["paper_alg1_s"]:
                 rec["paper_over_gpu"] = round(rec["paper_alg1_s"] / rec["s"], 1)
             out["sweep"].append(rec)
     for eta in ((1e-2, 1e-3, 1e-4) if vs_eta else ()):
@@ -715,7 +715,7 @@ def run_ours(args, rank, world, local_rank):
         # the thresholded Algorithm 1 leg alone (no throughput line), e.g. to profile it
         sides = tuple(int(x) for x in args.alg1_sides.split(",") if x)
         out = run_alg1(pw, rank, dev, not args.no_check, sides=sides, discard_sides=(),
-                       ops=tuple(args.alg1_ops.split(",")), vs_eta=False)
+                       ops=tuple(args.alg1_ops.split(",")), vs_eta=False, eta=args.alg1_eta)
         if rank == 0:
             print(json.dumps({"alg1_thresholded": out}), flush=True)
         return
@@ -933,6 +933,7 @@ def main():
     ap.add_argument("--only-alg1", action="store_true", help="run only the thresholded Algorithm 1 leg")
     ap.add_argument("--alg1-sides", default="256", help="sides for --only-alg1, comma separated")
     ap.add_argument("--alg1-ops", default="op1,op2", help="operators for --only-alg1")
+    ap.add_argument("--alg1-eta", type=float, default=5e-4, help="eta for --only-alg1")
     ap.add_argument("--fista-iters", type=int, default=50)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
