@@ -537,20 +537,23 @@ __global__ void k_a1_wlist(const double* v, int m, long long N, int slots, int* 
     }
 }
 
-// Max |x| over each of gridDim.x runs of len values (stride apart): out[blockIdx.x].
-__global__ void k_a1_absmax(const double* x, long long stride, long long len, double* out)
+// Max |x| over each of gridDim.y runs of len values (stride apart), blocks of a run splitting it:
+// out[blockIdx.y] holds the bits of the max (zeroed first); for non-negative doubles the bit
+// patterns order like the values, so an integer atomicMax gives the exact maximum.
+__global__ void k_a1_absmax(const double* x, long long stride, long long len, unsigned long long* out)
 {
     __shared__ double red[32];
-    const double* p = x + (long long)blockIdx.x * stride;
+    const double* p = x + (long long)blockIdx.y * stride;
     double m = 0.0;
-    for (long long i = threadIdx.x; i < len; i += blockDim.x) m = fmax(m, fabs(p[i]));
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
+        m = fmax(m, fabs(p[i]));
     for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
     __syncthreads();
     if (threadIdx.x < 32) {
         m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
         for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (threadIdx.x == 0) out[blockIdx.x] = m;
+        if (threadIdx.x == 0) atomicMax(out + blockIdx.y, (unsigned long long)__double_as_longlong(m));
     }
 }
 

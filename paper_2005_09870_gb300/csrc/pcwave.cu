@@ -2466,8 +2466,12 @@ pc_status alg1_run(pc_alg1* h, const pc_desc* desc, const double* u, const doubl
         if (!sp.smem && !db.alloc(&slab, (size_t)sp.grid * (2 * sA + sT + sR))) return oom();
         k_a1_generators<D><<<sp.grid, A1_THREADS, sp.smem ? sp.bytes : 0, st>>>(P, slab);
         count_launch();
-        k_a1_absmax<<<m, 256, 0, st>>>(v_d, N, N, vmax_d);
-        k_a1_absmax<<<m, 256, 0, st>>>(G_d, gtotal, gtotal, amax_d);
+        if (cudaMemsetAsync(vmax_d, 0, sizeof(double) * m, st) || cudaMemsetAsync(amax_d, 0, sizeof(double) * m, st))
+            return cuda_err("maxima set-up");
+        const dim3 gv((unsigned)std::min<int64_t>(256, (N + 255) / 256), m),
+            gg((unsigned)std::min<int64_t>(256, (gtotal + 255) / 256), m);
+        k_a1_absmax<<<gv, 256, 0, st>>>(v_d, N, N, (unsigned long long*)vmax_d);
+        k_a1_absmax<<<gg, 256, 0, st>>>(G_d, gtotal, gtotal, (unsigned long long*)amax_d);
         count_launch(2);
         if (cudaGetLastError() != cudaSuccess) return cuda_err("generator launch");
     }
