@@ -261,8 +261,8 @@ def test_alg1_oversize_reports_oom_and_leaves_the_context_usable(pw):
 def _oracle_rows(op, tau, rows):
     """Rows of sum_k A~_k B_k from the oracle's transforms (FP64, full periodic length): row mu is
     Psi^*(sum_k v_k . Psi A~_k[mu, :]) since B_k = Psi^* diag(v_k) Psi, with A_k[mu, :] = Psi^* F
-    and F(z) = sum_t u_k(t) psi_mu(z + t); A~_k keeps |a| >= tau_k.  Returns, per row, the row and
-    the number of its A_k entries within 1e-9 of tau_k (tied entries)."""
+    and F(z) = sum_t u_k(t) psi_mu(z + t); A~_k keeps |a| >= tau_k.  Returns, per row, the row with
+    the entries tied with tau_k (within 1e-9) kept, the row with them dropped, and their number."""
     d, n, L, r = op.d, op.n, op.levels, op.r
     K1 = 2 * r + 1
     shape = (n, n) if d == 2 else (n,)
@@ -272,6 +272,7 @@ def _oracle_rows(op, tau, rows):
         e[mu] = 1.0
         psi = oracle.idwt(d, n, L, op.delta, e, family=op.family).reshape(shape)
         s = np.zeros(op.N)
+        s_drop = np.zeros(op.N)
         ties = 0
         for k in range(op.m):
             uk = op.u[k].reshape((K1, K1) if d == 2 else (K1,))
@@ -285,11 +286,32 @@ def _oracle_rows(op, tau, rows):
                 for t in range(-r, r + 1):
                     F += uk[t + r] * np.roll(psi, -t)
             a = oracle.dwt(d, n, L, op.delta, F.reshape(-1), family=op.family)
-            ties += int(np.count_nonzero(np.abs(np.abs(a) - tau[k]) <= 1e-9 * tau[k]))
-            Ft = oracle.idwt(d, n, L, op.delta, np.where(np.abs(a) >= tau[k], a, 0.0), family=op.family)
-            s += op.v[k] * Ft
-        out.append((oracle.dwt(d, n, L, op.delta, s, family=op.family), ties))
+            tied = np.abs(np.abs(a) - tau[k]) <= 1e-9 * tau[k]
+            ties += int(np.count_nonzero(tied))
+            keep = np.abs(a) >= tau[k]
+            s += op.v[k] * oracle.idwt(d, n, L, op.delta, np.where(keep | tied, a, 0.0), family=op.family)
+            s_drop += op.v[k] * oracle.idwt(d, n, L, op.delta, np.where(keep & ~tied, a, 0.0), family=op.family)
+        out.append((oracle.dwt(d, n, L, op.delta, s, family=op.family),
+                    oracle.dwt(d, n, L, op.delta, s_drop, family=op.family), ties))
     return out
+
+
+def _check_rows(a, op, rows, tau, tol):
+    """Sampled rows of the GPU's Theta~ against _oracle_rows: element-wise within tol of the row's
+    largest magnitude (tied entries: either variant), zero where the GPU stores nothing."""
+    for mu, (ref, ref_drop, ties) in zip(rows, _oracle_rows(op, tau, rows)):
+        cols, vals = a.row(mu)
+        got = np.zeros(op.N)
+        got[cols] = vals
+        off = np.ones(op.N, dtype=bool)
+        off[cols] = False
+        res = []
+        for r in ((ref, ref_drop) if ties else (ref,)):
+            scale = np.abs(r).max()
+            err = np.abs(got - r).max() / scale
+            outside = np.abs(r[off]).max(initial=0.0) / scale
+            res.append((err, outside))
+        assert any(err <= tol and outside <= 1e-12 for err, outside in res), (mu, ties, res)
 
 
 @pytest.mark.parametrize("name,fp32", [("op1", True), ("op2", True), ("op1", False)])
@@ -311,21 +333,7 @@ def test_alg1_rows_at_256(pw, name, fp32):
             3 * (n >> 2) ** 2 + 11 * (n >> 2) + 40,        # level 2, band (1,1)
             (n >> 1) ** 2 + 77 * (n >> 1) + 101,           # level 1, band (0,1)
             2 * (n >> 1) ** 2 + 128 * (n >> 1) - 1]        # level 1, band (1,0), last column
-    checked = 0
-    for mu, (ref, ties) in zip(rows, _oracle_rows(op, a.tau, rows)):
-        if ties:
-            continue
-        cols, vals = a.row(mu)
-        scale = np.abs(ref).max()
-        got = np.zeros(op.N)
-        got[cols] = vals
-        tol = 1e-5 if fp32 else 1e-12
-        assert np.abs(got - ref).max() <= tol * scale, (mu, np.abs(got - ref).max() / scale)
-        off = np.ones(op.N, dtype=bool)
-        off[cols] = False
-        assert np.abs(ref[off]).max(initial=0.0) <= 1e-12 * scale
-        checked += 1
-    assert checked >= 4
+    _check_rows(a, op, rows, a.tau, 1e-5 if fp32 else 1e-12)
     a.close()
 
 
@@ -349,3 +357,22 @@ def test_alg1_discard_mode(pw):
     a.close()
     b.close()
     assert float(torch.ones(8, device="cuda").sum()) == 8.0
+
+
+@pytest.mark.parametrize("rule,fp32", [(1, True), (0, False)])
+def test_alg1_rows_1d_65536(pw, rule, fp32):
+    """A 1-D signal of 2^16 samples, six levels, db3: sampled rows of every level against the
+    oracle's transforms (both rules; the certified threshold is taken from the GPU and checked
+    on the sampled rows only through Theta~)."""
+    op = P.workload("small-1d", n=1 << 16, levels=6, delta=3)
+    desc = pw.make_desc(1, op.n, op.levels, op.delta, op.m, op.r, gap=-1,
+                        precision=pw.PC_FP32 if fp32 else pw.PC_FP64, family=op.family)
+    a = pw.PCAlg1(desc, op.u, op.v, 1e-3, rule=rule)
+    if rule == 1:
+        assert np.array_equal(a.tau, 1e-3 / (op.m * np.abs(op.v).max(1)))
+    n, L = op.n, op.levels
+    rows = [5, (n >> L) + 17]                                        # approximation, level L
+    rows += [(n >> j) + (n >> j) // 3 for j in (4, 2, 1)]           # levels 4, 2, 1
+    rows += [n - 1]                                                  # last row of level 1
+    _check_rows(a, op, rows, a.tau, 1e-5 if fp32 else 1e-12)
+    a.close()
