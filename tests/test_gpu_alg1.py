@@ -314,25 +314,26 @@ def _check_rows(a, op, rows, tau, tol):
         assert any(err <= tol and outside <= 1e-12 for err, outside in res), (mu, ties, res)
 
 
-@pytest.mark.parametrize("name,fp32", [("op1", True), ("op2", True), ("op1", False)])
-def test_alg1_rows_at_256(pw, name, fp32):
-    """The Symmlet-6 stand-ins at 256^2 (the benchmark's case; support boxes too large for shared
-    memory, so the global-scratch product path runs), eta = 5e-4, the plain cut: sampled rows of
-    every level against the oracle's transforms, element-wise; the columns the GPU does not store
-    are zero there."""
-    op = P.workload(name, n=256)
-    desc = pw.make_desc(2, 256, op.levels, op.delta, op.m, op.r, gap=-1,
+@pytest.mark.parametrize("name,n,fp32", [("op1", 256, True), ("op2", 256, True), ("op1", 256, False),
+                                         ("op1", 1024, True)])
+def test_alg1_rows_large(pw, name, n, fp32):
+    """The Symmlet-6 stand-ins at 256^2 and 1024^2 (the benchmark's cases; support boxes too large
+    for shared memory, so the global-scratch product path runs), eta = 5e-4, the plain cut:
+    sampled rows of every level against the oracle's transforms, element-wise; the columns the GPU
+    does not store are zero there.  (op1 at 1024^2 holds 4.8e10 FP32 entries, 192 GB.)"""
+    op = P.workload(name, n=n)
+    desc = pw.make_desc(2, n, op.levels, op.delta, op.m, op.r, gap=-1,
                         precision=pw.PC_FP32 if fp32 else pw.PC_FP64, family=op.family)
     a = pw.PCAlg1(desc, op.u, op.v, 5e-4, rule=pw.PC_ALG1_HARD)
     eps = 5e-4 / (op.m * np.abs(op.v).max(1))
     assert np.array_equal(a.tau, eps)
-    n, L = 256, op.levels
+    L = op.levels
     nL = n >> L
     rows = [3 * nL + 5,                                    # approximation
             nL * nL + 7 * nL + 2,                           # level L, band (0,1)
             3 * (n >> 2) ** 2 + 11 * (n >> 2) + 40,        # level 2, band (1,1)
             (n >> 1) ** 2 + 77 * (n >> 1) + 101,           # level 1, band (0,1)
-            2 * (n >> 1) ** 2 + 128 * (n >> 1) - 1]        # level 1, band (1,0), last column
+            2 * (n >> 1) ** 2 + 128 * (n >> 1) - 1]        # level 1, band (1,0), end of line 127
     _check_rows(a, op, rows, a.tau, 1e-5 if fp32 else 1e-12)
     a.close()
 
