@@ -401,6 +401,8 @@ def run_alg1(pw, rank, dev, check, sides=(128, 256, 512, 1024), discard_sides=(2
     import torch
     import pc_inputs as P
 
+    peak, _ = _peaks()
+
     def one(name, n, eta, rule, flags=0):
         rec = {"operator": name, "side": n, "eta": eta, "rule": "hard" if rule else "schur"}
         if flags:
@@ -416,11 +418,16 @@ def run_alg1(pw, rank, dev, check, sides=(128, 256, 512, 1024), discard_sides=(2
             t0 = time.perf_counter()
             a = pw.PCAlg1(desc, u, v, eta, rule=rule, flags=flags)
             wall = time.perf_counter() - t0
+            prod_ms = float(a.stage_ms[3])
+            gbs = 4.0 * a.nnz / (prod_ms * 1e-3) / 1e9          # FP32 entries written by the products
             rec.update({"N": op.N, "m": op.m, "s": round(wall, 4),
                         "stage_ms": {k: round(float(x), 3) for k, x in
                                      zip(("generators", "thresholds", "synthesis", "products"), a.stage_ms)},
                         "nnz": a.nnz, "entries_per_row": round(a.nnz / op.N, 1),
-                        "kept_per_row_per_term": round(float(a.kept.sum()) / op.N / op.m, 1)})
+                        "kept_per_row_per_term": round(float(a.kept.sum()) / op.N / op.m, 1),
+                        "products_roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak,
+                                              "unit": "GB/s", "frac": round(gbs / peak, 4),
+                                              "entries_per_s": round(a.nnz / (prod_ms * 1e-3), -6)}})
         except Exception as e:                       # recorded, not fatal to the bench line
             rec["error"] = str(e)[:160]
         finally:
