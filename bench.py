@@ -444,7 +444,7 @@ def run_alg1(pw, rank, dev, check, sides=(128, 256, 512, 1024), discard_sides=(2
             if "s" in rec and rec["paper_alg1_s"]:
                 rec["paper_over_gpu"] = round(rec["paper_alg1_s"] / rec["s"], 1)
             out["sweep"].append(rec)
-    for eta in ((1e-2, 1e-3, 1e-4) if vs_eta else ()):
+    for eta in ((1.0, 5e-4, 1e-6, 2e-11) if vs_eta else ()):     # the eta of the paper's figure
         for rule in (0, 1):
             for name in ops:
                 out["vs_eta_256"].append(one(name, 256, eta, rule))
