@@ -2233,18 +2233,22 @@ void host_segments(int D, int J, const Ax (*bx)[pcw::alg1::A1_MAXJ + 1], const i
     }
 }
 
+// Temporary device buffers of one call, stream-ordered on the call's stream (the pool allocator:
+// no device-wide synchronisation per allocation), freed in stream order on exit.
 struct DevBufs {
+    cudaStream_t st;
     std::vector<void*> ptrs;
+    explicit DevBufs(cudaStream_t s) : st(s) {}
     ~DevBufs()
     {
         for (void* p : ptrs)
-            if (p) cudaFree(p);
+            if (p) cudaFreeAsync(p, st);
     }
     template <class T>
     bool alloc(T** p, size_t count)
     {
         *p = nullptr;
-        if (cudaMalloc((void**)p, sizeof(T) * std::max<size_t>(count, 1)) != cudaSuccess) {
+        if (cudaMallocAsync((void**)p, sizeof(T) * std::max<size_t>(count, 1), st) != cudaSuccess) {
             *p = nullptr;
             (void)cudaGetLastError();  // an allocation failure is reported by status, not left pending
             return false;
@@ -2295,7 +2299,7 @@ pc_status alg1_run(pc_alg1* h, const pc_desc* desc, const double* u, const doubl
     using namespace pcw::alg1;
     const int n = h->n, J = h->J, Lf = h->Lf, m = h->m, r = h->r, ncls = h->ncls;
     const int64_t N = h->N;
-    DevBufs db;
+    DevBufs db(st);
     auto oom = [&]() { return a1_fail(h, PC_ERR_OOM, "device allocation failed"); };
     auto cuda_err = [&](const char* what) { return a1_fail(h, PC_ERR_CUDA, std::string(what) + " failed"); };
 
@@ -2369,31 +2373,40 @@ pc_status alg1_run(pc_alg1* h, const pc_desc* desc, const double* u, const doubl
 
     // segments: the entries of each row class grouped by column class (class of the entry's
     // position: band, y mod 2^(J - l) per axis), and the segments of each column class
-    std::vector<int> perm((size_t)gtotal), seg_len, seg_row_off(ncls + 1, 0), seg_cc;
+    std::vector<int> perm, seg_len, seg_row_off(ncls + 1, 0), seg_cc;
     std::vector<long long> seg_start;
-    for (int c = 0; c < ncls; ++c) {
-        const A1Class& C = h->cls[c];
-        std::vector<std::pair<int, int>> keyed;
-        keyed.reserve(C.glen);
-        host_segments(D, J, C.g, C.goffl, [&](int band, int l, int, int, int off, Ax b0, Ax b1) {
-            const int ph = 1 << (J - l);
-            for (int i0 = 0; i0 < b0.w; ++i0)
-                for (int i1 = 0; i1 < b1.w; ++i1) {
-                    const int q0 = (b0.a + i0) & (ph - 1), q1 = (D == 2) ? ((b1.a + i1) & (ph - 1)) : 0;
-                    const int cc = h->band_cbase[band] + (D == 2 ? q0 * ph + q1 : q0);
-                    keyed.push_back({cc, off + i0 * b1.w + i1});
-                }
-        });
-        std::sort(keyed.begin(), keyed.end());
-        seg_row_off[c] = (int)seg_len.size();
-        for (size_t i = 0; i < keyed.size(); ++i) {
-            perm[(size_t)C.goff + i] = keyed[i].second;
-            if (i == 0 || keyed[i].first != keyed[i - 1].first) {
-                seg_cc.push_back(keyed[i].first);
-                seg_start.push_back(C.goff + (long long)i);
-                seg_len.push_back(0);
+    if (h->rule == PC_ALG1_SCHUR) {
+        // (the plain cut needs no sums) a stable counting sort of each row's entries by column
+        // class, over the few column classes the row meets
+        perm.resize((size_t)gtotal);
+        std::vector<int> cnt(ncls, 0), keys, ccs;
+        for (int c = 0; c < ncls; ++c) {
+            const A1Class& C = h->cls[c];
+            ccs.assign((size_t)C.glen, 0);
+            keys.clear();
+            host_segments(D, J, C.g, C.goffl, [&](int band, int l, int, int, int off, Ax b0, Ax b1) {
+                const int ph = 1 << (J - l);
+                for (int i0 = 0; i0 < b0.w; ++i0)
+                    for (int i1 = 0; i1 < b1.w; ++i1) {
+                        const int q0 = (b0.a + i0) & (ph - 1), q1 = (D == 2) ? ((b1.a + i1) & (ph - 1)) : 0;
+                        const int cc = h->band_cbase[band] + (D == 2 ? q0 * ph + q1 : q0);
+                        if (cnt[cc]++ == 0) keys.push_back(cc);
+                        ccs[(size_t)off + i0 * b1.w + i1] = cc;
+                    }
+            });
+            std::sort(keys.begin(), keys.end());
+            seg_row_off[c] = (int)seg_len.size();
+            long long pos = C.goff;
+            for (int cc : keys) {  // segment start of each key, then the count is reused as a cursor
+                seg_cc.push_back(cc);
+                seg_start.push_back(pos);
+                seg_len.push_back(cnt[cc]);
+                const long long st0 = pos;
+                pos += cnt[cc];
+                cnt[cc] = (int)(st0 - C.goff);
             }
-            seg_len.back()++;
+            for (int e = 0; e < C.glen; ++e) perm[(size_t)C.goff + cnt[ccs[(size_t)e]]++] = e;
+            for (int cc : keys) cnt[cc] = 0;
         }
     }
     const int nseg = (int)seg_len.size();
@@ -2414,7 +2427,7 @@ pc_status alg1_run(pc_alg1* h, const pc_desc* desc, const double* u, const doubl
     long long *segst_d, *kept_d;
     const int K = (D == 2) ? (2 * r + 1) * (2 * r + 1) : 2 * r + 1;
     if (!db.alloc(&tab_d, tab.size()) || !db.alloc(&cls_d, ncls) || !db.alloc(&u_d, (size_t)m * K) ||
-        !db.alloc(&v_d, (size_t)m * N) || !db.alloc(&G_d, (size_t)m * gtotal) || !db.alloc(&perm_d, gtotal) ||
+        !db.alloc(&v_d, (size_t)m * N) || !db.alloc(&G_d, (size_t)m * gtotal) || !db.alloc(&perm_d, perm.size()) ||
         !db.alloc(&seglen_d, nseg) || !db.alloc(&segrow_d, ncls + 1) || !db.alloc(&colo_d, ncls + 1) ||
         !db.alloc(&cols_d, nseg) || !db.alloc(&segst_d, nseg) || !db.alloc(&segsum_d, (size_t)m * nseg) ||
         !db.alloc(&st_d, 6 * (size_t)m) || !db.alloc(&done_d, m) || !db.alloc(&vmax_d, m) || !db.alloc(&amax_d, m) ||
@@ -2424,12 +2437,14 @@ pc_status alg1_run(pc_alg1* h, const pc_desc* desc, const double* u, const doubl
         cudaMemcpyAsync(cls_d, h->cls.data(), sizeof(A1Class) * ncls, cudaMemcpyHostToDevice, st) ||
         cudaMemcpyAsync(u_d, u, sizeof(double) * m * K, cudaMemcpyDefault, st) ||
         cudaMemcpyAsync(v_d, v, sizeof(double) * m * N, cudaMemcpyDefault, st) ||
-        cudaMemcpyAsync(perm_d, perm.data(), sizeof(int) * gtotal, cudaMemcpyHostToDevice, st) ||
-        cudaMemcpyAsync(seglen_d, seg_len.data(), sizeof(int) * nseg, cudaMemcpyHostToDevice, st) ||
-        cudaMemcpyAsync(segrow_d, seg_row_off.data(), sizeof(int) * (ncls + 1), cudaMemcpyHostToDevice, st) ||
-        cudaMemcpyAsync(colo_d, colseg_off.data(), sizeof(int) * (ncls + 1), cudaMemcpyHostToDevice, st) ||
-        cudaMemcpyAsync(cols_d, colseg.data(), sizeof(int) * nseg, cudaMemcpyHostToDevice, st) ||
-        cudaMemcpyAsync(segst_d, seg_start.data(), sizeof(long long) * nseg, cudaMemcpyHostToDevice, st))
+        (nseg && (cudaMemcpyAsync(perm_d, perm.data(), sizeof(int) * perm.size(), cudaMemcpyHostToDevice, st) ||
+                  cudaMemcpyAsync(seglen_d, seg_len.data(), sizeof(int) * nseg, cudaMemcpyHostToDevice, st) ||
+                  cudaMemcpyAsync(segrow_d, seg_row_off.data(), sizeof(int) * (ncls + 1), cudaMemcpyHostToDevice,
+                                  st) ||
+                  cudaMemcpyAsync(colo_d, colseg_off.data(), sizeof(int) * (ncls + 1), cudaMemcpyHostToDevice, st) ||
+                  cudaMemcpyAsync(cols_d, colseg.data(), sizeof(int) * nseg, cudaMemcpyHostToDevice, st) ||
+                  cudaMemcpyAsync(segst_d, seg_start.data(), sizeof(long long) * nseg, cudaMemcpyHostToDevice,
+                                  st))))
         return cuda_err("upload");
     P.cls = cls_d;
     P.tab = tab_d;
