@@ -461,7 +461,7 @@ __device__ inline double factor_at(const A1Params& P, int j, int e, int p, int x
 // Stage 1: generator rows.  One CTA per (class, term): F(z) = sum_t u_k(t) psi_c(z + t) on the
 // class's level-0 generator box (psi_c = the separable product of 1-D factors, the sum over t
 // split per axis), then its analysis chain into G[k][class].
-template <int D>
+template <int D, int LF = 0>
 __global__ void __launch_bounds__(A1_THREADS) k_a1_generators(const __grid_constant__ A1Params P, double* gscratch)
 {
     extern __shared__ double smem[];
@@ -508,7 +508,7 @@ __global__ void __launch_bounds__(A1_THREADS) k_a1_generators(const __grid_const
             }
         }
         __syncthreads();
-        analysis_chain<D>(P, A, B, T, C.g, C.goffl, P.G + (long long)k * P.gtotal + C.goff);
+        analysis_chain<D, double, LF>(P, A, B, T, C.g, C.goffl, P.G + (long long)k * P.gtotal + C.goff);
     }
 }
 

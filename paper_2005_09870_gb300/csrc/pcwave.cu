@@ -2476,10 +2476,17 @@ pc_status alg1_run(pc_alg1* h, const pc_desc* desc, const double* u, const doubl
         P.sT = sT;
         P.sR = sR;
         const long long items = (long long)ncls * m;
-        const ScratchPlan sp = plan_scratch(k_a1_generators<D>, items, 2 * sA + sT + sR);
+        auto kgen = k_a1_generators<D, 0>;
+        if (D == 2) {  // 2-D: the common filter lengths with the taps in registers
+            if (Lf == 4) kgen = k_a1_generators<D, 4>;
+            if (Lf == 6) kgen = k_a1_generators<D, 6>;
+            if (Lf == 8) kgen = k_a1_generators<D, 8>;
+            if (Lf == 12) kgen = k_a1_generators<D, 12>;
+        }
+        const ScratchPlan sp = plan_scratch(kgen, items, 2 * sA + sT + sR);
         double* slab = nullptr;
         if (!sp.smem && !db.alloc(&slab, (size_t)sp.grid * (2 * sA + sT + sR))) return oom();
-        k_a1_generators<D><<<sp.grid, A1_THREADS, sp.smem ? sp.bytes : 0, st>>>(P, slab);
+        kgen<<<sp.grid, A1_THREADS, sp.smem ? sp.bytes : 0, st>>>(P, slab);
         count_launch();
         if (cudaMemsetAsync(vmax_d, 0, sizeof(double) * m, st) || cudaMemsetAsync(amax_d, 0, sizeof(double) * m, st))
             return cuda_err("maxima set-up");
