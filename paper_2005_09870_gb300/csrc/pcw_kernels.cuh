@@ -252,20 +252,36 @@ struct FiltDev {
 
 template <typename T>
 __global__ void k_filtered_pass1(const __grid_constant__ FiltDev fd, const T* __restrict__ u,
-                                 const T* __restrict__ wav, T* __restrict__ G)
+                                 const T* __restrict__ wav, T* __restrict__ G, int staged)
 {
+    extern __shared__ __align__(16) unsigned char fsm_raw[];
     const int bk = blockIdx.y;
     const int b = bk / fd.m, k = bk % fd.m;
     const FiltBand& B = fd.band[b];
     const int K = 2 * fd.r + 1, K0 = (fd.d == 2) ? K : 1;
     const int tot = K0 * B.U1;
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= tot) return;
-    const int t0i = idx / B.U1, q1 = idx % B.U1;
     const int len = wav_len(B.j, fd.Lf);
     const T* rho1 = wav + fd.wofs[B.j] + (B.e1 ? len : 0);
     const int Ku = (fd.d == 2) ? K * K : K;
     const T* uk = u + (int64_t)k * Ku;
+    if ((int)(blockIdx.x * blockDim.x) >= tot) return;  // a block with no outputs (smaller bands)
+    if (staged) {
+        // the block's kernel stencil and 1-D factor, staged once in shared memory
+        T* su = reinterpret_cast<T*>(fsm_raw);
+        T* sr = su + Ku;
+        for (int i = threadIdx.x; i < Ku + len; i += blockDim.x) {
+            if (i < Ku)
+                su[i] = uk[i];
+            else
+                sr[i - Ku] = rho1[i - Ku];
+        }
+        __syncthreads();
+        uk = su;
+        rho1 = sr;
+    }
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= tot) return;
+    const int t0i = idx / B.U1, q1 = idx % B.U1;
     KahanAcc<T> acc;
     acc.init();
     const int t0 = t0i - fd.r;
@@ -281,19 +297,29 @@ __global__ void k_filtered_pass1(const __grid_constant__ FiltDev fd, const T* __
 
 template <typename T>
 __global__ void k_filtered_pass2(const __grid_constant__ FiltDev fd, const T* __restrict__ wav,
-                                 const T* __restrict__ G, T* __restrict__ F)
+                                 const T* __restrict__ G, T* __restrict__ F, int staged)
 {
+    extern __shared__ __align__(16) unsigned char fsm_raw[];
     const int bk = blockIdx.y;
     const int b = bk / fd.m, k = bk % fd.m;
     const FiltBand& B = fd.band[b];
     const int tot = B.R0 * B.R1;
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= tot) return;
-    const int p0 = idx / B.R1, p1 = idx % B.R1;
     const int K = 2 * fd.r + 1, K0 = (fd.d == 2) ? K : 1;
     const int len = wav_len(B.j, fd.Lf);
     const T* rho0 = wav + fd.wofs[B.j] + (B.e0 ? len : 0);
     const T* Gk = G + B.Goff + (int64_t)k * K0 * B.U1;
+    if ((int)(blockIdx.x * blockDim.x) >= tot) return;  // a block with no outputs (smaller bands)
+    if (staged) {
+        // the band's 1-D factor, staged in shared memory (the pass-1 results are read along the
+        // row, coalesced, by consecutive threads)
+        T* sr = reinterpret_cast<T*>(fsm_raw);
+        for (int i = threadIdx.x; i < len; i += blockDim.x) sr[i] = rho0[i];
+        __syncthreads();
+        rho0 = sr;
+    }
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= tot) return;
+    const int p0 = idx / B.R1, p1 = idx % B.R1;
     KahanAcc<T> acc;
     acc.init();
     for (int q1 = p1; q1 < B.U1; q1 += fd.n) {

@@ -580,9 +580,18 @@ pc_status prepare_t(pc_op* h, cudaStream_t st)
             maxU = std::max(maxU, K0 * h->fd.band[b].U1);
             maxR = std::max(maxR, h->fd.band[b].R0 * h->fd.band[b].R1);
         }
+        // each block stages its gathered inputs (pass 1: the kernel stencil and the band's 1-D
+        // factor; pass 2: the factor) in shared memory when they fit 48 KB, else reads them from
+        // global memory
+        const int lenmax = wav_len(D.levels, h->Lf);
+        const int Ku = (D.dim == 2) ? h->K * h->K : h->K;
+        const size_t sm1 = sizeof(T) * (size_t)(Ku + lenmax), sm2 = sizeof(T) * (size_t)lenmax;
+        const int st1 = sm1 <= 48 * 1024, st2 = sm2 <= 48 * 1024;
         dim3 g1((maxU + 127) / 128, h->nb * D.m), g2((maxR + 127) / 128, h->nb * D.m);
-        k_filtered_pass1<T><<<g1, 128, 0, st>>>(h->fd, (const T*)h->u_d, (const T*)h->wavT_d, (T*)h->G_d);
-        k_filtered_pass2<T><<<g2, 128, 0, st>>>(h->fd, (const T*)h->wavT_d, (const T*)h->G_d, (T*)h->F_d);
+        k_filtered_pass1<T><<<g1, 128, st1 ? sm1 : 0, st>>>(h->fd, (const T*)h->u_d, (const T*)h->wavT_d,
+                                                           (T*)h->G_d, st1);
+        k_filtered_pass2<T><<<g2, 128, st2 ? sm2 : 0, st>>>(h->fd, (const T*)h->wavT_d, (const T*)h->G_d,
+                                                           (T*)h->F_d, st2);
     }
     // window tile masks
     k_tile_masks<T><<<h->tpa0 * h->tpa1, 256, 0, st>>>((const T*)h->v_d, D.dim, D.n, D.m, h->ts0, h->ts1, h->tpa1,
