@@ -7,7 +7,9 @@ A_k; entries whose magnitudes are equal (the translates of a row, and coincident
 on either side between two FP64 evaluations that round differently.  So every case checks:
   - tau_k against the oracle's (relative 1e-9), the kept counts against the oracle's up to the
     entries tied with tau (|a| within 1e-12 of tau); at eta ~ 0 the threshold falls among the
-    rounding-noise entries (below 1e-13 max|A_k|), which count as tied;
+    rounding-noise entries (below 1e-13 max|A_k|), which count as tied; at eta = 0 the certified
+    rule may stop at 0 or just below the smallest significant entry, so there the check is that
+    no entry above the noise is discarded;
   - Theta~ element-wise against sum_k (A_k restricted to |a| >= tau_k(GPU)) B_k built from the
     oracle's dense A_k = Psi^T U_k Psi and B_k = Psi^T V_k Psi (numpy products), with an allowance
     for the tied entries only: |dT| <= 1e-12 max|Theta| + sum_k |A_k on ties| |B_k|;
@@ -87,9 +89,21 @@ def _check_case(pw, op, eta, strict_when_untied=True, fp32=False, rule=0):
         top = amax * (1 + 1e-15) + 1e-300
         noise = 1e-13 * amax
         ties = (np.abs(a - tau[k]) <= 1e-12 * tau[k]) & (a > 0)
+        sig = a > noise
         if rule == 1:
             assert tau[k] == tau_o[k], (k, tau[k], tau_o[k])      # both eta / (m max|v_k|)
             amb = ties
+        elif eta == 0.0:
+            # eps_k = 0: nothing significant may go; where each side's rounding leaves exact zeros or
+            # ~1e-17 noise decides whether its threshold stops at 0 or just below the smallest entry
+            assert tau[k] <= a[sig].min(initial=np.inf) * (1 + 1e-9), (k, tau[k])
+            assert int(kept[k]) >= int(np.count_nonzero(sig)), (k, kept[k])
+            amb = ties | ((a > 0) & ~sig)
+            tied_any |= bool(amb.any()) or tau[k] != tau_o[k]
+            expect += np.where(sig, A[k], 0.0) @ B[k]
+            if amb.any():
+                allow += np.where(amb, a, 0.0) @ np.abs(B[k])
+            continue
         elif tau_o[k] <= noise or tau[k] <= noise:
             # eta ~ 0: the threshold sits among rounding-noise entries (exact zeros of A_k that
             # each FP64 evaluation leaves at its own ~1e-17 level), which both sides may keep
@@ -135,6 +149,9 @@ CASES = [
     (2, 32, 3, 3, 2, 3, 0),
     (2, 32, 3, 3, 2, 2, 1),         # Symmlet 6
     (2, 32, 5, 2, 1, 2, 0),         # L = log2 n
+    (2, 8, 1, 1, 0, 1, 0),          # Haar, one level, a delta kernel (A_k = I), one term
+    (1, 16, 4, 1, 0, 1, 0),         # Haar, full depth, delta kernel
+    (2, 16, 3, 1, 2, 3, 0),         # Haar, radius 2
 ]
 
 
